@@ -1,0 +1,189 @@
+/*
+ * nyspcg.h -- C ABI of the GB300 (sm_103a) Nystrom-preconditioned CG library.
+ *
+ * Solves regularized psd systems (A + mu I) x = b (Sec. 1.1, Eq. (1.1)) with
+ * the randomized Nystrom preconditioner of Frangella, Tropp & Udell,
+ * "Randomized Nystrom Preconditioning" (arXiv 2110.02820):
+ *   - nys_sketch           Algorithm 1 (randomized Nystrom approximation)
+ *   - nys_sketch_adaptive  Algorithm 5 with Algorithm 4 (adaptive rank)
+ *   - nys_precond_apply    Eq. (5.3), the inverse preconditioner P^{-1}
+ *   - pcg_solve            Algorithm 3 (Nystrom PCG), batched over systems,
+ *                          in FP64 or mixed precision with FP64-residual
+ *                          iterative refinement
+ *
+ * Conventions for every entry point:
+ *   - Matrices are ROW-MAJOR (C order).  An n x ell matrix M has element
+ *     (i, j) at M[i * ell + j].  Batches of vectors are stored system-major:
+ *     system s of a batch of n-vectors starts at V + s * n.
+ *   - Array arguments are DEVICE pointers unless the comment says "host".
+ *     The caller owns them; the library never frees or keeps them after the
+ *     call returns (a factor keeps its own copies).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is enqueued on it; entry points that must return a
+ *     scalar result synchronise that stream before returning.
+ *   - Errors are reported only through nys_status.  No entry point aborts,
+ *     throws or traps the GPU.  Arguments are checked on the host before
+ *     any launch; a bad argument returns NYS_ERR_ARG and enqueues nothing.
+ *   - Every reduction runs in a fixed order: results are bitwise
+ *     reproducible run to run on the same GPU and launch configuration.
+ */
+#ifndef NYSPCG_H
+#define NYSPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nys_status {
+  NYS_OK = 0,
+  NYS_ERR_ARG = 1,        /* invalid argument (shape, pointer, mu < 0, ell > n, ...) */
+  NYS_ERR_NOT_PSD = 2,    /* Cholesky of Omega^T Y_nu failed after 6 shift escalations */
+  NYS_ERR_BREAKDOWN = 3,  /* PCG: p^T (A+mu I) p <= 0 or a non-finite scalar */
+  NYS_ERR_MAXIT = 4,      /* PCG: iteration cap reached; x holds the last iterate */
+  NYS_ERR_TIMEOUT = 5,    /* a bounded device-side wait expired */
+  NYS_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+  NYS_ERR_OOM = 7         /* device allocation failed */
+} nys_status;
+
+/* Operator kinds: how x -> A x is computed (Sec. 1.1 accesses A only through
+ * matvecs). */
+typedef enum nys_op_kind {
+  NYS_OP_DENSE = 0, /* data: A, n x n symmetric psd, leading dimension ld (>= n) */
+  NYS_OP_GRAM = 1,  /* data: X, m x n; A = X^T X (ridge normal operator, Eq. (1.7)),
+                       applied matrix-free as X^T (X v) */
+  NYS_OP_RBF = 2    /* data: points, n x d; A = K, K_ij = exp(-||x_i-x_j||^2/(2 sigma^2))
+                       (Gaussian kernel of Sec. 6.5), never formed */
+} nys_op_kind;
+
+typedef enum nys_dtype { NYS_F64 = 0, NYS_F32 = 1 } nys_dtype;
+
+/* NYS_PREC_F64: every step in FP64.
+ * NYS_PREC_MIXED: sketch and tall-skinny products in FP32/TF32 with FP32
+ *   accumulation, U stored FP32, inner PCG on FP32 vectors with FP64
+ *   scalars; the ell x ell factorisations, the shift and the outer residual
+ *   r = b - (A + mu I) x stay FP64-accurate. */
+typedef enum nys_precision { NYS_PREC_F64 = 0, NYS_PREC_MIXED = 1 } nys_precision;
+
+typedef struct nys_operator {
+  int32_t kind;      /* nys_op_kind */
+  int32_t dtype;     /* nys_dtype of `data`: DENSE needs F64; GRAM and RBF need F32 */
+  int64_t n;         /* system dimension */
+  int64_t m;         /* GRAM: number of rows of X; otherwise ignored */
+  int64_t d;         /* RBF: point dimension (1..64); otherwise ignored */
+  int64_t ld;        /* row stride of `data` in elements (>= its row length) */
+  const void* data;  /* device pointer, row-major, 16-byte aligned */
+  double sigma;      /* RBF bandwidth (> 0); otherwise ignored */
+} nys_operator;
+
+/* Opaque factor: U (n x ell, orthonormal columns), lambda_hat (ell,
+ * descending, >= 0), the shift nu, ell.  Owned by the library. */
+typedef struct nys_factor nys_factor;
+
+/* Algorithm 1.  Draws Omega (n x ell) with the library's Philox4x32-10 +
+ * Box-Muller generator from `seed`, unless `omega` (device, n x ell FP64,
+ * row-major, raw Gaussian before the thin QR) is given; orthonormalises it
+ * (thin QR of step 2, computed by CholeskyQR2); forms Y = A Omega; shifts by
+ * nu = eps(||Y||_F) (FP64) or the FP32 spacing (mixed); factors
+ * Omega^T Y_nu = C^T C; B = Y_nu C^{-1}; thin SVD B = U Sigma W^T;
+ * lambda_hat = max(0, Sigma^2 - nu).  If the Cholesky factorisation fails, nu
+ * is multiplied by 10 and the shift redone, at most 6 times, then
+ * NYS_ERR_NOT_PSD.  1 <= ell <= min(n, 4096).  On success *out receives a new
+ * factor (free it with nys_factor_free).  Synchronises `stream`. */
+int32_t nys_sketch(const nys_operator* op, int64_t ell, uint64_t seed, const double* omega,
+                   int32_t precision, nys_factor** out, void* stream);
+
+typedef enum nys_adapt_rule {
+  NYS_RULE_ERR = 0,   /* Strategy 1 (Sec. 5.4.1): stop when the Algorithm 4 estimate <= tol */
+  NYS_RULE_RATIO = 1  /* Strategy 2 (Sec. 5.4.2): stop when lambda_hat_ell / mu <= tol */
+} nys_adapt_rule;
+
+typedef struct nys_adapt_info {
+  int64_t ell;          /* final sketch size */
+  int32_t doublings;    /* number of times the sketch grew */
+  int32_t estimates;    /* number of Algorithm 4 runs */
+  double err_est;       /* last Algorithm 4 estimate of ||A - A_nys|| (NaN if none) */
+  double lambda_ell;    /* lambda_hat_ell of the final factor */
+  double kappa_est;     /* (lambda_hat_ell + mu + err_est) / mu, Eq. (5.6) (NaN if no estimate) */
+} nys_adapt_info;
+
+/* Algorithm 5 (adaptive rank doubling, reusing Omega and Y) with
+ * nu = sqrt(n) eps(||Y||_2).  Blocks of Omega are drawn from `seed` unless
+ * `omega` (device, n x ell_max FP64 raw Gaussian) is given: block k uses the
+ * next columns of it in order.  The k-th Algorithm 4 estimate (q power steps
+ * on E = A - U Lam U^T) starts from `g` + k*n (device, [kmax][n] FP64) if
+ * given, where kmax = ceil(log2(ell_max/ell0)) + 1, else from a Philox
+ * draw.  After each estimate the loop stops if the rule holds; otherwise the
+ * sketch doubles; the last block is capped so that the sketch reaches
+ * exactly ell_max, after which the factor is returned without a further
+ * estimate.  `mu` is used by NYS_RULE_RATIO and for info->kappa_est.
+ * `info` (host) may be NULL.  Synchronises `stream`. */
+int32_t nys_sketch_adaptive(const nys_operator* op, int64_t ell0, int64_t ell_max, int32_t rule,
+                            double tol, int32_t q, double mu, uint64_t seed, const double* omega,
+                            const double* g, int32_t precision, nys_factor** out,
+                            nys_adapt_info* info, void* stream);
+
+/* Eq. (5.3): z_s = P_s^{-1} v_s = (lambda_hat_ell + mu_s) U (Lam + mu_s I)^{-1} U^T v_s
+ * + (I - U U^T) v_s for s = 0..nrhs-1.  `mu` is a HOST array of nrhs shifts
+ * (each >= 0, and > 0 when lambda_hat_ell = 0).  v and z are device arrays
+ * of nrhs n-vectors of type `dtype` (may not alias).  Asynchronous. */
+int32_t nys_precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const void* v,
+                          void* z, int32_t dtype, void* stream);
+
+typedef struct nys_pcg_opts {
+  double tol;                 /* stop when ||r||_2 <= tol ||b||_2 (default 1e-8) */
+  int32_t maxit;              /* iteration cap per (inner) solve (default 500) */
+  int32_t precision;          /* nys_precision */
+  double inner_tol;           /* mixed: relative tolerance of each inner solve (default 1e-4) */
+  int32_t max_refine;         /* mixed: cap on outer refinement steps (default 20) */
+  int32_t use_x0;             /* nonzero: x holds the initial guess; zero: start from x = 0 */
+  double* residual_history;   /* optional device buffer [nsys][maxit+1] FP64: recurrence
+                                 ||r_t|| of the (last inner) solve, NaN-padded; may be NULL */
+} nys_pcg_opts;
+
+typedef struct nys_pcg_result {
+  int32_t status;             /* per system: NYS_OK, NYS_ERR_MAXIT or NYS_ERR_BREAKDOWN */
+  int32_t iterations;         /* A-matvecs inside the PCG loop (summed over inner solves) */
+  int32_t refinements;        /* mixed: outer steps taken; FP64: 0 */
+  int32_t reserved;
+  double rel_residual;        /* FP64: recurrence ||r||/||b||; mixed: true FP64 ||b - A_mu x||/||b|| */
+} nys_pcg_result;
+
+/* Algorithm 3 for nsys independent systems (A + mu_s I) x_s = b_s sharing the
+ * operator and the factor (f == NULL gives plain CG).  `mu` is a HOST array
+ * [nsys]; b and x are device FP64 arrays [nsys][n]; `results` is a HOST array
+ * [nsys].  `opts` may be NULL (defaults).  Returns the worst per-system
+ * status.  Synchronises `stream`. */
+int32_t pcg_solve(const nys_operator* op, const nys_factor* f, const double* mu, int64_t nsys,
+                  const double* b, double* x, const nys_pcg_opts* opts,
+                  nys_pcg_result* results, void* stream);
+
+/* Read-only views of a factor's device arrays (valid until nys_factor_free):
+ * U (n x ell row-major, FP64 when *u_dtype == NYS_F64 else FP32) and
+ * lambda_hat (ell FP64, descending).  Any output pointer may be NULL. */
+int32_t nys_factor_get(const nys_factor* f, const void** U, int32_t* u_dtype,
+                       const double** lambda_hat, int64_t* n, int64_t* ell, double* nu);
+
+void nys_factor_free(nys_factor* f);
+
+const char* nys_status_str(int32_t status);
+
+/* y_s = (A + mu I) x_s for s = 0..nvec-1 (device FP64 [nvec][n]).  mode 0:
+ * the FP64-accurate product used for residuals; mode 1: the FP32 product
+ * used inside mixed-precision PCG.  Exposed so that each operator kernel can
+ * be checked on its own.  Asynchronous. */
+int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const double* x, double* y,
+                      int32_t mode, void* stream);
+
+/* Algorithm 4: q power steps on E = A - U Lam U^T from the start vector g
+ * (device FP64 [n]); *est (host) receives the estimate.  Synchronises. */
+int32_t nys_power_err_est(const nys_operator* op, const nys_factor* f, const double* g, int32_t q,
+                          double* est, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NYSPCG_H */
