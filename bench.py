@@ -1,0 +1,383 @@
+"""Benchmark: Nystrom PCG solves/sec on the matrix-free ridge workload.
+
+Workload (one "step" = one complete solve, every stage of the hot path):
+  X: m = 200000 x n = 4096 FP32, X_ij ~ N(0,1) / (j+1); A = X^T X applied as
+  X^T (X v); mu = 1e-3; b = X^T y, y ~ N(0,1); Nystrom sketch with ell = 512
+  (Algorithm 1, mixed precision); PCG (Algorithm 3) on FP32 vectors inside
+  FP64-residual iterative refinement to ||b - (A + mu I) x|| <= 1e-8 ||b||.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` = solves/sec over all ranks with the
+inputs resident in HBM; `e2e` = the same through the C ABI with host inputs
+(pinned host -> device copy of X and b, and the solution back, inside the
+timed region); `roofline` = the fused ridge matvec kernel (HBM bound)
+against the measured copy bandwidth; `cpu_baseline` = the FP64 oracle on a
+bounded row sample of the same workload.  X (3.3 GB) is larger than L2, so
+no flush is needed between steps.  Under torchrun every rank solves its own
+replica (the path has no exchange step); timing is the max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, ELL, MU, TOL = 200_000, 4096, 512, 1e-3, 1e-8
+INNER_TOL = 1e-4
+SEED = 0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=M)
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--ell", type=int, default=ELL)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--matvec-reps", type=int, default=20)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+
+def make_inputs(m, n):
+    from paper_2110_02820_gb300 import workloads as wl
+    X = wl.ridge_X(m, n, SEED)
+    y = wl.ridge_y(m, SEED)
+    return X, y
+
+
+def rhs_on_device(Xd, y):
+    """b = X^T y in FP64 (input preparation, chunked)."""
+    import torch
+    yd = torch.tensor(y, device=Xd.device)
+    b = torch.zeros(Xd.shape[1], dtype=torch.float64, device=Xd.device)
+    for r0 in range(0, Xd.shape[0], 16384):
+        b += Xd[r0:r0 + 16384].double().t() @ yd[r0:r0 + 16384]
+    return b
+
+
+def solve_once(ny, op, b, ell, seed):
+    f = ny.nys_sketch(op, ell, seed=seed, precision=ny.NYS_PREC_MIXED)
+    x, res, _ = ny.pcg_solve(op, f, MU, b, tol=TOL, precision=ny.NYS_PREC_MIXED,
+                             inner_tol=INNER_TOL, maxit=500, max_refine=20)
+    f.free()
+    return x, res[0]
+
+
+def count_launches(fn):
+    """Kernels of this library launched by one call of fn (torch profiler)."""
+    try:
+        import torch
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        names = {}
+        total = 0
+        for ev in prof.events():
+            if getattr(ev, "device_type", None) is None:
+                continue
+            nm = ev.name
+            if "nys::" in nm and str(ev.device_type).endswith("CUDA"):
+                total += 1
+                short = nm.split("(")[0].replace("void ", "")
+                names[short] = names.get(short, 0) + 1
+        return total, names
+    except Exception as e:  # pragma: no cover
+        return None, {"error": str(e)}
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+
+def cpu_baseline(m, n, ell, sample_rows):
+    """The FP64 oracle (Algorithm 1 + Algorithm 3 in numpy) on a row sample
+    of the workload; cost is linear in the number of rows, so solves/sec at
+    full size = 1 / (t_sample * m / sample_rows)."""
+    from oracle import nystrom as onys
+    from oracle import operators as oops
+    from oracle import pcg as opcg
+    from paper_2110_02820_gb300 import workloads as wl
+    cores = len(os.sched_getaffinity(0))
+    Xs = wl.ridge_X(sample_rows, n, SEED + 1)
+    ys = wl.ridge_y(sample_rows, SEED + 1)
+    X64 = Xs.astype(np.float64)
+    b = X64.T @ ys
+    Om = wl.omega(n, ell, SEED)
+    t0 = time.perf_counter()
+    f = onys.rand_nystrom(lambda V: X64.T @ (X64 @ V), Om)
+    out = opcg.nys_pcg(lambda v: X64.T @ (X64 @ v), MU, b, None,
+                       lambda r: onys.precond_inverse_apply(f["U"], f["lam"], MU, r), TOL, 500)
+    t = time.perf_counter() - t0
+    t_full = t * m / sample_rows
+    return {"value": 1.0 / t_full, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"rows {sample_rows} of {m} (n={n}, ell={ell}), FP64 numpy Algorithm 1 + "
+                      f"Algorithm 3 to rel. residual {TOL}: {t:.2f} s, {out['iterations']} "
+                      f"iterations; scaled linearly in rows"}
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rows = max(2000, args.m // 20)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    t0 = time.perf_counter()
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(args.m, args.n, args.ell, rows)
+        vals.append(1.0 / cb["value"])
+    dt = time.perf_counter() - t0
+    v = 1.0 / statistics.mean(vals)
+    line = {"metric": "PCG solves/sec to rel-residual 1e-8 and kernel-matvec TFLOP/s vs roofline, 1xGB300",
+            "impl": "reference", "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"ridge X {args.m}x{args.n} fp32, ell={args.ell}, mu={MU}, tol={TOL}",
+                       "parallelism": "replicas"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2110_02820_gb300 import nyspcg as ny
+    rank, world, local = dist_init(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    m, n, ell = args.m, args.n, args.ell
+    X, y = make_inputs(m, n)
+    Xd = torch.tensor(X, device=dev)
+    b = rhs_on_device(Xd, y)
+    op = ny.gram_operator(Xd)
+    torch.cuda.synchronize()
+
+    # warm-up (also builds the pools)
+    res = None
+    for w in range(args.warmup):
+        x, res = solve_once(ny, op, b, ell, seed=1000 + w)
+    torch.cuda.synchronize()
+
+    # timed region: K complete solves, inputs resident
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    ev0.record()
+    for k in range(args.steps):
+        x, res = solve_once(ny, op, b, ell, seed=k)
+        iters.append((res.iterations, res.refinements, res.rel_residual, res.status))
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = world * 1e3 / ms
+
+    # dominant kernel: the fused ridge matvec, timed on its stream
+    pf = torch.randn(n, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        ny.nys_op_matvec(op, MU, pf, mode=1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.matvec_reps):
+        ny.nys_op_matvec(op, MU, pf, mode=1)
+    e1.record()
+    torch.cuda.synchronize()
+    mv_ms = e0.elapsed_time(e1) / args.matvec_reps
+    bytes_mv = float(m) * n * 4  # X read once per matvec
+    achieved = bytes_mv / (mv_ms * 1e-3) / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = json.load(open(peaks_path))["hbm_gbs"]
+        peak_src = "measured"
+    else:
+        peak = 6800.0
+        peak_src = "fallback"
+
+    # launches per step
+    launches, names = count_launches(lambda: solve_once(ny, op, b, ell, seed=0))
+
+    # end to end: host inputs (pinned) -> device, solve, solution -> host
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        bh = b.cpu().pin_memory()
+        xh = torch.empty(n, dtype=torch.float64).pin_memory()
+        Xd2 = torch.empty_like(Xd)
+        bd2 = torch.empty_like(b)
+        op2 = ny.gram_operator(Xd2)
+        Xd2.copy_(Xh, non_blocking=True)
+        bd2.copy_(bh, non_blocking=True)
+        solve_once(ny, op2, bd2, ell, seed=7)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            Xd2.copy_(Xh, non_blocking=True)
+            bd2.copy_(bh, non_blocking=True)
+            xk, _ = solve_once(ny, op2, bd2, ell, seed=k)
+            xh.copy_(xk, non_blocking=True)
+            torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        dt = max_over_ranks(dt, world)
+        e2e = {"value": world / dt, "unit": "solves/s", "h2d_bytes_per_step": int(X.nbytes + n * 8),
+               "d2h_bytes_per_step": int(n * 8)}
+        del Xd2, Xh
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline(m, n, ell, max(2000, m // 20))
+
+    if rank == 0:
+        line = {
+            "metric": "PCG solves/sec to rel-residual 1e-8 and kernel-matvec TFLOP/s vs roofline, 1xGB300",
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ridge X {m}x{n} fp32 (col j scaled 1/(j+1)), A=X^T X, mu={MU}, "
+                                   f"ell={ell}, tol={TOL} rel. residual (FP64, refined)",
+                       "l2": "inputs larger than L2 (X 3.3 GB)", "parallelism": "replicas"},
+            "roofline": {"bound": "hbm", "kernel": "gram_fused_kernel (+reduce)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": None, "bytes_per_launch": bytes_mv, "ms_per_launch": mv_ms},
+            "cpu_baseline": cb,
+            "e2e": e2e,
+            "gpu_launches": (launches * args.steps) if launches is not None else None,
+            "clocks": clk,
+            "solve": {"inner_iterations": iters[-1][0], "refinements": iters[-1][1],
+                      "rel_residual": iters[-1][2], "status": iters[-1][3]},
+            "kernels_per_step": names,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

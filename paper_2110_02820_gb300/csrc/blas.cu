@@ -1,0 +1,460 @@
+// BLAS-like building blocks: a tiled SIMT GEMM (FP32 and FP64) with a
+// deterministic split-K reduction, elementwise conversions, fixed-order sums
+// of squares, the shift of Algorithm 1 (steps 4-5) and the Philox4x32-10 +
+// Box-Muller Gaussian generator of step 1.
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nys {
+
+// ---------------------------------------------------------------- host utilities
+
+static thread_local char g_last_err[512];
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file,
+           line);
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (cached[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+static void raise_pool_threshold() {
+  static bool done[64] = {false};
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && !done[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+  }
+}
+
+int32_t dmalloc(void** p, size_t bytes, cudaStream_t s) {
+  raise_pool_threshold();
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? NYS_ERR_OOM : NYS_ERR_CUDA;
+  }
+  return NYS_OK;
+}
+
+void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------- SIMT GEMM
+
+// C_z = opA(A) * B over the K-range of split z, written to Cp + z * split_stride.
+// Block tile BM x BN, K-slab BK, thread tile TM x TN; (BM/TM)*(BN/TN) threads.
+template <typename T, typename TOut, bool TA, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_kernel(int64_t M, int64_t N, int64_t K, const T* __restrict__ A, int64_t lda,
+            const T* __restrict__ B, int64_t ldb, TOut* __restrict__ Cp, int64_t ldc,
+            int64_t kchunk, int64_t split_stride) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ T As[2][BK][BM + 4];
+  __shared__ T Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
+  TOut* C = Cp + (int64_t)blockIdx.z * split_stride;
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = T(0);
+
+  constexpr int A_PER = (BM * BK + NT - 1) / NT;
+  constexpr int B_PER = (BN * BK + NT - 1) / NT;
+  T ra[A_PER], rb[B_PER];
+
+  auto load_regs = [&](int64_t k0) {
+#pragma unroll
+    for (int r = 0; r < A_PER; ++r) {
+      int e = tid + r * NT;
+      T v = T(0);
+      if (e < BM * BK) {
+        int i, k;
+        if (TA) { k = e / BM; i = e % BM; } else { i = e / BK; k = e % BK; }
+        int64_t gi = i0 + i, gk = k0 + k;
+        if (gi < M && gk < kend) v = TA ? A[gk * lda + gi] : A[gi * lda + gk];
+      }
+      ra[r] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < B_PER; ++r) {
+      int e = tid + r * NT;
+      T v = T(0);
+      if (e < BN * BK) {
+        int k = e / BN, j = e % BN;
+        int64_t gk = k0 + k, gj = j0 + j;
+        if (gk < kend && gj < N) v = B[gk * ldb + gj];
+      }
+      rb[r] = v;
+    }
+  };
+  auto store_regs = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < A_PER; ++r) {
+      int e = tid + r * NT;
+      if (e < BM * BK) {
+        int i, k;
+        if (TA) { k = e / BM; i = e % BM; } else { i = e / BK; k = e % BK; }
+        As[buf][k][i] = ra[r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < B_PER; ++r) {
+      int e = tid + r * NT;
+      if (e < BN * BK) {
+        int k = e / BN, j = e % BN;
+        Bs[buf][k][j] = rb[r];
+      }
+    }
+  };
+
+  int buf = 0;
+  if (kbeg < kend) {
+    load_regs(kbeg);
+    store_regs(0);
+  }
+  __syncthreads();
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = (k0 + BK < kend);
+    if (more) load_regs(k0 + BK);  // prefetch next slab into registers
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int t = 0; t < TM; ++t) a[t] = As[buf][kk][ty * TM + t];
+#pragma unroll
+      for (int t = 0; t < TN; ++t) b[t] = Bs[buf][kk][tx * TN + t];
+#pragma unroll
+      for (int x = 0; x < TM; ++x)
+#pragma unroll
+        for (int y = 0; y < TN; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+    if (more) store_regs(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int x = 0; x < TM; ++x) {
+    int64_t gi = i0 + ty * TM + x;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int y = 0; y < TN; ++y) {
+      int64_t gj = j0 + tx * TN + y;
+      if (gj < N) C[gi * ldc + gj] = (TOut)acc[x][y];
+    }
+  }
+}
+
+// Out[i][j] = sum_z P[z][i][j] (fixed order), P dense M x N per split.
+template <typename TAcc, typename TOut>
+__global__ void split_reduce_kernel(const TAcc* __restrict__ P, int64_t splits, int64_t M,
+                                    int64_t N, TOut* __restrict__ C, int64_t ldc) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * N) return;
+  int64_t i = e / N, j = e % N;
+  TAcc acc = 0;
+  for (int64_t z = 0; z < splits; ++z) acc += P[z * M * N + e];
+  C[i * ldc + j] = (TOut)acc;
+}
+
+template <typename T, typename TOut, int BM, int BN, int BK, int TM, int TN>
+static int32_t gemm_launch(bool trans_a, int64_t M, int64_t N, int64_t K, const T* A, int64_t lda,
+                           const T* B, int64_t ldb, TOut* C, int64_t ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return NYS_OK;
+  constexpr int NT = (BM / TM) * (BN / TN);
+  int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
+  int64_t target = 2 * (int64_t)num_sms();
+  int64_t splits = 1;
+  if (tiles < target && K > 4 * BK) {
+    splits = cdiv(target, tiles);
+    int64_t max_splits = cdiv(K, 256);  // at least 256 K per split
+    if (splits > max_splits) splits = max_splits;
+    if (splits > 64) splits = 64;
+    if (splits < 1) splits = 1;
+  }
+  int64_t kchunk = cdiv(cdiv(K, splits), BK) * BK;
+  splits = cdiv(K, kchunk);
+  if (K == 0) { splits = 1; kchunk = 0; }
+  dim3 grid((unsigned)cdiv(N, BN), (unsigned)cdiv(M, BM), (unsigned)splits);
+  if (splits == 1) {
+    if (trans_a)
+      gemm_kernel<T, TOut, true, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, C,
+                                                                         ldc, kchunk > 0 ? kchunk : 1, 0);
+    else
+      gemm_kernel<T, TOut, false, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb,
+                                                                          C, ldc, kchunk > 0 ? kchunk : 1, 0);
+    NYS_CUDA_TRY(cudaGetLastError());
+    return NYS_OK;
+  }
+  T* P = nullptr;
+  NYS_TRY(dmalloc((void**)&P, (size_t)splits * M * N * sizeof(T), s));
+  if (trans_a)
+    gemm_kernel<T, T, true, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, N,
+                                                                    kchunk, M * N);
+  else
+    gemm_kernel<T, T, false, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, N,
+                                                                     kchunk, M * N);
+  split_reduce_kernel<T, TOut><<<(unsigned)cdiv(M * N, 256), 256, 0, s>>>(P, splits, M, N, C, ldc);
+  cudaError_t e = cudaGetLastError();
+  dfree(P, s);
+  NYS_CUDA_TRY(e);
+  return NYS_OK;
+}
+
+int32_t gemm_f32(bool ta, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                 const float* B, int64_t ldb, float* C, int64_t ldc, cudaStream_t s) {
+  return gemm_launch<float, float, 128, 128, 8, 8, 8>(ta, M, N, K, A, lda, B, ldb, C, ldc, s);
+}
+
+int32_t gemm_f32_out64(bool ta, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
+  return gemm_launch<float, double, 128, 128, 8, 8, 8>(ta, M, N, K, A, lda, B, ldb, C, ldc, s);
+}
+
+int32_t gemm_f64(bool ta, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                 const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
+  return gemm_launch<double, double, 64, 64, 8, 4, 4>(ta, M, N, K, A, lda, B, ldb, C, ldc, s);
+}
+
+// ---------------------------------------------------------------- elementwise
+
+template <typename A, typename B>
+__global__ void convert_kernel(const A* in, B* out, int64_t count) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride)
+    out[e] = (B)in[e];
+}
+
+static unsigned grid_for(int64_t count, int threads = 256) {
+  int64_t b = cdiv(count, threads);
+  int64_t cap = 8LL * num_sms();
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+int32_t convert_f64_to_f32(const double* in, float* out, int64_t count, cudaStream_t s) {
+  convert_kernel<double, float><<<grid_for(count), 256, 0, s>>>(in, out, count);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+int32_t convert_f32_to_f64(const float* in, double* out, int64_t count, cudaStream_t s) {
+  convert_kernel<float, double><<<grid_for(count), 256, 0, s>>>(in, out, count);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+__global__ void add_inplace_kernel(double* y, const double* x, int64_t count) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride)
+    y[e] += x[e];
+}
+
+int32_t add_inplace_f64(double* y, const double* x, int64_t count, cudaStream_t s) {
+  add_inplace_kernel<<<grid_for(count), 256, 0, s>>>(y, x, count);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// Fixed-order sum of squares: per-block partials, the last block sums them.
+template <typename T>
+__global__ void sumsq_kernel(const T* __restrict__ x, int64_t count, double* partial,
+                             unsigned int* counter, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride) {
+    double v = (double)x[e];
+    acc += v * v;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (last_block_arrived(counter)) {
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(partial + b);
+      *out = t;
+    }
+  }
+}
+
+template <typename T>
+static int32_t sumsq_impl(const T* x, int64_t count, double* d_out, cudaStream_t s) {
+  unsigned blocks = grid_for(count);
+  unsigned char* aux = nullptr;
+  NYS_TRY(dmalloc((void**)&aux, blocks * sizeof(double) + 16, s));
+  double* partial = reinterpret_cast<double*>(aux + 16);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(aux);
+  cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  sumsq_kernel<T><<<blocks, 256, 0, s>>>(x, count, partial, counter, d_out);
+  cudaError_t e = cudaGetLastError();
+  dfree(aux, s);
+  NYS_CUDA_TRY(e);
+  return NYS_OK;
+}
+
+int32_t sumsq_f32(const float* x, int64_t count, double* d_out, cudaStream_t s) {
+  return sumsq_impl(x, count, d_out, s);
+}
+int32_t sumsq_f64(const double* x, int64_t count, double* d_out, cudaStream_t s) {
+  return sumsq_impl(x, count, d_out, s);
+}
+
+template <typename T>
+__global__ void shift_add_kernel(const T* Y, const T* Q, T* Ynu, int64_t count, const double* d_nu,
+                                 double factor) {
+  const T nu = (T)(d_nu[0] * factor);
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride)
+    Ynu[e] = Y[e] + nu * Q[e];
+}
+
+int32_t shift_add_f32(const float* Y, const float* Q, float* Ynu, int64_t count, const double* d_nu,
+                      double factor, cudaStream_t s) {
+  shift_add_kernel<float><<<grid_for(count), 256, 0, s>>>(Y, Q, Ynu, count, d_nu, factor);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+int32_t shift_add_f64(const double* Y, const double* Q, double* Ynu, int64_t count,
+                      const double* d_nu, double factor, cudaStream_t s) {
+  shift_add_kernel<double><<<grid_for(count), 256, 0, s>>>(Y, Q, Ynu, count, d_nu, factor);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// eps(x) in MATLAB's sense at the given mantissa width: the spacing of
+// floating-point numbers at |x|, 2^(floor(log2|x|) - p).
+__global__ void compute_nu_kernel(const double* sumsq, double scale, int mantissa_bits,
+                                  double* nu) {
+  double x = sqrt(sumsq[0]);
+  double pre = 1.0;
+  if (x > 0.0 && isfinite(x)) {
+    int e2;
+    frexp(x, &e2);  // x = f 2^e2, f in [0.5, 1)
+    pre = ldexp(1.0, (e2 - 1) - mantissa_bits);
+  } else {
+    pre = ldexp(1.0, -1074);
+  }
+  nu[0] = scale * pre;
+}
+
+int32_t compute_nu(const double* d_sumsq, double scale, int mantissa_bits, double* d_nu,
+                   cudaStream_t s) {
+  compute_nu_kernel<<<1, 1, 0, s>>>(d_sumsq, scale, mantissa_bits, d_nu);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+__global__ void lambda_kernel(const double* sigma, const double* d_nu, double* lam, int64_t ell) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ell) return;
+  double v = sigma[j] * sigma[j] - d_nu[0];
+  lam[j] = v > 0.0 ? v : 0.0;
+}
+
+int32_t lambda_from_sigma(const double* sigma, const double* d_nu, double* lam, int64_t ell,
+                          cudaStream_t s) {
+  lambda_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(sigma, d_nu, lam, ell);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+
+// Counter-based generator of Salmon, Moraes, Dror & Shaw (SC'11): ten rounds
+// of the Philox S-box on a 128-bit counter under a 64-bit key, the key bumped
+// by the Weyl constants between rounds.
+struct Philox4 {
+  uint32_t v[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(Philox4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, c.v[0]), lo0 = M0 * c.v[0];
+    uint32_t hi1 = __umulhi(M1, c.v[2]), lo1 = M1 * c.v[2];
+    Philox4 n;
+    n.v[0] = hi1 ^ c.v[1] ^ k0;
+    n.v[1] = lo1;
+    n.v[2] = hi0 ^ c.v[3] ^ k1;
+    n.v[3] = lo0;
+    c = n;
+    k0 += W0;
+    k1 += W1;
+  }
+  return c;
+}
+
+// Element e of stream (seed, stream_id): counter = (e / 4, stream lo, stream hi, 0);
+// the four 32-bit outputs give two Box-Muller pairs.
+__global__ void philox_gaussian_kernel(double* out, int64_t count, uint64_t seed,
+                                       uint64_t stream_id) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g * 4 < count; g += stride) {
+    Philox4 c;
+    c.v[0] = (uint32_t)g;
+    c.v[1] = (uint32_t)(g >> 32) ^ (uint32_t)stream_id;
+    c.v[2] = (uint32_t)(stream_id >> 32);
+    c.v[3] = 0x6e79u;  // fixed tag
+    Philox4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const float two_pi = 6.28318530717958647692f;
+    float z[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float u1 = ((float)r.v[2 * h] + 0.5f) * 2.3283064365386963e-10f;  // (0, 1)
+      float u2 = ((float)r.v[2 * h + 1] + 0.5f) * 2.3283064365386963e-10f;
+      float rad = sqrtf(-2.0f * logf(u1));
+      float sn, cs;
+      sincosf(two_pi * u2, &sn, &cs);
+      z[2 * h] = rad * cs;
+      z[2 * h + 1] = rad * sn;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (g * 4 + t < count) out[g * 4 + t] = (double)z[t];
+  }
+}
+
+int32_t philox_gaussian_f64(double* out, int64_t count, uint64_t seed, uint64_t stream_id,
+                            cudaStream_t s) {
+  philox_gaussian_kernel<<<grid_for(cdiv(count, 4)), 256, 0, s>>>(out, count, seed, stream_id);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+}  // namespace nys

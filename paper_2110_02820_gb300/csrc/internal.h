@@ -1,0 +1,126 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nyspcg.h"
+
+struct nys_factor {
+  int64_t n = 0, ell = 0;
+  int32_t precision = NYS_PREC_F64;
+  int32_t u_dtype = NYS_F64;  // NYS_F64 (double U) or NYS_F32 (float U)
+  void* U = nullptr;          // n x ell row-major
+  double* lam = nullptr;      // ell, descending
+  double nu = 0.0;
+  double lam_ell = 0.0;       // host copy of lam[ell-1]
+  int32_t escalations = 0;
+  int device = 0;
+};
+
+namespace nys {
+
+// ---------------------------------------------------------------- workspace
+
+// Stream-ordered device allocation (cudaMallocAsync from the device's
+// default pool, whose release threshold is raised once so that repeated
+// solves reuse memory instead of returning it to the driver).
+int32_t dmalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+// RAII list of stream-ordered allocations freed at scope exit.
+struct Scratch {
+  cudaStream_t s;
+  void* ptrs[64];
+  int count = 0;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (int i = 0; i < count; ++i) dfree(ptrs[i], s);
+  }
+  template <typename T>
+  int32_t get(T** p, size_t elems) {
+    void* q = nullptr;
+    int32_t st = dmalloc(&q, elems * sizeof(T) + 256, s);
+    if (st != NYS_OK) return st;
+    ptrs[count++] = q;
+    *p = reinterpret_cast<T*>(q);
+    return NYS_OK;
+  }
+};
+
+// ---------------------------------------------------------------- dense ell x ell FP64 (la_small.cu)
+
+// In-place upper Cholesky M = C^T C of a symmetric ell x ell matrix (upper
+// triangle read); on return the strict lower triangle is zero.  *d_info
+// (device int) is 0 on success, k+1 if the k-th pivot was not positive.
+int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s);
+// X = C^{-1} for upper-triangular C (ell x ell); X upper triangular.
+int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s);
+// M = (M + M^T) / 2.
+int32_t symmetrize(double* M, int64_t ell, cudaStream_t s);
+// M += shift * I (shift read from device scalar times factor).
+int32_t add_diag(double* M, int64_t ell, double shift, cudaStream_t s);
+// One-sided Jacobi SVD of the ell x ell matrix R: R = Ut Sigma V^T.  Writes
+// Ut (ell x ell row-major, columns = left singular vectors, sorted so that
+// sigma is descending) and sigma (ell).  *d_status = 0 ok, NYS_ERR_TIMEOUT if
+// a grid barrier wait expired.
+int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int* d_status,
+                   int* sweeps_out, cudaStream_t s);
+
+// ---------------------------------------------------------------- BLAS-like (blas.cu)
+
+// C (M x N, FP64 out) = op(A)^T... generic SIMT GEMM:
+//   C = opA(A) * B,  opA(A) is M x K.  trans_a=false: A is M x K row-major
+//   (lda); trans_a=true: A is K x M row-major (lda).  B is K x N row-major.
+// T = element type (float/double); accumulation in T; the result is written
+// as TOut (float/double) with leading dimension ldc.
+int32_t gemm_f32(bool trans_a, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                 const float* B, int64_t ldb, float* C, int64_t ldc, cudaStream_t s);
+int32_t gemm_f32_out64(bool trans_a, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
+int32_t gemm_f64(bool trans_a, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                 const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
+
+// y += x (elementwise)
+int32_t add_inplace_f64(double* y, const double* x, int64_t count, cudaStream_t s);
+int32_t convert_f64_to_f32(const double* in, float* out, int64_t count, cudaStream_t s);
+int32_t convert_f32_to_f64(const float* in, double* out, int64_t count, cudaStream_t s);
+// sum of squares of `count` values, written to d_out (FP64 accumulate, fixed order)
+int32_t sumsq_f32(const float* x, int64_t count, double* d_out, cudaStream_t s);
+int32_t sumsq_f64(const double* x, int64_t count, double* d_out, cudaStream_t s);
+// Y_nu = Y + nu * Q where nu = d_nu[0] * factor
+int32_t shift_add_f32(const float* Y, const float* Q, float* Ynu, int64_t count, const double* d_nu,
+                      double factor, cudaStream_t s);
+int32_t shift_add_f64(const double* Y, const double* Q, double* Ynu, int64_t count,
+                      const double* d_nu, double factor, cudaStream_t s);
+// Philox4x32-10 + Box-Muller N(0,1) draws; element e of the stream (seed, stream_id)
+int32_t philox_gaussian_f64(double* out, int64_t count, uint64_t seed, uint64_t stream_id,
+                            cudaStream_t s);
+// nu = 2^(floor(log2(scale * sqrt(d_sumsq[0]))) - mantissa_bits), written to d_nu
+int32_t compute_nu(const double* d_sumsq, double scale, int mantissa_bits, double* d_nu,
+                   cudaStream_t s);
+// Ut columns scaled: lam = max(0, sigma^2 - nu)
+int32_t lambda_from_sigma(const double* sigma, const double* d_nu, double* lam, int64_t ell,
+                          cudaStream_t s);
+
+// ---------------------------------------------------------------- operators (operators.cu)
+
+// V = A Q for an n x ell block (sketch).  Q, V: n x ell row-major, FP64 when
+// f64 else FP32.
+int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int64_t ell,
+                  cudaStream_t s);
+
+// Bytes of device workspace op_matvec_* needs (its first 256 bytes hold a
+// device error word that must start at zero).
+size_t op_matvec_work_bytes(const nys_operator* op, bool accurate);
+// v = (A + mu I) p in FP32 arithmetic (inner PCG of the mixed path; dense:
+// FP64 arithmetic on FP32 vectors).  `skip` (device int, may be NULL): when
+// nonzero every kernel returns at once (a converged solve).  `work` may be
+// NULL (allocated per call).
+int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* v, const int* skip,
+                      void* work, cudaStream_t s);
+// FP64-accurate v = (A + mu I) p (FP64 PCG and refinement residuals).
+int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double* v,
+                      const int* skip, void* work, cudaStream_t s);
+
+}  // namespace nys

@@ -1,0 +1,422 @@
+// Small dense FP64 linear algebra on ell x ell matrices (ell <= 4096):
+// Cholesky, triangular inverse and one-sided Jacobi SVD.  These carry the
+// ell x ell core of Algorithm 1 (Sec. 2.2): chol(Omega^T Y_nu), the
+// CholeskyQR passes of the thin QR/SVD, and the SVD of the small factor R.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so these kernels
+// keep the ell x ell working set in L2/shared memory and spread each step
+// over many SMs; the work is O(ell^3), tiny next to the n x ell passes.
+
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nys {
+
+// ============================================================ Cholesky (upper)
+
+constexpr int CH_NB = 32;
+
+// Factor the diagonal block D = M[k:k+nb, k:k+nb] in place: D = C_kk^T C_kk.
+__global__ void chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb, int* info) {
+  if (*info != 0) return;
+  __shared__ double D[CH_NB][CH_NB + 1];
+  __shared__ int bad;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
+  if (tx == 0 && ty == 0) bad = 0;
+  if (ty < nb && tx < nb) D[ty][tx] = M[(k + ty) * ell + k + tx];
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (tx == 0 && ty == 0) {
+      double d = D[j][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = (int)(k + j + 1);
+      } else {
+        D[j][j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    // row j right of the diagonal
+    if (ty == 0 && tx > j && tx < nb) D[j][tx] = D[j][tx] / D[j][j];
+    __syncthreads();
+    // trailing update of the upper triangle r <= c, r, c > j
+    if (ty > j && tx >= ty && tx < nb) D[ty][tx] -= D[j][ty] * D[j][tx];
+    __syncthreads();
+  }
+  if (bad) {
+    if (tx == 0 && ty == 0) atomicCAS(info, 0, bad);
+    return;
+  }
+  if (ty < nb && tx < nb) M[(k + ty) * ell + k + tx] = (tx >= ty) ? D[ty][tx] : 0.0;
+}
+
+// Row panel: C[k:k+nb, c] = C_kk^{-T} M[k:k+nb, c] for c >= k + nb (forward
+// substitution with the lower-triangular C_kk^T); one thread per column.
+__global__ void chol_panel_kernel(double* M, int64_t ell, int64_t k, int nb, const int* info) {
+  if (*info != 0) return;
+  __shared__ double Ck[CH_NB][CH_NB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int r = e / nb, c = e % nb;
+    Ck[r][c] = M[(k + r) * ell + k + c];
+  }
+  __syncthreads();
+  int64_t c = k + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ell) return;
+  double x[CH_NB];
+#pragma unroll
+  for (int r = 0; r < CH_NB; ++r) x[r] = (r < nb) ? M[(k + r) * ell + c] : 0.0;
+#pragma unroll
+  for (int r = 0; r < CH_NB; ++r) {
+    if (r < nb) {
+      double v = x[r];
+#pragma unroll
+      for (int t = 0; t < CH_NB; ++t)
+        if (t < r) v -= Ck[t][r] * x[t];
+      x[r] = v / Ck[r][r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < CH_NB; ++r)
+    if (r < nb) M[(k + r) * ell + c] = x[r];
+}
+
+// Trailing update of the upper triangle: M[i, j] -= sum_t C[k+t, i] C[k+t, j]
+// for k+nb <= i <= j.  32 x 32 output tiles, lower tiles skipped.
+__global__ void chol_trail_kernel(double* M, int64_t ell, int64_t k, int nb, const int* info) {
+  if (*info != 0) return;
+  const int64_t base = k + nb;
+  const int64_t ti = base + (int64_t)blockIdx.y * 32, tj = base + (int64_t)blockIdx.x * 32;
+  if (tj + 31 < ti) return;  // tile strictly below the diagonal
+  __shared__ double Pi[CH_NB][33], Pj[CH_NB][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < nb; r += 8) {
+    Pi[r][tx] = (ti + tx < ell) ? M[(k + r) * ell + ti + tx] : 0.0;
+    Pj[r][tx] = (tj + tx < ell) ? M[(k + r) * ell + tj + tx] : 0.0;
+  }
+  __syncthreads();
+  for (int rr = ty; rr < 32; rr += 8) {
+    int64_t i = ti + rr, j = tj + tx;
+    if (i < ell && j < ell && j >= i) {
+      double acc = 0.0;
+      for (int t = 0; t < nb; ++t) acc += Pi[t][rr] * Pj[t][tx];
+      M[i * ell + j] -= acc;
+    }
+  }
+}
+
+__global__ void zero_lower_kernel(double* M, int64_t ell) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ell * ell) return;
+  int64_t i = e / ell, j = e % ell;
+  if (j < i) M[e] = 0.0;
+}
+
+int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
+  NYS_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  for (int64_t k = 0; k < ell; k += CH_NB) {
+    int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
+    chol_diag_kernel<<<1, dim3(32, 32), 0, s>>>(M, ell, k, nb, d_info);
+    int64_t rest = ell - k - nb;
+    if (rest > 0) {
+      chol_panel_kernel<<<(unsigned)cdiv(rest, 128), 128, 0, s>>>(M, ell, k, nb, d_info);
+      unsigned t = (unsigned)cdiv(rest, 32);
+      chol_trail_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(M, ell, k, nb, d_info);
+    }
+  }
+  zero_lower_kernel<<<(unsigned)cdiv(ell * ell, 256), 256, 0, s>>>(M, ell);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// ============================================================ triangular inverse
+
+// Row j of X^T (= column j of X = C^{-1} e_j) by back substitution; one warp
+// per column.  XT[j][i] = X[i][j]; entries i > j are zero.
+__global__ void tri_inv_cols_kernel(const double* C, double* XT, int64_t ell) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= ell) return;
+  double* x = XT + j * ell;
+  for (int64_t i = lane; i < ell; i += 32) x[i] = 0.0;
+  __syncwarp();
+  if (lane == 0) x[j] = 1.0 / C[j * ell + j];
+  __syncwarp();
+  for (int64_t i = j - 1; i >= 0; --i) {
+    const double* Ci = C + i * ell;
+    double acc = 0.0;
+    for (int64_t t = i + 1 + lane; t <= j; t += 32) acc += Ci[t] * x[t];
+    acc = warp_sum(acc);
+    if (lane == 0) x[i] = -acc / Ci[i];
+    __syncwarp();
+  }
+}
+
+__global__ void transpose_kernel(const double* in, double* out, int64_t rows, int64_t cols) {
+  __shared__ double tile[32][33];
+  int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    int64_t i = by + r, j = bx + threadIdx.x;
+    if (i < rows && j < cols) tile[r][threadIdx.x] = in[i * cols + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    int64_t i = bx + r, j = by + threadIdx.x;  // out is cols x rows
+    if (i < cols && j < rows) out[i * rows + j] = tile[threadIdx.x][r];
+  }
+}
+
+int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s) {
+  double* XT = nullptr;
+  NYS_TRY(dmalloc((void**)&XT, ell * ell * sizeof(double), s));
+  tri_inv_cols_kernel<<<(unsigned)cdiv(ell, 4), 128, 0, s>>>(C, XT, ell);
+  dim3 g((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 32));
+  transpose_kernel<<<g, dim3(32, 8), 0, s>>>(XT, X, ell, ell);
+  cudaError_t e = cudaGetLastError();
+  dfree(XT, s);
+  NYS_CUDA_TRY(e);
+  return NYS_OK;
+}
+
+__global__ void symmetrize_kernel(double* M, int64_t ell) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ell * ell) return;
+  int64_t i = e / ell, j = e % ell;
+  if (j <= i) return;
+  double a = M[i * ell + j], b = M[j * ell + i];
+  double v = 0.5 * (a + b);
+  M[i * ell + j] = v;
+  M[j * ell + i] = v;
+}
+
+int32_t symmetrize(double* M, int64_t ell, cudaStream_t s) {
+  symmetrize_kernel<<<(unsigned)cdiv(ell * ell, 256), 256, 0, s>>>(M, ell);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+__global__ void add_diag_kernel(double* M, int64_t ell, double shift) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ell) M[i * ell + i] += shift;
+}
+
+int32_t add_diag(double* M, int64_t ell, double shift, cudaStream_t s) {
+  add_diag_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(M, ell, shift);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// ============================================================ one-sided Jacobi SVD
+
+// Bounded grid barrier for a cooperative launch.  Returns false (and sets
+// *status = NYS_ERR_TIMEOUT) if the wait did not end within the spin limit
+// or another block already failed; the caller then returns.
+__device__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* status) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = gen;
+    volatile int* vstat = status;
+    unsigned int g = *vgen;
+    __threadfence();
+    unsigned int nb = gridDim.x;
+    if (atomicAdd(count, 1u) == nb - 1) {
+      *count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (*vstat != 0) { ok = 0; break; }
+        if (++spins > (1ll << 26)) {  // ~ seconds: far beyond any legal wait
+          atomicCAS(status, 0, (int)NYS_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct JacobiArgs {
+  double* W;          // ell_pad x ell rows: row j = column j of the matrix being rotated
+  int64_t ell;        // true size (row length)
+  int64_t npad;       // number of columns incl. padding (even)
+  int max_sweeps;
+  unsigned int* bar;  // [2] barrier count, generation
+  int* rot_count;     // [max_sweeps]
+  int* status;
+  int* sweeps_done;
+};
+
+// Column pairs (p, q) of round r of the circle ordering on npad players.
+__device__ __forceinline__ void round_pair(int64_t npad, int64_t r, int64_t k, int64_t* p,
+                                           int64_t* q) {
+  auto pos = [&](int64_t i) -> int64_t {
+    if (i == 0) return 0;
+    return 1 + ((i - 1 + r) % (npad - 1));
+  };
+  *p = pos(k);
+  *q = pos(npad - 1 - k);
+}
+
+__global__ void jacobi_kernel(JacobiArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t npairs = a.npad / 2;
+  const double tol = 1e-15;
+  int sweep = 0;
+  for (; sweep < a.max_sweeps; ++sweep) {
+    for (int64_t r = 0; r < a.npad - 1; ++r) {
+      for (int64_t k = warp; k < npairs; k += nwarps) {
+        int64_t p, q;
+        round_pair(a.npad, r, k, &p, &q);
+        if (p >= a.ell || q >= a.ell) continue;  // padding column
+        double* wp = a.W + p * a.ell;
+        double* wq = a.W + q * a.ell;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int64_t i = lane; i < a.ell; i += 32) {
+          double x = wp[i], y = wq[i];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (fabs(ga) > tol * sqrt(al * be) && al * be > 0.0) {
+          double zeta = (be - al) / (2.0 * ga);
+          double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double c = 1.0 / sqrt(1.0 + t * t);
+          double sn = c * t;
+          for (int64_t i = lane; i < a.ell; i += 32) {
+            double x = wp[i], y = wq[i];
+            wp[i] = c * x - sn * y;
+            wq[i] = sn * x + c * y;
+          }
+          if (lane == 0) atomicAdd(&a.rot_count[sweep], 1);
+        }
+      }
+      if (!grid_barrier(a.bar, a.bar + 1, a.status)) return;
+    }
+    volatile int* rc = a.rot_count;
+    if (rc[sweep] == 0) {
+      ++sweep;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.sweeps_done = sweep;
+}
+
+// sigma_j = ||w_j||; sort descending (bitonic in shared memory, one block);
+// Ut[i][j] = w_{perm[j]}[i] / sigma_j.
+__global__ void jacobi_finish_kernel(const double* W, int64_t ell, int64_t pow2, double* Ut,
+                                     double* sigma) {
+  extern __shared__ unsigned char smem_raw[];
+  double* key = reinterpret_cast<double*>(smem_raw);
+  int* idx = reinterpret_cast<int*>(key + pow2);
+  for (int64_t j = threadIdx.x; j < pow2; j += blockDim.x) {
+    if (j < ell) {
+      const double* w = W + j * ell;
+      double acc = 0.0;
+      for (int64_t i = 0; i < ell; ++i) acc += w[i] * w[i];
+      key[j] = sqrt(acc);
+    } else {
+      key[j] = -1.0;
+    }
+    idx[j] = (int)j;
+  }
+  __syncthreads();
+  // bitonic sort, descending by key, ties by index ascending
+  for (int64_t size = 2; size <= pow2; size <<= 1) {
+    for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int64_t t = threadIdx.x; t < pow2; t += blockDim.x) {
+        int64_t partner = t ^ stride;
+        if (partner > t) {
+          bool desc = ((t & size) == 0);
+          double ka = key[t], kb = key[partner];
+          int ia = idx[t], ib = idx[partner];
+          bool a_before_b = (ka > kb) || (ka == kb && ia < ib);
+          bool swap = desc ? !a_before_b : a_before_b;
+          if (swap) {
+            key[t] = kb; key[partner] = ka;
+            idx[t] = ib; idx[partner] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int64_t j = threadIdx.x; j < ell; j += blockDim.x) sigma[j] = key[j];
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < ell * ell; e += blockDim.x) {
+    int64_t i = e / ell, j = e % ell;
+    double sg = key[j];
+    const double* w = W + (int64_t)idx[j] * ell;
+    Ut[e] = (sg > 0.0) ? w[i] / sg : (i == j ? 1.0 : 0.0);
+  }
+}
+
+int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int* d_status,
+                   int* sweeps_out, cudaStream_t s) {
+  const int max_sweeps = 40;
+  int64_t npad = ell + (ell & 1);
+  double* W = nullptr;
+  unsigned char* aux = nullptr;
+  NYS_TRY(dmalloc((void**)&W, ell * ell * sizeof(double), s));
+  size_t aux_bytes = 2 * sizeof(unsigned) + max_sweeps * sizeof(int) + 2 * sizeof(int);
+  int32_t st = dmalloc((void**)&aux, aux_bytes, s);
+  if (st != NYS_OK) { dfree(W, s); return st; }
+  // W rows = columns of R
+  dim3 g((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 32));
+  transpose_kernel<<<g, dim3(32, 8), 0, s>>>(R, W, ell, ell);
+  cudaMemsetAsync(aux, 0, aux_bytes, s);
+  cudaMemsetAsync(d_status, 0, sizeof(int), s);
+  JacobiArgs a;
+  a.W = W;
+  a.ell = ell;
+  a.npad = npad;
+  a.max_sweeps = max_sweeps;
+  a.bar = reinterpret_cast<unsigned int*>(aux);
+  a.rot_count = reinterpret_cast<int*>(aux + 2 * sizeof(unsigned));
+  a.sweeps_done = a.rot_count + max_sweeps;
+  a.status = d_status;
+  // grid: enough warps for all pairs, limited to co-resident blocks
+  int threads = 256;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, threads, 0);
+  int64_t want = cdiv(npad / 2, threads / 32);
+  int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+  int blocks = (int)(want < cap ? want : cap);
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(blocks), dim3(threads),
+                                              args, 0, s);
+  if (e == cudaSuccess) {
+    int64_t pow2 = 1;
+    while (pow2 < ell) pow2 <<= 1;
+    size_t sh = pow2 * (sizeof(double) + sizeof(int));
+    if (sh > 48 * 1024)
+      cudaFuncSetAttribute(jacobi_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sh);
+    jacobi_finish_kernel<<<1, 1024, sh, s>>>(W, ell, pow2, Ut, sigma);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && sweeps_out) {
+    e = cudaMemcpyAsync(sweeps_out, a.sweeps_done, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  dfree(aux, s);
+  dfree(W, s);
+  NYS_CUDA_TRY(e);
+  return NYS_OK;
+}
+
+}  // namespace nys

@@ -1,0 +1,549 @@
+// Operator kernels: x -> A x for the three operators (Sec. 1.1 accesses A
+// only through matvecs) and the sketch Y = A Omega of Algorithm 1, step 3.
+//
+//  dense : A n x n FP64.  Warp per row, FP64 FMA.
+//  gram  : A = X^T X, X m x n FP32 (ridge, Eq. (1.7)).  One pass over X:
+//          each CTA streams its rows through shared memory with bulk async
+//          copies (TMA engine) into a 3-stage mbarrier pipeline, forms
+//          t_i = x_i . p with a CTA-wide reduction and accumulates t_i x_i
+//          into a per-CTA n-vector held in registers; a second kernel sums
+//          the per-CTA partials in a fixed order.  X is read from HBM once.
+//  rbf   : A = K, K_ij = exp(-||x_i - x_j||^2 / (2 sigma^2)) (Sec. 6.5),
+//          computed on the fly tile by tile and never stored.
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace nys {
+
+// ============================================================ dense
+
+template <typename P, typename V>
+__global__ void dense_matvec_kernel(const double* __restrict__ A, int64_t n, int64_t ld,
+                                    const P* __restrict__ p, double mu, V* __restrict__ v,
+                                    const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const double* a = A + row * ld;
+  double acc = 0.0;
+  for (int64_t j = lane; j < n; j += 32) acc = fma(a[j], (double)p[j], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) v[row] = (V)(acc + mu * (double)p[row]);
+}
+
+// ============================================================ gram (fused single pass)
+
+constexpr int GR_THREADS = 256;
+constexpr int GR_ROWS = 4;  // rows per pipeline stage
+
+// part[blockIdx.x][0..n) = sum over this CTA's rows i of (x_i . p) x_i.
+// NG = float4 column groups per thread (n <= NG * 4 * 256).
+template <typename P, typename Acc, int NG>
+__global__ void __launch_bounds__(GR_THREADS, 1)
+gram_fused_kernel(const float* __restrict__ X, int64_t m, int64_t n, const P* __restrict__ p,
+                  Acc* __restrict__ part, int stages, int64_t rows_per_cta, int* err,
+                  const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  float* stage_mem = reinterpret_cast<float*>(smem + 128);
+  __shared__ Acc red[GR_THREADS / 32][GR_ROWS];
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n4 = n >> 2;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = (r0 + rows_per_cta < m) ? r0 + rows_per_cta : m;
+  Acc* out = part + (int64_t)blockIdx.x * n;
+
+  Acc pr[NG][4], acc[NG][4];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    int64_t c4 = tid + (int64_t)g * GR_THREADS;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      pr[g][q] = (c4 < n4) ? (Acc)p[4 * c4 + q] : Acc(0);
+      acc[g][q] = Acc(0);
+    }
+  }
+  if (r0 >= r1) {
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      int64_t c4 = tid + (int64_t)g * GR_THREADS;
+      if (c4 < n4)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[4 * c4 + q] = Acc(0);
+    }
+    return;
+  }
+  const int64_t nrows = r1 - r0;
+  const int64_t nchunks = (nrows + GR_ROWS - 1) / GR_ROWS;
+  const int64_t stage_elems = (int64_t)GR_ROWS * n;
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+    s_fail = 0;
+  }
+  __syncthreads();
+
+  auto issue = [&](int64_t c) {
+    int s = (int)(c % stages);
+    int64_t rows = nrows - c * GR_ROWS;
+    if (rows > GR_ROWS) rows = GR_ROWS;
+    uint32_t bytes = (uint32_t)(rows * n * sizeof(float));
+    mbar_arrive_expect_tx(&bars[s], bytes);
+    bulk_g2s(stage_mem + s * stage_elems, X + (r0 + c * GR_ROWS) * n, bytes, &bars[s]);
+  };
+  if (tid == 0) {
+    int64_t pre = (stages - 1 < nchunks) ? stages - 1 : nchunks;
+    for (int64_t c = 0; c < pre; ++c) issue(c);
+  }
+
+  int64_t issued = (stages - 1 < nchunks) ? stages - 1 : nchunks;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int s = (int)(c % stages);
+    if (c + stages - 1 < nchunks) {
+      if (tid == 0) issue(c + stages - 1);
+      issued = c + stages;
+    }
+    bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((c / stages) & 1));
+    if (!ok) atomicOr(&s_fail, 1);
+    int64_t rows = nrows - c * GR_ROWS;
+    if (rows > GR_ROWS) rows = GR_ROWS;
+    const float* st = stage_mem + s * stage_elems;
+
+    float xr[GR_ROWS][NG][4];
+    Acc d[GR_ROWS];
+#pragma unroll
+    for (int r = 0; r < GR_ROWS; ++r) {
+      d[r] = Acc(0);
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        int64_t c4 = tid + (int64_t)g * GR_THREADS;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rows && c4 < n4) v = reinterpret_cast<const float4*>(st + r * n)[c4];
+        xr[r][g][0] = v.x; xr[r][g][1] = v.y; xr[r][g][2] = v.z; xr[r][g][3] = v.w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[r] = fma((Acc)xr[r][g][q], pr[g][q], d[r]);
+      }
+      d[r] = warp_sum(d[r]);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < GR_ROWS; ++r) red[warp][r] = d[r];
+    }
+    __syncthreads();
+    if (s_fail) break;
+    Acc t[GR_ROWS];
+#pragma unroll
+    for (int r = 0; r < GR_ROWS; ++r) {
+      Acc v = Acc(0);
+#pragma unroll
+      for (int w = 0; w < GR_THREADS / 32; ++w) v += red[w][r];
+      t[r] = v;
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < GR_ROWS; ++r) acc[g][q] = fma(t[r], (Acc)xr[r][g][q], acc[g][q]);
+    __syncthreads();
+  }
+  if (s_fail) {
+    // drain: wait (bounded) for every copy this CTA issued, then report.
+    if (tid == 0) {
+      atomicCAS(err, 0, (int)NYS_ERR_TIMEOUT);
+      for (int64_t c = 0; c < issued; ++c)
+        mbar_wait_bounded(&bars[c % stages], (uint32_t)((c / stages) & 1), 1ll << 20);
+    }
+    return;
+  }
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    int64_t c4 = tid + (int64_t)g * GR_THREADS;
+    if (c4 < n4)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[4 * c4 + q] = acc[g][q];
+  }
+}
+
+// v_j = sum_c part[c][j] (fixed order) + mu p_j; optionally r_j = b_j - v_j.
+template <typename Acc, typename P, typename V>
+__global__ void gram_reduce_kernel(const Acc* __restrict__ part, int64_t nparts, int64_t n,
+                                   double mu, const P* __restrict__ p, V* __restrict__ v,
+                                   const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  Acc acc = Acc(0);
+  for (int64_t c = 0; c < nparts; ++c) acc += part[c * n + j];
+  v[j] = (V)((double)acc + mu * (double)p[j]);
+}
+
+// Generic two-pass path (any n, any ld): t = X p, then v = X^T t.
+template <typename P, typename Acc>
+__global__ void gram_xp_kernel(const float* __restrict__ X, int64_t m, int64_t n, int64_t ld,
+                               const P* __restrict__ p, Acc* __restrict__ t,
+                               const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= m) return;
+  const float* x = X + row * ld;
+  Acc acc = Acc(0);
+  for (int64_t j = lane; j < n; j += 32) acc = fma((Acc)x[j], (Acc)p[j], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) t[row] = acc;
+}
+
+template <typename Acc>
+__global__ void gram_xtt_kernel(const float* __restrict__ X, int64_t m, int64_t n, int64_t ld,
+                                const Acc* __restrict__ t, int64_t rows_per_chunk,
+                                Acc* __restrict__ part, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t c = blockIdx.y;
+  if (j >= n) return;
+  int64_t i0 = c * rows_per_chunk, i1 = i0 + rows_per_chunk < m ? i0 + rows_per_chunk : m;
+  Acc acc = Acc(0);
+  for (int64_t i = i0; i < i1; ++i) acc = fma((Acc)X[i * ld + j], t[i], acc);
+  part[c * n + j] = acc;
+}
+
+struct GramPlan {
+  bool fused;
+  int ng;
+  int stages;
+  int grid;
+  int64_t rows_per_cta;
+  size_t smem;
+};
+
+static GramPlan gram_plan(const nys_operator* op) {
+  GramPlan g{};
+  const int64_t n = op->n, m = op->m;
+  bool aligned = ((uintptr_t)op->data % 16 == 0) && (n % 4 == 0) && (op->ld == n);
+  int64_t n4 = n / 4;
+  int ng = (int)cdiv(n4, GR_THREADS);
+  g.fused = aligned && n4 > 0 && ng <= 8;
+  if (!g.fused) return g;
+  g.ng = ng <= 1 ? 1 : ng <= 2 ? 2 : ng <= 4 ? 4 : 8;
+  size_t stage_bytes = (size_t)GR_ROWS * n * sizeof(float);
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 4) stages = 4;
+  if (stages < 2) {
+    g.fused = false;
+    return g;
+  }
+  g.stages = stages;
+  g.smem = 128 + stages * stage_bytes;
+  g.grid = num_sms();
+  g.rows_per_cta = cdiv(m, g.grid);
+  return g;
+}
+
+template <typename P, typename Acc, int NG>
+static int32_t gram_fused_launch(const nys_operator* op, const GramPlan& g, const P* p, Acc* part,
+                                 int* err, const int* skip, cudaStream_t s) {
+  auto kern = gram_fused_kernel<P, Acc, NG>;
+  NYS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
+  kern<<<g.grid, GR_THREADS, g.smem, s>>>((const float*)op->data, op->m, op->n, p, part, g.stages,
+                                           g.rows_per_cta, err, skip);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+static size_t gram_work_bytes(const nys_operator* op, size_t acc_size) {
+  GramPlan g = gram_plan(op);
+  if (g.fused) return 256 + (size_t)g.grid * op->n * acc_size;
+  int64_t chunks = 4 * (int64_t)num_sms();
+  int64_t rpc = cdiv(op->m, chunks);
+  chunks = cdiv(op->m, rpc);
+  return 256 + ((size_t)op->m + 64) * acc_size + (size_t)chunks * op->n * acc_size;
+}
+
+// v = (X^T X + mu I) p; Acc = accumulation type (float: PCG inner, double: accurate).
+// `work` holds gram_work_bytes(op, sizeof(Acc)) bytes; its first 256 bytes
+// hold the timeout word.
+template <typename P, typename Acc, typename V>
+static int32_t gram_matvec(const nys_operator* op, double mu, const P* p, V* v, const int* skip,
+                           void* work, cudaStream_t s) {
+  const int64_t n = op->n, m = op->m;
+  GramPlan g = gram_plan(op);
+  int* err = reinterpret_cast<int*>(work);
+  Acc* base = reinterpret_cast<Acc*>(reinterpret_cast<unsigned char*>(work) + 256);
+  if (g.fused) {
+    Acc* part = base;
+    switch (g.ng) {
+      case 1: NYS_TRY((gram_fused_launch<P, Acc, 1>(op, g, p, part, err, skip, s))); break;
+      case 2: NYS_TRY((gram_fused_launch<P, Acc, 2>(op, g, p, part, err, skip, s))); break;
+      case 4: NYS_TRY((gram_fused_launch<P, Acc, 4>(op, g, p, part, err, skip, s))); break;
+      default: NYS_TRY((gram_fused_launch<P, Acc, 8>(op, g, p, part, err, skip, s))); break;
+    }
+    gram_reduce_kernel<Acc, P, V><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, g.grid, n, mu, p, v,
+                                                                         skip);
+    NYS_CUDA_TRY(cudaGetLastError());
+    return NYS_OK;
+  }
+  int64_t chunks = 4 * (int64_t)num_sms();
+  int64_t rpc = cdiv(m, chunks);
+  chunks = cdiv(m, rpc);
+  Acc* t = base;
+  Acc* part = base + m + 64;
+  gram_xp_kernel<P, Acc><<<(unsigned)cdiv(m, 8), 256, 0, s>>>((const float*)op->data, m, n, op->ld,
+                                                               p, t, skip);
+  dim3 grid((unsigned)cdiv(n, 128), (unsigned)chunks);
+  gram_xtt_kernel<Acc><<<grid, 128, 0, s>>>((const float*)op->data, m, n, op->ld, t, rpc, part,
+                                            skip);
+  gram_reduce_kernel<Acc, P, V><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, chunks, n, mu, p, v,
+                                                                       skip);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// ============================================================ rbf
+
+constexpr int RBF_DMAX = 64;
+constexpr int RBF_BI = 128;  // rows per CTA (one per thread)
+constexpr int RBF_BJ = 128;  // points per smem tile
+
+// v_i = sum_j exp(-||x_i - x_j||^2 / (2 sigma^2)) p_j + mu p_i.
+// T = arithmetic type of the distances, the exponential and the sum.
+template <typename T, typename P, typename V>
+__global__ void __launch_bounds__(RBF_BI)
+rbf_matvec_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld, double sigma,
+                  const P* __restrict__ p, double mu, V* __restrict__ v,
+                  const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float xs[RBF_BJ][RBF_DMAX + 1];
+  __shared__ T ps[RBF_BJ];
+  const int64_t i = (int64_t)blockIdx.x * RBF_BI + threadIdx.x;
+  float xi[RBF_DMAX];
+#pragma unroll
+  for (int k = 0; k < RBF_DMAX; ++k) xi[k] = (i < n && k < d) ? pts[i * ld + k] : 0.f;
+  const T scale = (T)(-1.0 / (2.0 * sigma * sigma));
+  T acc = T(0);
+  for (int64_t j0 = 0; j0 < n; j0 += RBF_BJ) {
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)RBF_BJ * d; e += RBF_BI) {
+      int64_t jj = e / d, k = e % d;
+      xs[jj][k] = (j0 + jj < n) ? pts[(j0 + jj) * ld + k] : 0.f;
+    }
+    for (int jj = threadIdx.x; jj < RBF_BJ; jj += RBF_BI) ps[jj] = (j0 + jj < n) ? (T)p[j0 + jj] : T(0);
+    __syncthreads();
+    const int jn = (int)((n - j0 < RBF_BJ) ? n - j0 : RBF_BJ);
+    for (int jj = 0; jj < jn; ++jj) {
+      T dist = T(0);
+#pragma unroll
+      for (int k = 0; k < RBF_DMAX; ++k) {
+        if (k < d) {
+          T df = (T)xi[k] - (T)xs[jj][k];
+          dist = fma(df, df, dist);
+        }
+      }
+      acc = fma(exp(dist * scale), ps[jj], acc);
+    }
+  }
+  if (i < n) v[i] = (V)((double)acc + mu * (double)p[i]);
+}
+
+// Y[i][l] = sum_j K_ij Q[j][l] for a 64-row x 64-column output tile per CTA.
+constexpr int RS_BI = 64, RS_BL = 64;
+template <typename T, int RS_BJ = (sizeof(T) == 8 ? 16 : 32)>
+__global__ void __launch_bounds__(256)
+rbf_sketch_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld, double sigma,
+                  const T* __restrict__ Q, int64_t ell, T* __restrict__ Y) {
+  __shared__ float xi[RS_BI][RBF_DMAX + 1];
+  __shared__ float xj[RS_BJ][RBF_DMAX + 1];
+  __shared__ T Ks[RS_BJ][RS_BI + 1];
+  __shared__ T Qs[RS_BJ][RS_BL + 1];
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * RS_BI, l0 = (int64_t)blockIdx.y * RS_BL;
+  const T scale = (T)(-1.0 / (2.0 * sigma * sigma));
+  for (int64_t e = tid; e < (int64_t)RS_BI * d; e += 256) {
+    int64_t r = e / d, k = e % d;
+    xi[r][k] = (i0 + r < n) ? pts[(i0 + r) * ld + k] : 0.f;
+  }
+  const int tr = tid / 16, tc = tid % 16;  // 16 x 16 threads, 4 x 4 outputs each
+  T acc[4][4] = {};
+  for (int64_t j0 = 0; j0 < n; j0 += RS_BJ) {
+    __syncthreads();
+    for (int64_t e = tid; e < (int64_t)RS_BJ * d; e += 256) {
+      int64_t r = e / d, k = e % d;
+      xj[r][k] = (j0 + r < n) ? pts[(j0 + r) * ld + k] : 0.f;
+    }
+    for (int e = tid; e < RS_BJ * RS_BL; e += 256) {
+      int r = e / RS_BL, c = e % RS_BL;
+      Qs[r][c] = (j0 + r < n && l0 + c < ell) ? Q[(j0 + r) * ell + l0 + c] : T(0);
+    }
+    __syncthreads();
+    for (int e = tid; e < RS_BI * RS_BJ; e += 256) {
+      int r = e % RS_BI, jj = e / RS_BI;
+      T dist = T(0);
+      for (int k = 0; k < d; ++k) {
+        T df = (T)xi[r][k] - (T)xj[jj][k];
+        dist = fma(df, df, dist);
+      }
+      Ks[jj][r] = (j0 + jj < n) ? exp(dist * scale) : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < RS_BJ; ++jj) {
+      T a[4], b[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) a[x] = Ks[jj][tr * 4 + x];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) b[y] = Qs[jj][tc * 4 + y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    int64_t i = i0 + tr * 4 + x;
+    if (i >= n) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      int64_t l = l0 + tc * 4 + y;
+      if (l < ell) Y[i * ell + l] = acc[x][y];
+    }
+  }
+}
+
+// ============================================================ dispatch
+
+int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int64_t ell,
+                  cudaStream_t s) {
+  const int64_t n = op->n;
+  if (op->kind == NYS_OP_DENSE) {
+    if (f64)
+      return gemm_f64(false, n, ell, n, (const double*)op->data, op->ld, (const double*)Q, ell,
+                      (double*)V, ell, s);
+    // mixed: FP64 matrix, FP32 block -> compute in FP64 and round
+    Scratch sc(s);
+    double *Qd, *Vd;
+    NYS_TRY(sc.get(&Qd, n * ell));
+    NYS_TRY(sc.get(&Vd, n * ell));
+    NYS_TRY(convert_f32_to_f64((const float*)Q, Qd, n * ell, s));
+    NYS_TRY(gemm_f64(false, n, ell, n, (const double*)op->data, op->ld, Qd, ell, Vd, ell, s));
+    return convert_f64_to_f32(Vd, (float*)V, n * ell, s);
+  }
+  if (op->kind == NYS_OP_GRAM) {
+    const int64_t m = op->m;
+    const float* X = (const float*)op->data;
+    Scratch sc(s);
+    if (f64) {
+      // exact FP64 products of the FP32 data
+      double *Xd, *Z;
+      NYS_TRY(sc.get(&Z, m * ell));
+      // Z = X Q computed from an FP64 copy of X in row blocks to bound memory
+      const int64_t blk = 16384;
+      NYS_TRY(sc.get(&Xd, (m < blk ? m : blk) * n));
+      for (int64_t r0 = 0; r0 < m; r0 += blk) {
+        int64_t rows = (m - r0 < blk) ? m - r0 : blk;
+        if (op->ld == n) {
+          NYS_TRY(convert_f32_to_f64(X + r0 * n, Xd, rows * n, s));
+        } else {
+          for (int64_t r = 0; r < rows; ++r)
+            NYS_TRY(convert_f32_to_f64(X + (r0 + r) * op->ld, Xd + r * n, n, s));
+        }
+        NYS_TRY(gemm_f64(false, rows, ell, n, Xd, n, (const double*)Q, ell, Z + r0 * ell, ell, s));
+      }
+      // V = X^T Z = sum over row blocks of Xd_b^T Z_b
+      double* acc;
+      double* tmp;
+      NYS_TRY(sc.get(&acc, n * ell));
+      NYS_TRY(sc.get(&tmp, n * ell));
+      NYS_CUDA_TRY(cudaMemsetAsync(acc, 0, n * ell * sizeof(double), s));
+      for (int64_t r0 = 0; r0 < m; r0 += blk) {
+        int64_t rows = (m - r0 < blk) ? m - r0 : blk;
+        if (op->ld == n) {
+          NYS_TRY(convert_f32_to_f64(X + r0 * n, Xd, rows * n, s));
+        } else {
+          for (int64_t r = 0; r < rows; ++r)
+            NYS_TRY(convert_f32_to_f64(X + (r0 + r) * op->ld, Xd + r * n, n, s));
+        }
+        NYS_TRY(gemm_f64(true, n, ell, rows, Xd, n, Z + r0 * ell, ell, tmp, ell, s));
+        NYS_TRY(add_inplace_f64(acc, tmp, n * ell, s));
+      }
+      NYS_CUDA_TRY(cudaMemcpyAsync(V, acc, n * ell * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      return NYS_OK;
+    }
+    float* Z;
+    NYS_TRY(sc.get(&Z, m * ell));
+    NYS_TRY(gemm_f32(false, m, ell, n, X, op->ld, (const float*)Q, ell, Z, ell, s));
+    return gemm_f32(true, n, ell, m, X, op->ld, Z, ell, (float*)V, ell, s);
+  }
+  // RBF
+  dim3 grid((unsigned)cdiv(n, RS_BI), (unsigned)cdiv(ell, RS_BL));
+  if (f64)
+    rbf_sketch_kernel<double><<<grid, 256, 0, s>>>((const float*)op->data, n, op->d, op->ld,
+                                                   op->sigma, (const double*)Q, ell, (double*)V);
+  else
+    rbf_sketch_kernel<float><<<grid, 256, 0, s>>>((const float*)op->data, n, op->d, op->ld,
+                                                  op->sigma, (const float*)Q, ell, (float*)V);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+size_t op_matvec_work_bytes(const nys_operator* op, bool accurate) {
+  if (op->kind == NYS_OP_GRAM) return gram_work_bytes(op, accurate ? sizeof(double) : sizeof(float));
+  return 256;
+}
+
+int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* v, const int* skip,
+                      void* work, cudaStream_t s) {
+  const int64_t n = op->n;
+  if (op->kind == NYS_OP_DENSE) {
+    dense_matvec_kernel<float, float><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(
+        (const double*)op->data, n, op->ld, p, mu, v, skip);
+    NYS_CUDA_TRY(cudaGetLastError());
+    return NYS_OK;
+  }
+  if (op->kind == NYS_OP_GRAM) {
+    if (work) return gram_matvec<float, float, float>(op, mu, p, v, skip, work, s);
+    Scratch sc(s);
+    unsigned char* w;
+    NYS_TRY(sc.get(&w, op_matvec_work_bytes(op, false)));
+    NYS_CUDA_TRY(cudaMemsetAsync(w, 0, 256, s));
+    return gram_matvec<float, float, float>(op, mu, p, v, skip, w, s);
+  }
+  rbf_matvec_kernel<float, float, float><<<(unsigned)cdiv(n, RBF_BI), RBF_BI, 0, s>>>(
+      (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double* v,
+                      const int* skip, void* work, cudaStream_t s) {
+  const int64_t n = op->n;
+  if (op->kind == NYS_OP_DENSE) {
+    dense_matvec_kernel<double, double><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(
+        (const double*)op->data, n, op->ld, p, mu, v, skip);
+    NYS_CUDA_TRY(cudaGetLastError());
+    return NYS_OK;
+  }
+  if (op->kind == NYS_OP_GRAM) {
+    if (work) return gram_matvec<double, double, double>(op, mu, p, v, skip, work, s);
+    Scratch sc(s);
+    unsigned char* w;
+    NYS_TRY(sc.get(&w, op_matvec_work_bytes(op, true)));
+    NYS_CUDA_TRY(cudaMemsetAsync(w, 0, 256, s));
+    return gram_matvec<double, double, double>(op, mu, p, v, skip, w, s);
+  }
+  rbf_matvec_kernel<double, double, double><<<(unsigned)cdiv(n, RBF_BI), RBF_BI, 0, s>>>(
+      (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip);
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+}  // namespace nys

@@ -1,0 +1,305 @@
+"""Thin Python binding of the C ABI in ``include/nyspcg.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``lib/libnyspcg.so``.  Tensors must be CUDA tensors; the current
+torch stream is passed to the library.  If the library has not been built
+the first call raises ``NysLibraryMissing`` (there is no CPU fallback).
+
+The function names are those of the C ABI: ``nys_sketch``,
+``nys_sketch_adaptive``, ``nys_precond_apply``, ``pcg_solve``,
+``nys_op_matvec``, ``nys_power_err_est``.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+NYS_OK, NYS_ERR_ARG, NYS_ERR_NOT_PSD, NYS_ERR_BREAKDOWN, NYS_ERR_MAXIT, NYS_ERR_TIMEOUT, \
+    NYS_ERR_CUDA, NYS_ERR_OOM = range(8)
+NYS_OP_DENSE, NYS_OP_GRAM, NYS_OP_RBF = range(3)
+NYS_F64, NYS_F32 = range(2)
+NYS_PREC_F64, NYS_PREC_MIXED = range(2)
+NYS_RULE_ERR, NYS_RULE_RATIO = range(2)
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libnyspcg.so")
+
+
+class NysLibraryMissing(RuntimeError):
+    pass
+
+
+class NysError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status} ({status_str(status)})")
+        self.status = status
+
+
+class _Operator(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("n", C.c_int64), ("m", C.c_int64),
+                ("d", C.c_int64), ("ld", C.c_int64), ("data", C.c_void_p), ("sigma", C.c_double)]
+
+
+class _AdaptInfo(C.Structure):
+    _fields_ = [("ell", C.c_int64), ("doublings", C.c_int32), ("estimates", C.c_int32),
+                ("err_est", C.c_double), ("lambda_ell", C.c_double), ("kappa_est", C.c_double)]
+
+
+class _PcgOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("precision", C.c_int32),
+                ("inner_tol", C.c_double), ("max_refine", C.c_int32), ("use_x0", C.c_int32),
+                ("residual_history", C.c_void_p)]
+
+
+class _PcgResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("refinements", C.c_int32),
+                ("reserved", C.c_int32), ("rel_residual", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+EXPORTS = ["nys_sketch", "nys_sketch_adaptive", "nys_precond_apply", "pcg_solve", "nys_factor_get",
+           "nys_factor_free", "nys_status_str", "nys_op_matvec", "nys_power_err_est"]
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise NysLibraryMissing(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2110_02820_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+        L.nys_sketch.argtypes = [C.POINTER(_Operator), i64, u64, vp, i32, C.POINTER(vp), vp]
+        L.nys_sketch_adaptive.argtypes = [C.POINTER(_Operator), i64, i64, i32, dbl, i32, dbl, u64,
+                                          vp, vp, i32, C.POINTER(vp), C.POINTER(_AdaptInfo), vp]
+        L.nys_precond_apply.argtypes = [vp, C.POINTER(dbl), i64, vp, vp, i32, vp]
+        L.pcg_solve.argtypes = [C.POINTER(_Operator), vp, C.POINTER(dbl), i64, vp, vp,
+                                C.POINTER(_PcgOpts), C.POINTER(_PcgResult), vp]
+        L.nys_factor_get.argtypes = [vp, C.POINTER(vp), C.POINTER(i32), C.POINTER(vp),
+                                     C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]
+        L.nys_factor_free.argtypes = [vp]
+        L.nys_factor_free.restype = None
+        L.nys_status_str.argtypes = [i32]
+        L.nys_status_str.restype = C.c_char_p
+        L.nys_op_matvec.argtypes = [C.POINTER(_Operator), dbl, i64, vp, vp, i32, vp]
+        L.nys_power_err_est.argtypes = [C.POINTER(_Operator), vp, vp, i32, C.POINTER(dbl), vp]
+        for name in EXPORTS:
+            f = getattr(L, name)
+            if f.restype is C.c_int:  # default
+                f.restype = C.c_int32
+        _lib = L
+        return _lib
+
+
+def status_str(status: int) -> str:
+    try:
+        return lib().nys_status_str(int(status)).decode()
+    except NysLibraryMissing:
+        return "?"
+
+
+def _stream() -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(None)
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _check(status: int, what: str) -> None:
+    if status != NYS_OK:
+        raise NysError(status, what)
+
+
+# ---------------------------------------------------------------- operators
+
+class Operator:
+    """An operator descriptor; keeps its data tensor alive."""
+
+    def __init__(self, kind: int, data: torch.Tensor, n: int, m: int = 0, d: int = 0,
+                 sigma: float = 0.0):
+        if not data.is_cuda or not data.is_contiguous():
+            raise ValueError("operator data must be a contiguous CUDA tensor")
+        self.data = data
+        self.kind = kind
+        dt = NYS_F64 if data.dtype == torch.float64 else NYS_F32
+        ld = data.shape[1]
+        self.c = _Operator(kind, dt, n, m, d, ld, data.data_ptr(), float(sigma))
+        self.n = n
+
+    @property
+    def ref(self):
+        return C.byref(self.c)
+
+
+def dense_operator(A: torch.Tensor) -> Operator:
+    """A: n x n symmetric psd, float64, on the GPU."""
+    return Operator(NYS_OP_DENSE, A, A.shape[0])
+
+
+def gram_operator(X: torch.Tensor) -> Operator:
+    """A = X^T X for X: m x n float32 on the GPU."""
+    return Operator(NYS_OP_GRAM, X, X.shape[1], m=X.shape[0])
+
+
+def rbf_operator(points: torch.Tensor, sigma: float) -> Operator:
+    """Gaussian kernel on n points (n x d float32 on the GPU)."""
+    return Operator(NYS_OP_RBF, points, points.shape[0], d=points.shape[1], sigma=sigma)
+
+
+# ---------------------------------------------------------------- factor
+
+class _CudaArray:
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 2, "strides": None}
+
+
+class Factor:
+    """Owns a library factor (U, lambda_hat); freed with nys_factor_free."""
+
+    def __init__(self, handle: C.c_void_p, device: int):
+        self.h = handle
+        self.device = device
+        U, ud, lam = C.c_void_p(), C.c_int32(), C.c_void_p()
+        n, ell, nu = C.c_int64(), C.c_int64(), C.c_double()
+        _check(lib().nys_factor_get(self.h, C.byref(U), C.byref(ud), C.byref(lam), C.byref(n),
+                                    C.byref(ell), C.byref(nu)), "nys_factor_get")
+        self._U, self._lam = U.value, lam.value
+        self.u_dtype = ud.value
+        self.n, self.ell, self.nu = n.value, ell.value, nu.value
+
+    def U(self) -> torch.Tensor:
+        """Copy of U (n x ell; float64 or float32)."""
+        ts = "<f8" if self.u_dtype == NYS_F64 else "<f4"
+        with torch.cuda.device(self.device):
+            return torch.as_tensor(_CudaArray(self._U, (self.n, self.ell), ts),
+                                   device=f"cuda:{self.device}").clone()
+
+    def lam(self) -> torch.Tensor:
+        with torch.cuda.device(self.device):
+            return torch.as_tensor(_CudaArray(self._lam, (self.ell,), "<f8"),
+                                   device=f"cuda:{self.device}").clone()
+
+    def free(self) -> None:
+        if self.h is not None and self.h.value:
+            lib().nys_factor_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- entry points
+
+def nys_sketch(op: Operator, ell: int, seed: int = 0, omega: torch.Tensor | None = None,
+               precision: int = NYS_PREC_F64) -> Factor:
+    if omega is not None:
+        assert omega.dtype == torch.float64 and tuple(omega.shape) == (op.n, ell)
+    h = C.c_void_p()
+    _check(lib().nys_sketch(op.ref, ell, seed, _ptr(omega), precision, C.byref(h), _stream()),
+           "nys_sketch")
+    return Factor(h, op.data.device.index or 0)
+
+
+@dataclass
+class AdaptInfo:
+    ell: int
+    doublings: int
+    estimates: int
+    err_est: float
+    lambda_ell: float
+    kappa_est: float
+
+
+def nys_sketch_adaptive(op: Operator, ell0: int, ell_max: int, rule: int, tol: float, q: int = 5,
+                        mu: float = 0.0, seed: int = 0, omega: torch.Tensor | None = None,
+                        g: torch.Tensor | None = None, precision: int = NYS_PREC_F64):
+    h = C.c_void_p()
+    info = _AdaptInfo()
+    _check(lib().nys_sketch_adaptive(op.ref, ell0, ell_max, rule, tol, q, mu, seed, _ptr(omega),
+                                     _ptr(g), precision, C.byref(h), C.byref(info), _stream()),
+           "nys_sketch_adaptive")
+    return Factor(h, op.data.device.index or 0), AdaptInfo(
+        info.ell, info.doublings, info.estimates, info.err_est, info.lambda_ell, info.kappa_est)
+
+
+def nys_precond_apply(f: Factor, mu, v: torch.Tensor) -> torch.Tensor:
+    """z = P^{-1} v for each row of v ([nrhs][n] or [n]); mu scalar or per row."""
+    vv = v if v.dim() == 2 else v[None]
+    nrhs = vv.shape[0]
+    mus = [float(mu)] * nrhs if not hasattr(mu, "__len__") else [float(m) for m in mu]
+    z = torch.empty_like(vv)
+    dt = NYS_F64 if vv.dtype == torch.float64 else NYS_F32
+    arr = (C.c_double * nrhs)(*mus)
+    _check(lib().nys_precond_apply(f.h, arr, nrhs, _ptr(vv), _ptr(z), dt, _stream()),
+           "nys_precond_apply")
+    return z if v.dim() == 2 else z[0]
+
+
+@dataclass
+class PcgResult:
+    status: int
+    iterations: int
+    refinements: int
+    rel_residual: float
+
+
+def pcg_solve(op: Operator, f: Factor | None, mu, b: torch.Tensor, x: torch.Tensor | None = None,
+              tol: float = 1e-8, maxit: int = 500, precision: int = NYS_PREC_F64,
+              inner_tol: float = 1e-4, max_refine: int = 20, history: bool = False):
+    """Solve (A + mu_s I) x_s = b_s for each row of b ([nsys][n] or [n], float64).
+
+    Returns (x, [PcgResult], history or None).  Statuses MAXIT and BREAKDOWN are
+    reported per system in the results; any other failure raises NysError."""
+    bb = b if b.dim() == 2 else b[None]
+    nsys, n = bb.shape
+    mus = [float(mu)] * nsys if not hasattr(mu, "__len__") else [float(m) for m in mu]
+    use_x0 = x is not None
+    xx = (x if x.dim() == 2 else x[None]).clone() if use_x0 else torch.empty_like(bb)
+    hist = torch.empty((nsys, maxit + 1), dtype=torch.float64, device=bb.device) if history else None
+    opts = _PcgOpts(tol, maxit, precision, inner_tol, max_refine, int(use_x0),
+                    hist.data_ptr() if hist is not None else None)
+    res = (_PcgResult * nsys)()
+    arr = (C.c_double * nsys)(*mus)
+    st = lib().pcg_solve(op.ref, f.h if f is not None else None, arr, nsys, _ptr(bb), _ptr(xx),
+                         C.byref(opts), res, _stream())
+    if st not in (NYS_OK, NYS_ERR_MAXIT, NYS_ERR_BREAKDOWN):
+        raise NysError(st, "pcg_solve")
+    out = [PcgResult(r.status, r.iterations, r.refinements, r.rel_residual) for r in res]
+    xo = xx if b.dim() == 2 else xx[0]
+    return xo, out, hist
+
+
+def nys_op_matvec(op: Operator, mu: float, x: torch.Tensor, mode: int = 0) -> torch.Tensor:
+    xx = x if x.dim() == 2 else x[None]
+    y = torch.empty_like(xx)
+    _check(lib().nys_op_matvec(op.ref, float(mu), xx.shape[0], _ptr(xx), _ptr(y), mode, _stream()),
+           "nys_op_matvec")
+    return y if x.dim() == 2 else y[0]
+
+
+def nys_power_err_est(op: Operator, f: Factor, g: torch.Tensor, q: int) -> float:
+    est = C.c_double()
+    _check(lib().nys_power_err_est(op.ref, f.h, _ptr(g), q, C.byref(est), _stream()),
+           "nys_power_err_est")
+    return est.value

@@ -1,0 +1,119 @@
+"""The C-ABI library builds, loads and exports every declared symbol; host
+argument checks reject bad calls before any device work (no GPU needed)."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\*?([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2110_02820_gb300 import build, nyspcg
+    build.build()
+    return nyspcg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["nys_sketch", "nys_sketch_adaptive", "nys_precond_apply", "pcg_solve",
+                     "nys_factor_get", "nys_factor_free", "nys_status_str", "nys_op_matvec",
+                     "nys_power_err_est"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_status_strings(L):
+    from paper_2110_02820_gb300 import nyspcg as ny
+    assert ny.status_str(0) == "ok"
+    assert "argument" in ny.status_str(1)
+    assert ny.status_str(99) == "unknown status"
+
+
+def _op(kind=0, dtype=0, n=64, m=0, d=0, ld=64, data=0x1000, sigma=0.0):
+    from paper_2110_02820_gb300.nyspcg import _Operator
+    return _Operator(kind, dtype, n, m, d, ld, data, sigma)
+
+
+def test_host_argument_checks_reject_before_device_work(L):
+    from paper_2110_02820_gb300 import nyspcg as ny
+    h = C.c_void_p()
+    # null operator / null output
+    assert L.nys_sketch(None, 4, 0, None, 0, C.byref(h), None) == ny.NYS_ERR_ARG
+    op = _op()
+    assert L.nys_sketch(C.byref(op), 4, 0, None, 0, None, None) == ny.NYS_ERR_ARG
+    # ell > n, ell < 1, bad precision
+    assert L.nys_sketch(C.byref(op), 65, 0, None, 0, C.byref(h), None) == ny.NYS_ERR_ARG
+    assert L.nys_sketch(C.byref(op), 0, 0, None, 0, C.byref(h), None) == ny.NYS_ERR_ARG
+    assert L.nys_sketch(C.byref(op), 4, 0, None, 7, C.byref(h), None) == ny.NYS_ERR_ARG
+    # dense operator must be FP64, ld >= n, data 16-byte aligned
+    assert L.nys_sketch(C.byref(_op(dtype=1)), 4, 0, None, 0, C.byref(h), None) == ny.NYS_ERR_ARG
+    assert L.nys_sketch(C.byref(_op(ld=10)), 4, 0, None, 0, C.byref(h), None) == ny.NYS_ERR_ARG
+    assert L.nys_sketch(C.byref(_op(data=0x1004)), 4, 0, None, 0, C.byref(h), None) == ny.NYS_ERR_ARG
+    # RBF: sigma > 0, 1 <= d <= 64
+    assert L.nys_sketch(C.byref(_op(kind=2, dtype=1, d=3, ld=3, sigma=0.0)), 4, 0, None, 0,
+                        C.byref(h), None) == ny.NYS_ERR_ARG
+    assert L.nys_sketch(C.byref(_op(kind=2, dtype=1, d=65, ld=65, sigma=1.0)), 4, 0, None, 0,
+                        C.byref(h), None) == ny.NYS_ERR_ARG
+    # gram: m > 0
+    assert L.nys_sketch(C.byref(_op(kind=1, dtype=1, m=0)), 4, 0, None, 0, C.byref(h),
+                        None) == ny.NYS_ERR_ARG
+
+
+def test_pcg_argument_checks(L):
+    from paper_2110_02820_gb300 import nyspcg as ny
+    op = _op()
+    res = (ny._PcgResult * 2)()
+    mu = (C.c_double * 2)(1e-3, -1.0)
+    # negative mu
+    assert L.pcg_solve(C.byref(op), None, mu, 2, C.c_void_p(0x2000), C.c_void_p(0x3000), None, res,
+                       None) == ny.NYS_ERR_ARG
+    mu = (C.c_double * 2)(1e-3, 1e-3)
+    # null b / x / results, nsys < 1
+    assert L.pcg_solve(C.byref(op), None, mu, 2, None, C.c_void_p(0x3000), None, res, None) == ny.NYS_ERR_ARG
+    assert L.pcg_solve(C.byref(op), None, mu, 0, C.c_void_p(0x2000), C.c_void_p(0x3000), None, res,
+                       None) == ny.NYS_ERR_ARG
+    # bad options: mixed with inner_tol outside (0, 1)
+    opts = ny._PcgOpts(1e-8, 100, ny.NYS_PREC_MIXED, 2.0, 5, 0, None)
+    assert L.pcg_solve(C.byref(op), None, mu, 2, C.c_void_p(0x2000), C.c_void_p(0x3000),
+                       C.byref(opts), res, None) == ny.NYS_ERR_ARG
+    # adaptive: ratio rule needs mu > 0; err rule needs q >= 1
+    h = C.c_void_p()
+    assert L.nys_sketch_adaptive(C.byref(op), 4, 16, ny.NYS_RULE_RATIO, 10.0, 0, 0.0, 0, None, None,
+                                 0, C.byref(h), None, None) == ny.NYS_ERR_ARG
+    assert L.nys_sketch_adaptive(C.byref(op), 4, 16, ny.NYS_RULE_ERR, 1.0, 0, 1.0, 0, None, None,
+                                 0, C.byref(h), None, None) == ny.NYS_ERR_ARG
+    assert L.nys_sketch_adaptive(C.byref(op), 4, 65, ny.NYS_RULE_ERR, 1.0, 5, 1.0, 0, None, None,
+                                 0, C.byref(h), None, None) == ny.NYS_ERR_ARG
+    # precond apply: null factor
+    assert L.nys_precond_apply(None, mu, 1, C.c_void_p(0x2000), C.c_void_p(0x3000), 0,
+                               None) == ny.NYS_ERR_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2110_02820_gb300 import nyspcg as ny
+    monkeypatch.setattr(ny, "_lib", None)
+    monkeypatch.setattr(ny, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(ny.NysLibraryMissing):
+        ny.lib()

@@ -1,0 +1,361 @@
+"""GPU parity: every entry point of the C ABI against the FP64 CPU oracle on
+the same seeded inputs.  Sizes span several tiles and a ragged tail.
+
+Tolerances:
+* FP64 paths: ``x`` within 1e-8 relative of the oracle's Algorithm 3 iterate
+  with the same Omega; lambda_hat within 1e-9 relative to lambda_1.
+* Mixed paths: ``x`` within 1e-5 relative of the FP64 solution after
+  refinement; FP32 matvecs within 1e-5 relative (norm-wise).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import nystrom as onys  # noqa: E402
+from oracle import operators as oops  # noqa: E402
+from oracle import pcg as opcg  # noqa: E402
+
+from paper_2110_02820_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ny():
+    from paper_2110_02820_gb300 import build, nyspcg
+    build.build()
+    nyspcg.lib()
+    return nyspcg
+
+
+def T(a, dtype=None):
+    t = torch.tensor(np.ascontiguousarray(a), device="cuda")
+    return t if dtype is None else t.to(dtype)
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+# ---------------------------------------------------------------- matvecs
+
+@pytest.mark.parametrize("n", [1, 33, 300, 2048])
+def test_dense_matvec(ny, n):
+    A, _ = wl.dense_spd(n, seed=n)
+    x = wl.rhs(n, seed=1, nrhs=3)
+    op = ny.dense_operator(T(A))
+    y = ny.nys_op_matvec(op, 0.25, T(x)).cpu().numpy()
+    ref = (A @ x.T).T + 0.25 * x
+    assert relerr(y, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("m,n", [(1000, 260), (3001, 512), (5000, 4096), (777, 9000)])
+def test_gram_matvec_accurate_and_fast(ny, m, n):
+    X = wl.ridge_X(m, n, seed=2)
+    x = wl.rhs(n, seed=2, nrhs=2)
+    op = ny.gram_operator(T(X))
+    ref = oops.gram_matmat(X, x.T).T + 1e-3 * x
+    y64 = ny.nys_op_matvec(op, 1e-3, T(x), mode=0).cpu().numpy()
+    assert relerr(y64, ref) <= 1e-12
+    y32 = ny.nys_op_matvec(op, 1e-3, T(x), mode=1).cpu().numpy()
+    assert relerr(y32, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("n,d", [(777, 7), (1500, 32), (300, 64)])
+def test_rbf_matvec_accurate_and_fast(ny, n, d):
+    P = wl.gmm_points(n, d, seed=3)
+    sigma = wl.median_distance(P, seed=3)
+    x = wl.rhs(n, seed=3)
+    op = ny.rbf_operator(T(P), sigma)
+    ref = oops.rbf_matmat(P, sigma, x) + 0.1 * x
+    y64 = ny.nys_op_matvec(op, 0.1, T(x), mode=0).cpu().numpy()
+    assert relerr(y64, ref) <= 1e-12
+    y32 = ny.nys_op_matvec(op, 0.1, T(x), mode=1).cpu().numpy()
+    assert relerr(y32, ref) <= 1e-5
+
+
+# ---------------------------------------------------------------- Algorithm 1
+
+@pytest.mark.parametrize("n,ell", [(200, 24), (513, 64), (2048, 64), (100, 1), (64, 64)])
+def test_sketch_f64_dense(ny, n, ell):
+    A, _ = wl.dense_spd(n, seed=5)
+    Om = wl.omega(n, ell, seed=5)
+    f = ny.nys_sketch(ny.dense_operator(T(A)), ell, omega=T(Om))
+    o = onys.rand_nystrom(lambda V: A @ V, Om)
+    lam = f.lam().cpu().numpy()
+    U = f.U().cpu().numpy()
+    assert np.abs(lam - o["lam"]).max() <= 1e-9 * o["lam"][0]
+    np.testing.assert_allclose(U.T @ U, np.eye(ell), atol=1e-11)
+    Ah_g = (U * lam) @ U.T
+    Ah_o = (o["U"] * o["lam"]) @ o["U"].T
+    assert np.linalg.norm(Ah_g - Ah_o, 2) <= 1e-9 * o["lam"][0]
+    assert f.nu == o["nu"]
+
+
+def test_sketch_exact_recovery_on_gpu(ny):
+    # rank(A) = 6 < ell = 16: U Lam U^T = A (Sec. 2.2); exercises the shifted CholeskyQR path
+    n, r, ell = 300, 6, 16
+    rng = np.random.default_rng(0)
+    Q = np.linalg.qr(rng.standard_normal((n, r)))[0]
+    A = (Q * np.linspace(4, 1, r)) @ Q.T
+    f = ny.nys_sketch(ny.dense_operator(T(A)), ell, omega=T(wl.omega(n, ell, 0)))
+    U, lam = f.U().cpu().numpy(), f.lam().cpu().numpy()
+    assert np.linalg.norm((U * lam) @ U.T - A, 2) <= 1e-10 * 4
+    assert np.all(lam[r:] <= 1e-10)
+
+
+def test_sketch_generated_omega_is_gaussian_and_seeded(ny):
+    n, ell = 500, 20
+    A, _ = wl.dense_spd(n, seed=1)
+    op = ny.dense_operator(T(A))
+    f1 = ny.nys_sketch(op, ell, seed=7)
+    f2 = ny.nys_sketch(op, ell, seed=7)
+    f3 = ny.nys_sketch(op, ell, seed=8)
+    l1, l2, l3 = (f.lam().cpu().numpy() for f in (f1, f2, f3))
+    np.testing.assert_array_equal(l1, l2)
+    assert not np.array_equal(l1, l3)
+    lam_true = wl.power_spectrum(n)
+    assert np.all(l1 <= lam_true[:ell] + 1e-12)
+
+
+@pytest.mark.parametrize("m,n,ell", [(4000, 512, 64), (20000, 1024, 128)])
+def test_sketch_mixed_gram(ny, m, n, ell):
+    X = wl.ridge_X(m, n, seed=6)
+    Om = wl.omega(n, ell, seed=6)
+    f = ny.nys_sketch(ny.gram_operator(T(X)), ell, omega=T(Om), precision=ny.NYS_PREC_MIXED)
+    o = onys.rand_nystrom(lambda V: oops.gram_matmat(X, V), Om)
+    lam = f.lam().cpu().numpy()
+    assert f.u_dtype == ny.NYS_F32
+    # FP32 sketch: top of the spectrum to ~1e-5, the whole spectrum to 1e-4 lambda_1
+    np.testing.assert_allclose(lam[:8], o["lam"][:8], rtol=1e-4)
+    assert np.abs(lam - o["lam"]).max() <= 1e-4 * o["lam"][0]
+    U = f.U().cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(U.T @ U, np.eye(ell), atol=1e-5)
+
+
+def test_sketch_rbf_f64(ny):
+    n, d, ell = 700, 5, 40
+    P = wl.gmm_points(n, d, seed=9)
+    sigma = wl.median_distance(P, seed=9)
+    Om = wl.omega(n, ell, seed=9)
+    f = ny.nys_sketch(ny.rbf_operator(T(P), sigma), ell, omega=T(Om))
+    o = onys.rand_nystrom(lambda V: oops.rbf_matmat(P, sigma, V), Om)
+    assert np.abs(f.lam().cpu().numpy() - o["lam"]).max() <= 1e-9 * o["lam"][0]
+
+
+# ---------------------------------------------------------------- Eq. (5.3)
+
+def test_precond_apply_f64_and_f32(ny):
+    n, ell = 1000, 48
+    A, _ = wl.dense_spd(n, seed=4)
+    Om = wl.omega(n, ell, seed=4)
+    f = ny.nys_sketch(ny.dense_operator(T(A)), ell, omega=T(Om))
+    U, lam = f.U().cpu().numpy(), f.lam().cpu().numpy()
+    V = wl.rhs(n, seed=4, nrhs=3)
+    mus = [1e-4, 1e-2, 1.0]
+    Z = ny.nys_precond_apply(f, mus, T(V)).cpu().numpy()
+    for s in range(3):
+        ref = onys.precond_inverse_apply(U, lam, mus[s], V[s])
+        assert relerr(Z[s], ref) <= 1e-13
+    Z32 = ny.nys_precond_apply(f, mus, T(V, torch.float32)).cpu().numpy()
+    for s in range(3):
+        ref = onys.precond_inverse_apply(U, lam, mus[s], V[s])
+        assert relerr(Z32[s], ref) <= 1e-5
+
+
+# ---------------------------------------------------------------- Algorithm 3
+
+def _oracle_pcg_dense(A, Om, mu, b, tol):
+    o = onys.rand_nystrom(lambda V: A @ V, Om)
+    return opcg.nys_pcg(lambda v: A @ v, mu, b, None,
+                        lambda r: onys.precond_inverse_apply(o["U"], o["lam"], mu, r), tol, 500)
+
+
+def test_pcg_dense_config_n2048(ny):
+    # dense FP64 workload: n = 2048, lambda_i = (i+1)^-1.5, mu = 1e-4, ell = 64, tol 1e-10
+    n, ell, mu, tol = 2048, 64, 1e-4, 1e-10
+    A, _ = wl.dense_spd(n, seed=0)
+    Om = wl.omega(n, ell, seed=0)
+    b = wl.rhs(n, seed=0)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(Om))
+    x, res, hist = ny.pcg_solve(op, f, mu, T(b), tol=tol, history=True)
+    ref = _oracle_pcg_dense(A, Om, mu, b, tol)
+    assert res[0].status == ny.NYS_OK
+    assert abs(res[0].iterations - ref["iterations"]) <= 1
+    assert relerr(x.cpu().numpy(), ref["x"]) <= 1e-8
+    xs = opcg.direct_solve(A, mu, b)
+    assert relerr(x.cpu().numpy(), xs) <= 1e-6
+    # recurrence residuals: the two factors differ by ~1e-9 lambda_1 (CholeskyQR2 +
+    # Jacobi vs Householder + LAPACK), which moves the Krylov path by ~1e-6 ||r_0||
+    # in mid-iteration; a wrong alpha or beta would be O(||r_0||)
+    h = hist[0].cpu().numpy()
+    k = min(len(ref["res_hist"]), res[0].iterations + 1)
+    assert np.abs(h[:k] - ref["res_hist"][:k]).max() <= 1e-5 * ref["res_hist"][0]
+    np.testing.assert_allclose(h[:10], ref["res_hist"][:10], rtol=1e-9)
+
+
+def test_pcg_integer_case_iteration_count_identical(ny):
+    A = wl.integer_spd(8, seed=0)
+    b = wl.integer_vector(8, seed=0)
+    op = ny.dense_operator(T(A))
+    x, res, _ = ny.pcg_solve(op, None, 1.0, T(b), tol=1e-10)
+    ref = opcg.nys_pcg(lambda v: A @ v, 1.0, b, None, lambda r: r.copy(), 1e-10, 50)
+    assert res[0].iterations == ref["iterations"]
+    assert relerr(x.cpu().numpy(), ref["x"]) <= 1e-12
+
+
+def test_pcg_plain_cg_and_maxit(ny):
+    n = 500
+    A, _ = wl.dense_spd(n, seed=3)
+    b = wl.rhs(n, seed=3)
+    op = ny.dense_operator(T(A))
+    x, res, _ = ny.pcg_solve(op, None, 1e-2, T(b), tol=1e-10, maxit=7)
+    ref = opcg.nys_pcg(lambda v: A @ v, 1e-2, b, None, lambda r: r.copy(), 1e-10, 7)
+    assert res[0].status == ny.NYS_ERR_MAXIT and ref["status"] == opcg.MAXIT
+    assert res[0].iterations == 7
+    assert relerr(x.cpu().numpy(), ref["x"]) <= 1e-10
+
+
+def test_pcg_initial_guess(ny):
+    n, ell, mu = 400, 30, 1e-3
+    A, _ = wl.dense_spd(n, seed=8)
+    b = wl.rhs(n, seed=8)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, 8)))
+    xs = opcg.direct_solve(A, mu, b)
+    x, res, _ = ny.pcg_solve(op, f, mu, T(b), x=T(xs), tol=1e-8)
+    assert res[0].iterations == 0
+
+
+def test_pcg_batched_columns_equal_single_solves(ny):
+    n, ell = 700, 40
+    A, _ = wl.dense_spd(n, seed=11)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, 11)))
+    mus = list(wl.regularization_path(6, 1e-6, 1e-1))
+    B = wl.rhs(n, seed=11, nrhs=6)
+    X, res, _ = ny.pcg_solve(op, f, mus, T(B), tol=1e-10)
+    for s in range(6):
+        x1, r1, _ = ny.pcg_solve(op, f, mus[s], T(B[s]), tol=1e-10)
+        assert r1[0].iterations == res[s].iterations
+        assert torch.equal(x1, X[s])
+        xs = opcg.direct_solve(A, mus[s], B[s])
+        assert relerr(X[s].cpu().numpy(), xs) <= 1e-10 * (1 + 1 / mus[s]) * 10
+
+
+def test_pcg_mixed_gram_refinement(ny):
+    m, n, ell, mu = 20000, 1024, 128, 1e-3
+    X = wl.ridge_X(m, n, seed=12)
+    y = wl.ridge_y(m, 12)
+    X64 = X.astype(np.float64)
+    b = X64.T @ y
+    op = ny.gram_operator(T(X))
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, 12)), precision=ny.NYS_PREC_MIXED)
+    x, res, _ = ny.pcg_solve(op, f, mu, T(b), tol=1e-8, precision=ny.NYS_PREC_MIXED)
+    assert res[0].status == ny.NYS_OK
+    assert res[0].rel_residual <= 1e-8
+    xg = x.cpu().numpy()
+    # oracle: true FP64 residual and the direct solution
+    r = b - (X64.T @ (X64 @ xg) + mu * xg)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-8
+    xs = opcg.direct_solve(X64.T @ X64, mu, b)
+    assert relerr(xg, xs) <= 1e-5
+
+
+def test_pcg_f64_gram_matches_oracle(ny):
+    m, n, ell, mu = 6000, 300, 40, 1e-2
+    X = wl.ridge_X(m, n, seed=13)
+    b = wl.rhs(n, seed=13)
+    Om = wl.omega(n, ell, 13)
+    op = ny.gram_operator(T(X))
+    f = ny.nys_sketch(op, ell, omega=T(Om))
+    x, res, _ = ny.pcg_solve(op, f, mu, T(b), tol=1e-10)
+    mm = lambda V: oops.gram_matmat(X, V)
+    o = onys.rand_nystrom(mm, Om)
+    ref = opcg.nys_pcg(lambda v: mm(v), mu, b, None,
+                       lambda r: onys.precond_inverse_apply(o["U"], o["lam"], mu, r), 1e-10, 500)
+    assert abs(res[0].iterations - ref["iterations"]) <= 1
+    assert relerr(x.cpu().numpy(), ref["x"]) <= 1e-8
+
+
+def test_pcg_rbf_mixed_refinement(ny):
+    n, d, ell = 3000, 8, 100
+    P = wl.gmm_points(n, d, seed=14)
+    sigma = wl.median_distance(P, seed=14)
+    mu = 1e-6 * n * 100
+    b = wl.rhs(n, seed=14)
+    op = ny.rbf_operator(T(P), sigma)
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, 14)), precision=ny.NYS_PREC_MIXED)
+    x, res, _ = ny.pcg_solve(op, f, mu, T(b), tol=1e-8, precision=ny.NYS_PREC_MIXED)
+    assert res[0].status == ny.NYS_OK, res
+    K = oops.rbf_block(P, P, sigma)
+    xs = opcg.direct_solve(K, mu, b)
+    assert relerr(x.cpu().numpy(), xs) <= 1e-5
+
+
+# ---------------------------------------------------------------- Algorithms 4 and 5
+
+def test_power_error_estimate(ny):
+    n, ell, q = 600, 30, 5
+    A, _ = wl.dense_spd(n, seed=15)
+    Om = wl.omega(n, ell, 15)
+    g = wl.power_starts(n, 1, 15)[0]
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(Om))
+    est = ny.nys_power_err_est(op, f, T(g), q)
+    U, lam = f.U().cpu().numpy(), f.lam().cpu().numpy()
+    ref = onys.power_error_estimate(lambda v: A @ v, U, lam, g, q)
+    assert abs(est - ref) <= 1e-10 * abs(ref)
+
+
+@pytest.mark.parametrize("rule", ["err", "ratio"])
+def test_adaptive_matches_oracle(ny, rule):
+    n, ell0, ell_max, q, mu = 512, 8, 200, 5, 1e-3
+    A, _ = wl.dense_spd(n, seed=16, eigenvalues=wl.power_spectrum(n, 2.0))
+    Om = wl.omega(n, ell_max, 16)
+    G = wl.power_starts(n, 8, 16)
+    tol = 30 * mu if rule == "err" else 10.0
+    op = ny.dense_operator(T(A))
+    f, info = ny.nys_sketch_adaptive(op, ell0, ell_max, ny.NYS_RULE_ERR if rule == "err" else ny.NYS_RULE_RATIO,
+                                     tol, q, mu, omega=T(Om), g=T(G))
+    o = onys.adaptive_nystrom(lambda V: A @ V, n, ell0, ell_max, tol, q, Om, G, rule=rule, mu=mu)
+    assert info.ell == o["ell"]
+    assert info.doublings == o["doublings"]
+    lam = f.lam().cpu().numpy()
+    assert np.abs(lam - o["lam"]).max() <= 1e-9 * o["lam"][0]
+    if rule == "err":
+        assert abs(info.err_est - o["E"]) <= 1e-8 * abs(o["E"])
+
+
+def test_adaptive_reaches_ell_max(ny):
+    n, ell0, ell_max = 300, 8, 100
+    A, _ = wl.dense_spd(n, seed=17)
+    Om = wl.omega(n, ell_max, 17)
+    G = wl.power_starts(n, 8, 17)
+    op = ny.dense_operator(T(A))
+    f, info = ny.nys_sketch_adaptive(op, ell0, ell_max, ny.NYS_RULE_ERR, 0.0, 3, 1e-3, omega=T(Om),
+                                     g=T(G))
+    o = onys.adaptive_nystrom(lambda V: A @ V, n, ell0, ell_max, 0.0, 3, Om, G)
+    assert info.ell == ell_max == o["ell"]
+    assert np.abs(f.lam().cpu().numpy() - o["lam"]).max() <= 1e-9 * o["lam"][0]
+
+
+# ---------------------------------------------------------------- failure paths
+
+def test_not_psd_is_reported(ny):
+    n, ell = 64, 4
+    A = -np.eye(n)
+    with pytest.raises(ny.NysError) as e:
+        ny.nys_sketch(ny.dense_operator(T(A)), ell, omega=T(wl.omega(n, ell, 0)))
+    assert e.value.status == ny.NYS_ERR_NOT_PSD
+
+
+def test_breakdown_is_reported(ny):
+    n = 64
+    A = -np.eye(n)
+    b = wl.rhs(n, seed=0)
+    x, res, _ = ny.pcg_solve(ny.dense_operator(T(A)), None, 0.0, T(b), tol=1e-10)
+    assert res[0].status == ny.NYS_ERR_BREAKDOWN and res[0].iterations == 0
