@@ -182,6 +182,31 @@ int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const dou
 int32_t nys_power_err_est(const nys_operator* op, const nys_factor* f, const double* g, int32_t q,
                           double* est, void* stream);
 
+/* Allocation-free ridge matvec: y = (X^T X + mu I) x in FP32 for an
+ * NYS_OP_GRAM operator, computed by the same fused single-pass kernel as the
+ * mixed-precision PCG matvec.  The paper has no counterpart; this exists for
+ * callers that cannot allocate device memory during the call -- for example
+ * code whose device memory is entirely reserved up front by another
+ * framework's pool, or latency-bound loops that cannot afford the implicit
+ * device synchronisation an allocation may cause.  Those callers still pass
+ * x and y (device FP32 [n], 16-byte aligned, distinct); everything else the
+ * kernel needs lives in one file-scope device array of 4 MiB + 256 bytes,
+ * which every GPU that loads this library holds until the process exits.
+ * Limit: (number of SMs) x n <= 2^20 floats, and n <= 6400 with n a multiple
+ * of 4 (the kernel's two-stage shared-memory pipeline); X must be
+ * row-contiguous (ld == n) and 16-byte aligned.
+ * Larger or unsupported shapes return NYS_ERR_ARG without touching the GPU.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the array and leaves its contents behind: the
+ * timeout word is cleared at the start of each call and the partials are
+ * fully overwritten, but calls that overlap on the GPU (several streams or
+ * threads at once) race on the array and give wrong results.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Synchronises
+ * `stream`; NYS_ERR_TIMEOUT if a bounded device wait expired. */
+int32_t nys_gram_matvec_f32_noalloc(const nys_operator* op, double mu, const float* x, float* y,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

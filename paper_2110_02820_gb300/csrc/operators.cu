@@ -12,6 +12,8 @@
 //          computed on the fly tile by tile and never stored.
 
 #include <algorithm>
+#include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -547,3 +549,73 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
 }
 
 }  // namespace nys
+
+// ============================================================ allocation-free ridge matvec
+//
+// nys_gram_matvec_f32_noalloc: the fused ridge matvec above for callers that
+// cannot allocate device memory.  Its scratch (the per-CTA partial n-vectors
+// and the timeout word) lives in one file-scope device array, so the call
+// needs no cudaMalloc.  The array is shared by every call on a device and
+// keeps the last call's contents.
+
+namespace {
+
+// 256-byte header (timeout word) + up to 2^20 partial floats (4 MiB).
+constexpr size_t kNoAllocHeaderFloats = 64;
+constexpr size_t kNoAllocPartialFloats = size_t(1) << 20;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocHeaderFloats + kNoAllocPartialFloats];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[128] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol itself is only a host-side stand-in, so the address is looked
+// up once per device (with that device current) and cached.
+int32_t noalloc_scratch_address(void** out) {
+  int dev = 0;
+  NYS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return NYS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    NYS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return NYS_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t nys_gram_matvec_f32_noalloc(const nys_operator* op, double mu, const float* x,
+                                               float* y, void* stream) {
+  using namespace nys;
+  if (!op || !x || !y || x == y) return NYS_ERR_ARG;
+  if (op->kind != NYS_OP_GRAM || op->dtype != NYS_F32 || !op->data || op->m <= 0 || op->n <= 0)
+    return NYS_ERR_ARG;
+  if (!(mu >= 0.0) || !std::isfinite(mu)) return NYS_ERR_ARG;
+  if (((uintptr_t)x & 15u) || ((uintptr_t)y & 15u)) return NYS_ERR_ARG;
+  GramPlan g = gram_plan(op);  // needs ld == n, n % 4 == 0, 16-byte aligned X
+  if (!g.fused) return NYS_ERR_ARG;
+  if ((size_t)g.grid * (size_t)op->n > kNoAllocPartialFloats) return NYS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* base = nullptr;
+  NYS_TRY(noalloc_scratch_address(&base));
+  int* err = reinterpret_cast<int*>(base);
+  float* part = reinterpret_cast<float*>(base) + kNoAllocHeaderFloats;
+  NYS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  switch (g.ng) {
+    case 1: NYS_TRY((gram_fused_launch<float, float, 1>(op, g, x, part, err, nullptr, s))); break;
+    case 2: NYS_TRY((gram_fused_launch<float, float, 2>(op, g, x, part, err, nullptr, s))); break;
+    case 4: NYS_TRY((gram_fused_launch<float, float, 4>(op, g, x, part, err, nullptr, s))); break;
+    default: NYS_TRY((gram_fused_launch<float, float, 8>(op, g, x, part, err, nullptr, s))); break;
+  }
+  gram_reduce_kernel<float, float, float><<<(unsigned)cdiv(op->n, 256), 256, 0, s>>>(
+      part, g.grid, op->n, mu, x, y, nullptr);
+  NYS_CUDA_TRY(cudaGetLastError());
+  int h_err = 0;
+  NYS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NYS_CUDA_TRY(cudaStreamSynchronize(s));
+  return h_err ? NYS_ERR_TIMEOUT : NYS_OK;
+}
+

@@ -303,3 +303,21 @@ def nys_power_err_est(op: Operator, f: Factor, g: torch.Tensor, q: int) -> float
     _check(lib().nys_power_err_est(op.ref, f.h, _ptr(g), q, C.byref(est), _stream()),
            "nys_power_err_est")
     return est.value
+
+
+def nys_gram_matvec_f32_noalloc(op: Operator, mu: float, x: torch.Tensor,
+                                y: torch.Tensor) -> None:
+    """y = (X^T X + mu I) x (FP32) with no device allocation inside the call.
+
+    For callers that cannot allocate device memory while it runs: the caller
+    provides x and y (float32 CUDA tensors of length n); the library's scratch
+    is a fixed 4 MiB device array shared by every call (calls that overlap on
+    the GPU race).  Raises NysError (NYS_ERR_ARG) for shapes beyond its limit."""
+    L = lib()
+    f = L.nys_gram_matvec_f32_noalloc
+    if f.argtypes is None:
+        f.argtypes = [C.POINTER(_Operator), C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+        f.restype = C.c_int32
+    if x.dtype != torch.float32 or y.dtype != torch.float32:
+        raise ValueError("x and y must be float32")
+    _check(f(op.ref, float(mu), _ptr(x), _ptr(y), _stream()), "nys_gram_matvec_f32_noalloc")
