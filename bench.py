@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--matvec-reps", type=int, default=20)
+    ap.add_argument("--solve-only", action="store_true",
+                    help="time the solves only (no matvec, launch-count, e2e or CPU legs); "
+                         "used for profiler launch lists")
     return ap.parse_args()
 
 
@@ -170,27 +173,22 @@ def solve_once(ny, op, b, ell, seed):
     return x, res[0]
 
 
-def count_launches(fn):
-    """Kernels of this library launched by one call of fn (torch profiler)."""
-    try:
-        import torch
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            fn()
-            torch.cuda.synchronize()
-        names = {}
-        total = 0
-        for ev in prof.events():
-            if getattr(ev, "device_type", None) is None:
-                continue
-            nm = ev.name
-            if "nys::" in nm and str(ev.device_type).endswith("CUDA"):
-                total += 1
-                short = nm.split("(")[0].replace("void ", "")
-                names[short] = names.get(short, 0) + 1
-        return total, names
-    except Exception as e:  # pragma: no cover
-        return None, {"error": str(e)}
+def phase_times(ny, op, b, ell, reps=2):
+    """Average ms of the sketch (Algorithm 1) and of the refined PCG solve."""
+    import torch
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    sk, so = [], []
+    for r in range(reps):
+        e[0].record()
+        f = ny.nys_sketch(op, ell, seed=500 + r, precision=ny.NYS_PREC_MIXED)
+        e[1].record()
+        ny.pcg_solve(op, f, MU, b, tol=TOL, precision=ny.NYS_PREC_MIXED, inner_tol=INNER_TOL)
+        e[2].record()
+        torch.cuda.synchronize()
+        sk.append(e[0].elapsed_time(e[1]))
+        so.append(e[1].elapsed_time(e[2]))
+        f.free()
+    return {"sketch_ms": statistics.mean(sk), "pcg_ms": statistics.mean(so)}
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
@@ -227,7 +225,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    rows = max(2000, args.m // 20)
+    rows = max(2000, args.m // 4)
     for _ in range(args.warmup):
         pass
     vals = []
@@ -276,17 +274,24 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = []
+    launches0 = ny.kernel_launch_count()
     ev0.record()
     for k in range(args.steps):
         x, res = solve_once(ny, op, b, ell, seed=k)
         iters.append((res.iterations, res.refinements, res.rel_residual, res.status))
     ev1.record()
     torch.cuda.synchronize()
+    launches_timed = ny.kernel_launch_count() - launches0
     barrier(world)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = max_over_ranks(ms, world)
     value = world * 1e3 / ms
+    if args.solve_only:
+        if rank == 0:
+            print(json.dumps({"solve_only": True, "ms_per_step": ms, "value": value,
+                              "solve": iters[-1]}), flush=True)
+        return
 
     # dominant kernel: the fused ridge matvec, timed on its stream
     pf = torch.randn(n, dtype=torch.float64, device=dev)
@@ -310,8 +315,8 @@ def run_ours(args):
         peak = 6800.0
         peak_src = "fallback"
 
-    # launches per step
-    launches, names = count_launches(lambda: solve_once(ny, op, b, ell, seed=0))
+    # where a step's time goes
+    phases = phase_times(ny, op, b, ell)
 
     # end to end: host inputs (pinned) -> device, solve, solution -> host
     e2e = None
@@ -342,7 +347,7 @@ def run_ours(args):
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cb = cpu_baseline(m, n, ell, max(2000, m // 20))
+        cb = cpu_baseline(m, n, ell, max(2000, m // 4))
 
     if rank == 0:
         line = {
@@ -359,11 +364,11 @@ def run_ours(args):
                          "traffic": None, "bytes_per_launch": bytes_mv, "ms_per_launch": mv_ms},
             "cpu_baseline": cb,
             "e2e": e2e,
-            "gpu_launches": (launches * args.steps) if launches is not None else None,
+            "gpu_launches": int(launches_timed),
             "clocks": clk,
             "solve": {"inner_iterations": iters[-1][0], "refinements": iters[-1][1],
                       "rel_residual": iters[-1][2], "status": iters[-1][3]},
-            "kernels_per_step": names,
+            "phases_ms": phases,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

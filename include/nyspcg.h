@@ -170,6 +170,11 @@ void nys_factor_free(nys_factor* f);
 
 const char* nys_status_str(int32_t status);
 
+/* Number of GPU kernels this library has launched in this process (all
+ * devices, all threads).  A diagnostic: the difference across a call is the
+ * number of kernels that call launched.  No paper counterpart. */
+uint64_t nys_kernel_launch_count(void);
+
 /* y_s = (A + mu I) x_s for s = 0..nvec-1 (device FP64 [nvec][n]).  mode 0:
  * the FP64-accurate product used for residuals; mode 1: the FP32 product
  * used inside mixed-precision PCG.  Exposed so that each operator kernel can
@@ -181,6 +186,17 @@ int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const dou
  * (device FP64 [n]); *est (host) receives the estimate.  Synchronises. */
 int32_t nys_power_err_est(const nys_operator* op, const nys_factor* f, const double* g, int32_t q,
                           double* est, void* stream);
+
+/* D = A B^T on the 5th-generation tensor cores: TF32 products (the low 13
+ * mantissa bits of each FP32 operand are ignored), FP32 accumulation.  A is
+ * M x K, B is N x K, D is M x N, all device FP32 row-major with leading
+ * dimensions lda, ldb >= K and ldd >= N (lda, ldb multiples of 4; A and B
+ * 16-byte aligned).  This is the kernel behind the mixed-precision sketch
+ * Y = X^T (X Omega) of the ridge operator (Algorithm 1, step 3), exposed so
+ * that it can be checked on its own.  NYS_ERR_ARG for unsupported shapes or
+ * alignment.  Synchronises `stream`. */
+int32_t nys_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                         const float* B, int64_t ldb, float* D, int64_t ldd, void* stream);
 
 /* Allocation-free ridge matvec: y = (X^T X + mu I) x in FP32 for an
  * NYS_OP_GRAM operator, computed by the same fused single-pass kernel as the

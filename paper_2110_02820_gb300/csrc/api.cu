@@ -163,7 +163,7 @@ static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool r
       // shifted CholeskyQR: G + s I with s = 11 (n ell + ell (ell + 1)) u max_i G_ii
       NYS_TRY(Ops<T>::gram(cur, cur, n, ell, ell, G, s));
       NYS_TRY(symmetrize(G, ell, s));
-      diag_max_kernel<<<1, 256, 0, s>>>(G, ell, dmax);
+      diag_max_kernel<<<1, 256, 0, s>>>(G, ell, dmax); count_launch();
       double h_dmax = 0.0;
       NYS_TRY(read_double(dmax, &h_dmax, s));
       const double u = Ops<T>::f64 ? ldexp(1.0, -53) : ldexp(1.0, -24);
@@ -275,7 +275,7 @@ static int32_t shifted_core(const T* Q, const T* Y, int64_t n, int64_t ell, bool
     NYS_TRY(read_int(info, &h, s));
     if (h == 0) break;
     if (esc >= kMaxEscalations) return NYS_ERR_NOT_PSD;
-    scale_scalar_kernel<<<1, 1, 0, s>>>(nu, 10.0);
+    scale_scalar_kernel<<<1, 1, 0, s>>>(nu, 10.0); count_launch();
   }
   NYS_TRY(tri_inv_upper(M, Ci, ell, s));
   NYS_TRY(Ops<T>::mul_small(Ynu, Ci, n, ell, ell, Bb, s));  // B = Y_nu C^{-1}
@@ -409,9 +409,9 @@ static int32_t lowrank_sub(const TU* U, int64_t n, int64_t ell, const double* c,
   NYS_TRY(sc.get(&part, nb * ell));
   NYS_TRY(sc.get(&w, ell));
   utx_partial_kernel<TU><<<dim3((unsigned)nb, (unsigned)cdiv(ell, 128)), 128, 0, s>>>(U, n, ell, x,
-                                                                                      rows, part);
-  utx_reduce_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(part, nb, ell, c, w);
-  uw_sub_kernel<TU><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(U, n, ell, w, y);
+                                                                                      rows, part); count_launch();
+  utx_reduce_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(part, nb, ell, c, w); count_launch();
+  uw_sub_kernel<TU><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(U, n, ell, w, y); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -430,7 +430,7 @@ static int32_t power_estimate(const nys_operator* op, const nys_factor* f, const
   NYS_CUDA_TRY(cudaMemsetAsync(work, 0, 256, s));
   const unsigned gb = (unsigned)(cdiv(n, 256) > 1024 ? 1024 : cdiv(n, 256));
   NYS_TRY(sumsq_f64(g, n, nrm, s));
-  scale_by_inv_norm_kernel<<<gb, 256, 0, s>>>(g, v0, n, nrm);  // v0 = g / ||g||
+  scale_by_inv_norm_kernel<<<gb, 256, 0, s>>>(g, v0, n, nrm); count_launch();  // v0 = g / ||g||
   double h = 0.0;
   NYS_CUDA_TRY(cudaMemsetAsync(e, 0, sizeof(double), s));
   for (int i = 0; i < q; ++i) {
@@ -439,9 +439,9 @@ static int32_t power_estimate(const nys_operator* op, const nys_factor* f, const
       NYS_TRY(lowrank_sub<double>((const double*)f->U, n, f->ell, f->lam, v0, v, s));
     else
       NYS_TRY(lowrank_sub<float>((const float*)f->U, n, f->ell, f->lam, v0, v, s));
-    dot_kernel<<<1, 1024, 0, s>>>(v0, v, n, e);  // E = v0^T v
+    dot_kernel<<<1, 1024, 0, s>>>(v0, v, n, e); count_launch();  // E = v0^T v
     NYS_TRY(sumsq_f64(v, n, nrm, s));
-    scale_by_inv_norm_kernel<<<gb, 256, 0, s>>>(v, v0, n, nrm);  // v0 = v / ||v||
+    scale_by_inv_norm_kernel<<<gb, 256, 0, s>>>(v, v0, n, nrm); count_launch();  // v0 = v / ||v||
   }
   NYS_CUDA_TRY(cudaGetLastError());
   NYS_TRY(read_double(e, &h, s));
@@ -506,7 +506,7 @@ static int32_t adaptive_impl(const nys_operator* op, int64_t ell0, int64_t ell_m
     // raw Gaussian block n x mm
     if (omega) {
       copy_cols_kernel<<<(unsigned)cdiv(n * mm, 256), 256, 0, s>>>(omega, ell_max, ell_tot, raw, n,
-                                                                  mm);
+                                                                  mm); count_launch();
     } else {
       NYS_TRY(philox_gaussian_f64(raw, n * mm, seed, 0x4164610000ull + (uint64_t)ell_tot, s));
     }
@@ -514,9 +514,9 @@ static int32_t adaptive_impl(const nys_operator* op, int64_t ell0, int64_t ell_m
     NYS_TRY(orthonormalize<T>(blk, n, mm, s));
     NYS_TRY(op_sketch(op, Ops<T>::f64, blk, yblk, mm, s));
     place_cols_kernel<T><<<(unsigned)cdiv(n * mm, 256), 256, 0, s>>>(blk, mm, Qall, ell_max,
-                                                                     ell_tot, n);
+                                                                     ell_tot, n); count_launch();
     place_cols_kernel<T><<<(unsigned)cdiv(n * mm, 256), 256, 0, s>>>(yblk, mm, Yall, ell_max,
-                                                                     ell_tot, n);
+                                                                     ell_tot, n); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     ell_tot += mm;
     return NYS_OK;
@@ -526,9 +526,9 @@ static int32_t adaptive_impl(const nys_operator* op, int64_t ell0, int64_t ell_m
     f = nullptr;
     NYS_TRY(factor_alloc(&f, n, ell_tot, Ops<T>::f64, precision));
     repack_kernel<T><<<(unsigned)cdiv(n * ell_tot, 256), 256, 0, s>>>(Qall, ell_max, Qc, ell_tot,
-                                                                      n, ell_tot);
+                                                                      n, ell_tot); count_launch();
     repack_kernel<T><<<(unsigned)cdiv(n * ell_tot, 256), 256, 0, s>>>(Yall, ell_max, Yc, ell_tot,
-                                                                      n, ell_tot);
+                                                                      n, ell_tot); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     return shifted_core<T>(Qc, Yc, n, ell_tot, true, sqrt((double)n), f, s);
   };
@@ -593,6 +593,8 @@ using namespace nys;
 // ==================================================================== C ABI
 
 extern "C" {
+
+uint64_t nys_kernel_launch_count(void) { return (uint64_t)nys::launch_count(); }
 
 const char* nys_status_str(int32_t st) {
   switch (st) {
@@ -747,6 +749,22 @@ int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const dou
   NYS_CUDA_TRY(cudaMemcpyAsync(&err, work, sizeof(int), cudaMemcpyDeviceToHost, s));
   NYS_CUDA_TRY(cudaStreamSynchronize(s));
   return err ? NYS_ERR_TIMEOUT : NYS_OK;
+}
+
+int32_t nys_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                         const float* B, int64_t ldb, float* D, int64_t ldd, void* stream) {
+  if (!A || !B || !D || ldd < N) return NYS_ERR_ARG;
+  if (!tc_gemm_supported(M, N, K, A, lda, B, ldb)) return NYS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  int* err;
+  NYS_TRY(sc.get(&err, 1));
+  NYS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  NYS_TRY(tc_gemm_tn_f32(M, N, K, A, lda, B, ldb, D, ldd, err, s));
+  int h = 0;
+  NYS_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NYS_CUDA_TRY(cudaStreamSynchronize(s));
+  return h ? NYS_ERR_TIMEOUT : NYS_OK;
 }
 
 int32_t nys_power_err_est(const nys_operator* op, const nys_factor* f, const double* g, int32_t q,

@@ -3,6 +3,7 @@
 // of squares, the shift of Algorithm 1 (steps 4-5) and the Philox4x32-10 +
 // Box-Muller Gaussian generator of step 1.
 
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -20,6 +21,12 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
   snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file,
            line);
 }
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int num_sms() {
   static int cached[64] = {0};
@@ -215,6 +222,7 @@ static int32_t gemm_launch(bool trans_a, int64_t M, int64_t N, int64_t K, const 
     else
       gemm_kernel<T, TOut, false, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb,
                                                                           C, ldc, kchunk > 0 ? kchunk : 1, 0);
+    count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     return NYS_OK;
   }
@@ -226,7 +234,8 @@ static int32_t gemm_launch(bool trans_a, int64_t M, int64_t N, int64_t K, const 
   else
     gemm_kernel<T, T, false, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, N,
                                                                      kchunk, M * N);
-  split_reduce_kernel<T, TOut><<<(unsigned)cdiv(M * N, 256), 256, 0, s>>>(P, splits, M, N, C, ldc);
+  count_launch();
+  split_reduce_kernel<T, TOut><<<(unsigned)cdiv(M * N, 256), 256, 0, s>>>(P, splits, M, N, C, ldc); count_launch();
   cudaError_t e = cudaGetLastError();
   dfree(P, s);
   NYS_CUDA_TRY(e);
@@ -266,13 +275,13 @@ static unsigned grid_for(int64_t count, int threads = 256) {
 }
 
 int32_t convert_f64_to_f32(const double* in, float* out, int64_t count, cudaStream_t s) {
-  convert_kernel<double, float><<<grid_for(count), 256, 0, s>>>(in, out, count);
+  convert_kernel<double, float><<<grid_for(count), 256, 0, s>>>(in, out, count); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
 
 int32_t convert_f32_to_f64(const float* in, double* out, int64_t count, cudaStream_t s) {
-  convert_kernel<float, double><<<grid_for(count), 256, 0, s>>>(in, out, count);
+  convert_kernel<float, double><<<grid_for(count), 256, 0, s>>>(in, out, count); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -284,7 +293,7 @@ __global__ void add_inplace_kernel(double* y, const double* x, int64_t count) {
 }
 
 int32_t add_inplace_f64(double* y, const double* x, int64_t count, cudaStream_t s) {
-  add_inplace_kernel<<<grid_for(count), 256, 0, s>>>(y, x, count);
+  add_inplace_kernel<<<grid_for(count), 256, 0, s>>>(y, x, count); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -319,7 +328,7 @@ static int32_t sumsq_impl(const T* x, int64_t count, double* d_out, cudaStream_t
   double* partial = reinterpret_cast<double*>(aux + 16);
   unsigned int* counter = reinterpret_cast<unsigned int*>(aux);
   cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
-  sumsq_kernel<T><<<blocks, 256, 0, s>>>(x, count, partial, counter, d_out);
+  sumsq_kernel<T><<<blocks, 256, 0, s>>>(x, count, partial, counter, d_out); count_launch();
   cudaError_t e = cudaGetLastError();
   dfree(aux, s);
   NYS_CUDA_TRY(e);
@@ -344,13 +353,13 @@ __global__ void shift_add_kernel(const T* Y, const T* Q, T* Ynu, int64_t count, 
 
 int32_t shift_add_f32(const float* Y, const float* Q, float* Ynu, int64_t count, const double* d_nu,
                       double factor, cudaStream_t s) {
-  shift_add_kernel<float><<<grid_for(count), 256, 0, s>>>(Y, Q, Ynu, count, d_nu, factor);
+  shift_add_kernel<float><<<grid_for(count), 256, 0, s>>>(Y, Q, Ynu, count, d_nu, factor); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
 int32_t shift_add_f64(const double* Y, const double* Q, double* Ynu, int64_t count,
                       const double* d_nu, double factor, cudaStream_t s) {
-  shift_add_kernel<double><<<grid_for(count), 256, 0, s>>>(Y, Q, Ynu, count, d_nu, factor);
+  shift_add_kernel<double><<<grid_for(count), 256, 0, s>>>(Y, Q, Ynu, count, d_nu, factor); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -373,7 +382,7 @@ __global__ void compute_nu_kernel(const double* sumsq, double scale, int mantiss
 
 int32_t compute_nu(const double* d_sumsq, double scale, int mantissa_bits, double* d_nu,
                    cudaStream_t s) {
-  compute_nu_kernel<<<1, 1, 0, s>>>(d_sumsq, scale, mantissa_bits, d_nu);
+  compute_nu_kernel<<<1, 1, 0, s>>>(d_sumsq, scale, mantissa_bits, d_nu); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -387,7 +396,7 @@ __global__ void lambda_kernel(const double* sigma, const double* d_nu, double* l
 
 int32_t lambda_from_sigma(const double* sigma, const double* d_nu, double* lam, int64_t ell,
                           cudaStream_t s) {
-  lambda_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(sigma, d_nu, lam, ell);
+  lambda_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(sigma, d_nu, lam, ell); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -452,7 +461,49 @@ __global__ void philox_gaussian_kernel(double* out, int64_t count, uint64_t seed
 
 int32_t philox_gaussian_f64(double* out, int64_t count, uint64_t seed, uint64_t stream_id,
                             cudaStream_t s) {
-  philox_gaussian_kernel<<<grid_for(cdiv(count, 4)), 256, 0, s>>>(out, count, seed, stream_id);
+  philox_gaussian_kernel<<<grid_for(cdiv(count, 4)), 256, 0, s>>>(out, count, seed, stream_id); count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+}  // namespace nys
+
+namespace nys {
+
+int32_t split_reduce_f32(const float* P, int64_t splits, int64_t M, int64_t N, float* D,
+                         int64_t ldd, cudaStream_t s) {
+  split_reduce_kernel<float, float><<<(unsigned)cdiv(M * N, 256), 256, 0, s>>>(P, splits, M, N, D,
+                                                                               ldd); count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// out[j * ld_out + i] = in[i * ld_in + j] for a rows x cols array: 32 x 32
+// tiles through shared memory (coalesced reads and writes).
+__global__ void transpose_f32_kernel(const float* __restrict__ in, int64_t rows, int64_t cols,
+                                     int64_t ld_in, float* __restrict__ out, int64_t ld_out) {
+  __shared__ float tile[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    int64_t i = by + r, j = bx + threadIdx.x;
+    if (i < rows && j < cols) tile[r][threadIdx.x] = in[i * ld_in + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    int64_t j = bx + r, i = by + threadIdx.x;
+    if (i < rows && j < cols) out[j * ld_out + i] = tile[threadIdx.x][r];
+  }
+}
+
+int32_t transpose_f32(const float* in, int64_t rows, int64_t cols, int64_t ld_in, float* out,
+                      cudaStream_t s) {
+  // rows are processed in bands so that grid.y stays below 65536
+  const int64_t band = 32768ll * 32;
+  for (int64_t r0 = 0; r0 < rows; r0 += band) {
+    int64_t rb = (rows - r0 < band) ? rows - r0 : band;
+    dim3 g((unsigned)cdiv(cols, 32), (unsigned)cdiv(rb, 32));
+    transpose_f32_kernel<<<g, dim3(32, 8), 0, s>>>(in + r0 * ld_in, rb, cols, ld_in, out + r0, rows); count_launch();
+  }
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }

@@ -36,6 +36,10 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Number of SMs of the current device (cached per device).
 int num_sms();
 
+// Process-wide count of kernel launches made by this library (every launch
+// site calls this right after its launch).
+void count_launch();
+
 // ---------------------------------------------------------------- device helpers
 
 template <typename T>

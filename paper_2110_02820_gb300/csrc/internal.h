@@ -20,6 +20,9 @@ struct nys_factor {
 
 namespace nys {
 
+// Kernel launches made by this library since the process started.
+unsigned long long launch_count();
+
 // ---------------------------------------------------------------- workspace
 
 // Stream-ordered device allocation (cudaMallocAsync from the device's
@@ -81,6 +84,20 @@ int32_t gemm_f32_out64(bool trans_a, int64_t M, int64_t N, int64_t K, const floa
 int32_t gemm_f64(bool trans_a, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
                  const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
 
+// D = sum over z of P[z] (M x N each), fixed order.
+int32_t split_reduce_f32(const float* P, int64_t splits, int64_t M, int64_t N, float* D,
+                         int64_t ldd, cudaStream_t s);
+// out (cols x rows, row stride rows) = transpose of in (rows x cols, row stride ld_in).
+int32_t transpose_f32(const float* in, int64_t rows, int64_t cols, int64_t ld_in, float* out,
+                      cudaStream_t s);
+// TF32 tensor-core GEMM D[M x N] = A[M x K] B[N x K]^T (tc_gemm.cu); *err
+// (device) receives NYS_ERR_TIMEOUT if a bounded wait expired.  Returns
+// NYS_ERR_ARG when the shapes or alignment are not supported.
+bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                       const float* B, int64_t ldb);
+int32_t tc_gemm_tn_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, float* D, int64_t ldd, int* err,
+                       cudaStream_t s);
 // y += x (elementwise)
 int32_t add_inplace_f64(double* y, const double* x, int64_t count, cudaStream_t s);
 int32_t convert_f64_to_f32(const double* in, float* out, int64_t count, cudaStream_t s);

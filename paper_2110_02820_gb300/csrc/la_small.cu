@@ -117,15 +117,15 @@ int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
   NYS_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   for (int64_t k = 0; k < ell; k += CH_NB) {
     int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
-    chol_diag_kernel<<<1, dim3(32, 32), 0, s>>>(M, ell, k, nb, d_info);
+    chol_diag_kernel<<<1, dim3(32, 32), 0, s>>>(M, ell, k, nb, d_info); count_launch();
     int64_t rest = ell - k - nb;
     if (rest > 0) {
-      chol_panel_kernel<<<(unsigned)cdiv(rest, 128), 128, 0, s>>>(M, ell, k, nb, d_info);
+      chol_panel_kernel<<<(unsigned)cdiv(rest, 128), 128, 0, s>>>(M, ell, k, nb, d_info); count_launch();
       unsigned t = (unsigned)cdiv(rest, 32);
-      chol_trail_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(M, ell, k, nb, d_info);
+      chol_trail_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(M, ell, k, nb, d_info); count_launch();
     }
   }
-  zero_lower_kernel<<<(unsigned)cdiv(ell * ell, 256), 256, 0, s>>>(M, ell);
+  zero_lower_kernel<<<(unsigned)cdiv(ell * ell, 256), 256, 0, s>>>(M, ell); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -170,9 +170,9 @@ __global__ void transpose_kernel(const double* in, double* out, int64_t rows, in
 int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s) {
   double* XT = nullptr;
   NYS_TRY(dmalloc((void**)&XT, ell * ell * sizeof(double), s));
-  tri_inv_cols_kernel<<<(unsigned)cdiv(ell, 4), 128, 0, s>>>(C, XT, ell);
+  tri_inv_cols_kernel<<<(unsigned)cdiv(ell, 4), 128, 0, s>>>(C, XT, ell); count_launch();
   dim3 g((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 32));
-  transpose_kernel<<<g, dim3(32, 8), 0, s>>>(XT, X, ell, ell);
+  transpose_kernel<<<g, dim3(32, 8), 0, s>>>(XT, X, ell, ell); count_launch();
   cudaError_t e = cudaGetLastError();
   dfree(XT, s);
   NYS_CUDA_TRY(e);
@@ -191,7 +191,7 @@ __global__ void symmetrize_kernel(double* M, int64_t ell) {
 }
 
 int32_t symmetrize(double* M, int64_t ell, cudaStream_t s) {
-  symmetrize_kernel<<<(unsigned)cdiv(ell * ell, 256), 256, 0, s>>>(M, ell);
+  symmetrize_kernel<<<(unsigned)cdiv(ell * ell, 256), 256, 0, s>>>(M, ell); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -202,7 +202,7 @@ __global__ void add_diag_kernel(double* M, int64_t ell, double shift) {
 }
 
 int32_t add_diag(double* M, int64_t ell, double shift, cudaStream_t s) {
-  add_diag_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(M, ell, shift);
+  add_diag_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(M, ell, shift); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -376,7 +376,7 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int*
   if (st != NYS_OK) { dfree(W, s); return st; }
   // W rows = columns of R
   dim3 g((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 32));
-  transpose_kernel<<<g, dim3(32, 8), 0, s>>>(R, W, ell, ell);
+  transpose_kernel<<<g, dim3(32, 8), 0, s>>>(R, W, ell, ell); count_launch();
   cudaMemsetAsync(aux, 0, aux_bytes, s);
   cudaMemsetAsync(d_status, 0, sizeof(int), s);
   JacobiArgs a;
@@ -399,6 +399,7 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int*
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(blocks), dim3(threads),
                                               args, 0, s);
+  count_launch();
   if (e == cudaSuccess) {
     int64_t pow2 = 1;
     while (pow2 < ell) pow2 <<= 1;
@@ -406,7 +407,7 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int*
     if (sh > 48 * 1024)
       cudaFuncSetAttribute(jacobi_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sh);
-    jacobi_finish_kernel<<<1, 1024, sh, s>>>(W, ell, pow2, Ut, sigma);
+    jacobi_finish_kernel<<<1, 1024, sh, s>>>(W, ell, pow2, Ut, sigma); count_launch();
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && sweeps_out) {

@@ -257,7 +257,7 @@ static int32_t gram_fused_launch(const nys_operator* op, const GramPlan& g, cons
   auto kern = gram_fused_kernel<P, Acc, NG>;
   NYS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
   kern<<<g.grid, GR_THREADS, g.smem, s>>>((const float*)op->data, op->m, op->n, p, part, g.stages,
-                                           g.rows_per_cta, err, skip);
+                                           g.rows_per_cta, err, skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -290,7 +290,7 @@ static int32_t gram_matvec(const nys_operator* op, double mu, const P* p, V* v, 
       default: NYS_TRY((gram_fused_launch<P, Acc, 8>(op, g, p, part, err, skip, s))); break;
     }
     gram_reduce_kernel<Acc, P, V><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, g.grid, n, mu, p, v,
-                                                                         skip);
+                                                                         skip); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     return NYS_OK;
   }
@@ -300,12 +300,12 @@ static int32_t gram_matvec(const nys_operator* op, double mu, const P* p, V* v, 
   Acc* t = base;
   Acc* part = base + m + 64;
   gram_xp_kernel<P, Acc><<<(unsigned)cdiv(m, 8), 256, 0, s>>>((const float*)op->data, m, n, op->ld,
-                                                               p, t, skip);
+                                                               p, t, skip); count_launch();
   dim3 grid((unsigned)cdiv(n, 128), (unsigned)chunks);
   gram_xtt_kernel<Acc><<<grid, 128, 0, s>>>((const float*)op->data, m, n, op->ld, t, rpc, part,
-                                            skip);
+                                            skip); count_launch();
   gram_reduce_kernel<Acc, P, V><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, chunks, n, mu, p, v,
-                                                                       skip);
+                                                                       skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -480,6 +480,27 @@ int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int6
       NYS_CUDA_TRY(cudaMemcpyAsync(V, acc, n * ell * sizeof(double), cudaMemcpyDeviceToDevice, s));
       return NYS_OK;
     }
+    if (tc_gemm_supported(ell, m, n, X, op->ld, X, op->ld) && (m % 4) == 0) {
+      // Tensor cores, both operands K-major:  Z^T = Q^T X^T  (ell x m, K = n),
+      // Y^T = Z^T (X^T)^T (ell x n, K = m) with X^T materialised once.
+      float *Qt, *Xt, *Zt, *Yt;
+      int* err;
+      NYS_TRY(sc.get(&Qt, ell * n));
+      NYS_TRY(sc.get(&Xt, n * m));
+      NYS_TRY(sc.get(&Zt, ell * m));
+      NYS_TRY(sc.get(&Yt, ell * n));
+      NYS_TRY(sc.get(&err, 1));
+      NYS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+      NYS_TRY(transpose_f32((const float*)Q, n, ell, ell, Qt, s));
+      NYS_TRY(transpose_f32(X, m, n, op->ld, Xt, s));
+      NYS_TRY(tc_gemm_tn_f32(ell, m, n, Qt, n, X, op->ld, Zt, m, err, s));
+      NYS_TRY(tc_gemm_tn_f32(ell, n, m, Zt, m, Xt, m, Yt, n, err, s));
+      NYS_TRY(transpose_f32(Yt, ell, n, n, (float*)V, s));
+      int h_err = 0;
+      NYS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      NYS_CUDA_TRY(cudaStreamSynchronize(s));
+      return h_err ? NYS_ERR_TIMEOUT : NYS_OK;
+    }
     float* Z;
     NYS_TRY(sc.get(&Z, m * ell));
     NYS_TRY(gemm_f32(false, m, ell, n, X, op->ld, (const float*)Q, ell, Z, ell, s));
@@ -492,7 +513,7 @@ int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int6
                                                    op->sigma, (const double*)Q, ell, (double*)V);
   else
     rbf_sketch_kernel<float><<<grid, 256, 0, s>>>((const float*)op->data, n, op->d, op->ld,
-                                                  op->sigma, (const float*)Q, ell, (float*)V);
+                                                  op->sigma, (const float*)Q, ell, (float*)V); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -507,7 +528,7 @@ int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* 
   const int64_t n = op->n;
   if (op->kind == NYS_OP_DENSE) {
     dense_matvec_kernel<float, float><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(
-        (const double*)op->data, n, op->ld, p, mu, v, skip);
+        (const double*)op->data, n, op->ld, p, mu, v, skip); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     return NYS_OK;
   }
@@ -520,7 +541,7 @@ int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* 
     return gram_matvec<float, float, float>(op, mu, p, v, skip, w, s);
   }
   rbf_matvec_kernel<float, float, float><<<(unsigned)cdiv(n, RBF_BI), RBF_BI, 0, s>>>(
-      (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip);
+      (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -530,7 +551,7 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
   const int64_t n = op->n;
   if (op->kind == NYS_OP_DENSE) {
     dense_matvec_kernel<double, double><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(
-        (const double*)op->data, n, op->ld, p, mu, v, skip);
+        (const double*)op->data, n, op->ld, p, mu, v, skip); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     return NYS_OK;
   }
@@ -543,7 +564,7 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
     return gram_matvec<double, double, double>(op, mu, p, v, skip, w, s);
   }
   rbf_matvec_kernel<double, double, double><<<(unsigned)cdiv(n, RBF_BI), RBF_BI, 0, s>>>(
-      (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip);
+      (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
@@ -611,7 +632,7 @@ extern "C" int32_t nys_gram_matvec_f32_noalloc(const nys_operator* op, double mu
     default: NYS_TRY((gram_fused_launch<float, float, 8>(op, g, x, part, err, nullptr, s))); break;
   }
   gram_reduce_kernel<float, float, float><<<(unsigned)cdiv(op->n, 256), 256, 0, s>>>(
-      part, g.grid, op->n, mu, x, y, nullptr);
+      part, g.grid, op->n, mu, x, y, nullptr); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   int h_err = 0;
   NYS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));

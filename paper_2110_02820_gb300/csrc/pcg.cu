@@ -377,15 +377,15 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
                                       (int)zsm));
 
   // ---- setup: state, r0, z0 = P^{-1} r0, p0 = z0, r0^T z0
-  init_state_kernel<T><<<(unsigned)nsys, 256, 0, s>>>(b_T, n, a.st, B.d_mu, lam_ell, tol, maxit);
+  init_state_kernel<T><<<(unsigned)nsys, 256, 0, s>>>(b_T, n, a.st, B.d_mu, lam_ell, tol, maxit); count_launch();
   if (use_x0) {
     for (int64_t q = 0; q < nsys; ++q)
       NYS_TRY(matvec_T<T>(op, mus_host[q], x + q * n, a.v + q * n, nullptr, B.op_work, s));
   }
-  init_r_kernel<T><<<dim3(gd, (unsigned)nsys), 256, 0, s>>>(b_dev, a.v, a.r, x, n, use_x0);
-  update_kernel<T, TU><<<g_u, PC_THREADS, 0, s>>>(a, 0);
-  z_kernel<T, TU><<<g_z, PC_THREADS, zsm, s>>>(a, 1);
-  p_kernel<T, TU><<<g_d, 256, 0, s>>>(a, 1);
+  init_r_kernel<T><<<dim3(gd, (unsigned)nsys), 256, 0, s>>>(b_dev, a.v, a.r, x, n, use_x0); count_launch();
+  update_kernel<T, TU><<<g_u, PC_THREADS, 0, s>>>(a, 0); count_launch();
+  z_kernel<T, TU><<<g_z, PC_THREADS, zsm, s>>>(a, 1); count_launch();
+  p_kernel<T, TU><<<g_d, 256, 0, s>>>(a, 1); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
 
   // ---- iterations, checked every `chunk`
@@ -396,10 +396,10 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
     for (int c = 0; c < chunk && launched < maxit; ++c, ++launched) {
       for (int64_t q = 0; q < nsys; ++q)
         NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work, s));
-      pv_alpha_kernel<T, TU><<<g_d, PC_THREADS, 0, s>>>(a);
-      update_kernel<T, TU><<<g_u, PC_THREADS, 0, s>>>(a, 1);
-      z_kernel<T, TU><<<g_z, PC_THREADS, zsm, s>>>(a, 0);
-      p_kernel<T, TU><<<g_d, 256, 0, s>>>(a, 0);
+      pv_alpha_kernel<T, TU><<<g_d, PC_THREADS, 0, s>>>(a); count_launch();
+      update_kernel<T, TU><<<g_u, PC_THREADS, 0, s>>>(a, 1); count_launch();
+      z_kernel<T, TU><<<g_z, PC_THREADS, zsm, s>>>(a, 0); count_launch();
+      p_kernel<T, TU><<<g_d, 256, 0, s>>>(a, 0); count_launch();
     }
     NYS_CUDA_TRY(cudaGetLastError());
     NYS_CUDA_TRY(cudaMemcpyAsync(hst.data(), a.st, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s));
@@ -512,7 +512,7 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   NYS_CUDA_TRY(cudaMemsetAsync(work, 0, 256, s));
   if (!use_x0) NYS_CUDA_TRY(cudaMemsetAsync(x, 0, nsys * n * sizeof(double), s));
   std::vector<double> bn2(nsys), rn2(nsys);
-  sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(b, n, nrm);
+  sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(b, n, nrm); count_launch();
   NYS_CUDA_TRY(cudaMemcpyAsync(bn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
   std::vector<int> active(nsys, 1), total_it(nsys, 0), outer(nsys, 0), stt(nsys, NYS_ERR_MAXIT);
   std::vector<double> rel(nsys, 1.0);
@@ -521,8 +521,8 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
     // true residual in FP64 for every system
     for (int64_t q = 0; q < nsys; ++q)
       NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
-    sub_kernel<<<gb, 256, 0, s>>>(b, v, r, nsys * n);
-    sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(r, n, nrm);
+    sub_kernel<<<gb, 256, 0, s>>>(b, v, r, nsys * n); count_launch();
+    sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(r, n, nrm); count_launch();
     NYS_CUDA_TRY(cudaMemcpyAsync(rn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
     NYS_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<int64_t> todo;
@@ -558,7 +558,7 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
                                    rr.data(), s)));
     for (int64_t t = 0; t < na; ++t) {
       int64_t q = todo[t];
-      axpy_to_f64_kernel<float><<<gb, 256, 0, s>>>(x + q * n, df + t * n, n);
+      axpy_to_f64_kernel<float><<<gb, 256, 0, s>>>(x + q * n, df + t * n, n); count_launch();
       total_it[q] += it[t];
       outer[q] += 1;
       if (st[t] == NYS_ERR_BREAKDOWN) {
@@ -614,13 +614,13 @@ static int32_t precond_apply_impl(const nys_factor* f, const TU* U, const double
   NYS_CUDA_TRY(cudaMemsetAsync(a.counters, 0, (size_t)nrhs * 4 * sizeof(unsigned), s));
   NYS_CUDA_TRY(cudaMemcpyAsync(B.d_mu, mu, nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
   // states: done = 0, thresh2 = -1 (never "converged"), maxit large
-  init_state_kernel<T><<<(unsigned)nrhs, 256, 0, s>>>(v, n, a.st, B.d_mu, f->lam_ell, 0.0, 1 << 30);
+  init_state_kernel<T><<<(unsigned)nrhs, 256, 0, s>>>(v, n, a.st, B.d_mu, f->lam_ell, 0.0, 1 << 30); count_launch();
   const size_t zsm = ell * sizeof(T);
   if (zsm > 48 * 1024)
     NYS_CUDA_TRY(cudaFuncSetAttribute(z_kernel<T, TU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)zsm));
-  update_kernel<T, TU><<<dim3((unsigned)a.nblk_u, (unsigned)nrhs), PC_THREADS, 0, s>>>(a, 0);
-  z_kernel<T, TU><<<dim3((unsigned)a.nblk_d, (unsigned)nrhs), PC_THREADS, zsm, s>>>(a, 1);
+  update_kernel<T, TU><<<dim3((unsigned)a.nblk_u, (unsigned)nrhs), PC_THREADS, 0, s>>>(a, 0); count_launch();
+  z_kernel<T, TU><<<dim3((unsigned)a.nblk_d, (unsigned)nrhs), PC_THREADS, zsm, s>>>(a, 1); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   // keep the buffers alive until the kernels have run
   NYS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -64,7 +64,8 @@ _lib = None
 _lock = threading.Lock()
 
 EXPORTS = ["nys_sketch", "nys_sketch_adaptive", "nys_precond_apply", "pcg_solve", "nys_factor_get",
-           "nys_factor_free", "nys_status_str", "nys_op_matvec", "nys_power_err_est"]
+           "nys_factor_free", "nys_status_str", "nys_op_matvec", "nys_power_err_est",
+           "nys_gemm_tf32_tn"]
 
 
 def lib() -> C.CDLL:
@@ -93,12 +94,20 @@ def lib() -> C.CDLL:
         L.nys_status_str.restype = C.c_char_p
         L.nys_op_matvec.argtypes = [C.POINTER(_Operator), dbl, i64, vp, vp, i32, vp]
         L.nys_power_err_est.argtypes = [C.POINTER(_Operator), vp, vp, i32, C.POINTER(dbl), vp]
+        L.nys_gemm_tf32_tn.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
+        L.nys_kernel_launch_count.argtypes = []
+        L.nys_kernel_launch_count.restype = C.c_uint64
         for name in EXPORTS:
             f = getattr(L, name)
             if f.restype is C.c_int:  # default
                 f.restype = C.c_int32
         _lib = L
         return _lib
+
+
+def kernel_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().nys_kernel_launch_count())
 
 
 def status_str(status: int) -> str:
@@ -296,6 +305,17 @@ def nys_op_matvec(op: Operator, mu: float, x: torch.Tensor, mode: int = 0) -> to
     _check(lib().nys_op_matvec(op.ref, float(mu), xx.shape[0], _ptr(xx), _ptr(y), mode, _stream()),
            "nys_op_matvec")
     return y if x.dim() == 2 else y[0]
+
+
+def nys_gemm_tf32_tn(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """D = A B^T (TF32 tensor cores, FP32 accumulate) for FP32 CUDA matrices."""
+    M, K = A.shape
+    N, K2 = B.shape
+    assert K == K2 and A.dtype == torch.float32 and B.dtype == torch.float32
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().nys_gemm_tf32_tn(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(D),
+                                  N, _stream()), "nys_gemm_tf32_tn")
+    return D
 
 
 def nys_power_err_est(op: Operator, f: Factor, g: torch.Tensor, q: int) -> float:
