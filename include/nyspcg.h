@@ -176,9 +176,11 @@ const char* nys_status_str(int32_t status);
 uint64_t nys_kernel_launch_count(void);
 
 /* y_s = (A + mu I) x_s for s = 0..nvec-1 (device FP64 [nvec][n]).  mode 0:
- * the FP64-accurate product used for residuals; mode 1: the FP32 product
- * used inside mixed-precision PCG.  Exposed so that each operator kernel can
- * be checked on its own.  Asynchronous. */
+ * FP64 arithmetic (the product inside FP64 PCG); mode 1: the FP32 product
+ * used inside mixed-precision PCG; mode 2: the FP64-accurate product of the
+ * mixed path's refinement residual (double-FP32 arithmetic for the ridge
+ * operator, ~2^-44 relative; FP64 for the others).  Exposed so that each
+ * operator kernel can be checked on its own.  Synchronises `stream`. */
 int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const double* x, double* y,
                       int32_t mode, void* stream);
 
@@ -186,6 +188,19 @@ int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const dou
  * (device FP64 [n]); *est (host) receives the estimate.  Synchronises. */
 int32_t nys_power_err_est(const nys_operator* op, const nys_factor* f, const double* g, int32_t q,
                           double* est, void* stream);
+
+/* Gaussian cross-kernel products for the kernel-ridge predictions and their
+ * gradient (Sec. 6.5 uses k(x, y) = exp(-||x - y||^2 / (2 sigma^2))):
+ *   kind 0: out_q[i] = sum_j k(t_i, x_j) v_q[j]
+ *   kind 1: out_q[i] = sum_j k(t_i, x_j) ||t_i - x_j||^2 / sigma^3 v_q[j]
+ *           (the derivative of kind 0 in sigma).
+ * targets: nt x d FP32 (row stride ldt), points: n x d FP32 (row stride ldp),
+ * v: device FP64 [nvec][n], out: device FP64 [nvec][nt], FP64 arithmetic.
+ * K_v^T g is the same call with the roles of targets and points swapped (the
+ * kernel is symmetric in its arguments).  1 <= d <= 64.  Synchronises. */
+int32_t nys_rbf_cross_matvec(const float* targets, int64_t nt, int64_t ldt, const float* points,
+                             int64_t n, int64_t ldp, int64_t d, double sigma, int64_t nvec,
+                             const double* v, double* out, int32_t kind, void* stream);
 
 /* D = A B^T on the 5th-generation tensor cores: TF32 products (the low 13
  * mantissa bits of each FP32 operand are ignored), FP32 accumulation.  A is

@@ -140,7 +140,7 @@ static int32_t read_double(const double* d, double* h, cudaStream_t s) {
 // al., SISC 2020) if the plain factorisation fails; then a third pass runs.
 template <typename T>
 static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool racc_init,
-                      cudaStream_t s) {
+                      int passes0, cudaStream_t s) {
   Scratch sc(s);
   double *G, *Gi, *Rn, *dmax;
   int* info;
@@ -149,7 +149,7 @@ static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool r
   NYS_TRY(sc.get(&Rn, ell * ell));
   NYS_TRY(sc.get(&dmax, 1));
   NYS_TRY(sc.get(&info, 1));
-  int passes = 2;
+  int passes = passes0;
   T* cur = X;
   T* other = tmp;
   for (int pass = 0; pass < passes; ++pass) {
@@ -173,12 +173,14 @@ static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool r
       NYS_TRY(chol_upper(G, ell, info, s));
       NYS_TRY(read_int(info, &h_info, s));
       if (h_info != 0) return NYS_ERR_NOT_PSD;
-      passes = 3;
+      passes = passes0 + 1;
     }
     NYS_TRY(tri_inv_upper(G, Gi, ell, s));
     NYS_TRY(Ops<T>::mul_small(cur, Gi, n, ell, ell, other, s));
     // Racc <- R_pass Racc
-    if (pass == 0 && racc_init) {
+    if (!Racc) {
+      // R not wanted
+    } else if (pass == 0 && racc_init) {
       NYS_CUDA_TRY(cudaMemcpyAsync(Racc, G, ell * ell * sizeof(double), cudaMemcpyDeviceToDevice, s));
     } else {
       NYS_TRY(gemm_f64(false, ell, ell, ell, G, ell, Racc, ell, Rn, ell, s));
@@ -192,15 +194,15 @@ static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool r
   return NYS_OK;
 }
 
-// Thin QR of a Gaussian block (Algorithm 1, step 2), in place.
+// Thin QR of a Gaussian block (Algorithm 1, step 2), in place.  A Gaussian
+// n x ell block with n >> ell has condition number near 1, so one
+// CholeskyQR pass already leaves orthogonality at rounding level.
 template <typename T>
 static int32_t orthonormalize(T* Om, int64_t n, int64_t ell, cudaStream_t s) {
   Scratch sc(s);
   T* tmp;
-  double* R;
   NYS_TRY(sc.get(&tmp, n * ell));
-  NYS_TRY(sc.get(&R, ell * ell));
-  return cholqr<T>(Om, n, ell, tmp, R, true, s);
+  return cholqr<T>(Om, n, ell, tmp, nullptr, true, (n >= 4 * ell) ? 1 : 2, s);
 }
 
 // ||Y||_2 by power iteration on Y^T Y (30 steps); only its binary exponent
@@ -280,7 +282,7 @@ static int32_t shifted_core(const T* Q, const T* Y, int64_t n, int64_t ell, bool
   NYS_TRY(tri_inv_upper(M, Ci, ell, s));
   NYS_TRY(Ops<T>::mul_small(Ynu, Ci, n, ell, ell, Bb, s));  // B = Y_nu C^{-1}
   // thin SVD of B: B = Qb R (CholeskyQR2), R = Ut Sigma V^T (one-sided Jacobi)
-  NYS_TRY(cholqr<T>(Bb, n, ell, Ynu, R, true, s));
+  NYS_TRY(cholqr<T>(Bb, n, ell, Ynu, R, true, 2, s));
   int sweeps = 0;
   NYS_TRY(jacobi_svd(R, Ut, sig, ell, jst, &sweeps, s));
   int hj = 0;
@@ -726,16 +728,19 @@ int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const dou
   NYS_TRY(check_op(op));
   if (nvec < 1 || !x || !y || x == y) return NYS_ERR_ARG;
   if (!(mu >= 0.0) || !std::isfinite(mu)) return NYS_ERR_ARG;
-  if (mode != 0 && mode != 1) return NYS_ERR_ARG;
+  if (mode != 0 && mode != 1 && mode != 2) return NYS_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = op->n;
   Scratch sc(s);
   unsigned char* work;
-  NYS_TRY(sc.get(&work, op_matvec_work_bytes(op, mode == 0)));
+  NYS_TRY(sc.get(&work, op_matvec_work_bytes(op, mode != 1)));
   NYS_CUDA_TRY(cudaMemsetAsync(work, 0, 256, s));
   if (mode == 0) {
     for (int64_t q = 0; q < nvec; ++q)
       NYS_TRY(op_matvec_f64(op, mu, x + q * n, y + q * n, nullptr, work, s));
+  } else if (mode == 2) {
+    for (int64_t q = 0; q < nvec; ++q)
+      NYS_TRY(op_matvec_residual(op, mu, x + q * n, y + q * n, nullptr, work, s));
   } else {
     float *xf, *yf;
     NYS_TRY(sc.get(&xf, nvec * n));
@@ -749,6 +754,19 @@ int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const dou
   NYS_CUDA_TRY(cudaMemcpyAsync(&err, work, sizeof(int), cudaMemcpyDeviceToHost, s));
   NYS_CUDA_TRY(cudaStreamSynchronize(s));
   return err ? NYS_ERR_TIMEOUT : NYS_OK;
+}
+
+int32_t nys_rbf_cross_matvec(const float* targets, int64_t nt, int64_t ldt, const float* points,
+                             int64_t n, int64_t ldp, int64_t d, double sigma, int64_t nvec,
+                             const double* v, double* out, int32_t kind, void* stream) {
+  if (!targets || !points || !v || !out || nt < 1 || n < 1 || nvec < 1) return NYS_ERR_ARG;
+  if (d < 1 || d > 64 || ldt < d || ldp < d) return NYS_ERR_ARG;
+  if (!(sigma > 0.0) || !std::isfinite(sigma) || (kind != 0 && kind != 1)) return NYS_ERR_ARG;
+  if ((const void*)v == (const void*)out) return NYS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  NYS_TRY(rbf_cross_matvec(targets, nt, ldt, points, n, ldp, d, sigma, nvec, v, out, kind, s));
+  NYS_CUDA_TRY(cudaStreamSynchronize(s));
+  return NYS_OK;
 }
 
 int32_t nys_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,

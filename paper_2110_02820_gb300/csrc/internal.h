@@ -136,8 +136,16 @@ size_t op_matvec_work_bytes(const nys_operator* op, bool accurate);
 // NULL (allocated per call).
 int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* v, const int* skip,
                       void* work, cudaStream_t s);
-// FP64-accurate v = (A + mu I) p (FP64 PCG and refinement residuals).
+// v = (A + mu I) p in FP64 arithmetic (FP64 PCG).
 int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double* v,
                       const int* skip, void* work, cudaStream_t s);
+// Gaussian cross-kernel products (FP64): kind 0 K(t, x) v, kind 1 dK/dsigma v.
+int32_t rbf_cross_matvec(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
+                         int64_t ldp, int64_t d, double sigma, int64_t nvec, const double* v,
+                         double* out, int kind, cudaStream_t s);
+// FP64-accurate v = (A + mu I) p for the refinement residual: the ridge
+// operator in double-FP32 arithmetic (~2^-44 relative), the others in FP64.
+int32_t op_matvec_residual(const nys_operator* op, double mu, const double* p, double* v,
+                           const int* skip, void* work, cudaStream_t s);
 
 }  // namespace nys

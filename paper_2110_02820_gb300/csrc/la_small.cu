@@ -235,7 +235,7 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* status
           ok = 0;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(20);
       }
     }
     __threadfence();
@@ -245,7 +245,8 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* status
 }
 
 struct JacobiArgs {
-  double* W;          // ell_pad x ell rows: row j = column j of the matrix being rotated
+  double* W;          // ell rows of length ell: row j = column j of the matrix being rotated
+  double* nrm;        // [ell] squared column norms, refreshed at every sweep start
   int64_t ell;        // true size (row length)
   int64_t npad;       // number of columns incl. padding (even)
   int max_sweeps;
@@ -266,14 +267,31 @@ __device__ __forceinline__ void round_pair(int64_t npad, int64_t r, int64_t k, i
   *q = pos(npad - 1 - k);
 }
 
-__global__ void jacobi_kernel(JacobiArgs a) {
+// One-sided (Hestenes) Jacobi: each warp orthogonalises column pairs of a
+// round; every block is one warp so that the FP64 work of a round spreads
+// over all SMs.  Column norms are carried from the 2x2 rotation
+// (alpha' = alpha - t gamma, beta' = beta + t gamma) and recomputed exactly
+// at the start of every sweep, so a pair costs one dot product plus the
+// rotation.
+__global__ void __launch_bounds__(32) jacobi_kernel(JacobiArgs a) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t warp = blockIdx.x;
+  const int64_t nwarps = gridDim.x;
   const int64_t npairs = a.npad / 2;
-  const double tol = 1e-15;
+  // Rotate only when the cosine of the angle between the two columns exceeds
+  // ell * eps: below that the computed inner product is rounding noise
+  // (~eps sqrt(ell)) and further sweeps would not terminate.
+  const double tol = (double)(a.ell < 8 ? 8 : a.ell) * 2.220446049250313e-16;
   int sweep = 0;
   for (; sweep < a.max_sweeps; ++sweep) {
+    for (int64_t j = warp; j < a.ell; j += nwarps) {
+      const double* wj = a.W + j * a.ell;
+      double acc = 0.0;
+      for (int64_t i = lane; i < a.ell; i += 32) acc = fma(wj[i], wj[i], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) a.nrm[j] = acc;
+    }
+    if (!grid_barrier(a.bar, a.bar + 1, a.status)) return;
     for (int64_t r = 0; r < a.npad - 1; ++r) {
       for (int64_t k = warp; k < npairs; k += nwarps) {
         int64_t p, q;
@@ -281,27 +299,25 @@ __global__ void jacobi_kernel(JacobiArgs a) {
         if (p >= a.ell || q >= a.ell) continue;  // padding column
         double* wp = a.W + p * a.ell;
         double* wq = a.W + q * a.ell;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int64_t i = lane; i < a.ell; i += 32) {
-          double x = wp[i], y = wq[i];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
+        const double al = a.nrm[p], be = a.nrm[q];
+        double ga = 0.0;
+        for (int64_t i = lane; i < a.ell; i += 32) ga = fma(wp[i], wq[i], ga);
         ga = warp_sum(ga);
         if (fabs(ga) > tol * sqrt(al * be) && al * be > 0.0) {
-          double zeta = (be - al) / (2.0 * ga);
-          double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + t * t);
-          double sn = c * t;
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t);
+          const double sn = c * t;
           for (int64_t i = lane; i < a.ell; i += 32) {
-            double x = wp[i], y = wq[i];
+            const double x = wp[i], y = wq[i];
             wp[i] = c * x - sn * y;
             wq[i] = sn * x + c * y;
           }
-          if (lane == 0) atomicAdd(&a.rot_count[sweep], 1);
+          if (lane == 0) {
+            a.nrm[p] = al - t * ga;
+            a.nrm[q] = be + t * ga;
+            atomicAdd(&a.rot_count[sweep], 1);
+          }
         }
       }
       if (!grid_barrier(a.bar, a.bar + 1, a.status)) return;
@@ -315,26 +331,28 @@ __global__ void jacobi_kernel(JacobiArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.sweeps_done = sweep;
 }
 
-// sigma_j = ||w_j||; sort descending (bitonic in shared memory, one block);
-// Ut[i][j] = w_{perm[j]}[i] / sigma_j.
-__global__ void jacobi_finish_kernel(const double* W, int64_t ell, int64_t pow2, double* Ut,
-                                     double* sigma) {
+// sigma_j = ||w_j|| (one warp per column).
+__global__ void col_norm_kernel(const double* W, int64_t ell, double* sigma) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= ell) return;
+  const double* w = W + j * ell;
+  double acc = 0.0;
+  for (int64_t i = lane; i < ell; i += 32) acc = fma(w[i], w[i], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) sigma[j] = sqrt(acc);
+}
+
+// Sort sigma descending (bitonic in shared memory, one block; ties by index).
+__global__ void sort_desc_kernel(double* sigma, int* perm, int64_t ell, int64_t pow2) {
   extern __shared__ unsigned char smem_raw[];
   double* key = reinterpret_cast<double*>(smem_raw);
   int* idx = reinterpret_cast<int*>(key + pow2);
   for (int64_t j = threadIdx.x; j < pow2; j += blockDim.x) {
-    if (j < ell) {
-      const double* w = W + j * ell;
-      double acc = 0.0;
-      for (int64_t i = 0; i < ell; ++i) acc += w[i] * w[i];
-      key[j] = sqrt(acc);
-    } else {
-      key[j] = -1.0;
-    }
+    key[j] = (j < ell) ? sigma[j] : -1.0;
     idx[j] = (int)j;
   }
   __syncthreads();
-  // bitonic sort, descending by key, ties by index ascending
   for (int64_t size = 2; size <= pow2; size <<= 1) {
     for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
       for (int64_t t = threadIdx.x; t < pow2; t += blockDim.x) {
@@ -354,33 +372,43 @@ __global__ void jacobi_finish_kernel(const double* W, int64_t ell, int64_t pow2,
       __syncthreads();
     }
   }
-  for (int64_t j = threadIdx.x; j < ell; j += blockDim.x) sigma[j] = key[j];
-  __syncthreads();
-  for (int64_t e = threadIdx.x; e < ell * ell; e += blockDim.x) {
-    int64_t i = e / ell, j = e % ell;
-    double sg = key[j];
-    const double* w = W + (int64_t)idx[j] * ell;
-    Ut[e] = (sg > 0.0) ? w[i] / sg : (i == j ? 1.0 : 0.0);
+  for (int64_t j = threadIdx.x; j < ell; j += blockDim.x) {
+    sigma[j] = key[j];
+    perm[j] = idx[j];
   }
+}
+
+// UtT[j][i] = w_{perm[j]}[i] / sigma_j (row j = j-th left singular vector).
+__global__ void gather_scale_kernel(const double* W, const int* perm, const double* sigma,
+                                    int64_t ell, double* UtT) {
+  const int64_t j = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ell) return;
+  const double sg = sigma[j];
+  UtT[j * ell + i] = (sg > 0.0) ? W[(int64_t)perm[j] * ell + i] / sg : (i == j ? 1.0 : 0.0);
 }
 
 int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int* d_status,
                    int* sweeps_out, cudaStream_t s) {
   const int max_sweeps = 40;
   int64_t npad = ell + (ell & 1);
-  double* W = nullptr;
+  double *W = nullptr, *UtT = nullptr, *nrm = nullptr;
   unsigned char* aux = nullptr;
-  NYS_TRY(dmalloc((void**)&W, ell * ell * sizeof(double), s));
-  size_t aux_bytes = 2 * sizeof(unsigned) + max_sweeps * sizeof(int) + 2 * sizeof(int);
-  int32_t st = dmalloc((void**)&aux, aux_bytes, s);
-  if (st != NYS_OK) { dfree(W, s); return st; }
+  Scratch sc(s);
+  NYS_TRY(sc.get(&W, ell * ell));
+  NYS_TRY(sc.get(&UtT, ell * ell));
+  NYS_TRY(sc.get(&nrm, ell));
+  size_t aux_bytes = 2 * sizeof(unsigned) + max_sweeps * sizeof(int) + 2 * sizeof(int) + ell * sizeof(int);
+  NYS_TRY(sc.get(&aux, aux_bytes));
+  int* perm = reinterpret_cast<int*>(aux + 2 * sizeof(unsigned) + (max_sweeps + 2) * sizeof(int));
   // W rows = columns of R
   dim3 g((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 32));
   transpose_kernel<<<g, dim3(32, 8), 0, s>>>(R, W, ell, ell); count_launch();
-  cudaMemsetAsync(aux, 0, aux_bytes, s);
-  cudaMemsetAsync(d_status, 0, sizeof(int), s);
+  NYS_CUDA_TRY(cudaMemsetAsync(aux, 0, aux_bytes, s));
+  NYS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
   JacobiArgs a;
   a.W = W;
+  a.nrm = nrm;
   a.ell = ell;
   a.npad = npad;
   a.max_sweeps = max_sweeps;
@@ -388,36 +416,37 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int*
   a.rot_count = reinterpret_cast<int*>(aux + 2 * sizeof(unsigned));
   a.sweeps_done = a.rot_count + max_sweeps;
   a.status = d_status;
-  // grid: enough warps for all pairs, limited to co-resident blocks
-  int threads = 256;
+  // one warp per block, as many blocks as pairs, limited to co-resident blocks
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, threads, 0);
-  int64_t want = cdiv(npad / 2, threads / 32);
+  NYS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 32, 0));
+  if (per_sm > 8) per_sm = 8;
+  int64_t want = npad / 2;
   int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
   int blocks = (int)(want < cap ? want : cap);
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(blocks), dim3(threads),
-                                              args, 0, s);
+  NYS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(blocks), dim3(32), args, 0, s));
   count_launch();
-  if (e == cudaSuccess) {
-    int64_t pow2 = 1;
-    while (pow2 < ell) pow2 <<= 1;
-    size_t sh = pow2 * (sizeof(double) + sizeof(int));
-    if (sh > 48 * 1024)
-      cudaFuncSetAttribute(jacobi_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sh);
-    jacobi_finish_kernel<<<1, 1024, sh, s>>>(W, ell, pow2, Ut, sigma); count_launch();
-    e = cudaGetLastError();
+  col_norm_kernel<<<(unsigned)cdiv(ell, 8), 256, 0, s>>>(W, ell, sigma); count_launch();
+  int64_t pow2 = 1;
+  while (pow2 < ell) pow2 <<= 1;
+  size_t sh = pow2 * (sizeof(double) + sizeof(int));
+  if (sh > 48 * 1024)
+    NYS_CUDA_TRY(cudaFuncSetAttribute(sort_desc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sh));
+  sort_desc_kernel<<<1, 1024, sh, s>>>(sigma, perm, ell, pow2); count_launch();
+  gather_scale_kernel<<<dim3((unsigned)cdiv(ell, 128), (unsigned)ell), 128, 0, s>>>(W, perm, sigma,
+                                                                                  ell, UtT);
+  count_launch();
+  // Ut (columns = left singular vectors) = UtT^T
+  transpose_kernel<<<g, dim3(32, 8), 0, s>>>(UtT, Ut, ell, ell); count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  if (sweeps_out) {
+    NYS_CUDA_TRY(cudaMemcpyAsync(sweeps_out, a.sweeps_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
   }
-  if (e == cudaSuccess && sweeps_out) {
-    e = cudaMemcpyAsync(sweeps_out, a.sweeps_done, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  }
-  dfree(aux, s);
-  dfree(W, s);
-  NYS_CUDA_TRY(e);
   return NYS_OK;
 }
+
 
 }  // namespace nys

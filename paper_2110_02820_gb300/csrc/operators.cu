@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -176,6 +177,192 @@ gram_fused_kernel(const float* __restrict__ X, int64_t m, int64_t n, const P* __
   }
 }
 
+// ------------------------------------------------------------ double-FP32 variant
+//
+// FP64-accurate ridge matvec for the refinement residual, in pairs of FP32
+// numbers ("float-float"): each product of an FP32 entry of X with an FP32
+// part of p is made error-free with one FMA, and the running sums carry their
+// rounding errors with Knuth's TwoSum.  Relative accuracy ~2^-44, on the FP32
+// pipes (GB300 issues FP32 far faster than FP64).  The rounded intrinsics
+// keep the compiler from contracting the error-free steps.
+
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add_prod(float x, float y, float& hi, float& lo) {
+  const float p = __fmul_rn(x, y);
+  const float pe = __fmaf_rn(x, y, -p);          // x*y = p + pe exactly
+  const float s = __fadd_rn(hi, p);              // TwoSum(hi, p)
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ FF ff_sum(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  FF r;
+  r.hi = __fadd_rn(s, e);                        // QuickTwoSum(s, e)
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+  return r;
+}
+
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = ff_sum(v, w);
+  }
+  return v;
+}
+
+// part[blockIdx.x][0..n) (FP64) = sum over this CTA's rows i of (x_i . p) x_i,
+// p given in FP64 and split into FP32 hi + lo parts.  Same streaming
+// structure as gram_fused_kernel.
+template <int NG>
+__global__ void __launch_bounds__(GR_THREADS, 1)
+gram_fused_ff_kernel(const float* __restrict__ X, int64_t m, int64_t n,
+                     const double* __restrict__ p, double* __restrict__ part, int stages,
+                     int64_t rows_per_cta, int* err, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  float* stage_mem = reinterpret_cast<float*>(smem + 128);
+  __shared__ FF red[GR_THREADS / 32][GR_ROWS];
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n4 = n >> 2;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = (r0 + rows_per_cta < m) ? r0 + rows_per_cta : m;
+  double* out = part + (int64_t)blockIdx.x * n;
+
+  float ph[NG][4], pl[NG][4];
+  FF acc[NG][4];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    int64_t c4 = tid + (int64_t)g * GR_THREADS;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double pv = (c4 < n4) ? p[4 * c4 + q] : 0.0;
+      ph[g][q] = __double2float_rn(pv);
+      pl[g][q] = __double2float_rn(pv - (double)ph[g][q]);
+      acc[g][q].hi = 0.f;
+      acc[g][q].lo = 0.f;
+    }
+  }
+  if (r0 >= r1) {
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      int64_t c4 = tid + (int64_t)g * GR_THREADS;
+      if (c4 < n4)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[4 * c4 + q] = 0.0;
+    }
+    return;
+  }
+  const int64_t nrows = r1 - r0;
+  const int64_t nchunks = (nrows + GR_ROWS - 1) / GR_ROWS;
+  const int64_t stage_elems = (int64_t)GR_ROWS * n;
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+    s_fail = 0;
+  }
+  __syncthreads();
+  auto issue = [&](int64_t c) {
+    int s = (int)(c % stages);
+    int64_t rows = nrows - c * GR_ROWS;
+    if (rows > GR_ROWS) rows = GR_ROWS;
+    uint32_t bytes = (uint32_t)(rows * n * sizeof(float));
+    mbar_arrive_expect_tx(&bars[s], bytes);
+    bulk_g2s(stage_mem + s * stage_elems, X + (r0 + c * GR_ROWS) * n, bytes, &bars[s]);
+  };
+  if (tid == 0) {
+    int64_t pre = (stages - 1 < nchunks) ? stages - 1 : nchunks;
+    for (int64_t c = 0; c < pre; ++c) issue(c);
+  }
+  int64_t issued = (stages - 1 < nchunks) ? stages - 1 : nchunks;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int s = (int)(c % stages);
+    if (c + stages - 1 < nchunks) {
+      if (tid == 0) issue(c + stages - 1);
+      issued = c + stages;
+    }
+    bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((c / stages) & 1));
+    if (!ok) atomicOr(&s_fail, 1);
+    int64_t rows = nrows - c * GR_ROWS;
+    if (rows > GR_ROWS) rows = GR_ROWS;
+    const float* st = stage_mem + s * stage_elems;
+    float xr[GR_ROWS][NG][4];
+    FF d[GR_ROWS];
+#pragma unroll
+    for (int r = 0; r < GR_ROWS; ++r) {
+      d[r].hi = 0.f;
+      d[r].lo = 0.f;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        int64_t c4 = tid + (int64_t)g * GR_THREADS;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rows && c4 < n4) v = reinterpret_cast<const float4*>(st + r * n)[c4];
+        xr[r][g][0] = v.x; xr[r][g][1] = v.y; xr[r][g][2] = v.z; xr[r][g][3] = v.w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ff_add_prod(xr[r][g][q], ph[g][q], d[r].hi, d[r].lo);
+          d[r].lo = __fmaf_rn(xr[r][g][q], pl[g][q], d[r].lo);
+        }
+      }
+      d[r] = ff_warp_sum(d[r]);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < GR_ROWS; ++r) red[warp][r] = d[r];
+    }
+    __syncthreads();
+    if (s_fail) break;
+    FF t[GR_ROWS];
+#pragma unroll
+    for (int r = 0; r < GR_ROWS; ++r) {
+      FF v = red[0][r];
+#pragma unroll
+      for (int w = 1; w < GR_THREADS / 32; ++w) v = ff_sum(v, red[w][r]);
+      t[r] = v;
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < GR_ROWS; ++r) {
+          ff_add_prod(xr[r][g][q], t[r].hi, acc[g][q].hi, acc[g][q].lo);
+          acc[g][q].lo = __fmaf_rn(xr[r][g][q], t[r].lo, acc[g][q].lo);
+        }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) {
+      atomicCAS(err, 0, (int)NYS_ERR_TIMEOUT);
+      for (int64_t c = 0; c < issued; ++c)
+        mbar_wait_bounded(&bars[c % stages], (uint32_t)((c / stages) & 1), 1ll << 20);
+    }
+    return;
+  }
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    int64_t c4 = tid + (int64_t)g * GR_THREADS;
+    if (c4 < n4)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        out[4 * c4 + q] = (double)acc[g][q].hi + (double)acc[g][q].lo;
+  }
+}
+
 // v_j = sum_c part[c][j] (fixed order) + mu p_j; optionally r_j = b_j - v_j.
 template <typename Acc, typename P, typename V>
 __global__ void gram_reduce_kernel(const Acc* __restrict__ part, int64_t nparts, int64_t n,
@@ -276,11 +463,37 @@ static size_t gram_work_bytes(const nys_operator* op, size_t acc_size) {
 // hold the timeout word.
 template <typename P, typename Acc, typename V>
 static int32_t gram_matvec(const nys_operator* op, double mu, const P* p, V* v, const int* skip,
-                           void* work, cudaStream_t s) {
+                           void* work, cudaStream_t s, bool double_fp32 = false) {
   const int64_t n = op->n, m = op->m;
   GramPlan g = gram_plan(op);
   int* err = reinterpret_cast<int*>(work);
   Acc* base = reinterpret_cast<Acc*>(reinterpret_cast<unsigned char*>(work) + 256);
+  if constexpr (std::is_same<P, double>::value && std::is_same<Acc, double>::value) {
+    if (g.fused && double_fp32) {
+      // FP64-accurate product in double-FP32 arithmetic
+      double* part = base;
+      auto launch = [&](auto kern) -> int32_t {
+        NYS_CUDA_TRY(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
+        kern<<<g.grid, GR_THREADS, g.smem, s>>>((const float*)op->data, op->m, op->n, p, part,
+                                                 g.stages, g.rows_per_cta, err, skip);
+        count_launch();
+        NYS_CUDA_TRY(cudaGetLastError());
+        return NYS_OK;
+      };
+      switch (g.ng) {
+        case 1: NYS_TRY(launch(gram_fused_ff_kernel<1>)); break;
+        case 2: NYS_TRY(launch(gram_fused_ff_kernel<2>)); break;
+        case 4: NYS_TRY(launch(gram_fused_ff_kernel<4>)); break;
+        default: NYS_TRY(launch(gram_fused_ff_kernel<8>)); break;
+      }
+      gram_reduce_kernel<double, P, V><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, g.grid, n, mu,
+                                                                             p, v, skip);
+      count_launch();
+      NYS_CUDA_TRY(cudaGetLastError());
+      return NYS_OK;
+    }
+  }
   if (g.fused) {
     Acc* part = base;
     switch (g.ng) {
@@ -567,6 +780,76 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
       (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
+}
+
+// ============================================================ cross kernel (FP64)
+//
+// out[q][i] = sum_j k(t_i, x_j) v[q][j] with k the Gaussian kernel (kind 0)
+// or its derivative in sigma, k(t, x) ||t - x||^2 / sigma^3 (kind 1).  Rows
+// are the target points, columns the source points; FP64 arithmetic.  Used
+// for predictions K_v alpha, their adjoint K_v^T g, and the sigma-derivative
+// products of the KRR gradient.
+constexpr int CX_BI = 128, CX_BJ = 64;
+__global__ void __launch_bounds__(CX_BI)
+rbf_cross_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
+                 const float* __restrict__ pts, int64_t n, int64_t ldp, int64_t d, double sigma,
+                 const double* __restrict__ v, double* __restrict__ out, int kind) {
+  __shared__ float xs[CX_BJ][RBF_DMAX + 1];
+  __shared__ double vs[CX_BJ];
+  const int64_t q = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * CX_BI + threadIdx.x;
+  float ti[RBF_DMAX];
+#pragma unroll
+  for (int k = 0; k < RBF_DMAX; ++k) ti[k] = (i < nt && k < d) ? tg[i * ldt + k] : 0.f;
+  const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+  const double inv_s3 = 1.0 / (sigma * sigma * sigma);
+  double acc = 0.0;
+  for (int64_t j0 = 0; j0 < n; j0 += CX_BJ) {
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)CX_BJ * d; e += CX_BI) {
+      int64_t jj = e / d, k = e % d;
+      xs[jj][k] = (j0 + jj < n) ? pts[(j0 + jj) * ldp + k] : 0.f;
+    }
+    for (int jj = threadIdx.x; jj < CX_BJ; jj += CX_BI)
+      vs[jj] = (j0 + jj < n) ? v[q * n + j0 + jj] : 0.0;
+    __syncthreads();
+    const int jn = (int)((n - j0 < CX_BJ) ? n - j0 : CX_BJ);
+    for (int jj = 0; jj < jn; ++jj) {
+      double dist = 0.0;
+#pragma unroll
+      for (int k = 0; k < RBF_DMAX; ++k) {
+        if (k < d) {
+          const double df = (double)ti[k] - (double)xs[jj][k];
+          dist = fma(df, df, dist);
+        }
+      }
+      double kv = exp(-dist * inv2s2);
+      if (kind == 1) kv *= dist * inv_s3;
+      acc = fma(kv, vs[jj], acc);
+    }
+  }
+  if (i < nt) out[q * nt + i] = acc;
+}
+
+int32_t rbf_cross_matvec(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
+                         int64_t ldp, int64_t d, double sigma, int64_t nvec, const double* v,
+                         double* out, int kind, cudaStream_t s) {
+  dim3 grid((unsigned)cdiv(nt, CX_BI), (unsigned)nvec);
+  rbf_cross_kernel<<<grid, CX_BI, 0, s>>>(tg, nt, ldt, pts, n, ldp, d, sigma, v, out, kind);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+int32_t op_matvec_residual(const nys_operator* op, double mu, const double* p, double* v,
+                           const int* skip, void* work, cudaStream_t s) {
+  if (op->kind != NYS_OP_GRAM) return op_matvec_f64(op, mu, p, v, skip, work, s);
+  if (work) return gram_matvec<double, double, double>(op, mu, p, v, skip, work, s, true);
+  Scratch sc(s);
+  unsigned char* w;
+  NYS_TRY(sc.get(&w, op_matvec_work_bytes(op, true)));
+  NYS_CUDA_TRY(cudaMemsetAsync(w, 0, 256, s));
+  return gram_matvec<double, double, double>(op, mu, p, v, skip, w, s, true);
 }
 
 }  // namespace nys

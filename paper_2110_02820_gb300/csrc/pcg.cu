@@ -2,19 +2,20 @@
 // Eq. (5.3), for one or many independent systems (A + mu_s I) x_s = b_s that
 // share the operator and the factor (U, lambda_hat).
 //
-// One iteration is five stream-ordered launches:
-//   matvec       v = (A + mu I) p                         (operator kernels)
-//   pv_alpha     alpha = (r^T z) / (p^T v)                 breakdown check
-//   update       x += alpha p, r -= alpha v, ||r||^2, W = U^T r (partials);
-//                the last block reduces W into w'_j = ((lam_ell+mu)/(lam_j+mu) - 1) w_j,
-//                counts the iteration and sets `done` on convergence or cap
-//   z            z = r + U w' = P^{-1} r (Eq. (5.3)),  r^T z -> beta
+// One iteration is six stream-ordered launches after the operator matvec:
+//   matvec       v = (A + mu I) p                          (operator kernels)
+//   pv_alpha     alpha = (r^T z) / (p^T v), breakdown check
+//   update       x += alpha p, r -= alpha v; ||r||^2 and W = U^T r as
+//                per-block partials (a warp walks 16-row groups of U with
+//                16-byte loads; the row residuals are broadcast by shuffle)
+//   wreduce      w'_j = ((lam_ell + mu)/(lam_j + mu) - 1) sum_b W_bj,
+//                ||r||^2, iteration count, convergence / cap -> `done`
+//   z            z = r + U w' = P^{-1} r,  r^T z -> beta
 //   p            p = z + beta p
-// Scalars live on the device in FP64; every dot product is a two-phase
-// fixed-order reduction (per-block partials, summed by the last block to
-// arrive), so results do not depend on scheduling.  Once a system's `done`
-// word is set every kernel of that system returns at once, so the host can
-// enqueue several iterations between convergence checks.
+// Scalars live on the device in FP64.  Every reduction runs in a fixed order
+// (per-block partials summed in index order), so results do not depend on
+// scheduling.  Once a system's `done` word is set every kernel of that system
+// returns at once, so the host enqueues several iterations between checks.
 
 #include <cstdio>
 #include <cstring>
@@ -30,10 +31,15 @@ struct SysState {
   double lam_ell_mu;  // lambda_hat_ell + mu
   double rz, pv, alpha, beta, rr, thresh2;
   int it, done, status, maxit;
+  int conv;  // set by wreduce when the test passes; p_kernel promotes it to `done`
+  int pad;
 };
 
 constexpr int PC_THREADS = 256;
-constexpr int PC_JPT = 16;  // U columns per thread in the U^T r partials (ell <= 4096)
+constexpr int PC_WARPS = PC_THREADS / 32;
+constexpr int PC_GROUP = 16;   // rows of U a warp handles per inner group
+constexpr int PC_MAXRG = 4;    // 32-row register groups per warp (rows per warp <= 128)
+constexpr int PC_CQ = 4;       // 16-byte vectors of U per lane per column chunk
 
 template <typename T, typename TU>
 struct PcgArgs {
@@ -44,11 +50,12 @@ struct PcgArgs {
   T *x, *r, *z, *p, *v;   // [nsys][n]
   TU* wpart;              // [nsys][nblk_u][ell]
   T* w;                   // [nsys][ell]  (w' = coefficient * U^T r)
-  double* dpart;          // [nsys][nblk] dot partials
+  double* dpart;          // [nsys][npart] dot partials
   unsigned int* counters; // [nsys][4]
-  int64_t nblk_u;         // blocks of the update kernel (row chunks)
-  int64_t rows_u;         // rows per update block
-  int64_t nblk_d;         // blocks of the dot kernels
+  int64_t nblk_u;         // blocks of the update / z kernels
+  int64_t rows_w;         // rows per warp in the update / z kernels (multiple of 16, <= 128)
+  int64_t nblk_d;         // blocks of the elementwise dot kernels
+  int64_t npart;          // stride of dpart per system
   double* hist;           // [nsys][maxit+1] or NULL
 };
 
@@ -68,7 +75,7 @@ pv_alpha_kernel(PcgArgs<T, TU> a) {
        i += (int64_t)gridDim.x * PC_THREADS)
     acc += (double)p[i] * (double)v[i];
   acc = block_sum(acc, red);
-  double* part = a.dpart + sidx * a.nblk_d;
+  double* part = a.dpart + sidx * a.npart;
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
   if (last_block_arrived(a.counters + sidx * 4 + 0)) {
     double t = 0.0;
@@ -86,132 +93,221 @@ pv_alpha_kernel(PcgArgs<T, TU> a) {
   }
 }
 
-// update (do_update) + ||r||^2 + U^T r partials; last block finishes w', the
-// iteration count and the convergence test.
-template <typename T, typename TU>
+// 16-byte vector of U: VE elements of type TU.
+template <typename TU, int VE>
+struct UVec {
+  TU e[VE];
+};
+
+template <typename TU, int VE>
+__device__ __forceinline__ UVec<TU, VE> load_uvec(const TU* p) {
+  UVec<TU, VE> v;
+  if constexpr (VE == 4 && sizeof(TU) == 4) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v.e[0] = q.x; v.e[1] = q.y; v.e[2] = q.z; v.e[3] = q.w;
+  } else if constexpr (VE == 2 && sizeof(TU) == 8) {
+    double2 q = *reinterpret_cast<const double2*>(p);
+    v.e[0] = q.x; v.e[1] = q.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < VE; ++k) v.e[k] = p[k];
+  }
+  return v;
+}
+
+// x += alpha p and r -= alpha v (do_update), ||r||^2 and W = U^T r partials.
+// Warp w of block b owns rows [(b*PC_WARPS + w) * rows_w, +rows_w).  VE = U
+// elements per vector load (16 bytes, or 1 when ell is not a multiple).
+// Dynamic shared memory: PC_WARPS x (32 * PC_CQ * VE) values of TU.
+template <typename T, typename TU, int VE>
 __global__ void __launch_bounds__(PC_THREADS)
 update_kernel(PcgArgs<T, TU> a, int do_update) {
   const int64_t sidx = blockIdx.y;
   SysState* st = a.st + sidx;
   if (st->done) return;
+  extern __shared__ __align__(16) unsigned char usm[];
+  TU* wsm = reinterpret_cast<TU*>(usm);
   __shared__ double red[32];
-  __shared__ T rs[PC_THREADS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* x = a.x + sidx * a.n;
   T* r = a.r + sidx * a.n;
   const T* p = a.p + sidx * a.n;
   const T* v = a.v + sidx * a.n;
   const double alpha = st->alpha;
-  const int64_t i0 = (int64_t)blockIdx.x * a.rows_u;
-  const int64_t i1 = (i0 + a.rows_u < a.n) ? i0 + a.rows_u : a.n;
-  TU acc[PC_JPT];
-#pragma unroll
-  for (int k = 0; k < PC_JPT; ++k) acc[k] = TU(0);
+  const int64_t row0 = ((int64_t)blockIdx.x * PC_WARPS + warp) * a.rows_w;
+  const int nrg = (int)(a.rows_w / 32 + ((a.rows_w % 32) ? 1 : 0));
+
+  // 1) residual update: lane owns rows row0 + 32 g + lane
+  T rg[PC_MAXRG];
   double rr = 0.0;
-  for (int64_t c0 = i0; c0 < i1; c0 += PC_THREADS) {
-    int64_t i = c0 + threadIdx.x;
-    T ri = T(0);
-    if (i < i1) {
-      ri = r[i];
+#pragma unroll
+  for (int g = 0; g < PC_MAXRG; ++g) {
+    rg[g] = T(0);
+    const int64_t i = row0 + 32 * g + lane;
+    if (g < nrg && 32 * g + lane < a.rows_w && i < a.n) {
+      T ri = r[i];
       if (do_update) {
         x[i] = (T)((double)x[i] + alpha * (double)p[i]);
         ri = (T)((double)ri - alpha * (double)v[i]);
         r[i] = ri;
       }
       rr += (double)ri * (double)ri;
-    }
-    __syncthreads();
-    rs[threadIdx.x] = ri;
-    __syncthreads();
-    if (a.U) {
-      int64_t rows = (i1 - c0 < PC_THREADS) ? i1 - c0 : PC_THREADS;
-      for (int64_t t = 0; t < rows; ++t) {
-        const TU* urow = a.U + (c0 + t) * a.ell;
-        const TU rt = (TU)rs[t];
-#pragma unroll
-        for (int k = 0; k < PC_JPT; ++k) {
-          int64_t j = threadIdx.x + (int64_t)k * PC_THREADS;
-          if (j < a.ell) acc[k] = fma(urow[j], rt, acc[k]);
-        }
-      }
+      rg[g] = ri;
     }
   }
   rr = block_sum(rr, red);
-  double* part = a.dpart + sidx * a.nblk_d;
+  double* part = a.dpart + sidx * a.npart;
   if (threadIdx.x == 0) part[blockIdx.x] = rr;
+
+  // 2) W = U^T r over this block's rows, one column chunk at a time
   if (a.U) {
+    constexpr int CW = 32 * PC_CQ * VE;  // columns per chunk
     TU* wp = a.wpart + (sidx * a.nblk_u + blockIdx.x) * a.ell;
+    const int64_t rows_here = (row0 < a.n) ? ((a.n - row0 < a.rows_w) ? a.n - row0 : a.rows_w) : 0;
+    for (int64_t c0 = 0; c0 < a.ell; c0 += CW) {
+      TU acc[PC_CQ][VE];
 #pragma unroll
-    for (int k = 0; k < PC_JPT; ++k) {
-      int64_t j = threadIdx.x + (int64_t)k * PC_THREADS;
-      if (j < a.ell) wp[j] = acc[k];
+      for (int q = 0; q < PC_CQ; ++q)
+#pragma unroll
+        for (int k = 0; k < VE; ++k) acc[q][k] = TU(0);
+      for (int64_t t0 = 0; t0 < rows_here; t0 += PC_GROUP) {
+#pragma unroll 4
+        for (int tt = 0; tt < PC_GROUP; ++tt) {
+          const int64_t t = t0 + tt;
+          const int g = (int)(t >> 5), src = (int)(t & 31);
+          T rsel = rg[0];
+#pragma unroll
+          for (int gg = 1; gg < PC_MAXRG; ++gg)
+            if (g == gg) rsel = rg[gg];
+          const TU rt = (TU)__shfl_sync(0xffffffffu, rsel, src);
+          if (t < rows_here) {
+            const TU* urow = a.U + (row0 + t) * a.ell + c0;
+#pragma unroll
+            for (int q = 0; q < PC_CQ; ++q) {
+              const int64_t col = (int64_t)(lane + 32 * q) * VE;
+              if (c0 + col < a.ell) {
+                UVec<TU, VE> u = load_uvec<TU, VE>(urow + col);
+#pragma unroll
+                for (int k = 0; k < VE; ++k) acc[q][k] = fma(u.e[k], rt, acc[q][k]);
+              }
+            }
+          }
+        }
+      }
+      // block combine over warps in a fixed order
+#pragma unroll
+      for (int q = 0; q < PC_CQ; ++q)
+#pragma unroll
+        for (int k = 0; k < VE; ++k) wsm[warp * CW + (lane + 32 * q) * VE + k] = acc[q][k];
+      __syncthreads();
+      for (int j = threadIdx.x; j < CW; j += PC_THREADS) {
+        if (c0 + j < a.ell) {
+          TU s = TU(0);
+#pragma unroll
+          for (int w = 0; w < PC_WARPS; ++w) s += wsm[w * CW + j];
+          wp[c0 + j] = s;
+        }
+      }
+      __syncthreads();
     }
   }
-  if (last_block_arrived(a.counters + sidx * 4 + 1)) {
-    double t = 0.0;
-    for (int64_t b = threadIdx.x; b < gridDim.x; b += PC_THREADS) t += __ldcg(part + b);
-    t = block_sum(t, red);
-    if (a.U) {
-      const double lm = st->lam_ell_mu, mu = st->mu;
-      const TU* wp = a.wpart + sidx * a.nblk_u * a.ell;
-      T* w = a.w + sidx * a.ell;
-      for (int64_t j = threadIdx.x; j < a.ell; j += PC_THREADS) {
-        TU s = TU(0);
-        for (int64_t b = 0; b < gridDim.x; ++b) s += __ldcg(wp + b * a.ell + j);
-        double coef = lm / (a.lam[j] + mu) - 1.0;
-        w[j] = (T)(coef * (double)s);
-      }
+}
+
+// w' = coefficient * sum over update blocks of W (fixed order); block 0 also
+// finishes ||r||^2, counts the iteration and records convergence or the cap.  grid.x covers ell
+// in chunks of 32 columns (at least one block).
+template <typename T, typename TU>
+__global__ void __launch_bounds__(PC_THREADS)
+wreduce_kernel(PcgArgs<T, TU> a, int do_update) {
+  const int64_t sidx = blockIdx.y;
+  SysState* st = a.st + sidx;
+  if (st->done) return;
+  __shared__ double red[32];
+  __shared__ TU ws[PC_WARPS][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (a.U) {
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    const TU* wp = a.wpart + sidx * a.nblk_u * a.ell;
+    TU s = TU(0);
+    if (j < a.ell)
+      for (int64_t b = warp; b < a.nblk_u; b += PC_WARPS) s += __ldcg(wp + b * a.ell + j);
+    ws[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && j < a.ell) {
+      TU tot = TU(0);
+#pragma unroll
+      for (int w = 0; w < PC_WARPS; ++w) tot += ws[w][lane];
+      const double coef = st->lam_ell_mu / (a.lam[j] + st->mu) - 1.0;
+      a.w[sidx * a.ell + j] = (T)(coef * (double)tot);
     }
+  }
+  if (blockIdx.x == 0) {
+    const double* part = a.dpart + sidx * a.npart;
+    double t = 0.0;
+    for (int64_t b = threadIdx.x; b < a.nblk_u; b += PC_THREADS) t += __ldcg(part + b);
+    t = block_sum(t, red);
     if (threadIdx.x == 0) {
       st->rr = t;
       if (do_update) st->it += 1;
       if (a.hist) a.hist[sidx * (st->maxit + 1) + st->it] = sqrt(t);
+      // other blocks of this launch still read `done` at entry, so the
+      // decision is recorded in `conv` and published by p_kernel
       if (!isfinite(t)) {
         st->status = NYS_ERR_BREAKDOWN;
-        st->done = 1;
+        st->conv = 1;
       } else if (t <= st->thresh2) {
-        st->done = 1;
+        st->conv = 1;
       } else if (st->it >= st->maxit) {
         st->status = NYS_ERR_MAXIT;
-        st->done = 1;
+        st->conv = 1;
       }
     }
   }
 }
 
-// z = r + U w' (= P^{-1} r), r^T z; last block: beta (setup: rz only).
-template <typename T, typename TU>
+// z = r + U w' (= P^{-1} r), r^T z; last block: beta (setup: rz only).  Same
+// row ownership as update_kernel; w' is staged in shared memory.
+template <typename T, typename TU, int VE>
 __global__ void __launch_bounds__(PC_THREADS)
 z_kernel(PcgArgs<T, TU> a, int setup) {
   const int64_t sidx = blockIdx.y;
   SysState* st = a.st + sidx;
   if (st->done && !setup) return;
-  extern __shared__ unsigned char zsm[];
-  T* ws = reinterpret_cast<T*>(zsm);
+  extern __shared__ __align__(16) unsigned char zsm[];
+  TU* ws = reinterpret_cast<TU*>(zsm);
   __shared__ double red[32];
   const T* r = a.r + sidx * a.n;
   T* z = a.z + sidx * a.n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (a.U)
-    for (int64_t j = threadIdx.x; j < a.ell; j += PC_THREADS) ws[j] = a.w[sidx * a.ell + j];
+    for (int64_t j = threadIdx.x; j < a.ell; j += PC_THREADS) ws[j] = (TU)a.w[sidx * a.ell + j];
   __syncthreads();
+  const int64_t row0 = ((int64_t)blockIdx.x * PC_WARPS + warp) * a.rows_w;
+  const int64_t rows_here = (row0 < a.n) ? ((a.n - row0 < a.rows_w) ? a.n - row0 : a.rows_w) : 0;
   double rz = 0.0;
-  const int64_t wstride = (int64_t)gridDim.x * (PC_THREADS / 32);
-  for (int64_t i = (int64_t)blockIdx.x * (PC_THREADS / 32) + warp; i < a.n; i += wstride) {
-    T zi = r[i];
+  for (int64_t t = 0; t < rows_here; ++t) {
+    const int64_t i = row0 + t;
+    const T ri = r[i];
+    T zi = ri;
     if (a.U) {
       const TU* urow = a.U + i * a.ell;
-      T s = T(0);
-      for (int64_t j = lane; j < a.ell; j += 32) s = fma((T)urow[j], ws[j], s);
+      TU s = TU(0);
+      for (int64_t col = (int64_t)lane * VE; col < a.ell; col += 32 * VE) {
+        UVec<TU, VE> u = load_uvec<TU, VE>(urow + col);
+        UVec<TU, VE> wv = load_uvec<TU, VE>(ws + col);
+#pragma unroll
+        for (int k = 0; k < VE; ++k) s = fma(u.e[k], wv.e[k], s);
+      }
       s = warp_sum(s);
-      zi = zi + s;
+      zi = (T)((double)ri + (double)s);
     }
     if (lane == 0) {
       z[i] = zi;
-      rz += (double)r[i] * (double)zi;
+      rz += (double)ri * (double)zi;
     }
   }
   rz = block_sum(rz, red);
-  double* part = a.dpart + sidx * a.nblk_d;
+  double* part = a.dpart + sidx * a.npart;
   if (threadIdx.x == 0) part[blockIdx.x] = rz;
   if (last_block_arrived(a.counters + sidx * 4 + 2)) {
     double t = 0.0;
@@ -239,6 +335,7 @@ __global__ void p_kernel(PcgArgs<T, TU> a, int setup) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = setup ? z[i] : (T)((double)z[i] + beta * (double)p[i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st->conv) st->done = 1;
 }
 
 // r = b - v (v = A_mu x0) or r = b; x = x0 or 0.
@@ -286,7 +383,6 @@ __global__ void init_state_kernel(const T* __restrict__ b, int64_t n, SysState* 
 template <typename T, typename TU>
 struct PcgBuffers {
   PcgArgs<T, TU> a;
-  SysState* st = nullptr;
   double* d_mu = nullptr;
   void* op_work = nullptr;
   std::vector<void*> allocs;
@@ -298,6 +394,62 @@ struct PcgBuffers {
     NYS_TRY(dmalloc(p, bytes + 256, s));
     allocs.push_back(*p);
     return NYS_OK;
+  }
+};
+
+// Launch geometry shared by PCG and the standalone preconditioner apply.
+template <typename T, typename TU>
+static void plan_geometry(PcgArgs<T, TU>& a) {
+  const int64_t sms = num_sms();
+  // rows per warp: a multiple of 16, enough blocks to cover the GPU twice
+  int64_t rw = cdiv(a.n, 2 * sms * PC_WARPS);
+  rw = cdiv(rw, PC_GROUP) * PC_GROUP;
+  if (rw < PC_GROUP) rw = PC_GROUP;
+  if (rw > 32 * PC_MAXRG) rw = 32 * PC_MAXRG;
+  a.rows_w = rw;
+  a.nblk_u = cdiv(a.n, rw * PC_WARPS);
+  a.nblk_d = 2 * sms;
+  a.npart = a.nblk_u > a.nblk_d ? a.nblk_u : a.nblk_d;
+}
+
+template <typename T, typename TU>
+struct PcgLaunch {
+  bool vec;
+  size_t usm, zsm;
+  dim3 g_u, g_w, g_d;
+  int32_t setup(PcgArgs<T, TU>& a, int64_t nsys) {
+    constexpr int VE = 16 / sizeof(TU);
+    vec = a.U && (a.ell % VE == 0) && (((uintptr_t)a.U & 15u) == 0);
+    const int ve = vec ? VE : 1;
+    usm = (size_t)PC_WARPS * 32 * PC_CQ * ve * sizeof(TU);
+    zsm = a.U ? (size_t)cdiv(a.ell, 4) * 4 * sizeof(TU) : 16;
+    g_u = dim3((unsigned)a.nblk_u, (unsigned)nsys);
+    g_w = dim3((unsigned)(a.U ? cdiv(a.ell, 32) : 1), (unsigned)nsys);
+    g_d = dim3((unsigned)a.nblk_d, (unsigned)nsys);
+    if (zsm > 48 * 1024) {
+      NYS_CUDA_TRY(cudaFuncSetAttribute(z_kernel<T, TU, VE>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
+      NYS_CUDA_TRY(cudaFuncSetAttribute(z_kernel<T, TU, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
+    }
+    return NYS_OK;
+  }
+  void update(PcgArgs<T, TU>& a, int do_update, cudaStream_t s) {
+    constexpr int VE = 16 / sizeof(TU);
+    if (vec)
+      update_kernel<T, TU, VE><<<g_u, PC_THREADS, usm, s>>>(a, do_update);
+    else
+      update_kernel<T, TU, 1><<<g_u, PC_THREADS, usm, s>>>(a, do_update);
+    count_launch();
+    wreduce_kernel<T, TU><<<g_w, PC_THREADS, 0, s>>>(a, do_update); count_launch();
+  }
+  void z(PcgArgs<T, TU>& a, int setup_flag, cudaStream_t s) {
+    constexpr int VE = 16 / sizeof(TU);
+    if (vec)
+      z_kernel<T, TU, VE><<<g_u, PC_THREADS, zsm, s>>>(a, setup_flag);
+    else
+      z_kernel<T, TU, 1><<<g_u, PC_THREADS, zsm, s>>>(a, setup_flag);
+    count_launch();
   }
 };
 
@@ -327,6 +479,7 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   PcgBuffers<T, TU> B;
   B.s = s;
   PcgArgs<T, TU>& a = B.a;
+  memset(&a, 0, sizeof(a));
   a.n = n;
   a.ell = U ? ell : 0;
   a.nsys = nsys;
@@ -334,21 +487,14 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   a.lam = lam;
   a.x = x;
   a.hist = hist;
-  const int sms = num_sms();
-  a.nblk_u = cdiv(n, 64);
-  if (a.nblk_u > 2 * sms) a.nblk_u = 2 * sms;
-  if (a.nblk_u < 1) a.nblk_u = 1;
-  a.rows_u = cdiv(n, a.nblk_u);
-  a.nblk_u = cdiv(n, a.rows_u);
-  a.nblk_d = 2 * sms;
-  if (a.nblk_d < a.nblk_u) a.nblk_d = a.nblk_u;
+  plan_geometry(a);
   const size_t vec = (size_t)nsys * n * sizeof(T);
   NYS_TRY(B.get((void**)&a.r, vec));
   NYS_TRY(B.get((void**)&a.z, vec));
   NYS_TRY(B.get((void**)&a.p, vec));
   NYS_TRY(B.get((void**)&a.v, vec));
   NYS_TRY(B.get((void**)&a.st, nsys * sizeof(SysState)));
-  NYS_TRY(B.get((void**)&a.dpart, (size_t)nsys * a.nblk_d * sizeof(double)));
+  NYS_TRY(B.get((void**)&a.dpart, (size_t)nsys * a.npart * sizeof(double)));
   NYS_TRY(B.get((void**)&a.counters, (size_t)nsys * 4 * sizeof(unsigned)));
   NYS_TRY(B.get((void**)&B.d_mu, nsys * sizeof(double)));
   if (U) {
@@ -361,31 +507,25 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   NYS_CUDA_TRY(cudaMemsetAsync(a.counters, 0, (size_t)nsys * 4 * sizeof(unsigned), s));
   NYS_CUDA_TRY(cudaMemcpyAsync(B.d_mu, mus_host, nsys * sizeof(double), cudaMemcpyHostToDevice, s));
   if (hist) {
-    // NaN padding
     std::vector<double> nanbuf((size_t)nsys * (maxit + 1), std::nan(""));
     NYS_CUDA_TRY(cudaMemcpyAsync(hist, nanbuf.data(), nanbuf.size() * sizeof(double),
                                  cudaMemcpyHostToDevice, s));
     NYS_CUDA_TRY(cudaStreamSynchronize(s));
   }
-  const unsigned gd = (unsigned)a.nblk_d;
-  const dim3 g_d(gd, (unsigned)nsys), g_u((unsigned)a.nblk_u, (unsigned)nsys);
-  const int64_t zblocks = a.nblk_d;
-  const dim3 g_z((unsigned)zblocks, (unsigned)nsys);
-  const size_t zsm = U ? ell * sizeof(T) : 0;
-  if (zsm > 48 * 1024)
-    NYS_CUDA_TRY(cudaFuncSetAttribute(z_kernel<T, TU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)zsm));
+  PcgLaunch<T, TU> L;
+  NYS_TRY(L.setup(a, nsys));
 
   // ---- setup: state, r0, z0 = P^{-1} r0, p0 = z0, r0^T z0
-  init_state_kernel<T><<<(unsigned)nsys, 256, 0, s>>>(b_T, n, a.st, B.d_mu, lam_ell, tol, maxit); count_launch();
+  init_state_kernel<T><<<(unsigned)nsys, 256, 0, s>>>(b_T, n, a.st, B.d_mu, lam_ell, tol, maxit);
+  count_launch();
   if (use_x0) {
     for (int64_t q = 0; q < nsys; ++q)
       NYS_TRY(matvec_T<T>(op, mus_host[q], x + q * n, a.v + q * n, nullptr, B.op_work, s));
   }
-  init_r_kernel<T><<<dim3(gd, (unsigned)nsys), 256, 0, s>>>(b_dev, a.v, a.r, x, n, use_x0); count_launch();
-  update_kernel<T, TU><<<g_u, PC_THREADS, 0, s>>>(a, 0); count_launch();
-  z_kernel<T, TU><<<g_z, PC_THREADS, zsm, s>>>(a, 1); count_launch();
-  p_kernel<T, TU><<<g_d, 256, 0, s>>>(a, 1); count_launch();
+  init_r_kernel<T><<<L.g_d, 256, 0, s>>>(b_dev, a.v, a.r, x, n, use_x0); count_launch();
+  L.update(a, 0, s);
+  L.z(a, 1, s);
+  p_kernel<T, TU><<<L.g_d, 256, 0, s>>>(a, 1); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
 
   // ---- iterations, checked every `chunk`
@@ -396,10 +536,10 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
     for (int c = 0; c < chunk && launched < maxit; ++c, ++launched) {
       for (int64_t q = 0; q < nsys; ++q)
         NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work, s));
-      pv_alpha_kernel<T, TU><<<g_d, PC_THREADS, 0, s>>>(a); count_launch();
-      update_kernel<T, TU><<<g_u, PC_THREADS, 0, s>>>(a, 1); count_launch();
-      z_kernel<T, TU><<<g_z, PC_THREADS, zsm, s>>>(a, 0); count_launch();
-      p_kernel<T, TU><<<g_d, 256, 0, s>>>(a, 0); count_launch();
+      pv_alpha_kernel<T, TU><<<L.g_d, PC_THREADS, 0, s>>>(a); count_launch();
+      L.update(a, 1, s);
+      L.z(a, 0, s);
+      p_kernel<T, TU><<<L.g_d, 256, 0, s>>>(a, 0); count_launch();
     }
     NYS_CUDA_TRY(cudaGetLastError());
     NYS_CUDA_TRY(cudaMemcpyAsync(hst.data(), a.st, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s));
@@ -520,7 +660,7 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   for (int k = 0; k <= max_refine; ++k) {
     // true residual in FP64 for every system
     for (int64_t q = 0; q < nsys; ++q)
-      NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+      NYS_TRY(op_matvec_residual(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
     sub_kernel<<<gb, 256, 0, s>>>(b, v, r, nsys * n); count_launch();
     sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(r, n, nrm); count_launch();
     NYS_CUDA_TRY(cudaMemcpyAsync(rn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -545,7 +685,6 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
     std::vector<double> mua(na);
     for (int64_t t = 0; t < na; ++t) {
       mua[t] = mu[todo[t]];
-      // gather the residual of system todo[t] into slot t (FP64 -> FP32 rhs)
       NYS_CUDA_TRY(cudaMemcpyAsync(v + t * n, r + todo[t] * n, n * sizeof(double),
                                    cudaMemcpyDeviceToDevice, s));
     }
@@ -587,40 +726,32 @@ static int32_t precond_apply_impl(const nys_factor* f, const TU* U, const double
   PcgBuffers<T, TU> B;
   B.s = s;
   PcgArgs<T, TU>& a = B.a;
+  memset(&a, 0, sizeof(a));
   a.n = n;
   a.ell = ell;
   a.nsys = nrhs;
   a.U = U;
   a.lam = f->lam;
   a.hist = nullptr;
-  const int sms = num_sms();
-  a.nblk_u = cdiv(n, 64);
-  if (a.nblk_u > 2 * sms) a.nblk_u = 2 * sms;
-  a.rows_u = cdiv(n, a.nblk_u);
-  a.nblk_u = cdiv(n, a.rows_u);
-  a.nblk_d = 2 * sms;
-  if (a.nblk_d < a.nblk_u) a.nblk_d = a.nblk_u;
+  plan_geometry(a);
   a.r = const_cast<T*>(v);
   a.z = z;
-  a.x = nullptr;
-  a.p = nullptr;
-  a.v = nullptr;
   NYS_TRY(B.get((void**)&a.st, nrhs * sizeof(SysState)));
-  NYS_TRY(B.get((void**)&a.dpart, (size_t)nrhs * a.nblk_d * sizeof(double)));
+  NYS_TRY(B.get((void**)&a.dpart, (size_t)nrhs * a.npart * sizeof(double)));
   NYS_TRY(B.get((void**)&a.counters, (size_t)nrhs * 4 * sizeof(unsigned)));
   NYS_TRY(B.get((void**)&a.wpart, (size_t)nrhs * a.nblk_u * ell * sizeof(TU)));
   NYS_TRY(B.get((void**)&a.w, (size_t)nrhs * ell * sizeof(T)));
   NYS_TRY(B.get((void**)&B.d_mu, nrhs * sizeof(double)));
   NYS_CUDA_TRY(cudaMemsetAsync(a.counters, 0, (size_t)nrhs * 4 * sizeof(unsigned), s));
   NYS_CUDA_TRY(cudaMemcpyAsync(B.d_mu, mu, nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-  // states: done = 0, thresh2 = -1 (never "converged"), maxit large
-  init_state_kernel<T><<<(unsigned)nrhs, 256, 0, s>>>(v, n, a.st, B.d_mu, f->lam_ell, 0.0, 1 << 30); count_launch();
-  const size_t zsm = ell * sizeof(T);
-  if (zsm > 48 * 1024)
-    NYS_CUDA_TRY(cudaFuncSetAttribute(z_kernel<T, TU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)zsm));
-  update_kernel<T, TU><<<dim3((unsigned)a.nblk_u, (unsigned)nrhs), PC_THREADS, 0, s>>>(a, 0); count_launch();
-  z_kernel<T, TU><<<dim3((unsigned)a.nblk_d, (unsigned)nrhs), PC_THREADS, zsm, s>>>(a, 1); count_launch();
+  // states: tol = 0 (never "converged"), cap never reached
+  init_state_kernel<T><<<(unsigned)nrhs, 256, 0, s>>>(v, n, a.st, B.d_mu, f->lam_ell, 0.0,
+                                                       1 << 30);
+  count_launch();
+  PcgLaunch<T, TU> L;
+  NYS_TRY(L.setup(a, nrhs));
+  L.update(a, 0, s);
+  L.z(a, 1, s);
   NYS_CUDA_TRY(cudaGetLastError());
   // keep the buffers alive until the kernels have run
   NYS_CUDA_TRY(cudaStreamSynchronize(s));

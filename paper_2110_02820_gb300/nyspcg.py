@@ -97,6 +97,8 @@ def lib() -> C.CDLL:
         L.nys_gemm_tf32_tn.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
         L.nys_kernel_launch_count.argtypes = []
         L.nys_kernel_launch_count.restype = C.c_uint64
+        L.nys_rbf_cross_matvec.argtypes = [vp, i64, i64, vp, i64, i64, i64, dbl, i64, vp, vp, i32,
+                                           vp]
         for name in EXPORTS:
             f = getattr(L, name)
             if f.restype is C.c_int:  # default
@@ -341,3 +343,16 @@ def nys_gram_matvec_f32_noalloc(op: Operator, mu: float, x: torch.Tensor,
     if x.dtype != torch.float32 or y.dtype != torch.float32:
         raise ValueError("x and y must be float32")
     _check(f(op.ref, float(mu), _ptr(x), _ptr(y), _stream()), "nys_gram_matvec_f32_noalloc")
+
+
+def nys_rbf_cross_matvec(targets: torch.Tensor, points: torch.Tensor, sigma: float,
+                         v: torch.Tensor, kind: int = 0) -> torch.Tensor:
+    """K(targets, points) v (kind 0) or dK/dsigma v (kind 1), FP64 ([nvec][n] or [n])."""
+    vv = v if v.dim() == 2 else v[None]
+    nt, d = targets.shape
+    n = points.shape[0]
+    out = torch.empty((vv.shape[0], nt), dtype=torch.float64, device=v.device)
+    _check(lib().nys_rbf_cross_matvec(_ptr(targets), nt, targets.stride(0), _ptr(points), n,
+                                      points.stride(0), d, float(sigma), vv.shape[0], _ptr(vv),
+                                      _ptr(out), kind, _stream()), "nys_rbf_cross_matvec")
+    return out if v.dim() == 2 else out[0]

@@ -61,6 +61,9 @@ def test_gram_matvec_accurate_and_fast(ny, m, n):
     assert relerr(y64, ref) <= 1e-12
     y32 = ny.nys_op_matvec(op, 1e-3, T(x), mode=1).cpu().numpy()
     assert relerr(y32, ref) <= 1e-5
+    # residual product (double-FP32 on the fused path): FP64-level accuracy
+    yres = ny.nys_op_matvec(op, 1e-3, T(x), mode=2).cpu().numpy()
+    assert relerr(yres, ref) <= 1e-12
 
 
 @pytest.mark.parametrize("n,d", [(777, 7), (1500, 32), (300, 64)])
