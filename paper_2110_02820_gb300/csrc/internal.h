@@ -139,6 +139,12 @@ int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* 
 // v = (A + mu I) p in FP64 arithmetic (FP64 PCG).
 int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double* v,
                       const int* skip, void* work, cudaStream_t s);
+// Batched FP32 matvec V[s] = (A + mu_s I) P[s] for nsys systems sharing the
+// operator (RBF only; NYS_ERR_ARG otherwise, and the caller loops).  d_mu:
+// device [nsys]; done0[s * done_stride] != 0 marks a converged system.
+int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_t nsys,
+                              const float* P, float* V, const int* done0, int64_t done_stride,
+                              cudaStream_t s);
 // Gaussian cross-kernel products (FP64): kind 0 K(t, x) v, kind 1 dK/dsigma v.
 int32_t rbf_cross_matvec(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
                          int64_t ldp, int64_t d, double sigma, int64_t nvec, const double* v,

@@ -53,7 +53,9 @@ __global__ void chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb, int*
 }
 
 // Row panel: C[k:k+nb, c] = C_kk^{-T} M[k:k+nb, c] for c >= k + nb (forward
-// substitution with the lower-triangular C_kk^T); one thread per column.
+// substitution with the lower-triangular C_kk^T).  One warp per column: lane
+// r holds row r; at step r lane r finishes x_r, broadcasts it, and the lanes
+// below subtract its contribution.
 __global__ void chol_panel_kernel(double* M, int64_t ell, int64_t k, int nb, const int* info) {
   if (*info != 0) return;
   __shared__ double Ck[CH_NB][CH_NB + 1];
@@ -62,24 +64,17 @@ __global__ void chol_panel_kernel(double* M, int64_t ell, int64_t k, int nb, con
     Ck[r][c] = M[(k + r) * ell + k + c];
   }
   __syncthreads();
-  int64_t c = k + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t c = k + nb + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= ell) return;
-  double x[CH_NB];
-#pragma unroll
-  for (int r = 0; r < CH_NB; ++r) x[r] = (r < nb) ? M[(k + r) * ell + c] : 0.0;
-#pragma unroll
-  for (int r = 0; r < CH_NB; ++r) {
-    if (r < nb) {
-      double v = x[r];
-#pragma unroll
-      for (int t = 0; t < CH_NB; ++t)
-        if (t < r) v -= Ck[t][r] * x[t];
-      x[r] = v / Ck[r][r];
-    }
+  double m = (lane < nb) ? M[(k + lane) * ell + c] : 0.0;
+  for (int r = 0; r < nb; ++r) {
+    double xr = (lane == r) ? m / Ck[r][r] : 0.0;
+    xr = __shfl_sync(0xffffffffu, xr, r);
+    if (lane == r) m = xr;
+    else if (lane > r && lane < nb) m -= Ck[r][lane] * xr;
   }
-#pragma unroll
-  for (int r = 0; r < CH_NB; ++r)
-    if (r < nb) M[(k + r) * ell + c] = x[r];
+  if (lane < nb) M[(k + lane) * ell + c] = m;
 }
 
 // Trailing update of the upper triangle: M[i, j] -= sum_t C[k+t, i] C[k+t, j]
@@ -120,7 +115,7 @@ int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
     chol_diag_kernel<<<1, dim3(32, 32), 0, s>>>(M, ell, k, nb, d_info); count_launch();
     int64_t rest = ell - k - nb;
     if (rest > 0) {
-      chol_panel_kernel<<<(unsigned)cdiv(rest, 128), 128, 0, s>>>(M, ell, k, nb, d_info); count_launch();
+      chol_panel_kernel<<<(unsigned)cdiv(rest, 8), 256, 0, s>>>(M, ell, k, nb, d_info); count_launch();
       unsigned t = (unsigned)cdiv(rest, 32);
       chol_trail_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(M, ell, k, nb, d_info); count_launch();
     }
@@ -167,15 +162,76 @@ __global__ void transpose_kernel(const double* in, double* out, int64_t rows, in
   }
 }
 
+// Column j of X = C^{-1} by column-oriented back substitution on CT = C^T
+// (row t of CT = column t of C, contiguous): with r_i = sum_{t>i} C_it x_t,
+// x_i = (delta_ij - r_i) / C_ii for i = j, j-1, ..., 0.  One warp per column;
+// r lives in shared memory, and the part of row t-1 of CT that this lane
+// needs (first TI_PF entries) is loaded while step t runs, so a step does not
+// wait on an L2 round trip.  Writes XT[j][i] = X[i][j].
+constexpr int TI_WARPS = 4;
+constexpr int TI_PF = 16;
+__global__ void __launch_bounds__(32 * TI_WARPS)
+tri_inv_cols2_kernel(const double* __restrict__ CT, const double* __restrict__ C, double* XT,
+                     int64_t ell) {
+  extern __shared__ double rsm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * TI_WARPS + wib;
+  if (j >= ell) return;
+  double* r = rsm + (int64_t)wib * ell;
+  double* x = XT + j * ell;
+  for (int64_t i = lane; i < ell; i += 32) {
+    r[i] = 0.0;
+    x[i] = 0.0;
+  }
+  __syncwarp();
+  double xt = 1.0 / C[j * ell + j];
+  if (lane == 0) x[j] = xt;
+  double pf[TI_PF];
+  {
+    const double* row = CT + j * ell;
+#pragma unroll
+    for (int q = 0; q < TI_PF; ++q) {
+      const int64_t i = lane + 32 * q;
+      pf[q] = (i < j) ? row[i] : 0.0;
+    }
+  }
+  for (int64_t t = j; t >= 1; --t) {
+    // r_i -= C[i][t] x_t for i < t, using the prefetched part of row t of CT
+    const double* row = CT + t * ell;
+    double nxt[TI_PF];
+    const double* nrow = CT + (t - 1) * ell;
+#pragma unroll
+    for (int q = 0; q < TI_PF; ++q) {
+      const int64_t i = lane + 32 * q;
+      nxt[q] = (i < t - 1) ? nrow[i] : 0.0;
+      if (i < t) r[i] = fma(pf[q], xt, r[i]);
+    }
+    for (int64_t i = lane + 32 * TI_PF; i < t; i += 32) r[i] = fma(row[i], xt, r[i]);
+    __syncwarp();
+    const int64_t i1 = t - 1;
+    xt = -r[i1] / C[i1 * ell + i1];
+    if (lane == 0) x[i1] = xt;
+#pragma unroll
+    for (int q = 0; q < TI_PF; ++q) pf[q] = nxt[q];
+    __syncwarp();
+  }
+}
+
 int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s) {
-  double* XT = nullptr;
-  NYS_TRY(dmalloc((void**)&XT, ell * ell * sizeof(double), s));
-  tri_inv_cols_kernel<<<(unsigned)cdiv(ell, 4), 128, 0, s>>>(C, XT, ell); count_launch();
+  Scratch sc(s);
+  double *XT, *CT;
+  NYS_TRY(sc.get(&XT, ell * ell));
+  NYS_TRY(sc.get(&CT, ell * ell));
   dim3 g((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 32));
+  transpose_kernel<<<g, dim3(32, 8), 0, s>>>(C, CT, ell, ell); count_launch();
+  const size_t sh = (size_t)TI_WARPS * ell * sizeof(double);
+  if (sh > 48 * 1024)
+    NYS_CUDA_TRY(cudaFuncSetAttribute(tri_inv_cols2_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  tri_inv_cols2_kernel<<<(unsigned)cdiv(ell, TI_WARPS), 32 * TI_WARPS, sh, s>>>(CT, C, XT, ell);
+  count_launch();
   transpose_kernel<<<g, dim3(32, 8), 0, s>>>(XT, X, ell, ell); count_launch();
-  cudaError_t e = cudaGetLastError();
-  dfree(XT, s);
-  NYS_CUDA_TRY(e);
+  NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
 
@@ -268,30 +324,53 @@ __device__ __forceinline__ void round_pair(int64_t npad, int64_t r, int64_t k, i
 }
 
 // One-sided (Hestenes) Jacobi: each warp orthogonalises column pairs of a
-// round; every block is one warp so that the FP64 work of a round spreads
-// over all SMs.  Column norms are carried from the 2x2 rotation
+// round; blocks of JC_WARPS warps spread the FP64 work of a round over all
+// SMs.  Column norms are carried from the 2x2 rotation
 // (alpha' = alpha - t gamma, beta' = beta + t gamma) and recomputed exactly
 // at the start of every sweep, so a pair costs one dot product plus the
-// rotation.
-__global__ void __launch_bounds__(32) jacobi_kernel(JacobiArgs a) {
+// rotation.  Whether any pair rotated is recorded once per block per sweep
+// (not per rotation), which keeps same-address atomics off the round's
+// critical path.
+constexpr int JC_WARPS = 2;
+
+__device__ __forceinline__ double pair_dot(const double* wp, const double* wq, int64_t ell,
+                                           int lane, bool vec2) {
+  double ga = 0.0;
+  if (vec2) {
+    const double2* p2 = reinterpret_cast<const double2*>(wp);
+    const double2* q2 = reinterpret_cast<const double2*>(wq);
+    for (int64_t i = lane; i < ell / 2; i += 32) {
+      const double2 x = p2[i], y = q2[i];
+      ga = fma(x.x, y.x, ga);
+      ga = fma(x.y, y.y, ga);
+    }
+  } else {
+    for (int64_t i = lane; i < ell; i += 32) ga = fma(wp[i], wq[i], ga);
+  }
+  return warp_sum(ga);
+}
+
+__global__ void __launch_bounds__(32 * JC_WARPS) jacobi_kernel(JacobiArgs a) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = blockIdx.x;
-  const int64_t nwarps = gridDim.x;
+  const int64_t warp = (int64_t)blockIdx.x * JC_WARPS + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * JC_WARPS;
   const int64_t npairs = a.npad / 2;
+  const bool vec2 = (a.ell % 2) == 0;
+  __shared__ int blk_rot;
   // Rotate only when the cosine of the angle between the two columns exceeds
   // ell * eps: below that the computed inner product is rounding noise
   // (~eps sqrt(ell)) and further sweeps would not terminate.
   const double tol = (double)(a.ell < 8 ? 8 : a.ell) * 2.220446049250313e-16;
   int sweep = 0;
   for (; sweep < a.max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) blk_rot = 0;
     for (int64_t j = warp; j < a.ell; j += nwarps) {
       const double* wj = a.W + j * a.ell;
-      double acc = 0.0;
-      for (int64_t i = lane; i < a.ell; i += 32) acc = fma(wj[i], wj[i], acc);
-      acc = warp_sum(acc);
+      const double acc = pair_dot(wj, wj, a.ell, lane, vec2);
       if (lane == 0) a.nrm[j] = acc;
     }
     if (!grid_barrier(a.bar, a.bar + 1, a.status)) return;
+    int rotated = 0;
     for (int64_t r = 0; r < a.npad - 1; ++r) {
       for (int64_t k = warp; k < npairs; k += nwarps) {
         int64_t p, q;
@@ -300,26 +379,45 @@ __global__ void __launch_bounds__(32) jacobi_kernel(JacobiArgs a) {
         double* wp = a.W + p * a.ell;
         double* wq = a.W + q * a.ell;
         const double al = a.nrm[p], be = a.nrm[q];
-        double ga = 0.0;
-        for (int64_t i = lane; i < a.ell; i += 32) ga = fma(wp[i], wq[i], ga);
-        ga = warp_sum(ga);
+        const double ga = pair_dot(wp, wq, a.ell, lane, vec2);
         if (fabs(ga) > tol * sqrt(al * be) && al * be > 0.0) {
           const double zeta = (be - al) / (2.0 * ga);
           const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t);
           const double sn = c * t;
-          for (int64_t i = lane; i < a.ell; i += 32) {
-            const double x = wp[i], y = wq[i];
-            wp[i] = c * x - sn * y;
-            wq[i] = sn * x + c * y;
+          if (vec2) {
+            double2* p2 = reinterpret_cast<double2*>(wp);
+            double2* q2 = reinterpret_cast<double2*>(wq);
+            for (int64_t i = lane; i < a.ell / 2; i += 32) {
+              const double2 x = p2[i], y = q2[i];
+              p2[i] = make_double2(c * x.x - sn * y.x, c * x.y - sn * y.y);
+              q2[i] = make_double2(sn * x.x + c * y.x, sn * x.y + c * y.y);
+            }
+          } else {
+            for (int64_t i = lane; i < a.ell; i += 32) {
+              const double x = wp[i], y = wq[i];
+              wp[i] = c * x - sn * y;
+              wq[i] = sn * x + c * y;
+            }
           }
           if (lane == 0) {
             a.nrm[p] = al - t * ga;
             a.nrm[q] = be + t * ga;
-            atomicAdd(&a.rot_count[sweep], 1);
           }
+          rotated = 1;
         }
       }
+      if (r == a.npad - 2) {
+        // last round of the sweep: publish this block's rotation flag before
+        // the barrier that ends the sweep
+        if (lane == 0 && rotated) blk_rot = 1;
+        __syncthreads();
+        if (threadIdx.x == 0 && blk_rot) atomicAdd(&a.rot_count[sweep], 1);
+      }
+      if (!grid_barrier(a.bar, a.bar + 1, a.status)) return;
+    }
+    if (a.npad - 1 == 0) {
+      if (threadIdx.x == 0 && blk_rot) atomicAdd(&a.rot_count[sweep], 1);
       if (!grid_barrier(a.bar, a.bar + 1, a.status)) return;
     }
     volatile int* rc = a.rot_count;
@@ -418,14 +516,16 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int*
   a.status = d_status;
   // one warp per block, as many blocks as pairs, limited to co-resident blocks
   int per_sm = 0;
-  NYS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 32, 0));
-  if (per_sm > 8) per_sm = 8;
-  int64_t want = npad / 2;
+  NYS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel,
+                                                             32 * JC_WARPS, 0));
+  if (per_sm > 2) per_sm = 2;
+  int64_t want = cdiv(npad / 2, JC_WARPS);
   int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
   int blocks = (int)(want < cap ? want : cap);
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
-  NYS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(blocks), dim3(32), args, 0, s));
+  NYS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(blocks), dim3(32 * JC_WARPS),
+                                           args, 0, s));
   count_launch();
   col_norm_kernel<<<(unsigned)cdiv(ell, 8), 256, 0, s>>>(W, ell, sigma); count_launch();
   int64_t pow2 = 1;

@@ -364,16 +364,29 @@ gram_fused_ff_kernel(const float* __restrict__ X, int64_t m, int64_t n,
 }
 
 // v_j = sum_c part[c][j] (fixed order) + mu p_j; optionally r_j = b_j - v_j.
+// Block = 32 columns x 8 warps: warp w sums partials w, w+8, ... of its
+// lane's column, then warp 0 adds the 8 warp sums in order.
 template <typename Acc, typename P, typename V>
-__global__ void gram_reduce_kernel(const Acc* __restrict__ part, int64_t nparts, int64_t n,
-                                   double mu, const P* __restrict__ p, V* __restrict__ v,
-                                   const int* __restrict__ skip) {
+__global__ void __launch_bounds__(256)
+gram_reduce_kernel(const Acc* __restrict__ part, int64_t nparts, int64_t n, double mu,
+                   const P* __restrict__ p, V* __restrict__ v, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  __shared__ Acc ws[8][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + lane;
   Acc acc = Acc(0);
-  for (int64_t c = 0; c < nparts; ++c) acc += part[c * n + j];
-  v[j] = (V)((double)acc + mu * (double)p[j]);
+  if (j < n) {
+#pragma unroll 4
+    for (int64_t c = warp; c < nparts; c += 8) acc += part[c * n + j];
+  }
+  ws[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && j < n) {
+    Acc t = Acc(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += ws[w][lane];
+    v[j] = (V)((double)t + mu * (double)p[j]);
+  }
 }
 
 // Generic two-pass path (any n, any ld): t = X p, then v = X^T t.
@@ -487,7 +500,7 @@ static int32_t gram_matvec(const nys_operator* op, double mu, const P* p, V* v, 
         case 4: NYS_TRY(launch(gram_fused_ff_kernel<4>)); break;
         default: NYS_TRY(launch(gram_fused_ff_kernel<8>)); break;
       }
-      gram_reduce_kernel<double, P, V><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, g.grid, n, mu,
+      gram_reduce_kernel<double, P, V><<<(unsigned)cdiv(n, 32), 256, 0, s>>>(part, g.grid, n, mu,
                                                                              p, v, skip);
       count_launch();
       NYS_CUDA_TRY(cudaGetLastError());
@@ -502,7 +515,7 @@ static int32_t gram_matvec(const nys_operator* op, double mu, const P* p, V* v, 
       case 4: NYS_TRY((gram_fused_launch<P, Acc, 4>(op, g, p, part, err, skip, s))); break;
       default: NYS_TRY((gram_fused_launch<P, Acc, 8>(op, g, p, part, err, skip, s))); break;
     }
-    gram_reduce_kernel<Acc, P, V><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, g.grid, n, mu, p, v,
+    gram_reduce_kernel<Acc, P, V><<<(unsigned)cdiv(n, 32), 256, 0, s>>>(part, g.grid, n, mu, p, v,
                                                                          skip); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     return NYS_OK;
@@ -517,7 +530,7 @@ static int32_t gram_matvec(const nys_operator* op, double mu, const P* p, V* v, 
   dim3 grid((unsigned)cdiv(n, 128), (unsigned)chunks);
   gram_xtt_kernel<Acc><<<grid, 128, 0, s>>>((const float*)op->data, m, n, op->ld, t, rpc, part,
                                             skip); count_launch();
-  gram_reduce_kernel<Acc, P, V><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, chunks, n, mu, p, v,
+  gram_reduce_kernel<Acc, P, V><<<(unsigned)cdiv(n, 32), 256, 0, s>>>(part, chunks, n, mu, p, v,
                                                                        skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
@@ -782,6 +795,101 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
   return NYS_OK;
 }
 
+// ============================================================ batched rbf (FP32)
+//
+// V[s][i] = sum_j K_ij P[s][j] + mu_s P[s][i] for S systems sharing the kernel
+// matrix: each 64 x 32 kernel tile is computed once per 64-system chunk and
+// contracted against all of them (a 64 x 64 x 32 FP32 product per tile), so
+// the exponentials are amortised over the batch.  A chunk whose systems have
+// all converged returns at once.
+constexpr int RB_BI = 64, RB_BJ = 32, RB_BS = 64;
+__global__ void __launch_bounds__(256)
+rbf_batched_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld, double sigma,
+                   int64_t nsys, const double* __restrict__ mus, const float* __restrict__ P,
+                   float* __restrict__ V, const int* __restrict__ done0, int64_t done_stride) {
+  __shared__ float xi[RB_BI][RBF_DMAX + 1];
+  __shared__ float xj[RB_BJ][RBF_DMAX + 1];
+  __shared__ float Ks[RB_BJ][RB_BI + 4];
+  __shared__ float Ps[RB_BJ][RB_BS + 4];
+  __shared__ int any_active;
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * RB_BI, s0 = (int64_t)blockIdx.y * RB_BS;
+  const int64_t ns = (nsys - s0 < RB_BS) ? nsys - s0 : RB_BS;
+  if (tid == 0) {
+    int act = 0;
+    for (int64_t q = 0; q < ns; ++q)
+      if (!done0 || !done0[(s0 + q) * done_stride]) act = 1;
+    any_active = act;
+  }
+  __syncthreads();
+  if (!any_active) return;
+  const float scale = (float)(-1.0 / (2.0 * sigma * sigma));
+  for (int64_t e = tid; e < (int64_t)RB_BI * d; e += 256) {
+    int64_t r = e / d, k = e % d;
+    xi[r][k] = (i0 + r < n) ? pts[(i0 + r) * ld + k] : 0.f;
+  }
+  const int tr = tid / 16, tc = tid % 16;  // 4 rows x 4 systems per thread
+  float acc[4][4] = {};
+  for (int64_t j0 = 0; j0 < n; j0 += RB_BJ) {
+    __syncthreads();
+    for (int64_t e = tid; e < (int64_t)RB_BJ * d; e += 256) {
+      int64_t r = e / d, k = e % d;
+      xj[r][k] = (j0 + r < n) ? pts[(j0 + r) * ld + k] : 0.f;
+    }
+    for (int e = tid; e < RB_BJ * RB_BS; e += 256) {
+      int q = e / RB_BJ, jj = e % RB_BJ;  // coalesced along j
+      Ps[jj][q] = (q < ns && j0 + jj < n) ? P[(s0 + q) * n + j0 + jj] : 0.f;
+    }
+    __syncthreads();
+    for (int e = tid; e < RB_BI * RB_BJ; e += 256) {
+      int r = e % RB_BI, jj = e / RB_BI;
+      float dist = 0.f;
+      for (int k = 0; k < d; ++k) {
+        float df = xi[r][k] - xj[jj][k];
+        dist = fmaf(df, df, dist);
+      }
+      Ks[jj][r] = (j0 + jj < n) ? __expf(dist * scale) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < RB_BJ; ++jj) {
+      float a[4], b[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) a[x] = Ks[jj][tr * 4 + x];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) b[y] = Ps[jj][tc * 4 + y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+    }
+  }
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    const int64_t q = s0 + tc * 4 + y;
+    if (q >= nsys) continue;
+    if (done0 && done0[q * done_stride]) continue;
+    const float mu = (float)mus[q];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int64_t i = i0 + tr * 4 + x;
+      if (i < n) V[q * n + i] = acc[x][y] + mu * P[q * n + i];
+    }
+  }
+}
+
+int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_t nsys,
+                              const float* P, float* V, const int* done0, int64_t done_stride,
+                              cudaStream_t s) {
+  if (op->kind != NYS_OP_RBF) return NYS_ERR_ARG;
+  dim3 grid((unsigned)cdiv(op->n, RB_BI), (unsigned)cdiv(nsys, RB_BS));
+  rbf_batched_kernel<<<grid, 256, 0, s>>>((const float*)op->data, op->n, op->d, op->ld, op->sigma,
+                                          nsys, d_mu, P, V, done0, done_stride);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
 // ============================================================ cross kernel (FP64)
 //
 // out[q][i] = sum_j k(t_i, x_j) v[q][j] with k the Gaussian kernel (kind 0)
@@ -914,7 +1022,7 @@ extern "C" int32_t nys_gram_matvec_f32_noalloc(const nys_operator* op, double mu
     case 4: NYS_TRY((gram_fused_launch<float, float, 4>(op, g, x, part, err, nullptr, s))); break;
     default: NYS_TRY((gram_fused_launch<float, float, 8>(op, g, x, part, err, nullptr, s))); break;
   }
-  gram_reduce_kernel<float, float, float><<<(unsigned)cdiv(op->n, 256), 256, 0, s>>>(
+  gram_reduce_kernel<float, float, float><<<(unsigned)cdiv(op->n, 32), 256, 0, s>>>(
       part, g.grid, op->n, mu, x, y, nullptr); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   int h_err = 0;

@@ -19,6 +19,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -285,23 +286,34 @@ z_kernel(PcgArgs<T, TU> a, int setup) {
   const int64_t row0 = ((int64_t)blockIdx.x * PC_WARPS + warp) * a.rows_w;
   const int64_t rows_here = (row0 < a.n) ? ((a.n - row0 < a.rows_w) ? a.n - row0 : a.rows_w) : 0;
   double rz = 0.0;
-  for (int64_t t = 0; t < rows_here; ++t) {
-    const int64_t i = row0 + t;
-    const T ri = r[i];
-    T zi = ri;
-    if (a.U) {
-      const TU* urow = a.U + i * a.ell;
-      TU s = TU(0);
-      for (int64_t col = (int64_t)lane * VE; col < a.ell; col += 32 * VE) {
-        UVec<TU, VE> u = load_uvec<TU, VE>(urow + col);
-        UVec<TU, VE> wv = load_uvec<TU, VE>(ws + col);
+  constexpr int ZB = 8;  // rows whose U loads are in flight together
+  for (int64_t t0 = 0; t0 < rows_here; t0 += ZB) {
+    TU sp[ZB];
 #pragma unroll
-        for (int k = 0; k < VE; ++k) s = fma(u.e[k], wv.e[k], s);
+    for (int b = 0; b < ZB; ++b) sp[b] = TU(0);
+    if (a.U) {
+      for (int64_t col = (int64_t)lane * VE; col < a.ell; col += 32 * VE) {
+        const UVec<TU, VE> wv = load_uvec<TU, VE>(ws + col);
+#pragma unroll
+        for (int b = 0; b < ZB; ++b) {
+          if (t0 + b < rows_here) {
+            const UVec<TU, VE> u = load_uvec<TU, VE>(a.U + (row0 + t0 + b) * a.ell + col);
+#pragma unroll
+            for (int k = 0; k < VE; ++k) sp[b] = fma(u.e[k], wv.e[k], sp[b]);
+          }
+        }
       }
-      s = warp_sum(s);
-      zi = (T)((double)ri + (double)s);
+#pragma unroll
+      for (int b = 0; b < ZB; ++b) sp[b] = warp_sum(sp[b]);
     }
-    if (lane == 0) {
+    if (lane < ZB && t0 + lane < rows_here) {
+      TU mine = sp[0];
+#pragma unroll
+      for (int b = 1; b < ZB; ++b)
+        if (lane == b) mine = sp[b];
+      const int64_t i = row0 + t0 + lane;
+      const T ri = r[i];
+      const T zi = a.U ? (T)((double)ri + (double)mine) : ri;
       z[i] = zi;
       rz += (double)ri * (double)zi;
     }
@@ -529,13 +541,21 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   NYS_CUDA_TRY(cudaGetLastError());
 
   // ---- iterations, checked every `chunk`
+  const bool batched_rbf = std::is_same<T, float>::value && nsys > 1 && op->kind == NYS_OP_RBF;
   std::vector<SysState> hst(nsys);
   int64_t launched = 0;
   int chunk = 4;
   while (true) {
     for (int c = 0; c < chunk && launched < maxit; ++c, ++launched) {
-      for (int64_t q = 0; q < nsys; ++q)
-        NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work, s));
+      if (batched_rbf) {
+        // one pass over the kernel matrix for all systems
+        NYS_TRY(op_matvec_batched_f32(op, B.d_mu, nsys, (const float*)a.p, (float*)a.v,
+                                      &a.st[0].done, (int64_t)(sizeof(SysState) / sizeof(int)), s));
+      } else {
+        for (int64_t q = 0; q < nsys; ++q)
+          NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work,
+                              s));
+      }
       pv_alpha_kernel<T, TU><<<L.g_d, PC_THREADS, 0, s>>>(a); count_launch();
       L.update(a, 1, s);
       L.z(a, 0, s);

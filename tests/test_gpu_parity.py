@@ -302,6 +302,28 @@ def test_pcg_rbf_mixed_refinement(ny):
     assert relerr(x.cpu().numpy(), xs) <= 1e-5
 
 
+def test_batched_rbf_regularization_path(ny):
+    # 8 shifts log-spaced in [1e-6, 1e-1] n times 4 right-hand sides = 32 systems
+    # sharing one factor; the batched FP32 kernel matvec serves all of them.
+    n, d, ell = 2000, 16, 200
+    P = wl.gmm_points(n, d, seed=41)
+    sigma = wl.median_distance(P, seed=41)
+    mus = np.repeat(wl.regularization_path(8, 1e-6 * n, 1e-1 * n), 4)
+    B = wl.rhs(n, seed=41, nrhs=4)
+    B = np.tile(B, (8, 1))
+    op = ny.rbf_operator(T(P), sigma)
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, 41)), precision=ny.NYS_PREC_MIXED)
+    X, res, _ = ny.pcg_solve(op, f, list(mus), T(B), tol=1e-8, precision=ny.NYS_PREC_MIXED)
+    K = oops.rbf_block(P, P, sigma)
+    Xg = X.cpu().numpy()
+    for s in [0, 5, 13, 22, 31]:
+        assert res[s].status == ny.NYS_OK, (s, res[s])
+        xs = opcg.direct_solve(K, mus[s], B[s])
+        assert relerr(Xg[s], xs) <= 1e-5
+    # systems converge unevenly: larger shifts need fewer iterations
+    assert res[31].iterations < res[0].iterations
+
+
 # ---------------------------------------------------------------- Algorithms 4 and 5
 
 def test_power_error_estimate(ny):
