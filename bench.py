@@ -54,6 +54,13 @@ def parse():
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no matvec, launch-count, e2e or CPU legs); "
                          "used for profiler launch lists")
+    ap.add_argument("--workload", default="ridge",
+                    choices=["ridge", "dense", "krr", "batched", "adjoint"],
+                    help="ridge (default): the headline line; the others measure the remaining "
+                         "workloads of the hot path (dense FP64; adaptive mixed kernel ridge; "
+                         "batched regularisation path; differentiable kernel ridge)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="non-default workloads: multiply the number of points by this factor")
     return ap.parse_args()
 
 
@@ -376,10 +383,144 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- other workloads
+
+def _events_ms(fn, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def run_workload(args):
+    """One JSON line for a non-default workload (solves/sec, per-phase times,
+    the dominant kernel's throughput).  Inputs are resident on the device."""
+    import torch
+
+    from paper_2110_02820_gb300 import nyspcg as ny
+    from paper_2110_02820_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)  # noqa: E731
+    line = {"metric": "PCG solves/sec to rel-residual target", "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "data": "synthetic", "workload": args.workload}
+    launches0 = ny.kernel_launch_count()
+    if args.workload == "dense":
+        n, ell, mu, tol = 2048, 64, 1e-4, 1e-10
+        A, _ = wl.dense_spd(n, seed=0)
+        b = T(wl.rhs(n, seed=0))
+        op = ny.dense_operator(T(A))
+
+        def step(seed):
+            f = ny.nys_sketch(op, ell, seed=seed)
+            x, res, _ = ny.pcg_solve(op, f, mu, b, tol=tol)
+            f.free()
+            return res[0]
+        for w in range(args.warmup):
+            step(100 + w)
+        launches0 = ny.kernel_launch_count()
+        ms, res = _events_ms(lambda: step(7), args.steps)
+        mv_ms, _ = _events_ms(lambda: ny.nys_op_matvec(op, mu, b, mode=0), 20)
+        line.update({"dtype": "f64", "config": {"workload": f"dense FP64 n={n}, lambda_i=(i+1)^-1.5, "
+                                                            f"mu={mu}, ell={ell}, tol={tol}"},
+                     "dominant_kernel": {"kernel": "dense_matvec_kernel<double>",
+                                         "ms_per_launch": mv_ms,
+                                         "gflops_fp64": 2 * n * n / (mv_ms * 1e6),
+                                         "l2_resident_bytes": n * n * 8}})
+    elif args.workload in ("krr", "batched"):
+        if args.workload == "krr":
+            n, d, ell0, ell_max = int(100000 * args.scale), 32, 128, 2048
+        else:
+            n, d, ell = int(50000 * args.scale), 16, 1024
+        P = wl.gmm_points(n, d, seed=0)
+        sigma = wl.median_distance(P, seed=0)
+        op = ny.rbf_operator(T(P), sigma)
+        if args.workload == "krr":
+            mu, tol = 1e-6 * n, 1e-8
+            b = T(wl.rhs(n, seed=0))
+
+            def step(seed):
+                f, info = ny.nys_sketch_adaptive(op, ell0, ell_max, ny.NYS_RULE_RATIO, 40.0, 0, mu,
+                                                 seed=seed, precision=ny.NYS_PREC_MIXED)
+                x, res, _ = ny.pcg_solve(op, f, mu, b, tol=tol, precision=ny.NYS_PREC_MIXED)
+                f.free()
+                return res[0], info
+            cfg = (f"kernel ridge n={n} d={d} GMM(10), sigma=median dist={sigma:.3f}, mu=1e-6 n, "
+                   f"adaptive ratio rule 40, ell {ell0}->{ell_max}, mixed + FP64 refinement, tol {tol}")
+        else:
+            mus = list(np.repeat(wl.regularization_path(32, 1e-8 * n, 1e-1 * n), 4))
+            B = T(np.tile(wl.rhs(n, seed=0, nrhs=4), (32, 1)))
+            tol = 1e-8
+
+            def step(seed):
+                f = ny.nys_sketch(op, ell, seed=seed, precision=ny.NYS_PREC_MIXED)
+                x, res, _ = ny.pcg_solve(op, f, mus, B, tol=tol, precision=ny.NYS_PREC_MIXED)
+                f.free()
+                return res, None
+            cfg = (f"batched regularisation path n={n} d={d}, 32 shifts log-spaced in "
+                   f"[1e-8, 1e-1] n x 4 rhs = 128 systems, ell={ell}, mixed, tol {tol} each")
+        for w in range(args.warmup):
+            step(100 + w)
+        launches0 = ny.kernel_launch_count()
+        ms, (res, info) = _events_ms(lambda: step(7), args.steps)
+        pf = T(wl.rhs(n, seed=3))
+        mv_ms, _ = _events_ms(lambda: ny.nys_op_matvec(op, 0.0, pf, mode=1), 3)
+        line.update({"dtype": "f32", "config": {"workload": cfg},
+                     "dominant_kernel": {"kernel": "rbf_matvec_f32_kernel (SIMT)",
+                                         "ms_per_launch": mv_ms,
+                                         "kernel_entries_per_s": n * n / (mv_ms * 1e-3)}})
+        if args.workload == "krr":
+            line["solve"] = {"iterations": res.iterations, "refinements": res.refinements,
+                             "rel_residual": res.rel_residual, "status": res.status,
+                             "ell": info.ell, "doublings": info.doublings,
+                             "lambda_ell": info.lambda_ell}
+        else:
+            its = [r.iterations for r in res]
+            line["solve"] = {"systems": len(res), "all_ok": all(r.status == 0 for r in res),
+                             "iterations_min": min(its), "iterations_max": max(its),
+                             "worst_rel_residual": max(r.rel_residual for r in res)}
+    else:  # adjoint
+        from paper_2110_02820_gb300 import krr
+        n, nv, d, ell = int(200000 * args.scale), int(10000 * args.scale), 16, 2048
+        P = wl.gmm_points(n, d, seed=0)
+        V = wl.gmm_points(nv, d, seed=1)
+        y, yv = T(wl.krr_targets(P, 0)), T(wl.krr_targets(V, 1))
+        sigma0 = wl.median_distance(P, seed=0)
+        Pt, Vt = T(P), T(V)
+
+        def step(seed):
+            sg = torch.tensor(sigma0, dtype=torch.float64, device=dev, requires_grad=True)
+            m = torch.tensor(1e-6 * n, dtype=torch.float64, device=dev, requires_grad=True)
+            L = krr.validation_loss(Pt, y, Vt, yv, sg, m, ell, precision=ny.NYS_PREC_MIXED,
+                                    tol=1e-8, seed=seed)
+            L.backward()
+            return float(L.detach()), float(m.grad), float(sg.grad)
+        for w in range(args.warmup):
+            step(100 + w)
+        launches0 = ny.kernel_launch_count()
+        ms, out = _events_ms(lambda: step(7), args.steps)
+        line.update({"dtype": "f32", "config": {"workload": f"differentiable KRR n_train={n} "
+                                                            f"n_val={nv} d={d} ell={ell} mixed"},
+                     "solve": {"loss": out[0], "dL_dmu": out[1], "dL_dsigma": out[2]}})
+    line["ms_per_step"] = ms
+    line["value"] = 1e3 / ms
+    line["gpu_launches"] = int(ny.kernel_launch_count() - launches0)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "ridge":
+        run_workload(args)
     else:
         run_ours(args)
 

@@ -166,6 +166,15 @@ int32_t pcg_solve(const nys_operator* op, const nys_factor* f, const double* mu,
 int32_t nys_factor_get(const nys_factor* f, const void** U, int32_t* u_dtype,
                        const double** lambda_hat, int64_t* n, int64_t* ell, double* nu);
 
+/* Diagnostics of a factor (host outputs, each may be NULL): how many times
+ * the shift nu was multiplied by 10 before the Cholesky factorisation of
+ * Omega^T Y_nu succeeded (Algorithm 1), the number of FP32 block-Jacobi
+ * sweeps of the thin SVD of the small factor, the number of FP64
+ * eigen-refinement steps that followed them (0 for a mixed-precision
+ * factor), and lambda_hat_ell. */
+int32_t nys_factor_stats(const nys_factor* f, int32_t* shift_escalations, int32_t* svd_sweeps,
+                         int32_t* svd_refinements, double* lambda_ell);
+
 void nys_factor_free(nys_factor* f);
 
 const char* nys_status_str(int32_t status);

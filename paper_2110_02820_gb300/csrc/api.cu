@@ -283,8 +283,8 @@ static int32_t shifted_core(const T* Q, const T* Y, int64_t n, int64_t ell, bool
   NYS_TRY(Ops<T>::mul_small(Ynu, Ci, n, ell, ell, Bb, s));  // B = Y_nu C^{-1}
   // thin SVD of B: B = Qb R (CholeskyQR2), R = Ut Sigma V^T (one-sided Jacobi)
   NYS_TRY(cholqr<T>(Bb, n, ell, Ynu, R, true, 2, s));
-  int sweeps = 0;
-  NYS_TRY(jacobi_svd(R, Ut, sig, ell, jst, &sweeps, s));
+  int sweeps = 0, refine = 0;
+  NYS_TRY(jacobi_svd(R, Ut, sig, ell, Ops<T>::f64, jst, &sweeps, &refine, s));
   int hj = 0;
   NYS_TRY(read_int(jst, &hj, s));
   if (hj != 0) return NYS_ERR_TIMEOUT;
@@ -293,6 +293,8 @@ static int32_t shifted_core(const T* Q, const T* Y, int64_t n, int64_t ell, bool
   NYS_TRY(read_double(nu, &f->nu, s));
   NYS_TRY(read_double(f->lam + (ell - 1), &f->lam_ell, s));
   f->escalations = esc;
+  f->svd_sweeps = sweeps;
+  f->svd_refine = refine;
   return NYS_OK;
 }
 
@@ -711,6 +713,16 @@ int32_t nys_factor_get(const nys_factor* f, const void** U, int32_t* u_dtype,
   return NYS_OK;
 }
 
+int32_t nys_factor_stats(const nys_factor* f, int32_t* shift_escalations, int32_t* svd_sweeps,
+                         int32_t* svd_refinements, double* lambda_ell) {
+  if (!f) return NYS_ERR_ARG;
+  if (shift_escalations) *shift_escalations = f->escalations;
+  if (svd_sweeps) *svd_sweeps = f->svd_sweeps;
+  if (svd_refinements) *svd_refinements = f->svd_refine;
+  if (lambda_ell) *lambda_ell = f->lam_ell;
+  return NYS_OK;
+}
+
 void nys_factor_free(nys_factor* f) {
   if (!f) return;
   int cur = 0;
@@ -764,7 +776,8 @@ int32_t nys_rbf_cross_matvec(const float* targets, int64_t nt, int64_t ldt, cons
   if (!(sigma > 0.0) || !std::isfinite(sigma) || (kind != 0 && kind != 1)) return NYS_ERR_ARG;
   if ((const void*)v == (const void*)out) return NYS_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  NYS_TRY(rbf_cross_matvec(targets, nt, ldt, points, n, ldp, d, sigma, nvec, v, out, kind, s));
+  NYS_TRY(rbf_dfl_products(targets, nt, ldt, points, n, ldp, d, sigma, kind, nullptr, nvec, v, out,
+                           s));
   NYS_CUDA_TRY(cudaStreamSynchronize(s));
   return NYS_OK;
 }

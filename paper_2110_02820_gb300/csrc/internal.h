@@ -15,6 +15,8 @@ struct nys_factor {
   double nu = 0.0;
   double lam_ell = 0.0;       // host copy of lam[ell-1]
   int32_t escalations = 0;
+  int32_t svd_sweeps = 0;
+  int32_t svd_refine = 0;
   int device = 0;
 };
 
@@ -63,12 +65,14 @@ int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s);
 int32_t symmetrize(double* M, int64_t ell, cudaStream_t s);
 // M += shift * I (shift read from device scalar times factor).
 int32_t add_diag(double* M, int64_t ell, double shift, cudaStream_t s);
-// One-sided Jacobi SVD of the ell x ell matrix R: R = Ut Sigma V^T.  Writes
-// Ut (ell x ell row-major, columns = left singular vectors, sorted so that
-// sigma is descending) and sigma (ell).  *d_status = 0 ok, NYS_ERR_TIMEOUT if
-// a grid barrier wait expired.
-int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, int* d_status,
-                   int* sweeps_out, cudaStream_t s);
+// Thin SVD of the ell x ell matrix R (svd_small.cu): R = Ut Sigma V^T.
+// Writes Ut (ell x ell row-major, columns = left singular vectors, sorted so
+// that sigma is descending) and sigma (ell).  FP32 block Jacobi; with
+// `refine`, FP64 eigen-refinement of R R^T to FP64 accuracy.  *d_status = 0
+// ok, NYS_ERR_TIMEOUT if a grid barrier wait expired.  *sweeps_out /
+// *refine_out (host, may be NULL): Jacobi sweeps and refinement steps.
+int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, bool refine,
+                   int* d_status, int* sweeps_out, int* refine_out, cudaStream_t s);
 
 // ---------------------------------------------------------------- BLAS-like (blas.cu)
 
@@ -145,6 +149,16 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
 int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_t nsys,
                               const float* P, float* V, const int* done0, int64_t done_stride,
                               cudaStream_t s);
+// y_q = (K + mu_q I) v_q, q < nvec, FP64-accurate in double-FP32 arithmetic
+// (rbf_residual.cu).  d_mu: device [nvec].  NYS_ERR_ARG unless RBF, d <= 64.
+int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_t nvec,
+                              const double* v, double* y, cudaStream_t s);
+// Double-FP32 Gaussian products between targets (nt x d) and points (n x d):
+// kind 0 y_q = K(t, x) v_q, kind 1 y_q = dK/dsigma v_q; d_mu (device [nvec],
+// or NULL) adds mu_q v_q and requires targets == points.
+int32_t rbf_dfl_products(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
+                         int64_t ldp, int64_t d, double sigma, int kind, const double* d_mu,
+                         int64_t nvec, const double* v, double* y, cudaStream_t s);
 // Gaussian cross-kernel products (FP64): kind 0 K(t, x) v, kind 1 dK/dsigma v.
 int32_t rbf_cross_matvec(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
                          int64_t ldp, int64_t d, double sigma, int64_t nvec, const double* v,

@@ -582,6 +582,60 @@ rbf_matvec_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t l
   if (i < n) v[i] = (V)((double)acc + mu * (double)p[i]);
 }
 
+// FP32 matvec (inner PCG): with c = -log2(e) / (2 sigma^2),
+//   K_ij = 2^(c ||x_i||^2 + c ||x_j||^2 - 2c x_i . x_j),
+// so a tile stores -2c x_j and c ||x_j||^2 once and each entry costs one
+// d-long FP32 dot, two adds and one exp2.  The norm expansion loses at most
+// ~u (||x_i||^2 + ||x_j||^2) / (2 sigma^2) in the exponent, a relative error
+// of a few u in K_ij for points at the bandwidth scale.
+__global__ void __launch_bounds__(RBF_BI)
+rbf_matvec_f32_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld,
+                      double sigma, const float* __restrict__ p, double mu, float* __restrict__ v,
+                      const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float xs[RBF_BJ][RBF_DMAX + 1];
+  __shared__ float aj[RBF_BJ];
+  __shared__ float ps[RBF_BJ];
+  const int64_t i = (int64_t)blockIdx.x * RBF_BI + threadIdx.x;
+  const float c = (float)(-1.4426950408889634 / (2.0 * sigma * sigma));
+  float xi[RBF_DMAX];
+  float ai = 0.f;
+#pragma unroll
+  for (int k = 0; k < RBF_DMAX; ++k) {
+    xi[k] = (i < n && k < d) ? pts[i * ld + k] : 0.f;
+    ai = fmaf(xi[k], xi[k], ai);
+  }
+  ai *= c;
+  float acc = 0.f;
+  for (int64_t j0 = 0; j0 < n; j0 += RBF_BJ) {
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)RBF_BJ * d; e += RBF_BI) {
+      int64_t jj = e / d, k = e % d;
+      xs[jj][k] = (j0 + jj < n) ? -2.f * c * pts[(j0 + jj) * ld + k] : 0.f;
+    }
+    for (int jj = threadIdx.x; jj < RBF_BJ; jj += RBF_BI) {
+      float s = 0.f;
+      if (j0 + jj < n)
+        for (int64_t k = 0; k < d; ++k) {
+          const float x = pts[(j0 + jj) * ld + k];
+          s = fmaf(x, x, s);
+        }
+      aj[jj] = c * s;
+      ps[jj] = (j0 + jj < n) ? p[j0 + jj] : 0.f;
+    }
+    __syncthreads();
+    const int jn = (int)((n - j0 < RBF_BJ) ? n - j0 : RBF_BJ);
+    for (int jj = 0; jj < jn; ++jj) {
+      float e = ai + aj[jj];
+#pragma unroll
+      for (int k = 0; k < RBF_DMAX; ++k)
+        if (k < d) e = fmaf(xi[k], xs[jj][k], e);
+      acc = fmaf(exp2f(fminf(e, 0.f)), ps[jj], acc);
+    }
+  }
+  if (i < n) v[i] = acc + (float)mu * p[i];
+}
+
 // Y[i][l] = sum_j K_ij Q[j][l] for a 64-row x 64-column output tile per CTA.
 constexpr int RS_BI = 64, RS_BL = 64;
 template <typename T, int RS_BJ = (sizeof(T) == 8 ? 16 : 32)>
@@ -766,7 +820,7 @@ int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* 
     NYS_CUDA_TRY(cudaMemsetAsync(w, 0, 256, s));
     return gram_matvec<float, float, float>(op, mu, p, v, skip, w, s);
   }
-  rbf_matvec_kernel<float, float, float><<<(unsigned)cdiv(n, RBF_BI), RBF_BI, 0, s>>>(
+  rbf_matvec_f32_kernel<<<(unsigned)cdiv(n, RBF_BI), RBF_BI, 0, s>>>(
       (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
@@ -951,6 +1005,15 @@ int32_t rbf_cross_matvec(const float* tg, int64_t nt, int64_t ldt, const float* 
 
 int32_t op_matvec_residual(const nys_operator* op, double mu, const double* p, double* v,
                            const int* skip, void* work, cudaStream_t s) {
+  if (op->kind == NYS_OP_RBF && op->d <= 64) {
+    Scratch sc(s);
+    double* dm;
+    NYS_TRY(sc.get(&dm, 1));
+    NYS_CUDA_TRY(cudaMemcpyAsync(dm, &mu, sizeof(double), cudaMemcpyHostToDevice, s));
+    NYS_TRY(rbf_residual_products(op, dm, 1, p, v, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    return NYS_OK;
+  }
   if (op->kind != NYS_OP_GRAM) return op_matvec_f64(op, mu, p, v, skip, work, s);
   if (work) return gram_matvec<double, double, double>(op, mu, p, v, skip, work, s, true);
   Scratch sc(s);

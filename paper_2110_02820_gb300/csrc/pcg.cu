@@ -413,10 +413,9 @@ struct PcgBuffers {
 template <typename T, typename TU>
 static void plan_geometry(PcgArgs<T, TU>& a) {
   const int64_t sms = num_sms();
-  // rows per warp: a multiple of 16, enough blocks to cover the GPU twice
+  // rows per warp: enough blocks to cover the GPU twice
   int64_t rw = cdiv(a.n, 2 * sms * PC_WARPS);
-  rw = cdiv(rw, PC_GROUP) * PC_GROUP;
-  if (rw < PC_GROUP) rw = PC_GROUP;
+  if (rw < 4) rw = 4;
   if (rw > 32 * PC_MAXRG) rw = 32 * PC_MAXRG;
   a.rows_w = rw;
   a.nblk_u = cdiv(a.n, rw * PC_WARPS);
@@ -671,16 +670,30 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   NYS_TRY(sc.get(&work, wbytes));
   NYS_CUDA_TRY(cudaMemsetAsync(work, 0, 256, s));
   if (!use_x0) NYS_CUDA_TRY(cudaMemsetAsync(x, 0, nsys * n * sizeof(double), s));
+  double* d_mus;
+  NYS_TRY(sc.get(&d_mus, nsys));
+  NYS_CUDA_TRY(cudaMemcpyAsync(d_mus, mu, nsys * sizeof(double), cudaMemcpyHostToDevice, s));
   std::vector<double> bn2(nsys), rn2(nsys);
   sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(b, n, nrm); count_launch();
   NYS_CUDA_TRY(cudaMemcpyAsync(bn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
   std::vector<int> active(nsys, 1), total_it(nsys, 0), outer(nsys, 0), stt(nsys, NYS_ERR_MAXIT);
-  std::vector<double> rel(nsys, 1.0);
+  std::vector<double> rel(nsys, 1.0), prev(nsys, 0.0);
   const unsigned gb = (unsigned)cdiv(n, 256) > 1024 ? 1024 : (unsigned)cdiv(n, 256);
+  // The refinement residual starts in double-FP32 arithmetic (kernel and ridge
+  // operators, ~2^-44 relative per product).  When it stops shrinking while a
+  // system is still above tol, that floor has been reached and the remaining
+  // passes take it in native FP64 (slower on this part, exact to FP64 rounding).
+  bool exact = op->kind == NYS_OP_DENSE;
   for (int k = 0; k <= max_refine; ++k) {
-    // true residual in FP64 for every system
-    for (int64_t q = 0; q < nsys; ++q)
-      NYS_TRY(op_matvec_residual(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+    if (exact) {
+      for (int64_t q = 0; q < nsys; ++q)
+        NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+    } else if (op->kind == NYS_OP_RBF && op->d <= 64) {
+      NYS_TRY(rbf_residual_products(op, d_mus, nsys, x, v, s));
+    } else {
+      for (int64_t q = 0; q < nsys; ++q)
+        NYS_TRY(op_matvec_residual(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+    }
     sub_kernel<<<gb, 256, 0, s>>>(b, v, r, nsys * n); count_launch();
     sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(r, n, nrm); count_launch();
     NYS_CUDA_TRY(cudaMemcpyAsync(rn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -700,6 +713,13 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       }
     }
     if (todo.empty()) break;
+    bool stalled = false;
+    for (int64_t t : todo) stalled |= k > 0 && rel[t] > 0.5 * prev[t];
+    for (int64_t q = 0; q < nsys; ++q) prev[q] = rel[q];
+    if (stalled && !exact) {
+      exact = true;
+      continue;  // the same iterate, its residual retaken in FP64
+    }
     // inner solves for the systems still active (batched over them)
     int64_t na = (int64_t)todo.size();
     std::vector<double> mua(na);

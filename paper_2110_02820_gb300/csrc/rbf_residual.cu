@@ -1,0 +1,242 @@
+// FP64-accurate Gaussian-kernel products in double-FP32 arithmetic, for the
+// refinement residual r = b - (K + mu I) x of the kernel-ridge workloads
+// (Sec. 6.5).  GB300 runs FP64 at a small fraction of its FP32 rate, so each
+// kernel entry is built from pairs of FP32 numbers ("double-float", Dekker
+// 1971) to ~2^-44 relative accuracy:
+//
+//   D_ij = ||x_i||^2 + ||x_j||^2 - 2 x_i . x_j   exact FP32 products (one FMA
+//                                                  each) summed with TwoSum;
+//   K_ij = exp(-D_ij / (2 sigma^2))               own double-float exp: e = k ln2 + r,
+//          r reduced again by 2^-5, expm1(r / 32) by its Taylor series to
+//          degree 8 (truncation < 1e-23), then five squarings
+//          p <- p (p + 2) (expm1(2s) = expm1(s) (expm1(s) + 2)) and a 2^k scale;
+//   y_q[i] = sum_j K_ij x_q[j]                    double-float accumulation.
+//
+// One thread per row i, a tile of points (and their norms) in shared memory,
+// up to RR_Q right-hand sides per launch in registers.
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nys {
+
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl dfl_make(float h, float l) {
+  dfl r;
+  r.hi = h;
+  r.lo = l;
+  return r;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ dfl dfl_norm(float s, float e) {
+  dfl r;
+  r.hi = __fadd_rn(s, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+  return r;
+}
+
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return dfl_norm(s, e);
+}
+
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return dfl_norm(p, e);
+}
+
+__device__ __forceinline__ dfl dfl_mul_f(dfl a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return dfl_norm(p, e);
+}
+
+// acc += a * b for FP32 a, b (exact product, TwoSum accumulation, lazy lo)
+__device__ __forceinline__ void dfl_acc_prod(float a, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  float s, e;
+  two_sum(hi, p, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ dfl dfl_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return dfl_make(h, __double2float_rn(x - (double)h));
+}
+
+// exp(e) for e <= 0 in double-float (see the file comment).
+__device__ __forceinline__ dfl dfl_exp_neg(dfl e, const dfl* inv_fact, dfl ln2) {
+  if (e.hi < -100.f) return dfl_make(0.f, 0.f);
+  const float k = rintf(__fmul_rn(e.hi, 1.4426950408889634f));
+  // r = e - k ln2 in double-float
+  dfl r = dfl_add(e, dfl_mul_f(ln2, -k));
+  // s = r / 32 (exact scaling)
+  dfl s = dfl_make(r.hi * 0.03125f, r.lo * 0.03125f);
+  // expm1(s) = s + s^2/2! + ... + s^8/8!  (Horner)
+  dfl p = inv_fact[8];
+#pragma unroll
+  for (int q = 7; q >= 1; --q) p = dfl_add(dfl_mul(p, s), inv_fact[q]);
+  p = dfl_mul(p, s);
+  // five doublings: expm1(2s) = expm1(s) (expm1(s) + 2)
+#pragma unroll
+  for (int q = 0; q < 5; ++q) p = dfl_mul(p, dfl_add(p, dfl_make(2.f, 0.f)));
+  dfl v = dfl_add(p, dfl_make(1.f, 0.f));
+  const int ki = (int)k;
+  v.hi = ldexpf(v.hi, ki);
+  v.lo = ldexpf(v.lo, ki);
+  return v;
+}
+
+constexpr int RR_BI = 128, RR_BJ = 64, RR_Q = 8, RR_DMAX = 64;
+
+// y[q][i] = sum_j K(t_i, x_j) v[q][j] (+ mu_q v[q][i] when t == x), FP64 out.
+// nrm_t, nrm_x: squared norms of the points in FP64.
+__global__ void __launch_bounds__(RR_BI)
+rbf_residual_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
+                    const double* __restrict__ nrm_t, const float* __restrict__ pts, int64_t n,
+                    int64_t d, int64_t ld, const double* __restrict__ nrm, double neg_inv_2s2,
+                    double inv_s3, int kind, int64_t nvec, const double* __restrict__ mus,
+                    const double* __restrict__ v, double* __restrict__ y) {
+  __shared__ float xs[RR_BJ][RR_DMAX + 1];
+  __shared__ dfl nj[RR_BJ];
+  __shared__ dfl vj[RR_Q][RR_BJ];
+  const int64_t i = (int64_t)blockIdx.x * RR_BI + threadIdx.x;
+  const int64_t q0 = (int64_t)blockIdx.y * RR_Q;
+  const int nq = (int)((nvec - q0 < RR_Q) ? nvec - q0 : RR_Q);
+  dfl inv_fact[9];
+  {
+    double f = 1.0;
+    inv_fact[0] = dfl_make(1.f, 0.f);
+#pragma unroll
+    for (int q = 1; q <= 8; ++q) {
+      f /= (double)q;
+      inv_fact[q] = dfl_from_double(f);
+    }
+  }
+  const dfl ln2 = dfl_from_double(0.6931471805599453094);
+  const dfl scale = dfl_from_double(neg_inv_2s2);
+  float xi[RR_DMAX];
+#pragma unroll
+  for (int k = 0; k < RR_DMAX; ++k) xi[k] = (i < nt && k < d) ? tg[i * ldt + k] : 0.f;
+  const dfl ni = dfl_from_double(i < nt ? nrm_t[i] : 0.0);
+  const dfl s3 = dfl_from_double(inv_s3);
+  float ah[RR_Q], al[RR_Q];
+#pragma unroll
+  for (int q = 0; q < RR_Q; ++q) {
+    ah[q] = 0.f;
+    al[q] = 0.f;
+  }
+  for (int64_t j0 = 0; j0 < n; j0 += RR_BJ) {
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)RR_BJ * d; e += RR_BI) {
+      int64_t jj = e / d, k = e % d;
+      xs[jj][k] = (j0 + jj < n) ? pts[(j0 + jj) * ld + k] : 0.f;
+    }
+    for (int jj = threadIdx.x; jj < RR_BJ; jj += RR_BI) {
+      nj[jj] = dfl_from_double(j0 + jj < n ? nrm[j0 + jj] : 0.0);
+      for (int q = 0; q < RR_Q; ++q)
+        vj[q][jj] = dfl_from_double((q < nq && j0 + jj < n) ? v[(q0 + q) * n + j0 + jj] : 0.0);
+    }
+    __syncthreads();
+    const int jn = (int)((n - j0 < RR_BJ) ? n - j0 : RR_BJ);
+    for (int jj = 0; jj < jn; ++jj) {
+      // dot = x_i . x_j exactly enough (double-float)
+      float dh = 0.f, dl = 0.f;
+#pragma unroll
+      for (int k = 0; k < RR_DMAX; ++k)
+        if (k < d) dfl_acc_prod(xi[k], xs[jj][k], dh, dl);
+      dfl dot = dfl_norm(dh, dl);
+      // D = ||x_i||^2 + ||x_j||^2 - 2 dot  (clamped at 0)
+      dfl D = dfl_add(dfl_add(ni, nj[jj]), dfl_make(-2.f * dot.hi, -2.f * dot.lo));
+      if (D.hi < 0.f) D = dfl_make(0.f, 0.f);
+      dfl Kij = dfl_exp_neg(dfl_mul(D, scale), inv_fact, ln2);
+      if (kind == 1) Kij = dfl_mul(Kij, dfl_mul(D, s3));  // dK/dsigma = K D / sigma^3
+#pragma unroll
+      for (int q = 0; q < RR_Q; ++q) {
+        if (q < nq) {
+          // acc += K * v with double-float operands
+          const dfl vv = vj[q][jj];
+          const float p = __fmul_rn(Kij.hi, vv.hi);
+          float e = __fmaf_rn(Kij.hi, vv.hi, -p);
+          e = __fmaf_rn(Kij.hi, vv.lo, e);
+          e = __fmaf_rn(Kij.lo, vv.hi, e);
+          float s, e2;
+          two_sum(ah[q], p, s, e2);
+          ah[q] = s;
+          al[q] = __fadd_rn(al[q], __fadd_rn(e2, e));
+        }
+      }
+    }
+  }
+  if (i < nt) {
+#pragma unroll
+    for (int q = 0; q < RR_Q; ++q)
+      if (q < nq) {
+        const int64_t g = q0 + q;
+        double out = (double)ah[q] + (double)al[q];
+        if (mus) out += mus[g] * v[g * n + i];  // only when targets are the points
+        y[g * nt + i] = out;
+      }
+  }
+}
+
+__global__ void sq_norms_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld,
+                                double* __restrict__ nrm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t k = 0; k < d; ++k) {
+    const double x = (double)pts[i * ld + k];
+    s = fma(x, x, s);
+  }
+  nrm[i] = s;
+}
+
+// y_q = (K + mu_q I) v_q for q < nvec (device FP64 arrays), FP64-accurate.
+int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_t nvec,
+                              const double* v, double* y, cudaStream_t s) {
+  if (op->kind != NYS_OP_RBF || op->d > RR_DMAX) return NYS_ERR_ARG;
+  const float* pts = (const float*)op->data;
+  return rbf_dfl_products(pts, op->n, op->ld, pts, op->n, op->ld, op->d, op->sigma, 0, d_mu, nvec,
+                          v, y, s);
+}
+
+int32_t rbf_dfl_products(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
+                         int64_t ldp, int64_t d, double sigma, int kind, const double* d_mu,
+                         int64_t nvec, const double* v, double* y, cudaStream_t s) {
+  if (d > RR_DMAX) return NYS_ERR_ARG;
+  Scratch sc(s);
+  double *nrm, *nrm_t;
+  NYS_TRY(sc.get(&nrm, n));
+  NYS_TRY(sc.get(&nrm_t, nt));
+  sq_norms_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(pts, n, d, ldp, nrm);
+  count_launch();
+  sq_norms_kernel<<<(unsigned)cdiv(nt, 256), 256, 0, s>>>(tg, nt, d, ldt, nrm_t);
+  count_launch();
+  dim3 grid((unsigned)cdiv(nt, RR_BI), (unsigned)cdiv(nvec, RR_Q));
+  rbf_residual_kernel<<<grid, RR_BI, 0, s>>>(tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm,
+                                             -1.0 / (2.0 * sigma * sigma),
+                                             1.0 / (sigma * sigma * sigma), kind, nvec, d_mu, v, y);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+}  // namespace nys

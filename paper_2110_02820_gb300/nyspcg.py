@@ -208,6 +208,18 @@ class Factor:
             return torch.as_tensor(_CudaArray(self._lam, (self.ell,), "<f8"),
                                    device=f"cuda:{self.device}").clone()
 
+    def stats(self) -> dict:
+        """Shift escalations, SVD sweeps and refinement steps, lambda_hat_ell."""
+        f = lib().nys_factor_stats
+        if f.argtypes is None:
+            f.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                          C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+            f.restype = C.c_int32
+        e, sw, rf, le = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+        _check(f(self.h, C.byref(e), C.byref(sw), C.byref(rf), C.byref(le)), "nys_factor_stats")
+        return {"shift_escalations": e.value, "svd_sweeps": sw.value,
+                "svd_refinements": rf.value, "lambda_ell": le.value}
+
     def free(self) -> None:
         if self.h is not None and self.h.value:
             lib().nys_factor_free(self.h)

@@ -77,6 +77,10 @@ def test_rbf_matvec_accurate_and_fast(ny, n, d):
     assert relerr(y64, ref) <= 1e-12
     y32 = ny.nys_op_matvec(op, 0.1, T(x), mode=1).cpu().numpy()
     assert relerr(y32, ref) <= 1e-5
+    # residual product: double-FP32 distances and exponential, FP64-level accuracy
+    yres = ny.nys_op_matvec(op, 0.1, T(x), mode=2).cpu().numpy()
+    assert relerr(yres, ref) <= 1e-12
+    np.testing.assert_allclose(yres, ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
 
 
 # ---------------------------------------------------------------- Algorithm 1
