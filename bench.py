@@ -86,14 +86,22 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
+def max_over_ranks(v, world, device="cuda"):
+    """Largest value over the ranks (the slowest replica's time); `device` is
+    "cuda" under NCCL, "cpu" under gloo."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(ms_per_step_max, world):
+    """Whole-job solves/s for replicas: every rank completes one solve per
+    step, and the job's step time is the slowest rank's."""
+    return world * 1e3 / ms_per_step_max
 
 
 # ---------------------------------------------------------------- clocks
@@ -293,7 +301,12 @@ def run_ours(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = max_over_ranks(ms, world)
-    value = world * 1e3 / ms
+    bad = [it for it in iters if it[3] != 0]
+    if bad:
+        # a solve that missed the residual target is not a solve of the metric
+        sys.stderr.write(f"bench: {len(bad)} of {len(iters)} timed solves did not converge: {bad[0]}\n")
+        sys.exit(3)
+    value = job_throughput(ms, world)
     if args.solve_only:
         if rank == 0:
             print(json.dumps({"solve_only": True, "ms_per_step": ms, "value": value,
@@ -427,6 +440,8 @@ def run_workload(args):
             step(100 + w)
         launches0 = ny.kernel_launch_count()
         ms, res = _events_ms(lambda: step(7), args.steps)
+        line["solve"] = {"iterations": res.iterations, "rel_residual": res.rel_residual,
+                         "status": res.status}
         mv_ms, _ = _events_ms(lambda: ny.nys_op_matvec(op, mu, b, mode=0), 20)
         line.update({"dtype": "f64", "config": {"workload": f"dense FP64 n={n}, lambda_i=(i+1)^-1.5, "
                                                             f"mu={mu}, ell={ell}, tol={tol}"},
@@ -509,6 +524,10 @@ def run_workload(args):
         line.update({"dtype": "f32", "config": {"workload": f"differentiable KRR n_train={n} "
                                                             f"n_val={nv} d={d} ell={ell} mixed"},
                      "solve": {"loss": out[0], "dL_dmu": out[1], "dL_dsigma": out[2]}})
+    sol = line.get("solve", {})
+    if sol.get("status", 0) != 0 or sol.get("all_ok", True) is False:
+        sys.stderr.write(f"bench: the {args.workload} solve did not converge: {sol}\n")
+        sys.exit(3)
     line["ms_per_step"] = ms
     line["value"] = 1e3 / ms
     line["gpu_launches"] = int(ny.kernel_launch_count() - launches0)

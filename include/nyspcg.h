@@ -170,8 +170,7 @@ int32_t nys_factor_get(const nys_factor* f, const void** U, int32_t* u_dtype,
  * the shift nu was multiplied by 10 before the Cholesky factorisation of
  * Omega^T Y_nu succeeded (Algorithm 1), the number of FP32 block-Jacobi
  * sweeps of the thin SVD of the small factor, the number of FP64
- * eigen-refinement steps that followed them (0 for a mixed-precision
- * factor), and lambda_hat_ell. */
+ * eigen-refinement steps that followed them, and lambda_hat_ell. */
 int32_t nys_factor_stats(const nys_factor* f, int32_t* shift_escalations, int32_t* svd_sweeps,
                          int32_t* svd_refinements, double* lambda_ell);
 
@@ -188,8 +187,11 @@ uint64_t nys_kernel_launch_count(void);
  * FP64 arithmetic (the product inside FP64 PCG); mode 1: the FP32 product
  * used inside mixed-precision PCG; mode 2: the FP64-accurate product of the
  * mixed path's refinement residual (double-FP32 arithmetic for the ridge
- * operator, ~2^-44 relative; FP64 for the others).  Exposed so that each
- * operator kernel can be checked on its own.  Synchronises `stream`. */
+ * operator and the Gaussian kernel, ~2^-44 relative; FP64 for dense).
+ * For the Gaussian kernel with d <= 32, mode 1 runs on the tensor cores
+ * (3xTF32 products, FP32 accuracy), all nvec vectors in one pass over the
+ * kernel matrix.  Exposed so that each operator kernel can be checked on
+ * its own.  Synchronises `stream`. */
 int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const double* x, double* y,
                       int32_t mode, void* stream);
 

@@ -21,9 +21,11 @@ Nystrom Preconditioning", arXiv 2110.02820) step by step:
 * ``pcg``        Algorithm 3 (Nystrom PCG), its independent-batch form, and
   FP64-residual iterative refinement around a float32 inner solve;
 * ``krr``        the KRR validation loss and its gradient by implicit
-  differentiation (adjoint solve);
-* ``philox``     the Philox4x32-10 counter-based generator with the
-  Box-Muller transform, written from Salmon et al. (SC'11).
+  differentiation (adjoint solve).
+
+The random test matrix Omega and the power-step start vectors are inputs:
+the parity tests draw them from ``workloads`` and pass the same arrays to
+both sides.
 
 Parity pins: every function here is checked by the ``-m "not gpu"`` tests
 against closed forms, invariants, library routines or brute force on tiny

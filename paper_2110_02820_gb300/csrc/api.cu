@@ -284,7 +284,10 @@ static int32_t shifted_core(const T* Q, const T* Y, int64_t n, int64_t ell, bool
   // thin SVD of B: B = Qb R (CholeskyQR2), R = Ut Sigma V^T (one-sided Jacobi)
   NYS_TRY(cholqr<T>(Bb, n, ell, Ynu, R, true, 2, s));
   int sweeps = 0, refine = 0;
-  NYS_TRY(jacobi_svd(R, Ut, sig, ell, Ops<T>::f64, jst, &sweeps, &refine, s));
+  // The FP64 refinement runs for both precisions: the preconditioner needs U
+  // orthonormal far below (lambda_ell + mu) / lambda_1, beyond what the FP32
+  // rotations leave (~1e-6).
+  NYS_TRY(jacobi_svd(R, Ut, sig, ell, true, jst, &sweeps, &refine, s));
   int hj = 0;
   NYS_TRY(read_int(jst, &hj, s));
   if (hj != 0) return NYS_ERR_TIMEOUT;
@@ -758,8 +761,15 @@ int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const dou
     NYS_TRY(sc.get(&xf, nvec * n));
     NYS_TRY(sc.get(&yf, nvec * n));
     NYS_TRY(convert_f64_to_f32(x, xf, nvec * n, s));
-    for (int64_t q = 0; q < nvec; ++q)
-      NYS_TRY(op_matvec_f32(op, mu, xf + q * n, yf + q * n, nullptr, work, s));
+    if (op->kind == NYS_OP_RBF && nvec > 1 && rbf_tc_supported(op->d)) {
+      // all vectors in one pass over the kernel matrix
+      NYS_TRY(rbf_tc_products((const float*)op->data, n, op->d, op->ld, op->sigma, nvec, xf, n, 1,
+                              nullptr, mu, yf, n, 3, nullptr, 0, nullptr,
+                              reinterpret_cast<int*>(work), s));
+    } else {
+      for (int64_t q = 0; q < nvec; ++q)
+        NYS_TRY(op_matvec_f32(op, mu, xf + q * n, yf + q * n, nullptr, work, s));
+    }
     NYS_TRY(convert_f32_to_f64(yf, y, nvec * n, s));
   }
   int err = 0;

@@ -148,7 +148,7 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
 // device [nsys]; done0[s * done_stride] != 0 marks a converged system.
 int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_t nsys,
                               const float* P, float* V, const int* done0, int64_t done_stride,
-                              cudaStream_t s);
+                              int* err, cudaStream_t s);
 // y_q = (K + mu_q I) v_q, q < nvec, FP64-accurate in double-FP32 arithmetic
 // (rbf_residual.cu).  d_mu: device [nvec].  NYS_ERR_ARG unless RBF, d <= 64.
 int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_t nvec,
@@ -163,6 +163,20 @@ int32_t rbf_dfl_products(const float* tg, int64_t nt, int64_t ldt, const float* 
 int32_t rbf_cross_matvec(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
                          int64_t ldp, int64_t d, double sigma, int64_t nvec, const double* v,
                          double* out, int kind, cudaStream_t s);
+// Gaussian-kernel products on the tensor cores (rbf_tc.cu), d <= 32:
+// Y[q] = K V[q] (+ shift), q < nvec, V and Y vector-major FP32 (row strides
+// ldv, ldy).  shift: 0 none, 1 mu0 V[q], 2 d_mu[q] V[q] (d_mu device).
+// passes: 3 (3xTF32 products, FP32 accuracy) or 1 (TF32).  done0 (device,
+// may be NULL): a block of vectors whose done0[q * done_stride] are all
+// nonzero is skipped.  work: NULL, or rbf_tc_work_bytes() bytes whose first
+// word is the device error word (err defaults to it; NYS_ERR_TIMEOUT is
+// written there if a bounded wait expired).
+bool rbf_tc_supported(int64_t d);
+size_t rbf_tc_work_bytes(int64_t n, int64_t nvec, int passes);
+int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, double sigma,
+                        int64_t nvec, const float* V, int64_t ldv, int shift, const double* d_mu,
+                        double mu0, float* Y, int64_t ldy, int passes, const int* done0,
+                        int64_t done_stride, void* work, int* err, cudaStream_t s);
 // FP64-accurate v = (A + mu I) p for the refinement residual: the ridge
 // operator in double-FP32 arithmetic (~2^-44 relative), the others in FP64.
 int32_t op_matvec_residual(const nys_operator* op, double mu, const double* p, double* v,

@@ -703,6 +703,10 @@ rbf_sketch_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t l
 
 // ============================================================ dispatch
 
+// Passes of the tensor-core kernel-times-test-matrix product in the
+// mixed-precision sketch: TF32 kernel entries against TF32 Omega.
+constexpr int kRbfSketchPasses = 1;
+
 int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int64_t ell,
                   cudaStream_t s) {
   const int64_t n = op->n;
@@ -787,6 +791,24 @@ int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int6
     return gemm_f32(true, n, ell, m, X, op->ld, Z, ell, (float*)V, ell, s);
   }
   // RBF
+  if (!f64 && rbf_tc_supported(op->d)) {
+    // tensor cores: Y^T = K Q^T with the vectors of the sketch as rows
+    Scratch sc(s);
+    float *Qt, *Yt;
+    int* err;
+    NYS_TRY(sc.get(&Qt, ell * n));
+    NYS_TRY(sc.get(&Yt, ell * n));
+    NYS_TRY(sc.get(&err, 1));
+    NYS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    NYS_TRY(transpose_f32((const float*)Q, n, ell, ell, Qt, s));
+    NYS_TRY(rbf_tc_products((const float*)op->data, n, op->d, op->ld, op->sigma, ell, Qt, n, 0,
+                            nullptr, 0.0, Yt, n, kRbfSketchPasses, nullptr, 0, nullptr, err, s));
+    NYS_TRY(transpose_f32(Yt, ell, n, n, (float*)V, s));
+    int h_err = 0;
+    NYS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    return h_err ? NYS_ERR_TIMEOUT : NYS_OK;
+  }
   dim3 grid((unsigned)cdiv(n, RS_BI), (unsigned)cdiv(ell, RS_BL));
   if (f64)
     rbf_sketch_kernel<double><<<grid, 256, 0, s>>>((const float*)op->data, n, op->d, op->ld,
@@ -800,6 +822,7 @@ int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int6
 
 size_t op_matvec_work_bytes(const nys_operator* op, bool accurate) {
   if (op->kind == NYS_OP_GRAM) return gram_work_bytes(op, accurate ? sizeof(double) : sizeof(float));
+  if (op->kind == NYS_OP_RBF && rbf_tc_supported(op->d)) return rbf_tc_work_bytes(op->n, 1, 3);
   return 256;
 }
 
@@ -820,6 +843,9 @@ int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* 
     NYS_CUDA_TRY(cudaMemsetAsync(w, 0, 256, s));
     return gram_matvec<float, float, float>(op, mu, p, v, skip, w, s);
   }
+  if (rbf_tc_supported(op->d))
+    return rbf_tc_products((const float*)op->data, n, op->d, op->ld, op->sigma, 1, p, n, 1, nullptr,
+                           mu, v, n, 3, skip, 0, work, nullptr, s);
   rbf_matvec_f32_kernel<<<(unsigned)cdiv(n, RBF_BI), RBF_BI, 0, s>>>(
       (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
@@ -934,8 +960,11 @@ rbf_batched_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t 
 
 int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_t nsys,
                               const float* P, float* V, const int* done0, int64_t done_stride,
-                              cudaStream_t s) {
+                              int* err, cudaStream_t s) {
   if (op->kind != NYS_OP_RBF) return NYS_ERR_ARG;
+  if (rbf_tc_supported(op->d))
+    return rbf_tc_products((const float*)op->data, op->n, op->d, op->ld, op->sigma, nsys, P, op->n,
+                           2, d_mu, 0.0, V, op->n, 3, done0, done_stride, nullptr, err, s);
   dim3 grid((unsigned)cdiv(op->n, RB_BI), (unsigned)cdiv(nsys, RB_BS));
   rbf_batched_kernel<<<grid, 256, 0, s>>>((const float*)op->data, op->n, op->d, op->ld, op->sigma,
                                           nsys, d_mu, P, V, done0, done_stride);

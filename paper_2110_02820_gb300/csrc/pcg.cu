@@ -549,7 +549,8 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
       if (batched_rbf) {
         // one pass over the kernel matrix for all systems
         NYS_TRY(op_matvec_batched_f32(op, B.d_mu, nsys, (const float*)a.p, (float*)a.v,
-                                      &a.st[0].done, (int64_t)(sizeof(SysState) / sizeof(int)), s));
+                                      &a.st[0].done, (int64_t)(sizeof(SysState) / sizeof(int)),
+                                      reinterpret_cast<int*>(B.op_work), s));
       } else {
         for (int64_t q = 0; q < nsys; ++q)
           NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work,
@@ -680,14 +681,17 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   std::vector<double> rel(nsys, 1.0), prev(nsys, 0.0);
   const unsigned gb = (unsigned)cdiv(n, 256) > 1024 ? 1024 : (unsigned)cdiv(n, 256);
   // The refinement residual starts in double-FP32 arithmetic (kernel and ridge
-  // operators, ~2^-44 relative per product).  When it stops shrinking while a
-  // system is still above tol, that floor has been reached and the remaining
-  // passes take it in native FP64 (slower on this part, exact to FP64 rounding).
+  // operators, ~2^-44 relative per product, enough for tol >= 1e-10 at the
+  // conditioning seen here).  Below that, when the residual of a system stops
+  // shrinking while it is still above tol, the floor of that arithmetic has
+  // been reached and the remaining passes take the residual of the systems
+  // still active in native FP64 (slower on this part, exact to FP64 rounding).
   bool exact = op->kind == NYS_OP_DENSE;
+  const bool may_escalate = !exact && tol < 1e-10;
   for (int k = 0; k <= max_refine; ++k) {
     if (exact) {
       for (int64_t q = 0; q < nsys; ++q)
-        NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+        if (active[q]) NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
     } else if (op->kind == NYS_OP_RBF && op->d <= 64) {
       NYS_TRY(rbf_residual_products(op, d_mus, nsys, x, v, s));
     } else {
@@ -700,8 +704,8 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
     NYS_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<int64_t> todo;
     for (int64_t q = 0; q < nsys; ++q) {
+      if (!active[q]) continue;  // its residual was not retaken
       rel[q] = bn2[q] > 0 ? sqrt(rn2[q] / bn2[q]) : sqrt(rn2[q]);
-      if (!active[q]) continue;
       if (rel[q] <= tol) {
         active[q] = 0;
         stt[q] = NYS_OK;
@@ -716,7 +720,7 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
     bool stalled = false;
     for (int64_t t : todo) stalled |= k > 0 && rel[t] > 0.5 * prev[t];
     for (int64_t q = 0; q < nsys; ++q) prev[q] = rel[q];
-    if (stalled && !exact) {
+    if (stalled && may_escalate && !exact) {
       exact = true;
       continue;  // the same iterate, its residual retaken in FP64
     }

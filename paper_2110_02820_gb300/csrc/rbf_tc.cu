@@ -1,0 +1,660 @@
+// Gaussian-kernel products on the 5th-generation tensor cores (sm_103a):
+//
+//   Y[s][i] = sum_j exp(-||x_i - x_j||^2 / (2 sigma^2)) V[s][j]  (+ mu_s V[s][i])
+//
+// for a block of vectors s, computed on the fly (the kernel matrix is never
+// stored).  This is the matrix-free operator of kernel ridge regression
+// (Sec. 6.2) applied inside PCG (one vector per system, Algorithm 3), to a
+// batch of systems that share the kernel (a regularisation path), and to
+// the n x ell test matrix of the sketch Y = K Omega (Algorithm 1).
+//
+// The exponent is formed by norm expansion,
+//   -||x_i - x_j||^2 / (2 sigma^2) log2(e) = cn_i + cn_j + m2c <x_i, x_j>,
+// with cn_i = -log2(e) ||x_i||^2 / (2 sigma^2) and m2c = log2(e) / sigma^2,
+// so the inner products form a GEMM with K = d.  That GEMM cancels: for
+// points far from the origin the inner product is much larger than the
+// distance, so it runs as 3xTF32 (x = hi + lo, each TF32; hi.hi + hi.lo +
+// lo.hi), which keeps it at FP32 accuracy.
+//
+// One CTA owns 128 rows i and sweeps all points j in tiles of 64:
+//   warp 0, lane 0: TMA producer.  X_I (hi, lo) once; per tile a stage of
+//                   X_J (hi, lo), cn_J and the tile's slice of the vectors,
+//                   into an NS-deep ring.
+//   warp 1, lane 0: MMA issuer.  GEMM1(t): P = X_I X_J^T (3 passes, K = 8
+//                   per MMA, into one of two 128 x 64 TMEM buffers).  With
+//                   several vectors, GEMM2(t-1): Yacc += K_{t-1} V_{t-1},
+//                   the kernel tile K read from TMEM as the A operand (3
+//                   passes, or 1 for the sketch).  Warp 1 also owns TMEM.
+//   warps 2..9:     two exp groups of four warps that take alternate tiles
+//                   (group g owns P / K buffer g), one thread per row i:
+//                   tcgen05.ld of the 64 inner products, k = 2^(cn_i + cn_j +
+//                   m2c p); then either (one vector) acc_i += k v_j on the
+//                   FP32 pipe, or the TF32 hi / lo split of k stored into the
+//                   tile's TMEM buffer for GEMM2.  Group 0 also promotes the
+//                   Yacc chunks and writes the result (+ mu_s v_i).
+// Tensor-core FP32 accumulation does not round to nearest; a long chain of
+// accumulating MMAs drifts toward zero (~1e-8 relative per MMA, measured), so
+// GEMM2 accumulates RT_CH tiles at a time and group 0 adds each chunk into
+// FP32 sums with ordinary rounding.  Every wait is bounded; on expiry the CTA
+// records NYS_ERR_TIMEOUT in *err, lets its copies in flight land, frees its
+// TMEM and returns.
+
+#include "common.cuh"
+#include "internal.h"
+#include "ptx.cuh"
+#include "tmap.h"
+
+namespace nys {
+
+namespace {
+
+constexpr int RT_BM = 128;   // rows i per CTA
+constexpr int RT_BN = 64;    // points j per tile
+constexpr int RT_DP = 32;    // padded point dimension (d <= 32)
+constexpr int RT_EXP_WARPS = 8;
+constexpr int RT_THREADS = 64 + 32 * RT_EXP_WARPS;
+constexpr uint32_t RT_TMEM_COLS = 512;
+// TMEM column map: P tiles at 0 / 64, K tiles (hi, lo) at 128 / 256, Yacc at 384 (/ 448).
+constexpr uint32_t TM_P = 0, TM_K = 128, TM_Y = 384;
+constexpr int RT_CH = 4;  // tiles per GEMM2 accumulation chunk
+
+template <int S, int P2>
+struct RtCfg {
+  static constexpr bool GEMV = (S == 1);        // one vector: no GEMM2
+  static constexpr int NV = GEMV ? 0 : (P2 == 3 ? 2 : 1);
+  static constexpr int A_BYTES = RT_BM * 128;   // X_I hi (or lo): 128 rows x 32 FP32
+  static constexpr int XJ_BYTES = RT_BN * 128;  // X_J hi (or lo)
+  static constexpr int VSLAB = GEMV ? 0 : S * 128;
+  static constexpr int CN_OFF = 2 * XJ_BYTES + NV * 2 * VSLAB;
+  static constexpr int VJ_OFF = CN_OFF + RT_BN * 4;  // one vector: v_J
+  static constexpr int TX = GEMV ? VJ_OFF + RT_BN * 4 : CN_OFF + RT_BN * 4;
+  static constexpr int STAGE = (TX + 1023) / 1024 * 1024;
+  static constexpr int NS = GEMV ? 6 : 3;
+  static constexpr bool CHUNKED = !GEMV && S <= 64;
+  static constexpr int SUM_BYTES = GEMV ? RT_BM * 8 : (CHUNKED ? S * RT_BM * 4 : 0);
+  static constexpr int SMEM = 1024 + 2 * A_BYTES + NS * STAGE + SUM_BYTES + 256;
+  static constexpr uint32_t EMPTY_COUNT = GEMV ? 1 + 4 : 1;
+  static_assert(GEMV || (S % 16 == 0 && S <= 128), "S");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+struct RtArgs {
+  const float* cn;     // [npad] cn_j (padding: -1e30, so that k = 0)
+  float m2c;
+  int64_t n;           // number of points
+  int ntiles;          // npad / RT_BN
+  int ksteps;          // ceil(d / 8): K-steps of GEMM1 (coordinates beyond d are zero)
+  int64_t nvec;
+  int64_t spad;        // rows of each V array in the stage map
+  int64_t vec;         // one vector: its index q (the rest of the fields index all vectors)
+  const float* vj;     // one vector: [npad] v_q (zero padded), loaded per tile
+  const double* mus;   // [nvec] shifts (device), or NULL: mu0 for every vector
+  float mu0;
+  const float* v;      // [nvec][ldv] vectors for the shift term, or NULL: no shift
+  int64_t ldv;
+  float* y;            // [nvec][ldy]
+  int64_t ldy;
+  const int* done0;    // done0[s * done_stride] != 0: vector s needs no product (or NULL)
+  int64_t done_stride;
+  int* err;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// A operand from tensor memory (the kernel tile), B from shared memory.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Round to the nearest TF32 value (ties away from zero), kept in an FP32
+// container: add half a unit of the 13 dropped bits, then clear them.
+// Integer ALU work (finite inputs below 2^127 only, which holds here).
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+}
+
+__device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void exp_bar_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * RT_EXP_WARPS) : "memory");
+}
+
+// Add Yacc chunk c (TMEM columns TM_Y + 64 (c & 1)) into the FP32 sums of
+// row r (sY[s][r]) and release the buffer.  Called by each warp of group 0.
+template <int S>
+__device__ __forceinline__ bool promote(uint32_t tmem, uint32_t lane_base, int c, uint64_t* ycf,
+                                        uint64_t* ycfree, float* sY, int r, int lane) {
+  if (!mbar_wait_bounded(&ycf[c & 1], (uint32_t)((c >> 1) & 1))) return false;
+  tc_fence_after();
+#pragma unroll 1
+  for (int c0 = 0; c0 < S; c0 += 16) {
+    uint32_t v[16];
+    tmem_ld16(tmem + lane_base + TM_Y + (uint32_t)((c & 1) * 64 + c0), v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float* p = &sY[(c0 + j) * RT_BM + r];
+      *p = (c == 0) ? __uint_as_float(v[j]) : *p + __uint_as_float(v[j]);
+    }
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&ycfree[c & 1]);
+  return true;
+}
+
+template <int S, int P2>
+__global__ void __launch_bounds__(RT_THREADS, 1)
+rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV,
+              RtArgs a) {
+  using Cfg = RtCfg<S, P2>;
+  constexpr int NS = Cfg::NS;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm =
+      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = sm;
+  unsigned char* sSt = sm + 2 * Cfg::A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sSt + NS * Cfg::STAGE);
+  uint64_t* empty = full + NS;
+  uint64_t* afull = empty + NS;
+  uint64_t* pfull = afull + 1;
+  uint64_t* pfree = pfull + 2;
+  uint64_t* kfull = pfree + 2;
+  uint64_t* kfree = kfull + 2;
+  uint64_t* yfull = kfree + 2;
+  uint64_t* ycf = yfull + 1;    // [2] chunk of Yacc complete (MMA -> group 0)
+  uint64_t* ycfree = ycf + 2;   // [2] chunk promoted, buffer free (group 0 -> MMA)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ycfree + 2);
+  float* sY = reinterpret_cast<float*>(sSt + NS * Cfg::STAGE + 256);
+  __shared__ int s_fail, s_skip;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * RT_BM;
+  const int64_t s0 = Cfg::GEMV ? a.vec : (int64_t)blockIdx.y * S;
+  const int T = a.ntiles;
+
+  if (threadIdx.x == 0) {
+    int skip = 0;
+    if (a.done0) {
+      skip = 1;
+      const int64_t s1 = (s0 + S < a.nvec) ? s0 + S : a.nvec;
+      for (int64_t s = s0; s < s1; ++s)
+        if (!a.done0[s * a.done_stride]) { skip = 0; break; }
+    }
+    s_skip = skip;
+    s_fail = 0;
+    if (!skip) {
+      for (int i = 0; i < NS; ++i) {
+        mbar_init(&full[i], 1);
+        mbar_init(&empty[i], Cfg::EMPTY_COUNT);
+      }
+      mbar_init(afull, 1);
+      for (int i = 0; i < 2; ++i) {
+        mbar_init(&pfull[i], 1);
+        mbar_init(&pfree[i], 4);
+        mbar_init(&kfull[i], 4);
+        mbar_init(&kfree[i], 1);
+        mbar_init(&ycf[i], 1);
+        mbar_init(&ycfree[i], 4);
+      }
+      mbar_init(yfull, 1);
+      fence_barrier_init();
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmX) : "memory");
+      if (!Cfg::GEMV) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmV) : "memory");
+    }
+  }
+  __syncthreads();
+  if (s_skip) return;
+  if (warp == 1) tmem_alloc(tmem_slot, RT_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      mbar_arrive_expect_tx(afull, 2u * Cfg::A_BYTES);
+      tma_load_2d(sA, &tmX, 0, (int)m0, afull);
+      tma_load_2d(sA + Cfg::A_BYTES / 2, &tmX, 0, (int)m0 + 64, afull);
+      tma_load_2d(sA + Cfg::A_BYTES, &tmX, RT_DP, (int)m0, afull);
+      tma_load_2d(sA + Cfg::A_BYTES + Cfg::A_BYTES / 2, &tmX, RT_DP, (int)m0 + 64, afull);
+      int issued = 0;
+      for (int t = 0; t < T; ++t) {
+        const int s = t % NS;
+        if (t >= NS && !mbar_wait_bounded(&empty[s], (uint32_t)(((t / NS) - 1) & 1))) {
+          atomicOr(&s_fail, 1);
+          break;
+        }
+        if (*(volatile int*)&s_fail) break;
+        unsigned char* st = sSt + s * Cfg::STAGE;
+        const int j0 = t * RT_BN;
+        mbar_arrive_expect_tx(&full[s], (uint32_t)Cfg::TX);
+        tma_load_2d(st, &tmX, 0, j0, &full[s]);
+        tma_load_2d(st + Cfg::XJ_BYTES, &tmX, RT_DP, j0, &full[s]);
+#pragma unroll
+        for (int arr = 0; arr < Cfg::NV; ++arr)
+#pragma unroll
+          for (int slab = 0; slab < 2; ++slab)
+            tma_load_2d(st + 2 * Cfg::XJ_BYTES + (arr * 2 + slab) * Cfg::VSLAB, &tmV,
+                        j0 + 32 * slab, (int)(arr * a.spad + s0), &full[s]);
+        bulk_g2s(st + Cfg::CN_OFF, a.cn + j0, RT_BN * 4, &full[s]);
+        if (Cfg::GEMV) bulk_g2s(st + Cfg::VJ_OFF, a.vj + j0, RT_BN * 4, &full[s]);
+        issued = t + 1;
+      }
+      if (*(volatile int*)&s_fail) {
+        // let the copies still in flight land before the CTA exits
+        mbar_wait_bounded(afull, 0u);
+        for (int t = (issued > NS ? issued - NS : 0); t < issued; ++t)
+          mbar_wait_bounded(&full[t % NS], (uint32_t)((t / NS) & 1));
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc1 = tf32_idesc(RT_BM, RT_BN);
+      constexpr uint32_t idesc2 = tf32_idesc(RT_BM, Cfg::GEMV ? 16 : S);
+      bool ok = mbar_wait_bounded(afull, 0u);
+      const uint64_t aHiD = sw128_kmajor_desc(smem_u32(sA));
+      const uint64_t aLoD = sw128_kmajor_desc(smem_u32(sA + Cfg::A_BYTES));
+      const int ks = a.ksteps;
+      const int tend = Cfg::GEMV ? T - 1 : T;
+      for (int t = 0; ok && t <= tend; ++t) {
+        if (t < T) {
+          const int s = t % NS, b = t & 1;
+          if (!mbar_wait_bounded(&full[s], (uint32_t)((t / NS) & 1))) { ok = false; break; }
+          if (t >= 2 && !mbar_wait_bounded(&pfree[b], (uint32_t)(((t - 2) >> 1) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t bHiD = sw128_kmajor_desc(smem_u32(sSt + s * Cfg::STAGE));
+          const uint64_t bLoD = bHiD + (uint64_t)(Cfg::XJ_BYTES >> 4);
+          const uint32_t dP = tmem + TM_P + (uint32_t)(b * RT_BN);
+#pragma unroll
+          for (int pass = 0; pass < 3; ++pass) {
+            const uint64_t ad = pass == 2 ? aLoD : aHiD;
+            const uint64_t bd = pass == 1 ? bLoD : bHiD;
+#pragma unroll
+            for (int k = 0; k < RT_DP / 8; ++k)
+              if (k < ks)
+                mma_tf32(dP, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc1,
+                         (pass > 0 || k > 0) ? 1u : 0u);
+          }
+          mma_commit(&pfull[b]);
+          if (Cfg::GEMV) mma_commit(&empty[s]);
+        }
+        if (!Cfg::GEMV && t >= 1) {
+          const int u = t - 1, bu = u & 1, su = u % NS;
+          if (!mbar_wait_bounded(&kfull[bu], (uint32_t)((u >> 1) & 1))) { ok = false; break; }
+          const int c = u / RT_CH;
+          const bool first = Cfg::CHUNKED ? (u % RT_CH == 0) : (u == 0);
+          if (Cfg::CHUNKED && first && c >= 2 &&
+              !mbar_wait_bounded(&ycfree[c & 1], (uint32_t)(((c - 2) >> 1) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t kHi = tmem + TM_K + (uint32_t)(bu * 2 * RT_BN);
+          const uint32_t kLo = kHi + RT_BN;
+          const uint64_t vD = sw128_kmajor_desc(smem_u32(sSt + su * Cfg::STAGE + 2 * Cfg::XJ_BYTES));
+          const uint32_t dY = tmem + TM_Y + (Cfg::CHUNKED ? (uint32_t)((c & 1) * 64) : 0u);
+#pragma unroll
+          for (int pass = 0; pass < P2; ++pass) {
+            const uint32_t ka = (pass == 2) ? kLo : kHi;
+            const int arr = (pass == 1) ? 1 : 0;
+#pragma unroll
+            for (int k = 0; k < RT_BN / 8; ++k) {
+              const uint64_t vd =
+                  vD + (uint64_t)(((arr * 2 + (k >> 2)) * Cfg::VSLAB) >> 4) + (uint64_t)(2 * (k & 3));
+              mma_tf32_ts(dY, ka + (uint32_t)(8 * k), vd, idesc2,
+                          (!first || pass > 0 || k > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&kfree[bu]);
+          mma_commit(&empty[su]);
+          if (Cfg::CHUNKED && (u % RT_CH == RT_CH - 1 || u == T - 1)) mma_commit(&ycf[c & 1]);
+        }
+      }
+      if (ok) {
+        if (!Cfg::GEMV && !Cfg::CHUNKED) mma_commit(yfull);
+      } else {
+        atomicOr(&s_fail, 1);
+      }
+    }
+  } else {
+    // ---------------- exp groups (warps 2..9); TMEM lane quarter q = warp % 4
+    const int g = (warp - 2) >> 2;
+    const int q = warp & 3;
+    const int r = 32 * q + lane;  // row within the CTA tile
+    const int64_t row = m0 + r;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const float ai = a.cn[row];
+    const float m2c = a.m2c;
+    bool ok = true;
+    float acc = 0.f, comp = 0.f;  // one vector: Kahan-compensated row sum
+    for (int t = g; t < T; t += 2) {
+      const int b = g, s = t % NS;
+      if (!mbar_wait_bounded(&pfull[b], (uint32_t)((t >> 1) & 1))) { ok = false; break; }
+      tc_fence_after();
+      uint32_t r0[32], r1[32];
+      tmem_ld32_nw(tmem + lane_base + TM_P + (uint32_t)(b * RT_BN), r0);
+      tmem_ld32_nw(tmem + lane_base + TM_P + (uint32_t)(b * RT_BN) + 32, r1);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pfree[b]);
+      // the stage (cn_J, v_J) is resident: GEMM1(t) consumed it
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((t / NS) & 1))) { ok = false; break; }
+      const float4* cn4 = reinterpret_cast<const float4*>(sSt + s * Cfg::STAGE + Cfg::CN_OFF);
+      if (Cfg::GEMV) {
+        const float4* v4 = reinterpret_cast<const float4*>(sSt + s * Cfg::STAGE + Cfg::VJ_OFF);
+        float ts = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t(&pr)[32] = h ? r1 : r0;
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            const float4 c4 = cn4[h * 8 + j4], w4 = v4[h * 8 + j4];
+            const float cj[4] = {c4.x, c4.y, c4.z, c4.w};
+            const float vj[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float kv = ex2_approx(fmaf(__uint_as_float(pr[j4 * 4 + e]), m2c, ai + cj[e]));
+              ts = fmaf(kv, vj[e], ts);
+            }
+          }
+        }
+        const float yk = ts - comp;
+        const float tk = acc + yk;
+        comp = (tk - acc) - yk;
+        acc = tk;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        continue;
+      }
+      if (t >= 2 && !mbar_wait_bounded(&kfree[b], (uint32_t)(((t - 2) >> 1) & 1))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t kHi = tmem + lane_base + TM_K + (uint32_t)(b * 2 * RT_BN);
+      const uint32_t kLo = kHi + RT_BN;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t(&pr)[32] = h ? r1 : r0;
+        uint32_t lo[32];
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 c4 = cn4[h * 8 + j4];
+          const float cj[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int jj = j4 * 4 + e;
+            const float kv = ex2_approx(fmaf(__uint_as_float(pr[jj]), m2c, ai + cj[e]));
+            const uint32_t hi = tf32_rna(kv);
+            lo[jj] = __float_as_uint(kv - __uint_as_float(hi));
+            pr[jj] = hi;
+          }
+        }
+        tmem_st32(kHi + (uint32_t)(32 * h), pr);
+        if (P2 == 3) tmem_st32(kLo + (uint32_t)(32 * h), lo);
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&kfull[b]);
+      if (Cfg::CHUNKED && g == 0 && t % RT_CH == 0 && t >= RT_CH) {
+        if (!promote<S>(tmem, lane_base, t / RT_CH - 1, ycf, ycfree, sY, r, lane)) {
+          ok = false;
+          break;
+        }
+      }
+    }
+    if (!ok) atomicOr(&s_fail, 1);
+    if (Cfg::GEMV) {
+      // combine the two groups' row sums and write y_i (+ mu v_i)
+      double* sD = reinterpret_cast<double*>(sY);
+      if (g == 1) sD[r] = (double)acc - (double)comp;
+      exp_bar_sync();
+      if (g == 0 && ok && !*(volatile int*)&s_fail && row < a.n) {
+        float val = (float)(((double)acc - (double)comp) + sD[r]);
+        if (a.v) val = fmaf(a.mus ? (float)a.mus[s0] : a.mu0, a.v[s0 * a.ldv + row], val);
+        a.y[s0 * a.ldy + row] = val;
+      }
+    } else if (g == 0) {
+      if (Cfg::CHUNKED) {
+        if (ok) ok = promote<S>(tmem, lane_base, (T - 1) / RT_CH, ycf, ycfree, sY, r, lane);
+        if (!ok) atomicOr(&s_fail, 1);
+        if (ok && row < a.n) {
+          for (int sv = 0; sv < S && s0 + sv < a.nvec; ++sv) {
+            float val = sY[sv * RT_BM + r];
+            const int64_t gv = s0 + sv;
+            if (a.v) val = fmaf(a.mus ? (float)a.mus[gv] : a.mu0, a.v[gv * a.ldv + row], val);
+            a.y[gv * a.ldy + row] = val;
+          }
+        }
+      } else {
+        if (ok) ok = mbar_wait_bounded(yfull, 0u, 1ll << 26);
+        if (!ok) atomicOr(&s_fail, 1);
+        tc_fence_after();
+        if (ok) {
+#pragma unroll 1
+          for (int c0 = 0; c0 < S; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lane_base + TM_Y + (uint32_t)c0, v);
+            if (row < a.n) {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int64_t sv = s0 + c0 + jj;
+                if (sv < a.nvec) {
+                  float val = __uint_as_float(v[jj]);
+                  if (a.v) val = fmaf(a.mus ? (float)a.mus[sv] : a.mu0, a.v[sv * a.ldv + row], val);
+                  a.y[sv * a.ldy + row] = val;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, RT_TMEM_COLS);
+  if (threadIdx.x == 0 && s_fail) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
+}
+
+// XS[j] = [tf32(x_j) | tf32(x_j - tf32(x_j))] (32 + 32 FP32, zero padded),
+// cn[j] = c ||x_j||^2 (FP64 sum of the FP32 coordinates), -1e30 for padding.
+__global__ void rt_prep_points_kernel(const float* __restrict__ pts, int64_t n, int64_t d,
+                                      int64_t ld, int64_t npad, double c, float* __restrict__ XS,
+                                      float* __restrict__ cn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= npad) return;
+  const float x = (j < n && lane < d) ? pts[j * ld + lane] : 0.0f;
+  const float hi = __uint_as_float(tf32_rna(x));
+  const float lo = __uint_as_float(tf32_rna(x - hi));
+  XS[j * 64 + lane] = hi;
+  XS[j * 64 + 32 + lane] = lo;
+  const double s2 = warp_sum((double)x * (double)x);
+  if (lane == 0) cn[j] = (j < n) ? (float)(c * s2) : -1e30f;
+}
+
+// VS[arr][s][j] (spad x npad each): nv = 2: arr 0 = tf32(v), arr 1 = v - tf32(v);
+// nv = 1: tf32(v); nv = 0: v itself (one vector, FP32 products).
+__global__ void rt_prep_vecs_kernel(const float* __restrict__ V, int64_t nvec, int64_t n,
+                                    int64_t ldv, int64_t spad, int64_t npad, int nv,
+                                    float* __restrict__ VS) {
+  const int64_t total = spad * npad;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / npad, j = e - s * npad;
+    const float v = (s < nvec && j < n) ? V[s * ldv + j] : 0.0f;
+    if (nv == 0) {
+      VS[e] = v;
+      continue;
+    }
+    const float hi = __uint_as_float(tf32_rna(v));
+    VS[e] = hi;
+    if (nv > 1) VS[total + e] = v - hi;
+  }
+}
+
+template <int S, int P2>
+int32_t rt_launch(const CUtensorMap& tx, const CUtensorMap& tv, const RtArgs& a, int64_t npad,
+                  int64_t nblk_y, cudaStream_t s) {
+  using Cfg = RtCfg<S, P2>;
+  auto kern = rbf_tc_kernel<S, P2>;
+  NYS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+  kern<<<dim3((unsigned)(npad / RT_BM), (unsigned)nblk_y), RT_THREADS, Cfg::SMEM, s>>>(tx, tv, a);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// Vectors per CTA: 1 (FP32 products on the exp warps) for one or two
+// vectors, else 64 (3xTF32 GEMM2) or 128 (TF32 GEMM2).
+int rt_block(int64_t nvec, int passes) {
+  if (nvec <= 2) return 1;
+  return passes == 3 ? 64 : 128;
+}
+
+}  // namespace
+
+bool rbf_tc_supported(int64_t d) { return d >= 1 && d <= RT_DP; }
+
+size_t rbf_tc_work_bytes(int64_t n, int64_t nvec, int passes) {
+  const int64_t npad = cdiv(n, RT_BM) * RT_BM;
+  const int S = rt_block(nvec, passes);
+  const int64_t spad = cdiv(nvec, S) * S;
+  const int nv = S == 1 ? 1 : (passes == 3 ? 2 : 1);
+  return 256 + (size_t)npad * 64 * 4 + 256 + (size_t)npad * 4 + 256 +
+         (size_t)nv * spad * npad * 4 + 256;
+}
+
+int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, double sigma,
+                        int64_t nvec, const float* V, int64_t ldv, int shift, const double* d_mu,
+                        double mu0, float* Y, int64_t ldy, int passes, const int* done0,
+                        int64_t done_stride, void* work, int* err, cudaStream_t s) {
+  if (!rbf_tc_supported(d) || n < 1 || nvec < 1 || (passes != 1 && passes != 3)) return NYS_ERR_ARG;
+  if (n > (1ll << 30) || (shift == 2 && !d_mu)) return NYS_ERR_ARG;
+  const int64_t npad = cdiv(n, RT_BM) * RT_BM;
+  const int S = rt_block(nvec, passes);
+  const int64_t spad = cdiv(nvec, S) * S;
+  const int nv = S == 1 ? 0 : (passes == 3 ? 2 : 1);
+  if (spad * (nv ? nv : 1) > (1ll << 30)) return NYS_ERR_ARG;
+  Scratch sc(s);
+  unsigned char* w = (unsigned char*)work;
+  if (!w) {
+    NYS_TRY(sc.get(&w, rbf_tc_work_bytes(n, nvec, passes)));
+    NYS_CUDA_TRY(cudaMemsetAsync(w, 0, 256, s));
+  }
+  if (!err) err = reinterpret_cast<int*>(w);
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  float* XS = reinterpret_cast<float*>(w + 256);
+  float* cn = reinterpret_cast<float*>(w + 256 + align((size_t)npad * 64 * 4));
+  float* VS = reinterpret_cast<float*>((unsigned char*)cn + align((size_t)npad * 4));
+  const double l2e = 1.4426950408889634;
+  const double c = -l2e / (2.0 * sigma * sigma);
+  rt_prep_points_kernel<<<(unsigned)cdiv(npad, 8), 256, 0, s>>>(pts, n, d, ld, npad, c, XS, cn);
+  count_launch();
+  const int64_t tot = spad * npad;
+  const unsigned gv = (unsigned)(cdiv(tot, 256) < 4096 ? cdiv(tot, 256) : 4096);
+  rt_prep_vecs_kernel<<<gv, 256, 0, s>>>(V, nvec, n, ldv, spad, npad, nv, VS); count_launch();
+  CUtensorMap tx, tv;
+  if (!tmap_f32_2d(&tx, XS, npad, 64, 64, 64, 32)) return NYS_ERR_CUDA;
+  if (S > 1 && !tmap_f32_2d(&tv, VS, nv * spad, npad, npad, S, 32)) return NYS_ERR_CUDA;
+  if (S == 1) tv = tx;  // unused
+  RtArgs a;
+  a.cn = cn;
+  a.m2c = (float)(l2e / (sigma * sigma));
+  a.n = n;
+  a.ntiles = (int)(npad / RT_BN);
+  a.ksteps = (int)cdiv(d, 8);
+  a.nvec = nvec;
+  a.spad = spad;
+  a.vec = 0;
+  a.vj = VS;
+  a.mus = shift == 2 ? d_mu : nullptr;
+  a.mu0 = (float)mu0;
+  a.v = shift ? V : nullptr;
+  a.ldv = ldv;
+  a.y = Y;
+  a.ldy = ldy;
+  a.done0 = done0;
+  a.done_stride = done_stride;
+  a.err = err;
+  if (S == 1) {
+    // one launch per vector (nvec <= 2), each reading its own padded copy
+    for (int64_t q = 0; q < nvec; ++q) {
+      RtArgs aq = a;
+      aq.vec = q;
+      aq.vj = VS + q * npad;
+      NYS_TRY((rt_launch<1, 3>(tx, tv, aq, npad, 1, s)));
+    }
+    return NYS_OK;
+  }
+  if (S == 64) return rt_launch<64, 3>(tx, tv, a, npad, spad / S, s);
+  return rt_launch<128, 1>(tx, tv, a, npad, spad / S, s);
+}
+
+}  // namespace nys

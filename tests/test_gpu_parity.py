@@ -145,6 +145,41 @@ def test_sketch_mixed_gram(ny, m, n, ell, tf32):
     np.testing.assert_allclose(U.T @ U, np.eye(ell), atol=1e-5)
 
 
+@pytest.mark.parametrize("n,d,nvec", [(777, 7, 1), (1000, 32, 20), (300, 16, 130), (50, 3, 2),
+                                      (4096, 16, 64)])
+def test_rbf_tensor_core_products(ny, n, d, nvec):
+    # the tensor-core kernel (3xTF32 inner products and products with the
+    # vectors): ragged n, one and several 64-vector chunks
+    P = wl.gmm_points(n, d, seed=13)
+    sigma = wl.median_distance(P, seed=13)
+    X = wl.rhs(n, seed=13, nrhs=nvec)
+    op = ny.rbf_operator(T(P), sigma)
+    Y = ny.nys_op_matvec(op, 0.25, T(X), mode=1).cpu().numpy()
+    ref = oops.rbf_matmat(P, sigma, X.T).T + 0.25 * X
+    # FP32 accumulation of n terms: each entry within a few units of 2^-24
+    # of the sum of the magnitudes of its terms (the condition of the sum)
+    scale = oops.rbf_matmat(P, sigma, np.abs(X).T).T + 0.25 * np.abs(X)
+    for q in range(nvec):
+        assert np.all(np.abs(Y[q] - ref[q]) <= 4e-6 * scale[q]), q
+        assert relerr(Y[q], ref[q]) <= 3e-5, q
+
+
+@pytest.mark.parametrize("n,d,ell", [(700, 5, 40), (3000, 16, 200)])
+def test_sketch_rbf_mixed_tensor_cores(ny, n, d, ell):
+    # K Omega on the tensor cores with TF32 kernel entries and TF32 Omega
+    P = wl.gmm_points(n, d, seed=19)
+    sigma = wl.median_distance(P, seed=19)
+    Om = wl.omega(n, ell, seed=19)
+    f = ny.nys_sketch(ny.rbf_operator(T(P), sigma), ell, omega=T(Om), precision=ny.NYS_PREC_MIXED)
+    o = onys.rand_nystrom(lambda V: oops.rbf_matmat(P, sigma, V), Om)
+    lam = f.lam().cpu().numpy()
+    np.testing.assert_allclose(lam[:8], o["lam"][:8], rtol=3e-3)
+    assert np.abs(lam - o["lam"]).max() <= 3e-3 * o["lam"][0]
+    U = f.U().cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(U.T @ U, np.eye(ell), atol=1e-5)
+    assert f.stats()["shift_escalations"] == 0
+
+
 def test_sketch_rbf_f64(ny):
     n, d, ell = 700, 5, 40
     P = wl.gmm_points(n, d, seed=9)
@@ -273,6 +308,25 @@ def test_pcg_mixed_gram_refinement(ny):
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-8
     xs = opcg.direct_solve(X64.T @ X64, mu, b)
     assert relerr(xg, xs) <= 1e-5
+
+
+def test_mixed_preconditioner_keeps_fp64_iteration_count(ny):
+    # lambda_1 / (lambda_ell + mu) ~ 1e6: the mixed factor's U must be
+    # orthonormal far below 1e-6 for P^{-1} to stay positive definite and as
+    # strong as the FP64 one (Eq. (5.3)); the iteration counts must agree.
+    m, n, ell, mu = 20000, 2048, 512, 1e-3
+    X = wl.ridge_X(m, n, seed=15)
+    b = wl.rhs(n, seed=15)
+    op = ny.gram_operator(T(X))
+    Om = T(wl.omega(n, ell, 15))
+    fm = ny.nys_sketch(op, ell, omega=Om, precision=ny.NYS_PREC_MIXED)
+    U = fm.U().double()
+    assert (U.T @ U - torch.eye(ell, dtype=torch.float64, device=U.device)).abs().max() <= 2e-6
+    f64 = ny.nys_sketch(op, ell, omega=Om)
+    _, r64, _ = ny.pcg_solve(op, f64, mu, T(b), tol=1e-8)
+    _, rm, _ = ny.pcg_solve(op, fm, mu, T(b), tol=1e-8, precision=ny.NYS_PREC_MIXED)
+    assert r64[0].status == ny.NYS_OK and rm[0].status == ny.NYS_OK, (r64, rm)
+    assert rm[0].iterations <= 2 * r64[0].iterations + 10, (r64, rm)
 
 
 def test_pcg_f64_gram_matches_oracle(ny):
