@@ -172,6 +172,15 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Ties the registers written by tcgen05.ld to a point after the wait, so
+// that no use of them can be scheduled before tcgen05.wait::ld.
+__device__ __forceinline__ void reg_fence32(uint32_t (&r)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; i += 8)
+    asm volatile("" : "+r"(r[i]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), "+r"(r[i + 4]),
+                 "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7])::"memory");
+}
+
 __device__ __forceinline__ void exp_bar_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * RT_EXP_WARPS) : "memory");
 }
@@ -266,8 +275,12 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  if (warp == 0) {
+  // all 512 columns of lane 0 onward: anything else is recorded and the CTA
+  // does no work (it frees what it was given and reports NYS_ERR_TIMEOUT)
+  const bool tmem_ok = tmem == 0u;
+  if (!tmem_ok) {
+    if (threadIdx.x == 0) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
+  } else if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
       mbar_arrive_expect_tx(afull, 2u * Cfg::A_BYTES);
@@ -303,6 +316,11 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         mbar_wait_bounded(afull, 0u);
         for (int t = (issued > NS ? issued - NS : 0); t < issued; ++t)
           mbar_wait_bounded(&full[t % NS], (uint32_t)((t / NS) & 1));
+      } else {
+        // the last stages' releases include the tensor core's asynchronous
+        // commit arrivals: they must land before the shared memory is freed
+        for (int t = (T > NS ? T - NS : 0); t < T; ++t)
+          if (!mbar_wait_bounded(&empty[t % NS], (uint32_t)((t / NS) & 1))) atomicOr(&s_fail, 1);
       }
     }
   } else if (warp == 1) {
@@ -374,9 +392,14 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
       if (ok) {
         if (!Cfg::GEMV && !Cfg::CHUNKED) mma_commit(yfull);
-      } else {
-        atomicOr(&s_fail, 1);
+        if (!Cfg::GEMV) {
+          // the kfree arrivals of the last two tiles are not awaited by the
+          // exp groups: wait here so that none lands after the CTA exits
+          for (int u = (T > 2 ? T - 2 : 0); u < T; ++u)
+            if (!mbar_wait_bounded(&kfree[u & 1], (uint32_t)((u >> 1) & 1))) ok = false;
+        }
       }
+      if (!ok) atomicOr(&s_fail, 1);
     }
   } else {
     // ---------------- exp groups (warps 2..9); TMEM lane quarter q = warp % 4
@@ -397,6 +420,8 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       tmem_ld32_nw(tmem + lane_base + TM_P + (uint32_t)(b * RT_BN), r0);
       tmem_ld32_nw(tmem + lane_base + TM_P + (uint32_t)(b * RT_BN) + 32, r1);
       tmem_wait_ld();
+      reg_fence32(r0);
+      reg_fence32(r1);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&pfree[b]);
