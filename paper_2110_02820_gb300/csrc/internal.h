@@ -159,6 +159,13 @@ int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_
 int32_t rbf_dfl_products(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
                          int64_t ldp, int64_t d, double sigma, int kind, const double* d_mu,
                          int64_t nvec, const double* v, double* y, cudaStream_t s);
+// The same products with FP64 kernel entries and FP64 sums (~4 units of
+// 2^-53 per entry): shift 0 none, 1 mu0 v_q, 2 d_mu[q] v_q (targets ==
+// points); skip (device, may be NULL) returns at once when nonzero.
+int32_t rbf_exact_products(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
+                           int64_t ldp, int64_t d, double sigma, int kind, int shift,
+                           const double* d_mu, double mu0, int64_t nvec, const double* v, double* y,
+                           const int* skip, cudaStream_t s);
 // Gaussian cross-kernel products (FP64): kind 0 K(t, x) v, kind 1 dK/dsigma v.
 int32_t rbf_cross_matvec(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
                          int64_t ldp, int64_t d, double sigma, int64_t nvec, const double* v,

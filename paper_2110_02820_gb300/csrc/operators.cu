@@ -869,6 +869,11 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
     NYS_CUDA_TRY(cudaMemsetAsync(w, 0, 256, s));
     return gram_matvec<double, double, double>(op, mu, p, v, skip, w, s);
   }
+  if (op->d <= 64) {
+    const float* pts = (const float*)op->data;
+    return rbf_exact_products(pts, n, op->ld, pts, n, op->ld, op->d, op->sigma, 0, 1, nullptr, mu,
+                              1, p, v, skip, s);
+  }
   rbf_matvec_kernel<double, double, double><<<(unsigned)cdiv(n, RBF_BI), RBF_BI, 0, s>>>(
       (const float*)op->data, n, op->d, op->ld, op->sigma, p, mu, v, skip); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());

@@ -681,15 +681,21 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   std::vector<double> rel(nsys, 1.0), prev(nsys, 0.0);
   const unsigned gb = (unsigned)cdiv(n, 256) > 1024 ? 1024 : (unsigned)cdiv(n, 256);
   // The refinement residual starts in double-FP32 arithmetic (kernel and ridge
-  // operators, ~2^-44 relative per product, enough for tol >= 1e-10 at the
-  // conditioning seen here).  Below that, when the residual of a system stops
-  // shrinking while it is still above tol, the floor of that arithmetic has
-  // been reached and the remaining passes take the residual of the systems
-  // still active in native FP64 (slower on this part, exact to FP64 rounding).
+  // operators, ~1e-13 relative per product).  Its floor relative to ||b|| is
+  // about that times ||A|| ||x|| / ||b||, which for a nearly flat kernel
+  // (||K|| / mu ~ 1e6) reaches 1e-7.  So when the residual of a system stops
+  // halving while it is still above tol, the remaining passes take the
+  // residual of the systems still active in native FP64 (slower on this part,
+  // exact to FP64 rounding).
   bool exact = op->kind == NYS_OP_DENSE;
-  const bool may_escalate = !exact && tol < 1e-10;
+  const bool may_escalate = !exact;
   for (int k = 0; k <= max_refine; ++k) {
-    if (exact) {
+    if (exact && op->kind == NYS_OP_RBF && op->d <= 64) {
+      // one pass over the kernel for every system (the exponentials dominate)
+      const float* pts = (const float*)op->data;
+      NYS_TRY(rbf_exact_products(pts, n, op->ld, pts, n, op->ld, op->d, op->sigma, 0, 2, d_mus,
+                                 0.0, nsys, x, v, nullptr, s));
+    } else if (exact) {
       for (int64_t q = 0; q < nsys; ++q)
         if (active[q]) NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
     } else if (op->kind == NYS_OP_RBF && op->d <= 64) {

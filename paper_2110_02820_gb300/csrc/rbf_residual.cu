@@ -15,6 +15,8 @@
 // One thread per row i, a tile of points (and their norms) in shared memory,
 // up to RR_Q right-hand sides per launch in registers.
 
+#include <cmath>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -197,6 +199,121 @@ rbf_residual_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
   }
 }
 
+// ---------------------------------------------------------------- FP64-accurate variant
+//
+// Same products with the kernel entries and the sums in FP64, for a residual
+// whose floor must sit below the double-float one (a nearly flat kernel with
+// ||K|| / mu ~ 1e6) and for the FP64 PCG path.  The inner products stay in
+// double-float (exact FP32 products, ~2^-48 relative); the exponential is our
+// own FP64 routine: k = round(e 64 / ln 2), r = e - k (ln2/64) with ln2/64
+// split into a 24-bit head and a tail (so k times the head is exact), 2^(k/64)
+// = 2^(k >> 6) T[k & 63] with T[j] = 2^(j/64) tabulated on the host in extended
+// precision, and e^r by its Taylor polynomial to degree 6 (|r| <= ln2/128,
+// truncation < 2e-20).  Error ~4 units of 2^-53 in K_ij.
+
+struct Exp64Consts {
+  double tab[64];  // 2^(j/64)
+  double l_hi, l_lo, inv_l;
+};
+
+__device__ __forceinline__ double exp64_neg(double e, const double* tab, double l_hi, double l_lo,
+                                            double inv_l) {
+  if (e < -708.0) return 0.0;
+  const double kd = rint(e * inv_l);
+  double r = fma(-kd, l_hi, e);
+  r = fma(-kd, l_lo, r);
+  double p = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  p = fma(p, r, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p = fma(p, r, 1.0);
+  const int k = (int)kd;
+  return ldexp(tab[k & 63] * p, k >> 6);
+}
+
+constexpr int RX_BI = 128, RX_BJ = 64, RX_Q = 8;
+
+// y[q][i] = sum_j K(t_i, x_j) v[q][j] (kind 0) or dK/dsigma (kind 1), plus the
+// shift (0 none, 1 mu0 v[q][i], 2 mus[q] v[q][i]; shifts need t == x).
+__global__ void __launch_bounds__(RX_BI)
+rbf_exact_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
+                 const double* __restrict__ nrm_t, const float* __restrict__ pts, int64_t n,
+                 int64_t d, int64_t ld, const double* __restrict__ nrm, double neg_inv_2s2,
+                 double inv_s3, int kind, int64_t nvec, int shift, const double* __restrict__ mus,
+                 double mu0, const double* __restrict__ v, double* __restrict__ y,
+                 const int* __restrict__ skip, const __grid_constant__ Exp64Consts ec) {
+  if (skip && *skip) return;
+  __shared__ float xs[RX_BJ][RR_DMAX + 1];
+  __shared__ double njs[RX_BJ];
+  __shared__ double vj[RX_Q][RX_BJ];
+  __shared__ double tab[64];
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) tab[t] = ec.tab[t];
+  const int64_t i = (int64_t)blockIdx.x * RX_BI + threadIdx.x;
+  const int64_t q0 = (int64_t)blockIdx.y * RX_Q;
+  const int nq = (int)((nvec - q0 < RX_Q) ? nvec - q0 : RX_Q);
+  float xi[RR_DMAX];
+#pragma unroll
+  for (int k = 0; k < RR_DMAX; ++k) xi[k] = (i < nt && k < d) ? tg[i * ldt + k] : 0.f;
+  const double ni = i < nt ? nrm_t[i] : 0.0;
+  double acc[RX_Q];
+#pragma unroll
+  for (int q = 0; q < RX_Q; ++q) acc[q] = 0.0;
+  for (int64_t j0 = 0; j0 < n; j0 += RX_BJ) {
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)RX_BJ * d; e += RX_BI) {
+      int64_t jj = e / d, k = e % d;
+      xs[jj][k] = (j0 + jj < n) ? pts[(j0 + jj) * ld + k] : 0.f;
+    }
+    for (int jj = threadIdx.x; jj < RX_BJ; jj += RX_BI) {
+      njs[jj] = j0 + jj < n ? nrm[j0 + jj] : 0.0;
+      for (int q = 0; q < RX_Q; ++q)
+        vj[q][jj] = (q < nq && j0 + jj < n) ? v[(q0 + q) * n + j0 + jj] : 0.0;
+    }
+    __syncthreads();
+    const int jn = (int)((n - j0 < RX_BJ) ? n - j0 : RX_BJ);
+    for (int jj = 0; jj < jn; ++jj) {
+      float dh = 0.f, dl = 0.f;
+#pragma unroll
+      for (int k = 0; k < RR_DMAX; ++k)
+        if (k < d) dfl_acc_prod(xi[k], xs[jj][k], dh, dl);
+      const double dot = (double)dh + (double)dl;
+      double D = (ni + njs[jj]) - 2.0 * dot;
+      if (D < 0.0) D = 0.0;
+      double K = exp64_neg(D * neg_inv_2s2, tab, ec.l_hi, ec.l_lo, ec.inv_l);
+      if (kind == 1) K *= D * inv_s3;  // dK/dsigma = K D / sigma^3
+#pragma unroll
+      for (int q = 0; q < RX_Q; ++q)
+        if (q < nq) acc[q] = fma(K, vj[q][jj], acc[q]);
+    }
+  }
+  if (i < nt) {
+#pragma unroll
+    for (int q = 0; q < RX_Q; ++q)
+      if (q < nq) {
+        const int64_t g = q0 + q;
+        double out = acc[q];
+        if (shift) out = fma(shift == 2 ? mus[g] : mu0, v[g * n + i], out);
+        y[g * nt + i] = out;
+      }
+  }
+}
+
+static Exp64Consts exp64_consts() {
+  static Exp64Consts c;
+  static bool init = false;
+  if (!init) {
+    const long double ln2 = logl(2.0L);
+    const long double L = ln2 / 64.0L;
+    c.l_hi = (double)(float)L;
+    c.l_lo = (double)(L - (long double)c.l_hi);
+    c.inv_l = (double)(64.0L / ln2);
+    for (int j = 0; j < 64; ++j) c.tab[j] = (double)exp2l((long double)j / 64.0L);
+    init = true;
+  }
+  return c;
+}
+
 __global__ void sq_norms_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld,
                                 double* __restrict__ nrm) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,6 +351,28 @@ int32_t rbf_dfl_products(const float* tg, int64_t nt, int64_t ldt, const float* 
   rbf_residual_kernel<<<grid, RR_BI, 0, s>>>(tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm,
                                              -1.0 / (2.0 * sigma * sigma),
                                              1.0 / (sigma * sigma * sigma), kind, nvec, d_mu, v, y);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+int32_t rbf_exact_products(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
+                           int64_t ldp, int64_t d, double sigma, int kind, int shift,
+                           const double* d_mu, double mu0, int64_t nvec, const double* v, double* y,
+                           const int* skip, cudaStream_t s) {
+  if (d > RR_DMAX || nvec < 1) return NYS_ERR_ARG;
+  Scratch sc(s);
+  double *nrm, *nrm_t;
+  NYS_TRY(sc.get(&nrm, n));
+  NYS_TRY(sc.get(&nrm_t, nt));
+  sq_norms_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(pts, n, d, ldp, nrm);
+  count_launch();
+  sq_norms_kernel<<<(unsigned)cdiv(nt, 256), 256, 0, s>>>(tg, nt, d, ldt, nrm_t);
+  count_launch();
+  dim3 grid((unsigned)cdiv(nt, RX_BI), (unsigned)cdiv(nvec, RX_Q));
+  rbf_exact_kernel<<<grid, RX_BI, 0, s>>>(tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm,
+                                          -1.0 / (2.0 * sigma * sigma), 1.0 / (sigma * sigma * sigma),
+                                          kind, nvec, shift, d_mu, mu0, v, y, skip, exp64_consts());
   count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;

@@ -547,6 +547,229 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (threadIdx.x == 0 && s_fail) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
 }
 
+// ---------------------------------------------------------------- one vector
+//
+// y_i = sum_j k(x_i, x_j) v_j (+ mu v_i): GEMM1 on the tensor cores in 128-point
+// tiles (3xTF32, N = 128), the exponentials and the products with v on the
+// exp warps (FP32, Kahan-compensated across tiles).  Four exp groups take
+// tiles round-robin, each with its own 128-column TMEM buffer, so that every
+// SMSP holds four exp warps to cover the tensor-memory latency; within a tile
+// the next 32 columns are loaded while the current ones are used.
+constexpr int GV_BN = 128;
+constexpr int GV_G = 4;
+constexpr int GV_THREADS = 64 + GV_G * 128;
+constexpr int GV_NS = 4;
+constexpr int GV_XJ = GV_BN * 128;            // X_J hi (or lo): 128 rows x 32 FP32
+constexpr int GV_CN = 2 * GV_XJ;              // cn_J
+constexpr int GV_VJ = GV_CN + GV_BN * 4;      // v_J
+constexpr int GV_TX = GV_VJ + GV_BN * 4;
+constexpr int GV_STAGE = (GV_TX + 1023) / 1024 * 1024;
+constexpr int GV_A = RT_BM * 128;
+constexpr int GV_SMEM = 1024 + 2 * GV_A + GV_NS * GV_STAGE + 256 + GV_G * RT_BM * 8;
+static_assert(GV_SMEM <= 227 * 1024, "shared memory");
+
+__device__ __forceinline__ void gv_bar_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(GV_G * 128) : "memory");
+}
+
+__global__ void __launch_bounds__(GV_THREADS, 1)
+rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm =
+      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = sm;
+  unsigned char* sSt = sm + 2 * GV_A;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sSt + GV_NS * GV_STAGE);
+  uint64_t* empty = full + GV_NS;
+  uint64_t* afull = empty + GV_NS;
+  uint64_t* pfull = afull + 1;
+  uint64_t* pfree = pfull + GV_G;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pfree + GV_G);
+  double* sD = reinterpret_cast<double*>(sSt + GV_NS * GV_STAGE + 256);  // [G][128]
+  __shared__ int s_fail, s_skip;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * RT_BM;
+  const int64_t q0 = a.vec;
+  const int T = a.ntiles;
+
+  if (threadIdx.x == 0) {
+    s_skip = (a.done0 && a.done0[q0 * a.done_stride]) ? 1 : 0;
+    s_fail = 0;
+    if (!s_skip) {
+      for (int i = 0; i < GV_NS; ++i) {
+        mbar_init(&full[i], 1);
+        mbar_init(&empty[i], 1 + 4);
+      }
+      mbar_init(afull, 1);
+      for (int i = 0; i < GV_G; ++i) {
+        mbar_init(&pfull[i], 1);
+        mbar_init(&pfree[i], 4);
+      }
+      fence_barrier_init();
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmX) : "memory");
+    }
+  }
+  __syncthreads();
+  if (s_skip) return;
+  if (warp == 1) tmem_alloc(tmem_slot, RT_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const bool tmem_ok = tmem == 0u;
+  if (!tmem_ok) {
+    if (threadIdx.x == 0) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
+  } else if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      mbar_arrive_expect_tx(afull, 2u * GV_A);
+      tma_load_2d(sA, &tmX, 0, (int)m0, afull);
+      tma_load_2d(sA + GV_A / 2, &tmX, 0, (int)m0 + 64, afull);
+      tma_load_2d(sA + GV_A, &tmX, RT_DP, (int)m0, afull);
+      tma_load_2d(sA + GV_A + GV_A / 2, &tmX, RT_DP, (int)m0 + 64, afull);
+      int issued = 0;
+      for (int t = 0; t < T; ++t) {
+        const int s = t % GV_NS;
+        if (t >= GV_NS && !mbar_wait_bounded(&empty[s], (uint32_t)(((t / GV_NS) - 1) & 1))) {
+          atomicOr(&s_fail, 1);
+          break;
+        }
+        if (*(volatile int*)&s_fail) break;
+        unsigned char* st = sSt + s * GV_STAGE;
+        const int j0 = t * GV_BN;
+        mbar_arrive_expect_tx(&full[s], (uint32_t)GV_TX);
+        tma_load_2d(st, &tmX, 0, j0, &full[s]);
+        tma_load_2d(st + GV_XJ / 2, &tmX, 0, j0 + 64, &full[s]);
+        tma_load_2d(st + GV_XJ, &tmX, RT_DP, j0, &full[s]);
+        tma_load_2d(st + GV_XJ + GV_XJ / 2, &tmX, RT_DP, j0 + 64, &full[s]);
+        bulk_g2s(st + GV_CN, a.cn + j0, GV_BN * 4, &full[s]);
+        bulk_g2s(st + GV_VJ, a.vj + j0, GV_BN * 4, &full[s]);
+        issued = t + 1;
+      }
+      if (*(volatile int*)&s_fail) {
+        mbar_wait_bounded(afull, 0u);
+        for (int t = (issued > GV_NS ? issued - GV_NS : 0); t < issued; ++t)
+          mbar_wait_bounded(&full[t % GV_NS], (uint32_t)((t / GV_NS) & 1));
+      } else {
+        // the last stages' releases include the tensor core's asynchronous
+        // commit arrivals: they must land before the shared memory is freed
+        for (int t = (T > GV_NS ? T - GV_NS : 0); t < T; ++t)
+          if (!mbar_wait_bounded(&empty[t % GV_NS], (uint32_t)((t / GV_NS) & 1)))
+            atomicOr(&s_fail, 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer (GEMM1 only)
+      constexpr uint32_t idesc = tf32_idesc(RT_BM, GV_BN);
+      bool ok = mbar_wait_bounded(afull, 0u);
+      const uint64_t aHiD = sw128_kmajor_desc(smem_u32(sA));
+      const uint64_t aLoD = sw128_kmajor_desc(smem_u32(sA + GV_A));
+      const int ks = a.ksteps;
+      for (int t = 0; ok && t < T; ++t) {
+        const int s = t % GV_NS, b = t % GV_G;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((t / GV_NS) & 1))) { ok = false; break; }
+        if (t >= GV_G && !mbar_wait_bounded(&pfree[b], (uint32_t)(((t - GV_G) / GV_G) & 1))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t bHiD = sw128_kmajor_desc(smem_u32(sSt + s * GV_STAGE));
+        const uint64_t bLoD = bHiD + (uint64_t)(GV_XJ >> 4);
+        const uint32_t dP = tmem + (uint32_t)(b * GV_BN);
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint64_t ad = pass == 2 ? aLoD : aHiD;
+          const uint64_t bd = pass == 1 ? bLoD : bHiD;
+#pragma unroll
+          for (int k = 0; k < RT_DP / 8; ++k)
+            if (k < ks)
+              mma_tf32(dP, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
+                       (pass > 0 || k > 0) ? 1u : 0u);
+        }
+        mma_commit(&pfull[b]);
+        mma_commit(&empty[s]);
+      }
+      if (!ok) atomicOr(&s_fail, 1);
+    }
+  } else {
+    // ---------------- exp groups (warps 2 .. 2 + 4G - 1); TMEM lane quarter q = warp % 4
+    const int g = (warp - 2) >> 2;
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    const int64_t row = m0 + r;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const float ai = a.cn[row];
+    const float m2c = a.m2c;
+    bool ok = true;
+    float acc = 0.f, comp = 0.f;
+    for (int t = g; t < T; t += GV_G) {
+      const int s = t % GV_NS;
+      if (!mbar_wait_bounded(&pfull[g], (uint32_t)((t / GV_G) & 1))) { ok = false; break; }
+      tc_fence_after();
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((t / GV_NS) & 1))) { ok = false; break; }
+      const float4* cn4 = reinterpret_cast<const float4*>(sSt + s * GV_STAGE + GV_CN);
+      const float4* v4 = reinterpret_cast<const float4*>(sSt + s * GV_STAGE + GV_VJ);
+      const uint32_t P = tmem + lane_base + (uint32_t)(g * GV_BN);
+      uint32_t ra[32], rb[32];
+      tmem_ld32_nw(P, ra);
+      tmem_wait_ld();
+      reg_fence32(ra);
+      float ts = 0.f;
+#pragma unroll
+      for (int c = 0; c < GV_BN / 32; ++c) {
+        uint32_t(&cur)[32] = (c & 1) ? rb : ra;
+        uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
+        if (c + 1 < GV_BN / 32) tmem_ld32_nw(P + (uint32_t)(32 * (c + 1)), nxt);
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 c4 = cn4[c * 8 + j4], w4 = v4[c * 8 + j4];
+          const float cj[4] = {c4.x, c4.y, c4.z, c4.w};
+          const float vj[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float kv = ex2_approx(fmaf(__uint_as_float(cur[j4 * 4 + e]), m2c, ai + cj[e]));
+            ts = fmaf(kv, vj[e], ts);
+          }
+        }
+        if (c + 1 < GV_BN / 32) {
+          tmem_wait_ld();
+          reg_fence32(nxt);
+          if (c + 2 == GV_BN / 32) {
+            // the whole tile is in registers: release the TMEM buffer
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pfree[g]);
+          }
+        }
+      }
+      const float yk = ts - comp;
+      const float tk = acc + yk;
+      comp = (tk - acc) - yk;
+      acc = tk;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if (!ok) atomicOr(&s_fail, 1);
+    sD[g * RT_BM + r] = (double)acc - (double)comp;
+    gv_bar_sync();
+    if (g == 0 && !*(volatile int*)&s_fail && row < a.n) {
+      double tot = 0.0;
+#pragma unroll
+      for (int h = 0; h < GV_G; ++h) tot += sD[h * RT_BM + r];
+      float val = (float)tot;
+      if (a.v) val = fmaf(a.mus ? (float)a.mus[q0] : a.mu0, a.v[q0 * a.ldv + row], val);
+      a.y[q0 * a.ldy + row] = val;
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, RT_TMEM_COLS);
+  if (threadIdx.x == 0 && s_fail) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
+}
+
 // XS[j] = [tf32(x_j) | tf32(x_j - tf32(x_j))] (32 + 32 FP32, zero padded),
 // cn[j] = c ||x_j||^2 (FP64 sum of the FP32 coordinates), -1e30 for padding.
 __global__ void rt_prep_points_kernel(const float* __restrict__ pts, int64_t n, int64_t d,
@@ -670,11 +893,16 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
   a.err = err;
   if (S == 1) {
     // one launch per vector (nvec <= 2), each reading its own padded copy
+    NYS_CUDA_TRY(
+        cudaFuncSetAttribute(rbf_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GV_SMEM));
     for (int64_t q = 0; q < nvec; ++q) {
       RtArgs aq = a;
       aq.vec = q;
       aq.vj = VS + q * npad;
-      NYS_TRY((rt_launch<1, 3>(tx, tv, aq, npad, 1, s)));
+      aq.ntiles = (int)(npad / GV_BN);
+      rbf_gemv_kernel<<<(unsigned)(npad / RT_BM), GV_THREADS, GV_SMEM, s>>>(tx, aq);
+      count_launch();
+      NYS_CUDA_TRY(cudaGetLastError());
     }
     return NYS_OK;
   }
