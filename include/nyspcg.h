@@ -134,7 +134,9 @@ int32_t nys_precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, c
 
 typedef struct nys_pcg_opts {
   double tol;                 /* stop when ||r||_2 <= tol ||b||_2 (default 1e-8) */
-  int32_t maxit;              /* iteration cap per (inner) solve (default 500) */
+  int32_t maxit;              /* iteration cap per system (default 500); in mixed precision
+                                 the cap on a system's inner iterations summed over all
+                                 refinement steps */
   int32_t precision;          /* nys_precision */
   double inner_tol;           /* mixed: relative tolerance of each inner solve (default 1e-4) */
   int32_t max_refine;         /* mixed: cap on outer refinement steps (default 20) */

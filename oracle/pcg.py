@@ -112,10 +112,11 @@ def refine_solve(matvec_hi, matvec_lo, precond_inv_lo, mu: float, b: np.ndarray,
         if rel <= tol:
             status = CONVERGED
             break
-        if k == max_refine:
+        if k == max_refine or inner_total >= maxit:
             break
+        # maxit bounds the inner iterations summed over all refinement steps
         inner = nys_pcg(matvec_lo, mu, r.astype(np.float32), None, precond_inv_lo, inner_tol,
-                        maxit, dtype=np.float32)
+                        maxit - inner_total, dtype=np.float32)
         inner_total += inner["iterations"]
         x = x + inner["x"].astype(np.float64)
     return dict(x=x, outer=len(hist) - 1, inner_iterations=inner_total, status=status,

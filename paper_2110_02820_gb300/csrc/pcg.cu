@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <type_traits>
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -718,7 +719,8 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       } else if (!std::isfinite(rel[q])) {
         active[q] = 0;
         stt[q] = NYS_ERR_BREAKDOWN;
-      } else if (k < max_refine) {
+      } else if (k < max_refine && total_it[q] < maxit) {
+        // maxit bounds a system's inner iterations over all refinements
         todo.push_back(q);
       }
     }
@@ -741,9 +743,11 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
     NYS_TRY(convert_f64_to_f32(v, rf, na * n, s));
     std::vector<int> it(na), st(na);
     std::vector<double> rr(na);
+    int budget = 1;
+    for (int64_t q : todo) budget = std::max(budget, maxit - total_it[q]);
     NYS_TRY((run_pcg<float, float>(op, U, f ? f->lam : nullptr, f ? f->ell : 0,
                                    f ? f->lam_ell : 0.0, mua.data(), na, v, rf, df, inner_tol,
-                                   maxit, 0, (k == 0) ? hist : nullptr, it.data(), st.data(),
+                                   budget, 0, (k == 0) ? hist : nullptr, it.data(), st.data(),
                                    rr.data(), s)));
     for (int64_t t = 0; t < na; ++t) {
       int64_t q = todo[t];
