@@ -50,7 +50,6 @@ def parse():
     ap.add_argument("--ell", type=int, default=ELL)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no matvec, launch-count, e2e or CPU legs); "
                          "used for profiler launch lists")
@@ -59,6 +58,9 @@ def parse():
                     help="ridge (default): the headline line; the others measure the remaining "
                          "workloads of the hot path (dense FP64; adaptive mixed kernel ridge; "
                          "batched regularisation path; differentiable kernel ridge)")
+    ap.add_argument("--matvec-only", action="store_true",
+                    help="run only the workload's dominant FP32 matvec (--steps times after "
+                         "--warmup); the command behind the ncu summaries in profiles/")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="non-default workloads: multiply the number of points by this factor")
     return ap.parse_args()
@@ -290,12 +292,14 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = []
     launches0 = ny.kernel_launch_count()
+    ny.timing_start(8192)  # CUDA events around each FP32 ridge matvec of the timed solves
     ev0.record()
     for k in range(args.steps):
         x, res = solve_once(ny, op, b, ell, seed=k)
         iters.append((res.iterations, res.refinements, res.rel_residual, res.status))
     ev1.record()
     torch.cuda.synchronize()
+    mv_total_ms, mv_count = ny.timing_stop()
     launches_timed = ny.kernel_launch_count() - launches0
     barrier(world)
     clk = clocks.stop()
@@ -313,18 +317,9 @@ def run_ours(args):
                               "solve": iters[-1]}), flush=True)
         return
 
-    # dominant kernel: the fused ridge matvec, timed on its stream
-    pf = torch.randn(n, dtype=torch.float64, device=dev)
-    for _ in range(3):
-        ny.nys_op_matvec(op, MU, pf, mode=1)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.matvec_reps):
-        ny.nys_op_matvec(op, MU, pf, mode=1)
-    e1.record()
-    torch.cuda.synchronize()
-    mv_ms = e0.elapsed_time(e1) / args.matvec_reps
+    # dominant kernel: the fused ridge matvec (gram_fused_kernel + its fixed-order
+    # reduction), its average duration over the matvecs of the timed solves
+    mv_ms = mv_total_ms / max(mv_count, 1)
     bytes_mv = float(m) * n * 4  # X read once per matvec
     achieved = bytes_mv / (mv_ms * 1e-3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -382,7 +377,8 @@ def run_ours(args):
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": measured_traffic() if (m, n) == (M, N) else None,
-                         "bytes_per_launch": bytes_mv, "ms_per_launch": mv_ms},
+                         "bytes_per_launch": bytes_mv, "ms_per_launch": mv_ms,
+                         "launches_timed": int(mv_count)},
             "cpu_baseline": cb,
             "e2e": e2e,
             "gpu_launches": int(launches_timed),
@@ -531,12 +527,15 @@ def run_workload(args):
         for w in range(args.warmup):
             step(100 + w)
         launches0 = ny.kernel_launch_count()
+        ny.timing_start(65536)
         ms, (res, info) = _events_ms(lambda: step(7), args.steps)
-        pf = T(wl.rhs(n, seed=3))
-        mv_ms, _ = _events_ms(lambda: ny.nys_op_matvec(op, 0.0, pf, mode=1), 3)
+        mv_total, mv_cnt = ny.timing_stop()
+        mv_ms = mv_total / max(mv_cnt, 1)
+        kern = ("rbf_gemv_kernel (tensor-core distances, one vector)" if args.workload == "krr"
+                else "rbf_tc_kernel<64,3> (tensor cores, 64 systems per CTA)")
         line.update({"dtype": "f32", "config": {"workload": cfg},
-                     "dominant_kernel": {"kernel": "rbf_matvec_f32_kernel (SIMT)",
-                                         "ms_per_launch": mv_ms,
+                     "dominant_kernel": {"kernel": kern, "ms_per_launch": mv_ms,
+                                         "launches_timed": mv_cnt,
                                          "kernel_entries_per_s": n * n / (mv_ms * 1e-3)}})
         if args.workload == "krr":
             line["solve"] = {"iterations": res.iterations, "refinements": res.refinements,
@@ -592,9 +591,41 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_matvec_only(args):
+    """The dominant FP32 product of a workload, alone: the ridge matvec at
+    m x n, or the one-vector Gaussian matvec at n = 100000 scale, d = 32."""
+    import torch
+
+    from paper_2110_02820_gb300 import nyspcg as ny
+    from paper_2110_02820_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if args.workload == "ridge":
+        X = torch.tensor(wl.ridge_X(args.m, args.n, SEED), device=dev)
+        op = ny.gram_operator(X)
+        v = torch.tensor(wl.rhs(args.n, SEED), device=dev)
+        mu, what = MU, f"ridge matvec {args.m}x{args.n}"
+    else:
+        n = int(100000 * args.scale)
+        P = wl.gmm_points(n, 32, SEED)
+        op = ny.rbf_operator(torch.tensor(P, device=dev), wl.median_distance(P, SEED))
+        v = torch.tensor(wl.rhs(n, SEED), device=dev)
+        mu, what = 1e-6 * n, f"Gaussian matvec n={n} d=32"
+    for _ in range(args.warmup):
+        ny.nys_op_matvec(op, mu, v, mode=1)
+    ny.timing_start(max(args.steps, 1))
+    for _ in range(args.steps):
+        y = ny.nys_op_matvec(op, mu, v, mode=1)
+    ms, cnt = ny.timing_stop()
+    print(json.dumps({"matvec_only": what, "ms_per_matvec": ms / max(cnt, 1), "timed": cnt,
+                      "checksum": float(y.abs().sum())}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.matvec_only:
+        run_matvec_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload != "ridge":
         run_workload(args)

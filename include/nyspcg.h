@@ -185,6 +185,17 @@ const char* nys_status_str(int32_t status);
  * number of kernels that call launched.  No paper counterpart. */
 uint64_t nys_kernel_launch_count(void);
 
+/* Diagnostics (no counterpart in the paper): CUDA-event timing of the FP32
+ * operator products that mixed-precision PCG runs (the ridge or Gaussian
+ * matvec), recorded on the stream each product is launched on.
+ * nys_timing_start allocates events for up to max_products products
+ * (NYS_ERR_ARG if < 1; later products are not timed) and enables the
+ * recording; nys_timing_stop waits for the recorded events, returns the
+ * summed duration in ms and the number of products timed, and disables it.
+ * Not for concurrent use from several host threads. */
+int32_t nys_timing_start(int32_t max_products);
+int32_t nys_timing_stop(double* total_ms, int64_t* products);
+
 /* y_s = (A + mu I) x_s for s = 0..nvec-1 (device FP64 [nvec][n]).  mode 0:
  * FP64 arithmetic (the product inside FP64 PCG); mode 1: the FP32 product
  * used inside mixed-precision PCG; mode 2: the FP64-accurate product of the

@@ -716,6 +716,12 @@ int32_t nys_factor_get(const nys_factor* f, const void** U, int32_t* u_dtype,
   return NYS_OK;
 }
 
+int32_t nys_timing_start(int32_t max_products) { return timing_start(max_products); }
+
+int32_t nys_timing_stop(double* total_ms, int64_t* products) {
+  return timing_stop(total_ms, products);
+}
+
 int32_t nys_factor_stats(const nys_factor* f, int32_t* shift_escalations, int32_t* svd_sweeps,
                          int32_t* svd_refinements, double* lambda_ell) {
   if (!f) return NYS_ERR_ARG;

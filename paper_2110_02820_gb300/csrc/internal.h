@@ -140,6 +140,9 @@ size_t op_matvec_work_bytes(const nys_operator* op, bool accurate);
 // NULL (allocated per call).
 int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* v, const int* skip,
                       void* work, cudaStream_t s);
+// Opt-in event timing of op_matvec_f32 (operators.cu).
+int32_t timing_start(int32_t max_products);
+int32_t timing_stop(double* total_ms, int64_t* products);
 // v = (A + mu I) p in FP64 arithmetic (FP64 PCG).
 int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double* v,
                       const int* skip, void* work, cudaStream_t s);

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -826,8 +827,68 @@ size_t op_matvec_work_bytes(const nys_operator* op, bool accurate) {
   return 256;
 }
 
+// ---------------------------------------------------------------- matvec timing
+//
+// Opt-in CUDA-event timing of the FP32 operator products (the inner PCG
+// matvec): a pool of event pairs recorded on the launching stream around each
+// product while enabled, summed when timing stops.
+namespace {
+std::mutex g_tm_mutex;
+bool g_tm_on = false;
+std::vector<cudaEvent_t> g_tm_ev;  // 2 per product
+size_t g_tm_used = 0;
+
+struct MatvecTimer {
+  cudaStream_t s;
+  int slot = -1;
+  explicit MatvecTimer(cudaStream_t st) : s(st) {
+    std::lock_guard<std::mutex> lk(g_tm_mutex);
+    if (g_tm_on && g_tm_used + 2 <= g_tm_ev.size()) {
+      slot = (int)g_tm_used;
+      g_tm_used += 2;
+      cudaEventRecord(g_tm_ev[slot], s);
+    }
+  }
+  ~MatvecTimer() {
+    if (slot >= 0) cudaEventRecord(g_tm_ev[slot + 1], s);
+  }
+};
+}  // namespace
+
+int32_t timing_start(int32_t max_products) {
+  std::lock_guard<std::mutex> lk(g_tm_mutex);
+  for (cudaEvent_t e : g_tm_ev) cudaEventDestroy(e);
+  g_tm_ev.clear();
+  g_tm_used = 0;
+  g_tm_on = false;
+  if (max_products < 1) return NYS_ERR_ARG;
+  g_tm_ev.resize(2 * (size_t)max_products);
+  for (auto& e : g_tm_ev) NYS_CUDA_TRY(cudaEventCreate(&e));
+  g_tm_on = true;
+  return NYS_OK;
+}
+
+int32_t timing_stop(double* total_ms, int64_t* products) {
+  std::lock_guard<std::mutex> lk(g_tm_mutex);
+  g_tm_on = false;
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < g_tm_used; i += 2) {
+    NYS_CUDA_TRY(cudaEventSynchronize(g_tm_ev[i + 1]));
+    float ms = 0.f;
+    NYS_CUDA_TRY(cudaEventElapsedTime(&ms, g_tm_ev[i], g_tm_ev[i + 1]));
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (products) *products = (int64_t)(g_tm_used / 2);
+  for (cudaEvent_t e : g_tm_ev) cudaEventDestroy(e);
+  g_tm_ev.clear();
+  g_tm_used = 0;
+  return NYS_OK;
+}
+
 int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* v, const int* skip,
                       void* work, cudaStream_t s) {
+  MatvecTimer timer(s);
   const int64_t n = op->n;
   if (op->kind == NYS_OP_DENSE) {
     dense_matvec_kernel<float, float><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(
@@ -967,6 +1028,7 @@ int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_
                               const float* P, float* V, const int* done0, int64_t done_stride,
                               int* err, cudaStream_t s) {
   if (op->kind != NYS_OP_RBF) return NYS_ERR_ARG;
+  MatvecTimer timer(s);
   if (rbf_tc_supported(op->d))
     return rbf_tc_products((const float*)op->data, op->n, op->d, op->ld, op->sigma, nsys, P, op->n,
                            2, d_mu, 0.0, V, op->n, 3, done0, done_stride, nullptr, err, s);

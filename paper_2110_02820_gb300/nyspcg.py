@@ -339,6 +339,26 @@ def nys_power_err_est(op: Operator, f: Factor, g: torch.Tensor, q: int) -> float
     return est.value
 
 
+def timing_start(max_products: int = 8192) -> None:
+    """Start CUDA-event timing of the FP32 operator products (diagnostics)."""
+    f = lib().nys_timing_start
+    if f.argtypes is None:
+        f.argtypes = [C.c_int32]
+        f.restype = C.c_int32
+    _check(f(int(max_products)), "nys_timing_start")
+
+
+def timing_stop() -> tuple[float, int]:
+    """Stop the timing; returns (summed ms, number of products timed)."""
+    f = lib().nys_timing_stop
+    if f.argtypes is None:
+        f.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        f.restype = C.c_int32
+    ms, cnt = C.c_double(), C.c_int64()
+    _check(f(C.byref(ms), C.byref(cnt)), "nys_timing_stop")
+    return ms.value, cnt.value
+
+
 def nys_gram_matvec_f32_noalloc(op: Operator, mu: float, x: torch.Tensor,
                                 y: torch.Tensor) -> None:
     """y = (X^T X + mu I) x (FP32) with no device allocation inside the call.
