@@ -11,7 +11,8 @@
 //     length ell) into shared memory and runs a full cyclic sweep over those
 //     2w columns there (one warp per column pair, __syncthreads between local
 //     rounds).  A sweep over all columns then needs nb - 1 grid barriers
-//     (nb = ell / w blocks) instead of ell - 1.  Column pairs whose cosine
+//     (nb = ell / w blocks) instead of ell - 1; after the first round of a
+//     sweep a task only rotates the w^2 pairs across its two blocks.  Column pairs whose cosine
 //     is below tol (just above the FP32 rounding level of the dot product)
 //     are skipped; a sweep with no rotation ends the iteration.
 //  2. FP64 path only: the FP32 vectors X seed the iterative refinement for
@@ -169,9 +170,19 @@ __global__ void __launch_bounds__(32 * WB) bjacobi_kernel(BJArgs a) {
         }
         __syncthreads();
         bool rot = false;
-        for (int lr = 0; lr < 2 * WB - 1; ++lr) {
+        // Round 0 of a sweep meets every pair of the two blocks (a cyclic
+        // sweep over their 2 WB columns); later rounds only the WB^2 pairs
+        // across the blocks (WB shifts), the pairs inside a block having had
+        // their turn in round 0.  Same sweep count, ~45 % fewer local rounds.
+        const int nlr = (r == 0) ? 2 * WB - 1 : WB;
+        for (int lr = 0; lr < nlr; ++lr) {
           int p, q;
-          circle_pair(2 * WB, lr, warp, &p, &q);
+          if (r == 0) {
+            circle_pair(2 * WB, lr, warp, &p, &q);
+          } else {
+            p = warp;
+            q = WB + (warp + lr) % WB;
+          }
           float4* P = sm4 + p * rq;
           float4* Q = sm4 + q * rq;
           float al = 0.f, be = 0.f, ga = 0.f;
@@ -307,39 +318,62 @@ __global__ void rows_to_cols_kernel(const float* __restrict__ W, int64_t ellp,
 
 // lambda_i = S_ii / G_ii and the separation threshold
 // delta = 2 (||S - diag(lambda)||_F + max|lambda| ||I - G||_F) (Frobenius
-// norms bound the spectral norms of the method from above).  One block.
-__global__ void oa_stats_kernel(const double* __restrict__ G, const double* __restrict__ S,
-                                int64_t ell, double* lam, double* delta) {
+// norms bound the spectral norms of the method from above).  Two passes with
+// a fixed summation order: per-block partials over row ranges, then one block.
+constexpr int OA_ROWS = 4;  // rows per block of the partial pass
+
+__global__ void oa_partial_kernel(const double* __restrict__ G, const double* __restrict__ S,
+                                  int64_t ell, double* lam, double* part) {
   __shared__ double red[32];
-  double lmax = 0.0;
-  for (int64_t i = threadIdx.x; i < ell; i += blockDim.x) {
-    const double l = S[i * ell + i] / G[i * ell + i];
-    lam[i] = l;
-    lmax = fmax(lmax, fabs(l));
-  }
-  __syncthreads();
-  double off = 0.0, orth = 0.0;
-  for (int64_t e = threadIdx.x; e < ell * ell; e += blockDim.x) {
-    const int64_t i = e / ell, j = e - i * ell;
-    const double d = S[e] - (i == j ? lam[i] : 0.0);
-    const double o = (i == j ? 1.0 : 0.0) - G[e];
-    off = fma(d, d, off);
-    orth = fma(o, o, orth);
+  const int64_t r0 = (int64_t)blockIdx.x * OA_ROWS;
+  const int64_t r1 = (r0 + OA_ROWS < ell) ? r0 + OA_ROWS : ell;
+  double off = 0.0, orth = 0.0, lmax = 0.0;
+  for (int64_t i = r0; i < r1; ++i) {
+    const double li = S[i * ell + i] / G[i * ell + i];
+    if (threadIdx.x == 0) lam[i] = li;
+    lmax = fmax(lmax, fabs(li));
+    for (int64_t j = threadIdx.x; j < ell; j += blockDim.x) {
+      const int64_t e = i * ell + j;
+      const double d = S[e] - (i == j ? li : 0.0);
+      const double o = (i == j ? 1.0 : 0.0) - G[e];
+      off = fma(d, d, off);
+      orth = fma(o, o, orth);
+    }
   }
   off = block_sum(off, red);
   orth = block_sum(orth, red);
-  // block max of lmax (fixed order)
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = off;
+    part[3 * blockIdx.x + 1] = orth;
+    part[3 * blockIdx.x + 2] = lmax;
+  }
+}
+
+__global__ void oa_final_kernel(const double* __restrict__ part, int64_t nblk, double* delta) {
+  __shared__ double red[32];
+  double off = 0.0, orth = 0.0, lmax = 0.0;
+  for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) {
+    off += part[3 * b];
+    orth += part[3 * b + 1];
+    lmax = fmax(lmax, part[3 * b + 2]);
+  }
+  off = block_sum(off, red);
+  orth = block_sum(orth, red);
   lmax = warp_max(lmax);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    *delta = 2.0 * (sqrt(off) + m * sqrt(orth));
+    delta[0] = 2.0 * (sqrt(off) + m * sqrt(orth));
+    delta[1] = m;
   }
 }
 
-// F = I + E of the refinement step; emax = max |E_ij|.
+// F = I + E of the refinement step.  emax receives the size of the step as it
+// matters for R R^T = U Sigma^2 U^T: max over pairs of the orthogonality defect
+// |(I - G)_ij| and of |E_ij| |lambda_j - lambda_i| / max|lambda| (a rotation
+// between nearly equal eigenvalues changes U Sigma^2 U^T by that much only).
 __global__ void oa_update_kernel(const double* __restrict__ G, const double* __restrict__ S,
                                  const double* __restrict__ lam, const double* __restrict__ delta,
                                  int64_t ell, double* __restrict__ F, unsigned long long* emax) {
@@ -350,18 +384,20 @@ __global__ void oa_update_kernel(const double* __restrict__ G, const double* __r
     const int64_t e = i * ell + j;
     const double rij = (i == j ? 1.0 : 0.0) - G[e];
     double eij = 0.5 * rij;
+    ae = fabs(rij);
     if (i != j) {
       const double d = lam[j] - lam[i];
-      if (fabs(d) > *delta) {
+      if (fabs(d) > delta[0]) {
         // first-order correction, kept only while it is small: a pair barely
         // above the threshold would otherwise get a large step that costs
         // orthogonality in the next one
         const double lin = (S[e] + lam[j] * rij) / d;
         if (fabs(lin) <= kOaCap) eij = lin;
       }
+      const double lm = delta[1] > 0.0 ? delta[1] : 1.0;
+      ae = fmax(ae, fabs(eij) * fabs(d) / lm);
     }
     F[e] = (i == j ? 1.0 : 0.0) + eij;
-    ae = fabs(eij);
     if (ae != ae) ae = __longlong_as_double(0x7ff0000000000000ll);  // NaN -> +inf
   }
   ae = warp_max(ae);
@@ -483,7 +519,10 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, bool
     NYS_TRY(sc.get(&S, cnt));
     NYS_TRY(sc.get(&F, cnt));
     NYS_TRY(sc.get(&lam, ell));
-    NYS_TRY(sc.get(&delta, 1));
+    NYS_TRY(sc.get(&delta, 2));
+    const int64_t oa_blocks = cdiv(ell, OA_ROWS);
+    double* part;
+    NYS_TRY(sc.get(&part, 3 * oa_blocks));
     rows_to_cols_kernel<<<tg, dim3(32, 8), 0, s>>>(Wm, ellp, nullptr, rn, X, ell); count_launch();
     const dim3 ug((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 8));
     double em_prev = 1.0;
@@ -491,7 +530,8 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, bool
       NYS_TRY(gemm_f64(true, ell, ell, ell, X, ell, X, ell, G, ell, s));  // G = X^T X
       NYS_TRY(gemm_f64(true, ell, ell, ell, R, ell, X, ell, T, ell, s));  // T = R^T X
       NYS_TRY(gemm_f64(true, ell, ell, ell, T, ell, T, ell, S, ell, s));  // S = T^T T
-      oa_stats_kernel<<<1, 1024, 0, s>>>(G, S, ell, lam, delta); count_launch();
+      oa_partial_kernel<<<(unsigned)oa_blocks, 256, 0, s>>>(G, S, ell, lam, part); count_launch();
+      oa_final_kernel<<<1, 256, 0, s>>>(part, oa_blocks, delta); count_launch();
       oa_update_kernel<<<ug, dim3(32, 8), 0, s>>>(G, S, lam, delta, ell, F, &aux->emax[k]);
       count_launch();
       NYS_TRY(gemm_f64(false, ell, ell, ell, X, ell, F, ell, Xn, ell, s));  // X <- X (I + E)
@@ -505,11 +545,11 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, bool
       double em;
       memcpy(&em, &eb, sizeof(em));
       if (!std::isfinite(em)) return NYS_ERR_BREAKDOWN;  // non-finite entries in R
-      // The error after this step is O(em^2): below FP64 rounding once
-      // em < 3e-8.  Corrections between close, small eigenvalues bottom out
-      // at their rounding level (~eps lambda_1 / gap); a small step that no
-      // longer halves is that floor, and further steps change nothing.
-      if (em < 3e-8 || (em < 1e-6 && em > 0.5 * em_prev)) break;
+      // The step converges quadratically; once its size (relative to
+      // max|lambda|) is below 1e-9 the error it leaves is at the FP64
+      // rounding level of U Sigma^2 U^T.  A small step that no longer halves
+      // has reached the rounding floor, and further steps change nothing.
+      if (em < 1e-9 || (em < 1e-6 && em > 0.5 * em_prev)) break;
       em_prev = em;
     }
     sig_from_eig_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(lam, ell, sigma); count_launch();
