@@ -563,12 +563,20 @@ def run_workload(args):
         sigma0 = wl.median_distance(P, seed=0)
         Pt, Vt = T(P), T(V)
 
+        phase = {}
+
         def step(seed):
             sg = torch.tensor(sigma0, dtype=torch.float64, device=dev, requires_grad=True)
             m = torch.tensor(1e-6 * n, dtype=torch.float64, device=dev, requires_grad=True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
             L = krr.validation_loss(Pt, y, Vt, yv, sg, m, ell, precision=ny.NYS_PREC_MIXED,
                                     tol=1e-8, seed=seed)
+            e1.record()
             L.backward()
+            e2.record()
+            torch.cuda.synchronize()
+            phase["forward_ms"], phase["backward_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
             return float(L.detach()), float(m.grad), float(sg.grad)
         for w in range(args.warmup):
             step(100 + w)
@@ -576,7 +584,8 @@ def run_workload(args):
         ms, out = _events_ms(lambda: step(7), args.steps)
         line.update({"dtype": "f32", "config": {"workload": f"differentiable KRR n_train={n} "
                                                             f"n_val={nv} d={d} ell={ell} mixed"},
-                     "solve": {"loss": out[0], "dL_dmu": out[1], "dL_dsigma": out[2]}})
+                     "solve": {"loss": out[0], "dL_dmu": out[1], "dL_dsigma": out[2]},
+                     "phases_ms": dict(phase)})
     sol = line.get("solve", {})
     if args.workload == "batched":
         line["metric"] = "converged PCG systems/sec (rel-residual 1e-8 each)"

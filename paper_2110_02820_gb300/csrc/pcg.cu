@@ -690,20 +690,58 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   // exact to FP64 rounding).
   bool exact = op->kind == NYS_OP_DENSE;
   const bool may_escalate = !exact;
+  // The Gaussian residual runs as one pass over the kernel for all systems
+  // still active (gathered into contiguous buffers when some are done).
+  double *xa = nullptr, *va = nullptr, *d_musa = nullptr;
+  std::vector<double> musa;
+  std::vector<int64_t> act;
   for (int k = 0; k <= max_refine; ++k) {
-    if (exact && op->kind == NYS_OP_RBF && op->d <= 64) {
-      // one pass over the kernel for every system (the exponentials dominate)
+    const bool rbf_pass = op->kind == NYS_OP_RBF && op->d <= 64;
+    if (k == 0 && !use_x0) {
+      // x = 0: the residual is b itself, no product needed
+      NYS_CUDA_TRY(cudaMemsetAsync(v, 0, nsys * n * sizeof(double), s));
+    } else if (rbf_pass) {
+      act.clear();
+      for (int64_t q = 0; q < nsys; ++q)
+        if (active[q]) act.push_back(q);
+      const int64_t na = (int64_t)act.size();
+      const double *xs = x, *ms = d_mus;
+      double* vs = v;
+      if (na < nsys) {
+        if (!xa) {
+          NYS_TRY(sc.get(&xa, nsys * n));
+          NYS_TRY(sc.get(&va, nsys * n));
+          NYS_TRY(sc.get(&d_musa, nsys));
+        }
+        musa.resize(na);
+        for (int64_t t = 0; t < na; ++t) {
+          musa[t] = mu[act[t]];
+          NYS_CUDA_TRY(cudaMemcpyAsync(xa + t * n, x + act[t] * n, n * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
+        }
+        NYS_CUDA_TRY(cudaMemcpyAsync(d_musa, musa.data(), na * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+        xs = xa;
+        ms = d_musa;
+        vs = va;
+      }
       const float* pts = (const float*)op->data;
-      NYS_TRY(rbf_exact_products(pts, n, op->ld, pts, n, op->ld, op->d, op->sigma, 0, 2, d_mus,
-                                 0.0, nsys, x, v, nullptr, s));
+      if (exact)
+        NYS_TRY(rbf_exact_products(pts, n, op->ld, pts, n, op->ld, op->d, op->sigma, 0, 2, ms, 0.0,
+                                   na, xs, vs, nullptr, s));
+      else
+        NYS_TRY(rbf_residual_products(op, ms, na, xs, vs, s));
+      if (na < nsys)
+        for (int64_t t = 0; t < na; ++t)
+          NYS_CUDA_TRY(cudaMemcpyAsync(v + act[t] * n, va + t * n, n * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
     } else if (exact) {
       for (int64_t q = 0; q < nsys; ++q)
         if (active[q]) NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
-    } else if (op->kind == NYS_OP_RBF && op->d <= 64) {
-      NYS_TRY(rbf_residual_products(op, d_mus, nsys, x, v, s));
     } else {
       for (int64_t q = 0; q < nsys; ++q)
-        NYS_TRY(op_matvec_residual(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+        if (active[q])
+          NYS_TRY(op_matvec_residual(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
     }
     sub_kernel<<<gb, 256, 0, s>>>(b, v, r, nsys * n); count_launch();
     sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(r, n, nrm); count_launch();
@@ -719,7 +757,9 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       } else if (!std::isfinite(rel[q])) {
         active[q] = 0;
         stt[q] = NYS_ERR_BREAKDOWN;
-      } else if (k < max_refine && total_it[q] < maxit) {
+      } else if (total_it[q] >= maxit) {
+        active[q] = 0;  // its iteration budget is spent: NYS_ERR_MAXIT
+      } else if (k < max_refine) {
         // maxit bounds a system's inner iterations over all refinements
         todo.push_back(q);
       }

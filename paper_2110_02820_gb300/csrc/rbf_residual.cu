@@ -106,98 +106,7 @@ __device__ __forceinline__ dfl dfl_exp_neg(dfl e, const dfl* inv_fact, dfl ln2) 
   return v;
 }
 
-constexpr int RR_BI = 128, RR_BJ = 64, RR_Q = 8, RR_DMAX = 64;
-
-// y[q][i] = sum_j K(t_i, x_j) v[q][j] (+ mu_q v[q][i] when t == x), FP64 out.
-// nrm_t, nrm_x: squared norms of the points in FP64.
-__global__ void __launch_bounds__(RR_BI)
-rbf_residual_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
-                    const double* __restrict__ nrm_t, const float* __restrict__ pts, int64_t n,
-                    int64_t d, int64_t ld, const double* __restrict__ nrm, double neg_inv_2s2,
-                    double inv_s3, int kind, int64_t nvec, const double* __restrict__ mus,
-                    const double* __restrict__ v, double* __restrict__ y) {
-  __shared__ float xs[RR_BJ][RR_DMAX + 1];
-  __shared__ dfl nj[RR_BJ];
-  __shared__ dfl vj[RR_Q][RR_BJ];
-  const int64_t i = (int64_t)blockIdx.x * RR_BI + threadIdx.x;
-  const int64_t q0 = (int64_t)blockIdx.y * RR_Q;
-  const int nq = (int)((nvec - q0 < RR_Q) ? nvec - q0 : RR_Q);
-  dfl inv_fact[9];
-  {
-    double f = 1.0;
-    inv_fact[0] = dfl_make(1.f, 0.f);
-#pragma unroll
-    for (int q = 1; q <= 8; ++q) {
-      f /= (double)q;
-      inv_fact[q] = dfl_from_double(f);
-    }
-  }
-  const dfl ln2 = dfl_from_double(0.6931471805599453094);
-  const dfl scale = dfl_from_double(neg_inv_2s2);
-  float xi[RR_DMAX];
-#pragma unroll
-  for (int k = 0; k < RR_DMAX; ++k) xi[k] = (i < nt && k < d) ? tg[i * ldt + k] : 0.f;
-  const dfl ni = dfl_from_double(i < nt ? nrm_t[i] : 0.0);
-  const dfl s3 = dfl_from_double(inv_s3);
-  float ah[RR_Q], al[RR_Q];
-#pragma unroll
-  for (int q = 0; q < RR_Q; ++q) {
-    ah[q] = 0.f;
-    al[q] = 0.f;
-  }
-  for (int64_t j0 = 0; j0 < n; j0 += RR_BJ) {
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)RR_BJ * d; e += RR_BI) {
-      int64_t jj = e / d, k = e % d;
-      xs[jj][k] = (j0 + jj < n) ? pts[(j0 + jj) * ld + k] : 0.f;
-    }
-    for (int jj = threadIdx.x; jj < RR_BJ; jj += RR_BI) {
-      nj[jj] = dfl_from_double(j0 + jj < n ? nrm[j0 + jj] : 0.0);
-      for (int q = 0; q < RR_Q; ++q)
-        vj[q][jj] = dfl_from_double((q < nq && j0 + jj < n) ? v[(q0 + q) * n + j0 + jj] : 0.0);
-    }
-    __syncthreads();
-    const int jn = (int)((n - j0 < RR_BJ) ? n - j0 : RR_BJ);
-    for (int jj = 0; jj < jn; ++jj) {
-      // dot = x_i . x_j exactly enough (double-float)
-      float dh = 0.f, dl = 0.f;
-#pragma unroll
-      for (int k = 0; k < RR_DMAX; ++k)
-        if (k < d) dfl_acc_prod(xi[k], xs[jj][k], dh, dl);
-      dfl dot = dfl_norm(dh, dl);
-      // D = ||x_i||^2 + ||x_j||^2 - 2 dot  (clamped at 0)
-      dfl D = dfl_add(dfl_add(ni, nj[jj]), dfl_make(-2.f * dot.hi, -2.f * dot.lo));
-      if (D.hi < 0.f) D = dfl_make(0.f, 0.f);
-      dfl Kij = dfl_exp_neg(dfl_mul(D, scale), inv_fact, ln2);
-      if (kind == 1) Kij = dfl_mul(Kij, dfl_mul(D, s3));  // dK/dsigma = K D / sigma^3
-#pragma unroll
-      for (int q = 0; q < RR_Q; ++q) {
-        if (q < nq) {
-          // acc += K * v with double-float operands
-          const dfl vv = vj[q][jj];
-          const float p = __fmul_rn(Kij.hi, vv.hi);
-          float e = __fmaf_rn(Kij.hi, vv.hi, -p);
-          e = __fmaf_rn(Kij.hi, vv.lo, e);
-          e = __fmaf_rn(Kij.lo, vv.hi, e);
-          float s, e2;
-          two_sum(ah[q], p, s, e2);
-          ah[q] = s;
-          al[q] = __fadd_rn(al[q], __fadd_rn(e2, e));
-        }
-      }
-    }
-  }
-  if (i < nt) {
-#pragma unroll
-    for (int q = 0; q < RR_Q; ++q)
-      if (q < nq) {
-        const int64_t g = q0 + q;
-        double out = (double)ah[q] + (double)al[q];
-        if (mus) out += mus[g] * v[g * n + i];  // only when targets are the points
-        y[g * nt + i] = out;
-      }
-  }
-}
+constexpr int RR_DMAX = 64;
 
 // ---------------------------------------------------------------- FP64-accurate variant
 //
@@ -232,67 +141,155 @@ __device__ __forceinline__ double exp64_neg(double e, const double* tab, double 
   return ldexp(tab[k & 63] * p, k >> 6);
 }
 
-constexpr int RX_BI = 128, RX_BJ = 64, RX_Q = 8;
+// ---------------------------------------------------------------- the products kernel
+//
+// y[q][i] = sum_j k(t_i, x_j) v[q][j] for RP_Q vectors per block, ROWS target
+// rows per thread (two for d <= 32, so that each point coordinate read from
+// shared memory serves two rows), the point tile read as float4 broadcasts.
+// kind 0: k = K(t, x); kind 1: k = dK/dsigma = K D / sigma^3.  EXACT: k and the
+// sums in FP64 (own FP64 exponential); otherwise double-float throughout.
+// shift: 0 none, 1 mu0 v[q][i], 2 mus[q] v[q][i] (targets are the points).
+constexpr int RP_THREADS = 128, RP_BJ = 64, RP_Q = 8;
 
-// y[q][i] = sum_j K(t_i, x_j) v[q][j] (kind 0) or dK/dsigma (kind 1), plus the
-// shift (0 none, 1 mu0 v[q][i], 2 mus[q] v[q][i]; shifts need t == x).
-__global__ void __launch_bounds__(RX_BI)
-rbf_exact_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
-                 const double* __restrict__ nrm_t, const float* __restrict__ pts, int64_t n,
-                 int64_t d, int64_t ld, const double* __restrict__ nrm, double neg_inv_2s2,
-                 double inv_s3, int kind, int64_t nvec, int shift, const double* __restrict__ mus,
-                 double mu0, const double* __restrict__ v, double* __restrict__ y,
-                 const int* __restrict__ skip, const __grid_constant__ Exp64Consts ec) {
+template <int DMAX, int ROWS, bool EXACT>
+__global__ void __launch_bounds__(RP_THREADS)
+rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
+                    const double* __restrict__ nrm_t, const float* __restrict__ pts, int64_t n,
+                    int64_t d, int64_t ld, const double* __restrict__ nrm, double neg_inv_2s2,
+                    double inv_s3, int kind, int64_t nvec, int shift,
+                    const double* __restrict__ mus, double mu0, const double* __restrict__ v,
+                    double* __restrict__ y, const int* __restrict__ skip,
+                    const __grid_constant__ Exp64Consts ec) {
   if (skip && *skip) return;
-  __shared__ float xs[RX_BJ][RR_DMAX + 1];
-  __shared__ double njs[RX_BJ];
-  __shared__ double vj[RX_Q][RX_BJ];
+  __shared__ __align__(16) float xs[RP_BJ][DMAX];
+  __shared__ double njs[RP_BJ];
+  __shared__ double vjd[EXACT ? RP_Q : 1][RP_BJ];
+  __shared__ float2 vjf[EXACT ? 1 : RP_Q][RP_BJ];
   __shared__ double tab[64];
-  for (int t = threadIdx.x; t < 64; t += blockDim.x) tab[t] = ec.tab[t];
-  const int64_t i = (int64_t)blockIdx.x * RX_BI + threadIdx.x;
-  const int64_t q0 = (int64_t)blockIdx.y * RX_Q;
-  const int nq = (int)((nvec - q0 < RX_Q) ? nvec - q0 : RX_Q);
-  float xi[RR_DMAX];
-#pragma unroll
-  for (int k = 0; k < RR_DMAX; ++k) xi[k] = (i < nt && k < d) ? tg[i * ldt + k] : 0.f;
-  const double ni = i < nt ? nrm_t[i] : 0.0;
-  double acc[RX_Q];
-#pragma unroll
-  for (int q = 0; q < RX_Q; ++q) acc[q] = 0.0;
-  for (int64_t j0 = 0; j0 < n; j0 += RX_BJ) {
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)RX_BJ * d; e += RX_BI) {
-      int64_t jj = e / d, k = e % d;
-      xs[jj][k] = (j0 + jj < n) ? pts[(j0 + jj) * ld + k] : 0.f;
-    }
-    for (int jj = threadIdx.x; jj < RX_BJ; jj += RX_BI) {
-      njs[jj] = j0 + jj < n ? nrm[j0 + jj] : 0.0;
-      for (int q = 0; q < RX_Q; ++q)
-        vj[q][jj] = (q < nq && j0 + jj < n) ? v[(q0 + q) * n + j0 + jj] : 0.0;
-    }
-    __syncthreads();
-    const int jn = (int)((n - j0 < RX_BJ) ? n - j0 : RX_BJ);
-    for (int jj = 0; jj < jn; ++jj) {
-      float dh = 0.f, dl = 0.f;
-#pragma unroll
-      for (int k = 0; k < RR_DMAX; ++k)
-        if (k < d) dfl_acc_prod(xi[k], xs[jj][k], dh, dl);
-      const double dot = (double)dh + (double)dl;
-      double D = (ni + njs[jj]) - 2.0 * dot;
-      if (D < 0.0) D = 0.0;
-      double K = exp64_neg(D * neg_inv_2s2, tab, ec.l_hi, ec.l_lo, ec.inv_l);
-      if (kind == 1) K *= D * inv_s3;  // dK/dsigma = K D / sigma^3
-#pragma unroll
-      for (int q = 0; q < RX_Q; ++q)
-        if (q < nq) acc[q] = fma(K, vj[q][jj], acc[q]);
+  __shared__ dfl inv_fact[9];
+  if (EXACT) {
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) tab[t] = ec.tab[t];
+  } else if (threadIdx.x == 0) {
+    double f = 1.0;
+    inv_fact[0] = dfl_make(1.f, 0.f);
+    for (int q = 1; q <= 8; ++q) {
+      f /= (double)q;
+      inv_fact[q] = dfl_from_double(f);
     }
   }
-  if (i < nt) {
+  const dfl ln2 = dfl_from_double(0.6931471805599453094);
+  const dfl scale = dfl_from_double(neg_inv_2s2);
+  const dfl s3 = dfl_from_double(inv_s3);
+  const int64_t ib = (int64_t)blockIdx.x * (RP_THREADS * ROWS) + threadIdx.x;
+  const int64_t q0 = (int64_t)blockIdx.y * RP_Q;
+  const int nq = (int)((nvec - q0 < RP_Q) ? nvec - q0 : RP_Q);
+  float xi[ROWS][DMAX];
+  double ni[ROWS];
 #pragma unroll
-    for (int q = 0; q < RX_Q; ++q)
+  for (int r = 0; r < ROWS; ++r) {
+    const int64_t i = ib + (int64_t)r * RP_THREADS;
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) xi[r][k] = (i < nt && k < d) ? tg[i * ldt + k] : 0.f;
+    ni[r] = i < nt ? nrm_t[i] : 0.0;
+  }
+  double acc[EXACT ? ROWS : 1][EXACT ? RP_Q : 1];
+  float ah[EXACT ? 1 : ROWS][EXACT ? 1 : RP_Q], al[EXACT ? 1 : ROWS][EXACT ? 1 : RP_Q];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int q = 0; q < RP_Q; ++q) {
+      if (EXACT) acc[EXACT ? r : 0][EXACT ? q : 0] = 0.0;
+      else {
+        ah[EXACT ? 0 : r][EXACT ? 0 : q] = 0.f;
+        al[EXACT ? 0 : r][EXACT ? 0 : q] = 0.f;
+      }
+    }
+  for (int64_t j0 = 0; j0 < n; j0 += RP_BJ) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < RP_BJ * DMAX; e += RP_THREADS) {
+      const int jj = e / DMAX, k = e - jj * DMAX;
+      xs[jj][k] = (j0 + jj < n && k < d) ? pts[(j0 + jj) * ld + k] : 0.f;
+    }
+    for (int jj = threadIdx.x; jj < RP_BJ; jj += RP_THREADS) {
+      njs[jj] = j0 + jj < n ? nrm[j0 + jj] : 0.0;
+#pragma unroll
+      for (int q = 0; q < RP_Q; ++q) {
+        const double vv = (q < nq && j0 + jj < n) ? v[(q0 + q) * n + j0 + jj] : 0.0;
+        if (EXACT) {
+          vjd[EXACT ? q : 0][jj] = vv;
+        } else {
+          const dfl t = dfl_from_double(vv);
+          vjf[EXACT ? 0 : q][jj] = make_float2(t.hi, t.lo);
+        }
+      }
+    }
+    __syncthreads();
+    const int jn = (int)((n - j0 < RP_BJ) ? n - j0 : RP_BJ);
+    for (int jj = 0; jj < jn; ++jj) {
+      // inner products <t_i, x_j> in double-float (exact FP32 products)
+      float dh[ROWS], dl[ROWS];
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) dh[r] = dl[r] = 0.f;
+      const float4* xr = reinterpret_cast<const float4*>(xs[jj]);
+#pragma unroll
+      for (int k4 = 0; k4 < DMAX / 4; ++k4) {
+        const float4 xj = xr[k4];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          dfl_acc_prod(xi[r][4 * k4 + 0], xj.x, dh[r], dl[r]);
+          dfl_acc_prod(xi[r][4 * k4 + 1], xj.y, dh[r], dl[r]);
+          dfl_acc_prod(xi[r][4 * k4 + 2], xj.z, dh[r], dl[r]);
+          dfl_acc_prod(xi[r][4 * k4 + 3], xj.w, dh[r], dl[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        if (EXACT) {
+          double D = (ni[r] + njs[jj]) - 2.0 * ((double)dh[r] + (double)dl[r]);
+          if (D < 0.0) D = 0.0;
+          double K = exp64_neg(D * neg_inv_2s2, tab, ec.l_hi, ec.l_lo, ec.inv_l);
+          if (kind == 1) K *= D * inv_s3;
+#pragma unroll
+          for (int q = 0; q < RP_Q; ++q)
+            if (q < nq) acc[EXACT ? r : 0][EXACT ? q : 0] =
+                fma(K, vjd[EXACT ? q : 0][jj], acc[EXACT ? r : 0][EXACT ? q : 0]);
+        } else {
+          const dfl dot = dfl_norm(dh[r], dl[r]);
+          dfl D = dfl_add(dfl_add(dfl_from_double(ni[r]), dfl_from_double(njs[jj])),
+                          dfl_make(-2.f * dot.hi, -2.f * dot.lo));
+          if (D.hi < 0.f) D = dfl_make(0.f, 0.f);
+          dfl Kij = dfl_exp_neg(dfl_mul(D, scale), inv_fact, ln2);
+          if (kind == 1) Kij = dfl_mul(Kij, dfl_mul(D, s3));
+#pragma unroll
+          for (int q = 0; q < RP_Q; ++q) {
+            if (q < nq) {
+              const float2 vv = vjf[EXACT ? 0 : q][jj];
+              const float p = __fmul_rn(Kij.hi, vv.x);
+              float e = __fmaf_rn(Kij.hi, vv.x, -p);
+              e = __fmaf_rn(Kij.hi, vv.y, e);
+              e = __fmaf_rn(Kij.lo, vv.x, e);
+              float sum, e2;
+              two_sum(ah[EXACT ? 0 : r][EXACT ? 0 : q], p, sum, e2);
+              ah[EXACT ? 0 : r][EXACT ? 0 : q] = sum;
+              al[EXACT ? 0 : r][EXACT ? 0 : q] =
+                  __fadd_rn(al[EXACT ? 0 : r][EXACT ? 0 : q], __fadd_rn(e2, e));
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int64_t i = ib + (int64_t)r * RP_THREADS;
+    if (i >= nt) continue;
+#pragma unroll
+    for (int q = 0; q < RP_Q; ++q)
       if (q < nq) {
         const int64_t g = q0 + q;
-        double out = acc[q];
+        double out = EXACT ? acc[EXACT ? r : 0][EXACT ? q : 0]
+                           : (double)ah[EXACT ? 0 : r][EXACT ? 0 : q] +
+                                 (double)al[EXACT ? 0 : r][EXACT ? 0 : q];
         if (shift) out = fma(shift == 2 ? mus[g] : mu0, v[g * n + i], out);
         y[g * nt + i] = out;
       }
@@ -335,10 +332,43 @@ int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_
                           v, y, s);
 }
 
-int32_t rbf_dfl_products(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
-                         int64_t ldp, int64_t d, double sigma, int kind, const double* d_mu,
-                         int64_t nvec, const double* v, double* y, cudaStream_t s) {
-  if (d > RR_DMAX) return NYS_ERR_ARG;
+namespace {
+
+template <bool EXACT>
+int32_t products_launch(const float* tg, int64_t nt, int64_t ldt, const double* nrm_t,
+                        const float* pts, int64_t n, int64_t ldp, const double* nrm, int64_t d,
+                        double sigma, int kind, int shift, const double* d_mu, double mu0,
+                        int64_t nvec, const double* v, double* y, const int* skip,
+                        cudaStream_t s) {
+  const double a = -1.0 / (2.0 * sigma * sigma), b = 1.0 / (sigma * sigma * sigma);
+  const Exp64Consts ec = exp64_consts();
+  const unsigned gy = (unsigned)cdiv(nvec, RP_Q);
+  if (d <= 16) {
+    rbf_products_kernel<16, 2, EXACT>
+        <<<dim3((unsigned)cdiv(nt, 2 * RP_THREADS), gy), RP_THREADS, 0, s>>>(
+            tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y,
+            skip, ec);
+  } else if (d <= 32) {
+    rbf_products_kernel<32, 2, EXACT>
+        <<<dim3((unsigned)cdiv(nt, 2 * RP_THREADS), gy), RP_THREADS, 0, s>>>(
+            tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y,
+            skip, ec);
+  } else {
+    rbf_products_kernel<64, 1, EXACT>
+        <<<dim3((unsigned)cdiv(nt, RP_THREADS), gy), RP_THREADS, 0, s>>>(
+            tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y,
+            skip, ec);
+  }
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+int32_t products(bool exact, const float* tg, int64_t nt, int64_t ldt, const float* pts,
+                 int64_t n, int64_t ldp, int64_t d, double sigma, int kind, int shift,
+                 const double* d_mu, double mu0, int64_t nvec, const double* v, double* y,
+                 const int* skip, cudaStream_t s) {
+  if (d > RR_DMAX || d < 1 || nvec < 1 || (shift == 2 && !d_mu)) return NYS_ERR_ARG;
   Scratch sc(s);
   double *nrm, *nrm_t;
   NYS_TRY(sc.get(&nrm, n));
@@ -347,35 +377,27 @@ int32_t rbf_dfl_products(const float* tg, int64_t nt, int64_t ldt, const float* 
   count_launch();
   sq_norms_kernel<<<(unsigned)cdiv(nt, 256), 256, 0, s>>>(tg, nt, d, ldt, nrm_t);
   count_launch();
-  dim3 grid((unsigned)cdiv(nt, RR_BI), (unsigned)cdiv(nvec, RR_Q));
-  rbf_residual_kernel<<<grid, RR_BI, 0, s>>>(tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm,
-                                             -1.0 / (2.0 * sigma * sigma),
-                                             1.0 / (sigma * sigma * sigma), kind, nvec, d_mu, v, y);
-  count_launch();
-  NYS_CUDA_TRY(cudaGetLastError());
-  return NYS_OK;
+  return exact ? products_launch<true>(tg, nt, ldt, nrm_t, pts, n, ldp, nrm, d, sigma, kind, shift,
+                                       d_mu, mu0, nvec, v, y, skip, s)
+               : products_launch<false>(tg, nt, ldt, nrm_t, pts, n, ldp, nrm, d, sigma, kind,
+                                        shift, d_mu, mu0, nvec, v, y, skip, s);
+}
+
+}  // namespace
+
+int32_t rbf_dfl_products(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
+                         int64_t ldp, int64_t d, double sigma, int kind, const double* d_mu,
+                         int64_t nvec, const double* v, double* y, cudaStream_t s) {
+  return products(false, tg, nt, ldt, pts, n, ldp, d, sigma, kind, d_mu ? 2 : 0, d_mu, 0.0, nvec,
+                  v, y, nullptr, s);
 }
 
 int32_t rbf_exact_products(const float* tg, int64_t nt, int64_t ldt, const float* pts, int64_t n,
                            int64_t ldp, int64_t d, double sigma, int kind, int shift,
                            const double* d_mu, double mu0, int64_t nvec, const double* v, double* y,
                            const int* skip, cudaStream_t s) {
-  if (d > RR_DMAX || nvec < 1) return NYS_ERR_ARG;
-  Scratch sc(s);
-  double *nrm, *nrm_t;
-  NYS_TRY(sc.get(&nrm, n));
-  NYS_TRY(sc.get(&nrm_t, nt));
-  sq_norms_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(pts, n, d, ldp, nrm);
-  count_launch();
-  sq_norms_kernel<<<(unsigned)cdiv(nt, 256), 256, 0, s>>>(tg, nt, d, ldt, nrm_t);
-  count_launch();
-  dim3 grid((unsigned)cdiv(nt, RX_BI), (unsigned)cdiv(nvec, RX_Q));
-  rbf_exact_kernel<<<grid, RX_BI, 0, s>>>(tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm,
-                                          -1.0 / (2.0 * sigma * sigma), 1.0 / (sigma * sigma * sigma),
-                                          kind, nvec, shift, d_mu, mu0, v, y, skip, exp64_consts());
-  count_launch();
-  NYS_CUDA_TRY(cudaGetLastError());
-  return NYS_OK;
+  return products(true, tg, nt, ldt, pts, n, ldp, d, sigma, kind, shift, d_mu, mu0, nvec, v, y,
+                  skip, s);
 }
 
 }  // namespace nys

@@ -53,7 +53,8 @@ struct SvdAux {
   int sweeps;
   int pad;
   unsigned long long maxbits;           // max |R_ij| (bit pattern of a non-negative double)
-  unsigned long long emax[kMaxRefine];  // max |E_ij| per refinement step
+  unsigned long long emax[kMaxRefine];   // step size per refinement step
+  unsigned long long e2max[kMaxRefine];  // max E_ij^2 per refinement step
 };
 
 // Bounded grid barrier for a cooperative launch.  Returns false (and sets
@@ -373,13 +374,15 @@ __global__ void oa_final_kernel(const double* __restrict__ part, int64_t nblk, d
 // F = I + E of the refinement step.  emax receives the size of the step as it
 // matters for R R^T = U Sigma^2 U^T: max over pairs of the orthogonality defect
 // |(I - G)_ij| and of |E_ij| |lambda_j - lambda_i| / max|lambda| (a rotation
-// between nearly equal eigenvalues changes U Sigma^2 U^T by that much only).
+// between nearly equal eigenvalues changes U Sigma^2 U^T by that much only);
+// e2max receives max E_ij^2, the orthogonality defect the step itself leaves.
 __global__ void oa_update_kernel(const double* __restrict__ G, const double* __restrict__ S,
                                  const double* __restrict__ lam, const double* __restrict__ delta,
-                                 int64_t ell, double* __restrict__ F, unsigned long long* emax) {
+                                 int64_t ell, double* __restrict__ F, unsigned long long* emax,
+                                 unsigned long long* e2max) {
   const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
   const int64_t i = (int64_t)blockIdx.y * 8 + threadIdx.y;
-  double ae = 0.0;
+  double ae = 0.0, e2 = 0.0;
   if (i < ell && j < ell) {
     const int64_t e = i * ell + j;
     const double rij = (i == j ? 1.0 : 0.0) - G[e];
@@ -397,11 +400,17 @@ __global__ void oa_update_kernel(const double* __restrict__ G, const double* __r
       const double lm = delta[1] > 0.0 ? delta[1] : 1.0;
       ae = fmax(ae, fabs(eij) * fabs(d) / lm);
     }
+    e2 = eij * eij;  // the orthogonality defect the step itself leaves
     F[e] = (i == j ? 1.0 : 0.0) + eij;
     if (ae != ae) ae = __longlong_as_double(0x7ff0000000000000ll);  // NaN -> +inf
+    if (e2 != e2) e2 = __longlong_as_double(0x7ff0000000000000ll);
   }
   ae = warp_max(ae);
-  if ((threadIdx.x & 31) == 0) atomicMax(emax, (unsigned long long)__double_as_longlong(ae));
+  e2 = warp_max(e2);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(emax, (unsigned long long)__double_as_longlong(ae));
+    atomicMax(e2max, (unsigned long long)__double_as_longlong(e2));
+  }
 }
 
 __global__ void sig_from_eig_kernel(const double* lam, int64_t ell, double* sigma) {
@@ -532,24 +541,29 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, bool
       NYS_TRY(gemm_f64(true, ell, ell, ell, T, ell, T, ell, S, ell, s));  // S = T^T T
       oa_partial_kernel<<<(unsigned)oa_blocks, 256, 0, s>>>(G, S, ell, lam, part); count_launch();
       oa_final_kernel<<<1, 256, 0, s>>>(part, oa_blocks, delta); count_launch();
-      oa_update_kernel<<<ug, dim3(32, 8), 0, s>>>(G, S, lam, delta, ell, F, &aux->emax[k]);
+      oa_update_kernel<<<ug, dim3(32, 8), 0, s>>>(G, S, lam, delta, ell, F, &aux->emax[k],
+                                                  &aux->e2max[k]);
       count_launch();
       NYS_TRY(gemm_f64(false, ell, ell, ell, X, ell, F, ell, Xn, ell, s));  // X <- X (I + E)
       double* tmp = X;
       X = Xn;
       Xn = tmp;
       ++steps;
-      unsigned long long eb = 0;
-      NYS_CUDA_TRY(cudaMemcpyAsync(&eb, &aux->emax[k], sizeof(eb), cudaMemcpyDeviceToHost, s));
+      unsigned long long eb[2] = {0, 0};
+      NYS_CUDA_TRY(cudaMemcpyAsync(&eb[0], &aux->emax[k], sizeof(eb[0]), cudaMemcpyDeviceToHost, s));
+      NYS_CUDA_TRY(cudaMemcpyAsync(&eb[1], &aux->e2max[k], sizeof(eb[1]), cudaMemcpyDeviceToHost, s));
       NYS_CUDA_TRY(cudaStreamSynchronize(s));
-      double em;
-      memcpy(&em, &eb, sizeof(em));
-      if (!std::isfinite(em)) return NYS_ERR_BREAKDOWN;  // non-finite entries in R
+      double em, e2;
+      memcpy(&em, &eb[0], sizeof(em));
+      memcpy(&e2, &eb[1], sizeof(e2));
+      if (!std::isfinite(em) || !std::isfinite(e2)) return NYS_ERR_BREAKDOWN;  // non-finite R
       // The step converges quadratically; once its size (relative to
-      // max|lambda|) is below 1e-9 the error it leaves is at the FP64
+      // max|lambda|) is below 1e-8 the error it leaves is at the FP64
       // rounding level of U Sigma^2 U^T.  A small step that no longer halves
       // has reached the rounding floor, and further steps change nothing.
-      if (em < 1e-9 || (em < 1e-6 && em > 0.5 * em_prev)) break;
+      // A step that was itself large (E^2 above 1e-12) is always followed by
+      // another, which restores the orthogonality it cost.
+      if ((em < 1e-8 || (em < 1e-6 && em > 0.5 * em_prev)) && e2 < 1e-12) break;
       em_prev = em;
     }
     sig_from_eig_kernel<<<(unsigned)cdiv(ell, 256), 256, 0, s>>>(lam, ell, sigma); count_launch();
