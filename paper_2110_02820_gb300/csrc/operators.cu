@@ -34,8 +34,28 @@ __global__ void dense_matvec_kernel(const double* __restrict__ A, int64_t n, int
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
   const double* a = A + row * ld;
-  double acc = 0.0;
-  for (int64_t j = lane; j < n; j += 32) acc = fma(a[j], (double)p[j], acc);
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+  int64_t j0 = 0;
+  if (((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0)) {
+    // 16-byte loads, four independent accumulators (loads stay in flight)
+    const double2* a2 = reinterpret_cast<const double2*>(a);
+    const int64_t n2 = n >> 1;
+    int64_t c = lane;
+    for (; c + 96 < n2; c += 128) {
+      const double2 x0 = a2[c], x1 = a2[c + 32], x2 = a2[c + 64], x3 = a2[c + 96];
+      acc0 = fma(x0.x, (double)p[2 * c], fma(x0.y, (double)p[2 * c + 1], acc0));
+      acc1 = fma(x1.x, (double)p[2 * c + 64], fma(x1.y, (double)p[2 * c + 65], acc1));
+      acc2 = fma(x2.x, (double)p[2 * c + 128], fma(x2.y, (double)p[2 * c + 129], acc2));
+      acc3 = fma(x3.x, (double)p[2 * c + 192], fma(x3.y, (double)p[2 * c + 193], acc3));
+    }
+    for (; c < n2; c += 32) {
+      const double2 x0 = a2[c];
+      acc0 = fma(x0.x, (double)p[2 * c], fma(x0.y, (double)p[2 * c + 1], acc0));
+    }
+    j0 = n2 << 1;
+  }
+  for (int64_t j = j0 + lane; j < n; j += 32) acc0 = fma(a[j], (double)p[j], acc0);
+  double acc = (acc0 + acc1) + (acc2 + acc3);
   acc = warp_sum(acc);
   if (lane == 0) v[row] = (V)(acc + mu * (double)p[row]);
 }

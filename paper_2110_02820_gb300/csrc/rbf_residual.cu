@@ -114,44 +114,50 @@ constexpr int RR_DMAX = 64;
 // whose floor must sit below the double-float one (a nearly flat kernel with
 // ||K|| / mu ~ 1e6) and for the FP64 PCG path.  The inner products stay in
 // double-float (exact FP32 products, ~2^-48 relative); the exponential is our
-// own FP64 routine: k = round(e 64 / ln 2), r = e - k (ln2/64) with ln2/64
-// split into a 24-bit head and a tail (so k times the head is exact), 2^(k/64)
-// = 2^(k >> 6) T[k & 63] with T[j] = 2^(j/64) tabulated on the host in extended
-// precision, and e^r by its Taylor polynomial to degree 6 (|r| <= ln2/128,
-// truncation < 2e-20).  Error ~4 units of 2^-53 in K_ij.
+// own FP64 routine: k = round(e 1024 / ln 2), r = e - k (ln2/1024) with ln2/1024
+// split into a 24-bit head and a tail (so k times the head is exact), 2^(k/1024)
+// = 2^(k >> 10) T[k & 1023] with T[j] = 2^(j/1024) (built per block with exp2),
+// and e^r by its Taylor polynomial to degree 4 (|r| <= ln2/2048, truncation
+// < 4e-20).  Error ~3 units of 2^-53 in K_ij; ~13 FP64 operations per entry.
 
 struct Exp64Consts {
-  double tab[64];  // 2^(j/64)
-  double l_hi, l_lo, inv_l;
+  double l_hi, l_lo, inv_l;  // ln2 / 1024 (24-bit head and tail), 1024 / ln2
 };
 
+constexpr int EXP_TAB = 1024;
+
+// exp(e) for -700 <= e <= 0 (0 below): k = round(e 1024 / ln2), r = e - k ln2/1024
+// (|r| <= ln2/2048), e^r to degree 4 (truncation < 4e-20), times 2^(j/1024) for
+// j = k mod 1024 from the table, scaled by 2^(k / 1024) through the exponent
+// field (the result stays a normal number on this range).
 __device__ __forceinline__ double exp64_neg(double e, const double* tab, double l_hi, double l_lo,
                                             double inv_l) {
-  if (e < -708.0) return 0.0;
+  if (e < -700.0) return 0.0;
   const double kd = rint(e * inv_l);
   double r = fma(-kd, l_hi, e);
   r = fma(-kd, l_lo, r);
-  double p = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-  p = fma(p, r, 1.0 / 24.0);
-  p = fma(p, r, 1.0 / 6.0);
+  double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   p = fma(p, r, 0.5);
   p = fma(p, r, 1.0);
   p = fma(p, r, 1.0);
   const int k = (int)kd;
-  return ldexp(tab[k & 63] * p, k >> 6);
+  const double t = tab[k & (EXP_TAB - 1)] * p;
+  return __longlong_as_double(__double_as_longlong(t) + ((long long)(k >> 10) << 52));
 }
 
 // ---------------------------------------------------------------- the products kernel
 //
-// y[q][i] = sum_j k(t_i, x_j) v[q][j] for RP_Q vectors per block, ROWS target
-// rows per thread (two for d <= 32, so that each point coordinate read from
-// shared memory serves two rows), the point tile read as float4 broadcasts.
+// y[q][i] = sum_j k(t_i, x_j) v[q][j] for RP_Q vectors per block (8, or 32 for
+// many vectors, so that each entry's exponential serves more of them), ROWS
+// target rows per thread (two for d <= 32 with 8 vectors, so that each point
+// coordinate read from shared memory serves two rows), the point tile read as
+// float4 broadcasts.
 // kind 0: k = K(t, x); kind 1: k = dK/dsigma = K D / sigma^3.  EXACT: k and the
 // sums in FP64 (own FP64 exponential); otherwise double-float throughout.
 // shift: 0 none, 1 mu0 v[q][i], 2 mus[q] v[q][i] (targets are the points).
-constexpr int RP_THREADS = 128, RP_BJ = 64, RP_Q = 8;
+constexpr int RP_THREADS = 128, RP_BJ = 64;
 
-template <int DMAX, int ROWS, bool EXACT>
+template <int DMAX, int ROWS, int RP_Q, bool EXACT>
 __global__ void __launch_bounds__(RP_THREADS)
 rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
                     const double* __restrict__ nrm_t, const float* __restrict__ pts, int64_t n,
@@ -165,10 +171,11 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
   __shared__ double njs[RP_BJ];
   __shared__ double vjd[EXACT ? RP_Q : 1][RP_BJ];
   __shared__ float2 vjf[EXACT ? 1 : RP_Q][RP_BJ];
-  __shared__ double tab[64];
+  __shared__ double tab[EXACT ? EXP_TAB : 1];
   __shared__ dfl inv_fact[9];
   if (EXACT) {
-    for (int t = threadIdx.x; t < 64; t += blockDim.x) tab[t] = ec.tab[t];
+    for (int t = threadIdx.x; t < EXP_TAB; t += blockDim.x)
+      tab[EXACT ? t : 0] = exp2((double)t / (double)EXP_TAB);
   } else if (threadIdx.x == 0) {
     double f = 1.0;
     inv_fact[0] = dfl_make(1.f, 0.f);
@@ -192,6 +199,9 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
     for (int k = 0; k < DMAX; ++k) xi[r][k] = (i < nt && k < d) ? tg[i * ldt + k] : 0.f;
     ni[r] = i < nt ? nrm_t[i] : 0.0;
   }
+  double ai[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) ai[r] = neg_inv_2s2 * ni[r];
   double acc[EXACT ? ROWS : 1][EXACT ? RP_Q : 1];
   float ah[EXACT ? 1 : ROWS][EXACT ? 1 : RP_Q], al[EXACT ? 1 : ROWS][EXACT ? 1 : RP_Q];
 #pragma unroll
@@ -211,7 +221,7 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
       xs[jj][k] = (j0 + jj < n && k < d) ? pts[(j0 + jj) * ld + k] : 0.f;
     }
     for (int jj = threadIdx.x; jj < RP_BJ; jj += RP_THREADS) {
-      njs[jj] = j0 + jj < n ? nrm[j0 + jj] : 0.0;
+      njs[jj] = j0 + jj < n ? (EXACT ? neg_inv_2s2 * nrm[j0 + jj] : nrm[j0 + jj]) : 0.0;
 #pragma unroll
       for (int q = 0; q < RP_Q; ++q) {
         const double vv = (q < nq && j0 + jj < n) ? v[(q0 + q) * n + j0 + jj] : 0.0;
@@ -245,10 +255,11 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
         if (EXACT) {
-          double D = (ni[r] + njs[jj]) - 2.0 * ((double)dh[r] + (double)dl[r]);
-          if (D < 0.0) D = 0.0;
-          double K = exp64_neg(D * neg_inv_2s2, tab, ec.l_hi, ec.l_lo, ec.inv_l);
-          if (kind == 1) K *= D * inv_s3;
+          // exponent = c ||t_i||^2 + c ||x_j||^2 - 2c <t_i, x_j>, c = -1/(2 sigma^2)
+          const double dot = (double)dh[r] + (double)dl[r];
+          const double ex = fmin(fma(-2.0 * neg_inv_2s2, dot, ai[r] + njs[jj]), 0.0);
+          double K = exp64_neg(ex, tab, ec.l_hi, ec.l_lo, ec.inv_l);
+          if (kind == 1) K *= (ex / neg_inv_2s2) * inv_s3;  // D = exponent / c
 #pragma unroll
           for (int q = 0; q < RP_Q; ++q)
             if (q < nq) acc[EXACT ? r : 0][EXACT ? q : 0] =
@@ -301,11 +312,10 @@ static Exp64Consts exp64_consts() {
   static bool init = false;
   if (!init) {
     const long double ln2 = logl(2.0L);
-    const long double L = ln2 / 64.0L;
+    const long double L = ln2 / (long double)EXP_TAB;
     c.l_hi = (double)(float)L;
     c.l_lo = (double)(L - (long double)c.l_hi);
-    c.inv_l = (double)(64.0L / ln2);
-    for (int j = 0; j < 64; ++j) c.tab[j] = (double)exp2l((long double)j / 64.0L);
+    c.inv_l = (double)((long double)EXP_TAB / ln2);
     init = true;
   }
   return c;
@@ -334,6 +344,18 @@ int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_
 
 namespace {
 
+template <int DMAX, int ROWS, int Q, bool EXACT>
+void products_go(const float* tg, int64_t nt, int64_t ldt, const double* nrm_t, const float* pts,
+                 int64_t n, int64_t ldp, const double* nrm, int64_t d, double a, double b, int kind,
+                 int shift, const double* d_mu, double mu0, int64_t nvec, const double* v,
+                 double* y, const int* skip, const Exp64Consts& ec, cudaStream_t s) {
+  rbf_products_kernel<DMAX, ROWS, Q, EXACT>
+      <<<dim3((unsigned)cdiv(nt, ROWS * RP_THREADS), (unsigned)cdiv(nvec, Q)), RP_THREADS, 0, s>>>(
+          tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y, skip,
+          ec);
+  count_launch();
+}
+
 template <bool EXACT>
 int32_t products_launch(const float* tg, int64_t nt, int64_t ldt, const double* nrm_t,
                         const float* pts, int64_t n, int64_t ldp, const double* nrm, int64_t d,
@@ -342,24 +364,19 @@ int32_t products_launch(const float* tg, int64_t nt, int64_t ldt, const double* 
                         cudaStream_t s) {
   const double a = -1.0 / (2.0 * sigma * sigma), b = 1.0 / (sigma * sigma * sigma);
   const Exp64Consts ec = exp64_consts();
-  const unsigned gy = (unsigned)cdiv(nvec, RP_Q);
-  if (d <= 16) {
-    rbf_products_kernel<16, 2, EXACT>
-        <<<dim3((unsigned)cdiv(nt, 2 * RP_THREADS), gy), RP_THREADS, 0, s>>>(
-            tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y,
-            skip, ec);
-  } else if (d <= 32) {
-    rbf_products_kernel<32, 2, EXACT>
-        <<<dim3((unsigned)cdiv(nt, 2 * RP_THREADS), gy), RP_THREADS, 0, s>>>(
-            tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y,
-            skip, ec);
+#define NYS_PRODUCTS(DM, R, Q)                                                                  \
+  products_go<DM, R, Q, EXACT>(tg, nt, ldt, nrm_t, pts, n, ldp, nrm, d, a, b, kind, shift, d_mu, \
+                               mu0, nvec, v, y, skip, ec, s)
+  if (nvec <= 8) {
+    if (d <= 16) NYS_PRODUCTS(16, 2, 8);
+    else if (d <= 32) NYS_PRODUCTS(32, 2, 8);
+    else NYS_PRODUCTS(64, 1, 8);
   } else {
-    rbf_products_kernel<64, 1, EXACT>
-        <<<dim3((unsigned)cdiv(nt, RP_THREADS), gy), RP_THREADS, 0, s>>>(
-            tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y,
-            skip, ec);
+    if (d <= 16) NYS_PRODUCTS(16, 1, 32);
+    else if (d <= 32) NYS_PRODUCTS(32, 1, 32);
+    else NYS_PRODUCTS(64, 1, 32);
   }
-  count_launch();
+#undef NYS_PRODUCTS
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }

@@ -39,6 +39,8 @@
 // records NYS_ERR_TIMEOUT in *err, lets its copies in flight land, frees its
 // TMEM and returns.
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "internal.h"
 #include "ptx.cuh"
@@ -81,6 +83,7 @@ struct RtCfg {
 struct RtArgs {
   const float* cn;     // [npad] cn_j (padding: -1e30, so that k = 0)
   float m2c;
+  const float* m2c_dev;  // one vector: m2c for the scaled FP16 points (device)
   int64_t n;           // number of points
   int ntiles;          // npad / RT_BN
   int ksteps;          // ceil(d / 8): K-steps of GEMM1 (coordinates beyond d are zero)
@@ -555,17 +558,41 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 // tiles round-robin, each with its own 128-column TMEM buffer, so that every
 // SMSP holds four exp warps to cover the tensor-memory latency; within a tile
 // the next 32 columns are loaded while the current ones are used.
+//
+// GEMM1 runs on FP16 splits: each point, scaled by a power of two so that its
+// largest coordinate lies in [2^9, 2^10), is one 128-byte row [hi(32) | lo(32)]
+// of FP16 values (hi = fp16(x), lo = fp16(x - hi)), and the inner products are
+// hi.hi + hi.lo + lo.hi as kind::f16 MMAs (K = 16, FP32 accumulation): the
+// 2^-22 relative accuracy of 3xTF32 at twice its tensor rate.
 constexpr int GV_BN = 128;
 constexpr int GV_G = 4;
 constexpr int GV_THREADS = 64 + GV_G * 128;
-constexpr int GV_NS = 4;
-constexpr int GV_XJ = GV_BN * 128;            // X_J hi (or lo): 128 rows x 32 FP32
-constexpr int GV_CN = 2 * GV_XJ;              // cn_J
+constexpr int GV_NS = 6;
+constexpr int GV_XJ = GV_BN * 128;            // X_J [hi | lo]: 128 rows x 64 FP16
+constexpr int GV_CN = GV_XJ;                  // cn_J
 constexpr int GV_VJ = GV_CN + GV_BN * 4;      // v_J
 constexpr int GV_TX = GV_VJ + GV_BN * 4;
 constexpr int GV_STAGE = (GV_TX + 1023) / 1024 * 1024;
-constexpr int GV_A = RT_BM * 128;
-constexpr int GV_SMEM = 1024 + 2 * GV_A + GV_NS * GV_STAGE + 256 + GV_G * RT_BM * 8;
+constexpr int GV_A = RT_BM * 128;             // X_I [hi | lo]
+constexpr int GV_SMEM = 1024 + GV_A + GV_NS * GV_STAGE + 256 + GV_G * RT_BM * 8;
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Instruction descriptor: kind::f16 with FP16 A and B (both K-major), FP32 D.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+  return (1u << 4)                      // D format: F32
+         | (0u << 7)                    // A format: F16
+         | (0u << 10)                   // B format: F16
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
 static_assert(GV_SMEM <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ void gv_bar_sync() {
@@ -578,7 +605,7 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
   unsigned char* sm =
       reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;
-  unsigned char* sSt = sm + 2 * GV_A;
+  unsigned char* sSt = sm + GV_A;
   uint64_t* full = reinterpret_cast<uint64_t*>(sSt + GV_NS * GV_STAGE);
   uint64_t* empty = full + GV_NS;
   uint64_t* afull = empty + GV_NS;
@@ -623,11 +650,9 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
   } else if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      mbar_arrive_expect_tx(afull, 2u * GV_A);
+      mbar_arrive_expect_tx(afull, (uint32_t)GV_A);
       tma_load_2d(sA, &tmX, 0, (int)m0, afull);
       tma_load_2d(sA + GV_A / 2, &tmX, 0, (int)m0 + 64, afull);
-      tma_load_2d(sA + GV_A, &tmX, RT_DP, (int)m0, afull);
-      tma_load_2d(sA + GV_A + GV_A / 2, &tmX, RT_DP, (int)m0 + 64, afull);
       int issued = 0;
       for (int t = 0; t < T; ++t) {
         const int s = t % GV_NS;
@@ -641,8 +666,6 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
         mbar_arrive_expect_tx(&full[s], (uint32_t)GV_TX);
         tma_load_2d(st, &tmX, 0, j0, &full[s]);
         tma_load_2d(st + GV_XJ / 2, &tmX, 0, j0 + 64, &full[s]);
-        tma_load_2d(st + GV_XJ, &tmX, RT_DP, j0, &full[s]);
-        tma_load_2d(st + GV_XJ + GV_XJ / 2, &tmX, RT_DP, j0 + 64, &full[s]);
         bulk_g2s(st + GV_CN, a.cn + j0, GV_BN * 4, &full[s]);
         bulk_g2s(st + GV_VJ, a.vj + j0, GV_BN * 4, &full[s]);
         issued = t + 1;
@@ -662,11 +685,11 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer (GEMM1 only)
-      constexpr uint32_t idesc = tf32_idesc(RT_BM, GV_BN);
+      constexpr uint32_t idesc = f16_idesc(RT_BM, GV_BN);
       bool ok = mbar_wait_bounded(afull, 0u);
       const uint64_t aHiD = sw128_kmajor_desc(smem_u32(sA));
-      const uint64_t aLoD = sw128_kmajor_desc(smem_u32(sA + GV_A));
-      const int ks = a.ksteps;
+      const uint64_t aLoD = aHiD + (uint64_t)(64 >> 4);  // lo half of each 128-byte row
+      const int ks = a.ksteps;                             // ceil(d / 16)
       for (int t = 0; ok && t < T; ++t) {
         const int s = t % GV_NS, b = t % GV_G;
         if (!mbar_wait_bounded(&full[s], (uint32_t)((t / GV_NS) & 1))) { ok = false; break; }
@@ -676,17 +699,17 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
         }
         tc_fence_after();
         const uint64_t bHiD = sw128_kmajor_desc(smem_u32(sSt + s * GV_STAGE));
-        const uint64_t bLoD = bHiD + (uint64_t)(GV_XJ >> 4);
+        const uint64_t bLoD = bHiD + (uint64_t)(64 >> 4);
         const uint32_t dP = tmem + (uint32_t)(b * GV_BN);
 #pragma unroll
         for (int pass = 0; pass < 3; ++pass) {
           const uint64_t ad = pass == 2 ? aLoD : aHiD;
           const uint64_t bd = pass == 1 ? bLoD : bHiD;
 #pragma unroll
-          for (int k = 0; k < RT_DP / 8; ++k)
+          for (int k = 0; k < 2; ++k)  // 16 FP16 (32 bytes) per K-step, d <= 32
             if (k < ks)
-              mma_tf32(dP, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
-                       (pass > 0 || k > 0) ? 1u : 0u);
+              mma_f16(dP, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
+                      (pass > 0 || k > 0) ? 1u : 0u);
         }
         mma_commit(&pfull[b]);
         mma_commit(&empty[s]);
@@ -701,7 +724,7 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
     const int64_t row = m0 + r;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const float ai = a.cn[row];
-    const float m2c = a.m2c;
+    const float m2c = *a.m2c_dev;  // log2(e) / (sigma^2 scale^2) for the scaled points
     bool ok = true;
     float acc = 0.f, comp = 0.f;
     for (int t = g; t < T; t += GV_G) {
@@ -768,6 +791,44 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
   __syncthreads();
   if (warp == 1) tmem_dealloc(tmem, RT_TMEM_COLS);
   if (threadIdx.x == 0 && s_fail) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
+}
+
+// max |x_jk| over the points (bit pattern of a non-negative float).
+__global__ void rt_absmax_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld,
+                                 unsigned int* out) {
+  float m = 0.f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / d, k = e - j * d;
+    m = fmaxf(m, fabsf(pts[j * ld + k]));
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// One-vector layout: XS16[j] = [fp16(s x_j) | fp16(s x_j - fp16(s x_j))] (32 + 32
+// FP16, zero padded) with s = 2^(10 - e), max |x| in [2^(e-1), 2^e); cn as for
+// the FP32 layout; *m2c_dev = m2c / s^2.
+__global__ void rt_prep_points16_kernel(const float* __restrict__ pts, int64_t n, int64_t d,
+                                        int64_t ld, int64_t npad, double c, double m2c,
+                                        const unsigned int* absmax, __half* __restrict__ XS16,
+                                        float* __restrict__ cn, float* m2c_dev) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const float mx = __uint_as_float(*absmax);
+  int e = 0;
+  if (mx > 0.f) frexpf(mx, &e);
+  const float sc = mx > 0.f ? ldexpf(1.f, 10 - e) : 1.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *m2c_dev = (float)(m2c / ((double)sc * (double)sc));
+  if (j >= npad) return;
+  const float x = (j < n && lane < d) ? pts[j * ld + lane] : 0.0f;
+  const float xs = x * sc;
+  const __half hi = __float2half_rn(xs);
+  const __half lo = __float2half_rn(xs - __half2float(hi));
+  XS16[j * 64 + lane] = hi;
+  XS16[j * 64 + 32 + lane] = lo;
+  const double s2 = warp_sum((double)x * (double)x);
+  if (lane == 0) cn[j] = (j < n) ? (float)(c * s2) : -1e30f;
 }
 
 // XS[j] = [tf32(x_j) | tf32(x_j - tf32(x_j))] (32 + 32 FP32, zero padded),
@@ -863,18 +924,20 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
   float* VS = reinterpret_cast<float*>((unsigned char*)cn + align((size_t)npad * 4));
   const double l2e = 1.4426950408889634;
   const double c = -l2e / (2.0 * sigma * sigma);
-  rt_prep_points_kernel<<<(unsigned)cdiv(npad, 8), 256, 0, s>>>(pts, n, d, ld, npad, c, XS, cn);
-  count_launch();
+  if (S > 1) {  // one vector uses the FP16 layout below
+    rt_prep_points_kernel<<<(unsigned)cdiv(npad, 8), 256, 0, s>>>(pts, n, d, ld, npad, c, XS, cn);
+    count_launch();
+  }
   const int64_t tot = spad * npad;
   const unsigned gv = (unsigned)(cdiv(tot, 256) < 4096 ? cdiv(tot, 256) : 4096);
   rt_prep_vecs_kernel<<<gv, 256, 0, s>>>(V, nvec, n, ldv, spad, npad, nv, VS); count_launch();
   CUtensorMap tx, tv;
-  if (!tmap_f32_2d(&tx, XS, npad, 64, 64, 64, 32)) return NYS_ERR_CUDA;
+  if (S > 1 && !tmap_f32_2d(&tx, XS, npad, 64, 64, 64, 32)) return NYS_ERR_CUDA;
   if (S > 1 && !tmap_f32_2d(&tv, VS, nv * spad, npad, npad, S, 32)) return NYS_ERR_CUDA;
-  if (S == 1) tv = tx;  // unused
   RtArgs a;
   a.cn = cn;
   a.m2c = (float)(l2e / (sigma * sigma));
+  a.m2c_dev = nullptr;
   a.n = n;
   a.ntiles = (int)(npad / RT_BN);
   a.ksteps = (int)cdiv(d, 8);
@@ -892,7 +955,21 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
   a.done_stride = done_stride;
   a.err = err;
   if (S == 1) {
-    // one launch per vector (nvec <= 2), each reading its own padded copy
+    // FP16 split layout of the points (in the FP32 layout's space), then one
+    // launch per vector (nvec <= 2), each reading its own padded copy
+    unsigned int* absmax = reinterpret_cast<unsigned int*>(w + 64);
+    float* m2c_dev = reinterpret_cast<float*>(w + 72);
+    NYS_CUDA_TRY(cudaMemsetAsync(absmax, 0, sizeof(unsigned int), s));
+    const int64_t nd = n * d;
+    rt_absmax_kernel<<<(unsigned)(cdiv(nd, 256) < 1024 ? cdiv(nd, 256) : 1024), 256, 0, s>>>(
+        pts, n, d, ld, absmax);
+    count_launch();
+    __half* XS16 = reinterpret_cast<__half*>(XS);
+    rt_prep_points16_kernel<<<(unsigned)cdiv(npad, 8), 256, 0, s>>>(
+        pts, n, d, ld, npad, c, l2e / (sigma * sigma), absmax, XS16, cn, m2c_dev);
+    count_launch();
+    CUtensorMap tx16;
+    if (!tmap_f16_2d(&tx16, XS16, npad, 64, 64, 64, 64)) return NYS_ERR_CUDA;
     NYS_CUDA_TRY(
         cudaFuncSetAttribute(rbf_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GV_SMEM));
     for (int64_t q = 0; q < nvec; ++q) {
@@ -900,7 +977,9 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
       aq.vec = q;
       aq.vj = VS + q * npad;
       aq.ntiles = (int)(npad / GV_BN);
-      rbf_gemv_kernel<<<(unsigned)(npad / RT_BM), GV_THREADS, GV_SMEM, s>>>(tx, aq);
+      aq.ksteps = (int)cdiv(d, 16);
+      aq.m2c_dev = m2c_dev;
+      rbf_gemv_kernel<<<(unsigned)(npad / RT_BM), GV_THREADS, GV_SMEM, s>>>(tx16, aq);
       count_launch();
       NYS_CUDA_TRY(cudaGetLastError());
     }

@@ -197,6 +197,20 @@ bool tmap_f32_2d(CUtensorMap* tm, const float* base, int64_t rows, int64_t cols,
   return r == CUDA_SUCCESS;
 }
 
+bool tmap_f16_2d(CUtensorMap* tm, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                 int box_rows, int box_cols) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), gdim, gstride,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // 2-D FP32 tensor map over a row-major [rows x cols] array with row stride ld
 // (elements); box = [box_rows x 32 cols], 128-byte swizzle, zero fill.
 static bool make_map(CUtensorMap* tm, const float* base, int64_t rows, int64_t cols, int64_t ld,

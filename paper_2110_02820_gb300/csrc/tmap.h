@@ -13,5 +13,8 @@ namespace nys {
 // false when the driver entry point is missing or rejects the map.
 bool tmap_f32_2d(CUtensorMap* tm, const float* base, int64_t rows, int64_t cols, int64_t ld,
                  int box_rows, int box_cols);
+// The same for FP16 elements (ld * 2 a multiple of 16, box_cols * 2 <= 128).
+bool tmap_f16_2d(CUtensorMap* tm, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                 int box_rows, int box_cols);
 
 }  // namespace nys
