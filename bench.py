@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--matvec-only", action="store_true",
                     help="run only the workload's dominant FP32 matvec (--steps times after "
                          "--warmup); the command behind the ncu summaries in profiles/")
+    ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "columns"],
+                    help="krr workload: adaptive Gaussian sketch (default) or column-sampling "
+                         "Nystrom at --cols sampled points")
+    ap.add_argument("--cols", type=int, default=1024)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="non-default workloads: multiply the number of points by this factor")
     return ap.parse_args()
@@ -493,8 +497,12 @@ def run_workload(args):
             def step(seed):
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record()
-                f, info = ny.nys_sketch_adaptive(op, ell0, ell_max, ny.NYS_RULE_RATIO, 40.0, 0, mu,
-                                                 seed=seed, precision=ny.NYS_PREC_MIXED)
+                if args.sketch == "columns":
+                    f = ny.nys_sketch_columns(op, args.cols, seed=seed, precision=ny.NYS_PREC_MIXED)
+                    info = None
+                else:
+                    f, info = ny.nys_sketch_adaptive(op, ell0, ell_max, ny.NYS_RULE_RATIO, 40.0, 0,
+                                                     mu, seed=seed, precision=ny.NYS_PREC_MIXED)
                 e1.record()
                 x, res, _ = ny.pcg_solve(op, f, mu, b, tol=tol, precision=ny.NYS_PREC_MIXED)
                 e2.record()
@@ -502,8 +510,10 @@ def run_workload(args):
                 phase["sketch_ms"], phase["pcg_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
                 f.free()
                 return res[0], info
+            sk = (f"column sampling, ell={args.cols} uniform points" if args.sketch == "columns"
+                  else f"adaptive ratio rule 40, ell {ell0}->{ell_max}")
             cfg = (f"kernel ridge n={n} d={d} GMM(10), sigma=median dist={sigma:.3f}, mu=1e-6 n, "
-                   f"adaptive ratio rule 40, ell {ell0}->{ell_max}, mixed + FP64 refinement, tol {tol}")
+                   f"{sk}, mixed + FP64 refinement, tol {tol}")
         else:
             mus = list(np.repeat(wl.regularization_path(32, 1e-8 * n, 1e-1 * n), 4))
             B = T(np.tile(wl.rhs(n, seed=0, nrhs=4), (32, 1)))
@@ -540,8 +550,9 @@ def run_workload(args):
         if args.workload == "krr":
             line["solve"] = {"iterations": res.iterations, "refinements": res.refinements,
                              "rel_residual": res.rel_residual, "status": res.status,
-                             "ell": info.ell, "doublings": info.doublings,
-                             "lambda_ell": info.lambda_ell}
+                             "ell": info.ell if info else args.cols,
+                             "doublings": info.doublings if info else None,
+                             "lambda_ell": info.lambda_ell if info else None}
         else:
             its = [r.iterations for r in res]
             ok = [r.status == 0 for r in res]

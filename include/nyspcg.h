@@ -95,6 +95,20 @@ typedef struct nys_factor nys_factor;
 int32_t nys_sketch(const nys_operator* op, int64_t ell, uint64_t seed, const double* omega,
                    int32_t precision, nys_factor** out, void* stream);
 
+/* Column-sampling Nystrom sketch (Sec. 2.2, random projection versus column
+ * sampling; the construction the paper uses for kernel ridge regression):
+ * Algorithm 1 with Omega = I[:, S] for ell distinct column indices S, so that
+ * the thin QR is trivial and Y = A[:, S].  The Gaussian kernel evaluates those
+ * ell columns directly (n ell entries, against n^2 ell for a random
+ * projection); dense A gathers them; the ridge operator forms X^T (X Omega).
+ * `cols` (device, int64 [ell], distinct, in [0, n)) gives S; if NULL, S is
+ * drawn uniformly without replacement from `seed`.  Indices are not checked on
+ * the device: out-of-range or repeated entries are a caller error.  Gaussian
+ * operators need d <= 64.  Otherwise as nys_sketch (factor, statuses,
+ * precision).  Synchronises `stream`. */
+int32_t nys_sketch_columns(const nys_operator* op, int64_t ell, uint64_t seed, const int64_t* cols,
+                           int32_t precision, nys_factor** out, void* stream);
+
 typedef enum nys_adapt_rule {
   NYS_RULE_ERR = 0,   /* Strategy 1 (Sec. 5.4.1): stop when the Algorithm 4 estimate <= tol */
   NYS_RULE_RATIO = 1  /* Strategy 2 (Sec. 5.4.2): stop when lambda_hat_ell / mu <= tol */

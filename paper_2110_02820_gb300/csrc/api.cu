@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -354,6 +355,58 @@ static int32_t sketch_impl(const nys_operator* op, int64_t ell, uint64_t seed, c
   return NYS_OK;
 }
 
+// ell distinct indices of [0, n), uniformly without replacement: a partial
+// Fisher-Yates shuffle (swaps kept in a map) driven by SplitMix64 from `seed`.
+static void sample_columns(int64_t n, int64_t ell, uint64_t seed, std::vector<int64_t>& out) {
+  uint64_t st = seed ^ 0x636f6c756d6e73ull;  // stream tag
+  auto next = [&st]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  std::unordered_map<int64_t, int64_t> swapped;
+  auto at = [&swapped](int64_t i) {
+    auto it = swapped.find(i);
+    return it == swapped.end() ? i : it->second;
+  };
+  out.resize(ell);
+  for (int64_t c = 0; c < ell; ++c) {
+    const int64_t r = c + (int64_t)(next() % (uint64_t)(n - c));
+    const int64_t vc = at(c), vr = at(r);
+    swapped[r] = vc;
+    swapped[c] = vr;
+    out[c] = vr;
+  }
+}
+
+template <typename T>
+static int32_t columns_impl(const nys_operator* op, int64_t ell, const int64_t* cols,
+                            int precision, nys_factor** out, cudaStream_t s) {
+  const int64_t n = op->n;
+  nys_factor* f = nullptr;
+  NYS_TRY(factor_alloc(&f, n, ell, Ops<T>::f64, precision));
+  int32_t st;
+  {
+    Scratch sc(s);
+    T *Q, *Y;
+    st = sc.get(&Q, n * ell);
+    if (st == NYS_OK) st = sc.get(&Y, n * ell);
+    if (st == NYS_OK) st = op_columns(op, Ops<T>::f64, cols, ell, Q, Y, s);
+    if (st == NYS_OK) st = shifted_core<T>(Q, Y, n, ell, false, 1.0, f, s);
+    if (st == NYS_OK) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = NYS_ERR_CUDA;
+    }
+  }
+  if (st != NYS_OK) {
+    nys_factor_free(f);
+    return st;
+  }
+  *out = f;
+  return NYS_OK;
+}
+
 // ---------------------------------------------------------------- Algorithm 4
 
 // y -= U diag(c) U^T x  (x, y FP64 n; U n x ell of type TU; c FP64 ell)
@@ -627,6 +680,30 @@ int32_t nys_sketch(const nys_operator* op, int64_t ell, uint64_t seed, const dou
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == NYS_PREC_F64) return sketch_impl<double>(op, ell, seed, omega, precision, out, s);
   return sketch_impl<float>(op, ell, seed, omega, precision, out, s);
+}
+
+int32_t nys_sketch_columns(const nys_operator* op, int64_t ell, uint64_t seed, const int64_t* cols,
+                           int32_t precision, nys_factor** out, void* stream) {
+  if (!out) return NYS_ERR_ARG;
+  *out = nullptr;
+  NYS_TRY(check_op(op));
+  if (ell < 1 || ell > op->n || ell > kMaxEll) return NYS_ERR_ARG;
+  if (precision != NYS_PREC_F64 && precision != NYS_PREC_MIXED) return NYS_ERR_ARG;
+  if (op->kind == NYS_OP_RBF && op->d > 64) return NYS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  const int64_t* dcols = cols;
+  if (!dcols) {
+    std::vector<int64_t> h;
+    sample_columns(op->n, ell, seed, h);
+    int64_t* d;
+    NYS_TRY(sc.get(&d, ell));
+    NYS_CUDA_TRY(cudaMemcpyAsync(d, h.data(), ell * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));  // h goes out of scope
+    dcols = d;
+  }
+  if (precision == NYS_PREC_F64) return columns_impl<double>(op, ell, dcols, precision, out, s);
+  return columns_impl<float>(op, ell, dcols, precision, out, s);
 }
 
 int32_t nys_sketch_adaptive(const nys_operator* op, int64_t ell0, int64_t ell_max, int32_t rule,

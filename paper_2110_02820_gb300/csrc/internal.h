@@ -131,6 +131,11 @@ int32_t lambda_from_sigma(const double* sigma, const double* d_nu, double* lam, 
 int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int64_t ell,
                   cudaStream_t s);
 
+// Column sampling: Q = I[:, cols] and Y = A Q = A[:, cols] (n x ell, FP64 when
+// f64 else FP32); cols device [ell], distinct indices in [0, n).
+int32_t op_columns(const nys_operator* op, bool f64, const int64_t* cols, int64_t ell, void* Q,
+                   void* Y, cudaStream_t s);
+
 // Bytes of device workspace op_matvec_* needs (its first 256 bytes hold a
 // device error word that must start at zero).
 size_t op_matvec_work_bytes(const nys_operator* op, bool accurate);

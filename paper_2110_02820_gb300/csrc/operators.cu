@@ -841,6 +841,96 @@ int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int6
   return NYS_OK;
 }
 
+// ============================================================ column sampling
+//
+// Q = I[:, S] (the selection matrix of the sampled columns S) and Y = A Q =
+// A[:, S] for the column-sampling Nystrom sketch (Sec. 2.2, random projection
+// versus column sampling): the Gaussian kernel evaluates its l columns directly
+// (n l entries instead of n^2 l), dense A gathers them, the ridge operator
+// forms X^T (X Q).
+
+template <typename T>
+__global__ void selection_kernel(const int64_t* __restrict__ cols, int64_t n, int64_t ell,
+                                 T* __restrict__ Q) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * ell;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ell, c = e - i * ell;
+    Q[e] = (cols[c] == i) ? T(1) : T(0);
+  }
+}
+
+template <typename T>
+__global__ void dense_columns_kernel(const double* __restrict__ A, int64_t n, int64_t ld,
+                                     const int64_t* __restrict__ cols, int64_t ell,
+                                     T* __restrict__ Y) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * ell;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ell, c = e - i * ell;
+    Y[e] = (T)A[i * ld + cols[c]];  // A symmetric: A[i][S_c]
+  }
+}
+
+// Y[i][c] = exp(-||x_i - x_{S_c}||^2 / (2 sigma^2)); distances by direct
+// differences (FP64 sums for T = double).  Block: 32 columns x 8 rows.
+template <typename T>
+__global__ void rbf_columns_kernel(const float* __restrict__ pts, int64_t n, int64_t d,
+                                   int64_t ld, double sigma, const int64_t* __restrict__ cols,
+                                   int64_t ell, T* __restrict__ Y) {
+  __shared__ float xc[32][RBF_DMAX + 1];
+  const int64_t c0 = (int64_t)blockIdx.x * 32;
+  for (int e = threadIdx.y * 32 + threadIdx.x; e < 32 * d; e += 256) {
+    const int cc = e / (int)d, k = e - cc * (int)d;
+    xc[cc][k] = (c0 + cc < ell) ? pts[cols[c0 + cc] * ld + k] : 0.f;
+  }
+  __syncthreads();
+  const int64_t c = c0 + threadIdx.x;
+  const T scale = (T)(-1.0 / (2.0 * sigma * sigma));
+  for (int64_t i = (int64_t)blockIdx.y * 8 + threadIdx.y; i < n; i += (int64_t)gridDim.y * 8) {
+    T dist = T(0);
+    for (int64_t k = 0; k < d; ++k) {
+      const T df = (T)pts[i * ld + k] - (T)xc[threadIdx.x][k];
+      dist = fma(df, df, dist);
+    }
+    if (c < ell) Y[i * ell + c] = exp(dist * scale);
+  }
+}
+
+int32_t op_columns(const nys_operator* op, bool f64, const int64_t* cols, int64_t ell, void* Q,
+                   void* Y, cudaStream_t s) {
+  const int64_t n = op->n;
+  const unsigned g = (unsigned)(cdiv(n * ell, 256) < 8192 ? cdiv(n * ell, 256) : 8192);
+  if (f64)
+    selection_kernel<double><<<g, 256, 0, s>>>(cols, n, ell, (double*)Q);
+  else
+    selection_kernel<float><<<g, 256, 0, s>>>(cols, n, ell, (float*)Q);
+  count_launch();
+  if (op->kind == NYS_OP_GRAM) return op_sketch(op, f64, Q, Y, ell, s);
+  if (op->kind == NYS_OP_DENSE) {
+    if (f64)
+      dense_columns_kernel<double><<<g, 256, 0, s>>>((const double*)op->data, n, op->ld, cols,
+                                                     ell, (double*)Y);
+    else
+      dense_columns_kernel<float><<<g, 256, 0, s>>>((const double*)op->data, n, op->ld, cols, ell,
+                                                    (float*)Y);
+    count_launch();
+    NYS_CUDA_TRY(cudaGetLastError());
+    return NYS_OK;
+  }
+  if (op->d > RBF_DMAX) return NYS_ERR_ARG;
+  const unsigned gy = (unsigned)(cdiv(n, 8) < 2048 ? cdiv(n, 8) : 2048);
+  const dim3 grid((unsigned)cdiv(ell, 32), gy);
+  if (f64)
+    rbf_columns_kernel<double><<<grid, dim3(32, 8), 0, s>>>((const float*)op->data, n, op->d,
+                                                            op->ld, op->sigma, cols, ell,
+                                                            (double*)Y);
+  else
+    rbf_columns_kernel<float><<<grid, dim3(32, 8), 0, s>>>((const float*)op->data, n, op->d,
+                                                           op->ld, op->sigma, cols, ell, (float*)Y);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
 size_t op_matvec_work_bytes(const nys_operator* op, bool accurate) {
   if (op->kind == NYS_OP_GRAM) return gram_work_bytes(op, accurate ? sizeof(double) : sizeof(float));
   if (op->kind == NYS_OP_RBF && rbf_tc_supported(op->d)) return rbf_tc_work_bytes(op->n, 1, 3);

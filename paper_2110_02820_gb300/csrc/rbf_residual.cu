@@ -2,18 +2,23 @@
 // refinement residual r = b - (K + mu I) x of the kernel-ridge workloads
 // (Sec. 6.5).  GB300 runs FP64 at a small fraction of its FP32 rate, so each
 // kernel entry is built from pairs of FP32 numbers ("double-float", Dekker
-// 1971) to ~2^-44 relative accuracy:
+// 1971) to a few units of 2^-48 relative accuracy, with no FP64 operation in
+// the inner loop:
 //
-//   D_ij = ||x_i||^2 + ||x_j||^2 - 2 x_i . x_j   exact FP32 products (one FMA
-//                                                  each) summed with TwoSum;
-//   K_ij = exp(-D_ij / (2 sigma^2))               own double-float exp: e = k ln2 + r,
-//          r reduced again by 2^-5, expm1(r / 32) by its Taylor series to
-//          degree 8 (truncation < 1e-23), then five squarings
-//          p <- p (p + 2) (expm1(2s) = expm1(s) (expm1(s) + 2)) and a 2^k scale;
-//   y_q[i] = sum_j K_ij x_q[j]                    double-float accumulation.
+//   e_ij = c ||x_i||^2 + c ||x_j||^2 - 2c x_i . x_j   (c = -1/(2 sigma^2)): the
+//          inner product from exact FP32 products (one FMA each) summed with
+//          TwoSum; the two norm terms rounded to double-float once per row and
+//          once per point tile;
+//   K_ij = exp(e_ij)                                  own double-float exp:
+//          e / ln2 = k/1024 + f (|f| <= 2^-11), 2^(k/1024) = 2^(k >> 10) T[k & 1023]
+//          with T[j] = 2^(j/1024) in double-float (built per block), and
+//          e^(f ln2) = 1 + g + g^2/2 + g^3/6 + g^4/24 (|g| <= ln2 2^-11, truncation
+//          below 4e-20) with g^2 split exactly;
+//   y_q[i] = sum_j K_ij x_q[j]                        double-float accumulation.
 //
-// One thread per row i, a tile of points (and their norms) in shared memory,
-// up to RR_Q right-hand sides per launch in registers.
+// One thread per row i (two for d <= 32 with few vectors), a tile of points
+// (and their norm terms) in shared memory, up to RP_Q right-hand sides per
+// launch in registers.
 
 #include <cmath>
 
@@ -46,25 +51,11 @@ __device__ __forceinline__ dfl dfl_norm(float s, float e) {
   return r;
 }
 
-__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
-  float s, e;
-  two_sum(a.hi, b.hi, s, e);
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  return dfl_norm(s, e);
-}
-
 __device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  return dfl_norm(p, e);
-}
-
-__device__ __forceinline__ dfl dfl_mul_f(dfl a, float b) {
-  const float p = __fmul_rn(a.hi, b);
-  float e = __fmaf_rn(a.hi, b, -p);
-  e = __fmaf_rn(a.lo, b, e);
   return dfl_norm(p, e);
 }
 
@@ -83,27 +74,52 @@ __device__ __forceinline__ dfl dfl_from_double(double x) {
   return dfl_make(h, __double2float_rn(x - (double)h));
 }
 
-// exp(e) for e <= 0 in double-float (see the file comment).
-__device__ __forceinline__ dfl dfl_exp_neg(dfl e, const dfl* inv_fact, dfl ln2) {
-  if (e.hi < -100.f) return dfl_make(0.f, 0.f);
-  const float k = rintf(__fmul_rn(e.hi, 1.4426950408889634f));
-  // r = e - k ln2 in double-float
-  dfl r = dfl_add(e, dfl_mul_f(ln2, -k));
-  // s = r / 32 (exact scaling)
-  dfl s = dfl_make(r.hi * 0.03125f, r.lo * 0.03125f);
-  // expm1(s) = s + s^2/2! + ... + s^8/8!  (Horner)
-  dfl p = inv_fact[8];
-#pragma unroll
-  for (int q = 7; q >= 1; --q) p = dfl_add(dfl_mul(p, s), inv_fact[q]);
-  p = dfl_mul(p, s);
-  // five doublings: expm1(2s) = expm1(s) (expm1(s) + 2)
-#pragma unroll
-  for (int q = 0; q < 5; ++q) p = dfl_mul(p, dfl_add(p, dfl_make(2.f, 0.f)));
-  dfl v = dfl_add(p, dfl_make(1.f, 0.f));
-  const int ki = (int)k;
-  v.hi = ldexpf(v.hi, ki);
-  v.lo = ldexpf(v.lo, ki);
-  return v;
+// log2(e) and ln 2 as double-float constants
+constexpr double kLog2e = 1.44269504088896340736, kLn2 = 0.69314718055994530942;
+constexpr float kLog2eHi = (float)kLog2e, kLog2eLo = (float)(kLog2e - (double)kLog2eHi);
+constexpr float kLn2Hi = (float)kLn2, kLn2Lo = (float)(kLn2 - (double)kLn2Hi);
+constexpr int DFL_TAB = 1024;
+
+// exp(e) for e <= 0 in double-float (see the file comment); tab[j] = 2^(j/1024)
+// as (hi, lo).  Zero below e = -126 ln 2, where K_ij < 2^-126.
+__device__ __forceinline__ dfl dfl_exp_neg(dfl e, const float2* tab) {
+  // t = e / ln 2
+  const float th = __fmul_rn(e.hi, kLog2eHi);
+  float tl = __fmaf_rn(e.hi, kLog2eHi, -th);
+  tl = __fmaf_rn(e.hi, kLog2eLo, tl);
+  tl = __fmaf_rn(e.lo, kLog2eHi, tl);
+  if (th < -126.f) return dfl_make(0.f, 0.f);
+  // k = round(1024 th) through the 1.5 2^23 shifter (exact on |1024 th| < 2^22)
+  const float kf = __fadd_rn(__fmul_rn(th, 1024.f), 12582912.f);
+  const int k = __float_as_int(kf) - 0x4B400000;
+  const float kr = __fsub_rn(kf, 12582912.f);
+  // f = (th - k/1024) + tl: the first difference is exact; tl (~2^-24 |t|) can be
+  // as large as f itself, so the sum is kept as a double-float
+  float fh, fl;
+  two_sum(__fmaf_rn(-kr, 0.0009765625f, th), tl, fh, fl);
+  // g = f ln 2
+  const float gh = __fmul_rn(fh, kLn2Hi);
+  float gl = __fmaf_rn(fh, kLn2Hi, -gh);
+  gl = __fmaf_rn(fh, kLn2Lo, gl);
+  gl = __fmaf_rn(fl, kLn2Hi, gl);
+  // e^g = 1 + gh + [gl + gh^2/2 + gh gl + gh^3/6 + gh^4/24], gh^2 = sq + sqe exactly
+  const float sq = __fmul_rn(gh, gh);
+  const float sqe = __fmaf_rn(gh, gh, -sq);
+  const float c6 = __fmaf_rn(gh, 1.f / 24.f, 1.f / 6.f);
+  float small = __fmaf_rn(__fmul_rn(sq, gh), c6, __fmul_rn(0.5f, sqe));
+  small = __fmaf_rn(gh, gl, small);
+  const float ph = __fadd_rn(1.f, gh);
+  const float ea = __fsub_rn(gh, __fsub_rn(ph, 1.f));  // exact: |gh| < 1
+  const float pl = __fadd_rn(__fadd_rn(ea, __fmul_rn(0.5f, sq)), __fadd_rn(gl, small));
+  // times 2^(j/1024) (double-float table) and 2^(k >> 10) (exponent field; k >> 10 >= -126)
+  const float2 T = tab[k & (DFL_TAB - 1)];
+  const float vh = __fmul_rn(T.x, ph);
+  float vl = __fmaf_rn(T.x, ph, -vh);
+  vl = __fmaf_rn(T.x, pl, vl);
+  vl = __fmaf_rn(T.y, ph, vl);
+  const float sc = __int_as_float(((k >> 10) + 127) << 23);
+  const dfl v = dfl_norm(vh, vl);
+  return dfl_make(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
 
 constexpr int RR_DMAX = 64;
@@ -168,25 +184,24 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
                     const __grid_constant__ Exp64Consts ec) {
   if (skip && *skip) return;
   __shared__ __align__(16) float xs[RP_BJ][DMAX];
-  __shared__ double njs[RP_BJ];
+  __shared__ double njs[EXACT ? RP_BJ : 1];
+  __shared__ float2 bjs[EXACT ? 1 : RP_BJ];
   __shared__ double vjd[EXACT ? RP_Q : 1][RP_BJ];
   __shared__ float2 vjf[EXACT ? 1 : RP_Q][RP_BJ];
   __shared__ double tab[EXACT ? EXP_TAB : 1];
-  __shared__ dfl inv_fact[9];
+  __shared__ float2 tab2[EXACT ? 1 : DFL_TAB];
   if (EXACT) {
     for (int t = threadIdx.x; t < EXP_TAB; t += blockDim.x)
       tab[EXACT ? t : 0] = exp2((double)t / (double)EXP_TAB);
-  } else if (threadIdx.x == 0) {
-    double f = 1.0;
-    inv_fact[0] = dfl_make(1.f, 0.f);
-    for (int q = 1; q <= 8; ++q) {
-      f /= (double)q;
-      inv_fact[q] = dfl_from_double(f);
+  } else {
+    for (int t = threadIdx.x; t < DFL_TAB; t += blockDim.x) {
+      const dfl T = dfl_from_double(exp2((double)t / (double)DFL_TAB));
+      tab2[EXACT ? 0 : t] = make_float2(T.hi, T.lo);
     }
   }
-  const dfl ln2 = dfl_from_double(0.6931471805599453094);
-  const dfl scale = dfl_from_double(neg_inv_2s2);
-  const dfl s3 = dfl_from_double(inv_s3);
+  // -2c = 1/sigma^2 and D / sigma^3 = e (1 / (c sigma^3)) in double-float
+  const dfl c2 = dfl_from_double(-2.0 * neg_inv_2s2);
+  const dfl wd = dfl_from_double(inv_s3 / neg_inv_2s2);
   const int64_t ib = (int64_t)blockIdx.x * (RP_THREADS * ROWS) + threadIdx.x;
   const int64_t q0 = (int64_t)blockIdx.y * RP_Q;
   const int nq = (int)((nvec - q0 < RP_Q) ? nvec - q0 : RP_Q);
@@ -200,8 +215,12 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
     ni[r] = i < nt ? nrm_t[i] : 0.0;
   }
   double ai[ROWS];
+  dfl aid[ROWS];
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r) ai[r] = neg_inv_2s2 * ni[r];
+  for (int r = 0; r < ROWS; ++r) {
+    ai[r] = neg_inv_2s2 * ni[r];
+    aid[r] = dfl_from_double(ai[r]);
+  }
   double acc[EXACT ? ROWS : 1][EXACT ? RP_Q : 1];
   float ah[EXACT ? 1 : ROWS][EXACT ? 1 : RP_Q], al[EXACT ? 1 : ROWS][EXACT ? 1 : RP_Q];
 #pragma unroll
@@ -221,7 +240,13 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
       xs[jj][k] = (j0 + jj < n && k < d) ? pts[(j0 + jj) * ld + k] : 0.f;
     }
     for (int jj = threadIdx.x; jj < RP_BJ; jj += RP_THREADS) {
-      njs[jj] = j0 + jj < n ? (EXACT ? neg_inv_2s2 * nrm[j0 + jj] : nrm[j0 + jj]) : 0.0;
+      const double bj = j0 + jj < n ? neg_inv_2s2 * nrm[j0 + jj] : 0.0;
+      if (EXACT) {
+        njs[EXACT ? jj : 0] = bj;
+      } else {
+        const dfl t = dfl_from_double(bj);
+        bjs[EXACT ? 0 : jj] = make_float2(t.hi, t.lo);
+      }
 #pragma unroll
       for (int q = 0; q < RP_Q; ++q) {
         const double vv = (q < nq && j0 + jj < n) ? v[(q0 + q) * n + j0 + jj] : 0.0;
@@ -257,7 +282,7 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
         if (EXACT) {
           // exponent = c ||t_i||^2 + c ||x_j||^2 - 2c <t_i, x_j>, c = -1/(2 sigma^2)
           const double dot = (double)dh[r] + (double)dl[r];
-          const double ex = fmin(fma(-2.0 * neg_inv_2s2, dot, ai[r] + njs[jj]), 0.0);
+          const double ex = fmin(fma(-2.0 * neg_inv_2s2, dot, ai[r] + njs[EXACT ? jj : 0]), 0.0);
           double K = exp64_neg(ex, tab, ec.l_hi, ec.l_lo, ec.inv_l);
           if (kind == 1) K *= (ex / neg_inv_2s2) * inv_s3;  // D = exponent / c
 #pragma unroll
@@ -265,12 +290,21 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
             if (q < nq) acc[EXACT ? r : 0][EXACT ? q : 0] =
                 fma(K, vjd[EXACT ? q : 0][jj], acc[EXACT ? r : 0][EXACT ? q : 0]);
         } else {
+          // e = c ||t_i||^2 + c ||x_j||^2 + (-2c) <t_i, x_j> in double-float
           const dfl dot = dfl_norm(dh[r], dl[r]);
-          dfl D = dfl_add(dfl_add(dfl_from_double(ni[r]), dfl_from_double(njs[jj])),
-                          dfl_make(-2.f * dot.hi, -2.f * dot.lo));
-          if (D.hi < 0.f) D = dfl_make(0.f, 0.f);
-          dfl Kij = dfl_exp_neg(dfl_mul(D, scale), inv_fact, ln2);
-          if (kind == 1) Kij = dfl_mul(Kij, dfl_mul(D, s3));
+          const float mh = __fmul_rn(dot.hi, c2.hi);
+          float ml = __fmaf_rn(dot.hi, c2.hi, -mh);
+          ml = __fmaf_rn(dot.hi, c2.lo, ml);
+          ml = __fmaf_rn(dot.lo, c2.hi, ml);
+          const float2 bj = bjs[EXACT ? 0 : jj];
+          float s1, e1, s2, e2;
+          two_sum(aid[r].hi, bj.x, s1, e1);
+          two_sum(s1, mh, s2, e2);
+          const float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(aid[r].lo, bj.y), ml));
+          dfl ex = dfl_norm(s2, lo);
+          if (ex.hi > 0.f) ex = dfl_make(0.f, 0.f);  // D >= 0
+          dfl Kij = dfl_exp_neg(ex, tab2);
+          if (kind == 1) Kij = dfl_mul(Kij, dfl_mul(ex, wd));
 #pragma unroll
           for (int q = 0; q < RP_Q; ++q) {
             if (q < nq) {

@@ -254,6 +254,22 @@ class AdaptInfo:
     kappa_est: float
 
 
+def nys_sketch_columns(op: Operator, ell: int, seed: int = 0, cols: torch.Tensor | None = None,
+                       precision: int = NYS_PREC_F64) -> Factor:
+    """Column-sampling sketch: Algorithm 1 with Omega = I[:, cols] (cols an
+    int64 CUDA tensor of distinct indices, or drawn from `seed` when None)."""
+    f = lib().nys_sketch_columns
+    if f.argtypes is None:
+        f.argtypes = [C.POINTER(_Operator), C.c_int64, C.c_uint64, C.c_void_p, C.c_int32,
+                      C.POINTER(C.c_void_p), C.c_void_p]
+        f.restype = C.c_int32
+    if cols is not None and (cols.dtype != torch.int64 or not cols.is_cuda):
+        raise ValueError("cols must be an int64 CUDA tensor")
+    h = C.c_void_p()
+    _check(f(op.ref, ell, seed, _ptr(cols), precision, C.byref(h), _stream()), "nys_sketch_columns")
+    return Factor(h, op.data.device.index or 0)
+
+
 def nys_sketch_adaptive(op: Operator, ell0: int, ell_max: int, rule: int, tol: float, q: int = 5,
                         mu: float = 0.0, seed: int = 0, omega: torch.Tensor | None = None,
                         g: torch.Tensor | None = None, precision: int = NYS_PREC_F64):

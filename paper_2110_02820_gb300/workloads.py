@@ -25,7 +25,7 @@ import os
 import numpy as np
 
 # Stream tags: one per kind of array.
-S_OMEGA, S_B, S_Y, S_X, S_G, S_W, S_Q, S_MEANS, S_LABEL, S_NOISE, S_SUB = range(11)
+S_OMEGA, S_B, S_Y, S_X, S_G, S_W, S_Q, S_MEANS, S_LABEL, S_NOISE, S_SUB, S_COLS = range(12)
 
 _CHUNK_ROWS = 8192
 
@@ -159,6 +159,18 @@ def rhs(n: int, seed: int, nrhs: int | None = None) -> np.ndarray:
     if nrhs is None:
         return gaussian((n,), seed, S_B)
     return gaussian((nrhs, n), seed, S_B)
+
+
+def column_indices(n: int, ell: int, seed: int) -> np.ndarray:
+    """ell distinct indices of [0, n) (int64), uniformly without replacement."""
+    return rng(seed, S_COLS).choice(n, size=ell, replace=False).astype(np.int64)
+
+
+def selection(n: int, cols: np.ndarray) -> np.ndarray:
+    """The n x ell FP64 matrix I[:, cols]."""
+    Q = np.zeros((n, len(cols)))
+    Q[cols, np.arange(len(cols))] = 1.0
+    return Q
 
 
 def power_starts(n: int, count: int, seed: int) -> np.ndarray:

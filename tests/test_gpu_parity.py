@@ -83,6 +83,23 @@ def test_rbf_matvec_accurate_and_fast(ny, n, d):
     np.testing.assert_allclose(yres, ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("n,d", [(2500, 32), (1300, 16), (700, 7), (400, 64)])
+def test_rbf_residual_products_entrywise(ny, n, d):
+    # double-FP32 entries and sums (Sec. 6.5 residual): every output entry within a
+    # few units of 2^-46 of the sum of the magnitudes of its terms
+    P = wl.gmm_points(n, d, seed=31)
+    sigma = wl.median_distance(P, seed=31)
+    X = wl.rhs(n, seed=31, nrhs=2)
+    X[1] = np.abs(X[1])  # one vector without cancellation
+    op = ny.rbf_operator(T(P), sigma)
+    Y = ny.nys_op_matvec(op, 0.1, T(X), mode=2).cpu().numpy()
+    ref = oops.rbf_matmat(P, sigma, X.T).T + 0.1 * X
+    scale = oops.rbf_matmat(P, sigma, np.abs(X).T).T + 0.1 * np.abs(X)
+    for q in range(2):
+        err = np.abs(Y[q] - ref[q]) / scale[q]
+        assert err.max() <= 6e-14, (q, err.max())
+
+
 # ---------------------------------------------------------------- Algorithm 1
 
 @pytest.mark.parametrize("n,ell", [(200, 24), (513, 64), (2048, 64), (100, 1), (64, 64)])
@@ -445,3 +462,68 @@ def test_breakdown_is_reported(ny):
     b = wl.rhs(n, seed=0)
     x, res, _ = ny.pcg_solve(ny.dense_operator(T(A)), None, 0.0, T(b), tol=1e-10)
     assert res[0].status == ny.NYS_ERR_BREAKDOWN and res[0].iterations == 0
+
+
+# ---------------------------------------------------------------- column sampling (Sec. 2.2)
+
+@pytest.mark.parametrize("n,ell", [(300, 24), (2048, 64)])
+def test_column_sketch_dense_f64(ny, n, ell):
+    A, _ = wl.dense_spd(n, seed=23)
+    S = wl.column_indices(n, ell, seed=23)
+    f = ny.nys_sketch_columns(ny.dense_operator(T(A)), ell, cols=T(S))
+    o = onys.rand_nystrom(lambda V: A @ V, wl.selection(n, S))
+    lam, U = f.lam().cpu().numpy(), f.U().cpu().numpy()
+    assert np.abs(lam - o["lam"]).max() <= 1e-9 * o["lam"][0]
+    Ah_g = (U * lam) @ U.T
+    Ah_o = (o["U"] * o["lam"]) @ o["U"].T
+    assert np.linalg.norm(Ah_g - Ah_o, 2) <= 1e-9 * o["lam"][0]
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_column_sketch_rbf(ny, precision):
+    n, d, ell = 1500, 8, 80
+    P = wl.gmm_points(n, d, seed=24)
+    sigma = wl.median_distance(P, seed=24)
+    S = wl.column_indices(n, ell, seed=24)
+    prec = ny.NYS_PREC_F64 if precision == "f64" else ny.NYS_PREC_MIXED
+    f = ny.nys_sketch_columns(ny.rbf_operator(T(P), sigma), ell, cols=T(S), precision=prec)
+    o = onys.rand_nystrom(lambda V: oops.rbf_matmat(P, sigma, V), wl.selection(n, S))
+    lam = f.lam().cpu().numpy()
+    tol = 1e-9 if precision == "f64" else 3e-3
+    np.testing.assert_allclose(lam[:8], o["lam"][:8], rtol=tol)
+    assert np.abs(lam - o["lam"]).max() <= tol * o["lam"][0]
+
+
+def test_column_sketch_exact_recovery_and_solve(ny):
+    # rank(A) = 6 <= ell sampled columns spanning it: U Lam U^T = A, and PCG with
+    # that factor converges in at most a few steps (Sec. 2.2, Alg. 3)
+    n, r, ell = 400, 6, 20
+    rng = np.random.default_rng(7)
+    F = rng.standard_normal((n, r))
+    A = F @ F.T
+    S = wl.column_indices(n, ell, seed=25)
+    f = ny.nys_sketch_columns(ny.dense_operator(T(A)), ell, cols=T(S))
+    U, lam = f.U().cpu().numpy(), f.lam().cpu().numpy()
+    assert np.linalg.norm((U * lam) @ U.T - A, 2) <= 1e-9 * np.linalg.norm(A, 2)
+    b = wl.rhs(n, seed=25)
+    x, res, _ = ny.pcg_solve(ny.dense_operator(T(A)), f, 1e-2, T(b), tol=1e-10)
+    assert res[0].status == ny.NYS_OK and res[0].iterations <= 4, res
+
+
+def test_column_sketch_seeded_sampling_and_krr_solve(ny):
+    n, d, ell = 3000, 8, 100
+    P = wl.gmm_points(n, d, seed=26)
+    sigma = wl.median_distance(P, seed=26)
+    op = ny.rbf_operator(T(P), sigma)
+    f1 = ny.nys_sketch_columns(op, ell, seed=11, precision=ny.NYS_PREC_MIXED)
+    f2 = ny.nys_sketch_columns(op, ell, seed=11, precision=ny.NYS_PREC_MIXED)
+    f3 = ny.nys_sketch_columns(op, ell, seed=12, precision=ny.NYS_PREC_MIXED)
+    l1, l2, l3 = (f.lam().cpu().numpy() for f in (f1, f2, f3))
+    np.testing.assert_array_equal(l1, l2)
+    assert not np.array_equal(l1, l3)
+    mu = 1e-6 * n * 100
+    b = wl.rhs(n, seed=26)
+    x, res, _ = ny.pcg_solve(op, f1, mu, T(b), tol=1e-8, precision=ny.NYS_PREC_MIXED)
+    assert res[0].status == ny.NYS_OK, res
+    xs = opcg.direct_solve(oops.rbf_block(P, P, sigma), mu, b)
+    assert relerr(x.cpu().numpy(), xs) <= 1e-5

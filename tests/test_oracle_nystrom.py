@@ -299,3 +299,37 @@ def test_effective_dimension_is_trace_formula():
     A, _ = spd_with_spectrum(n, wl.power_spectrum(n), 2)
     tr = np.trace(A @ np.linalg.inv(A + mu * np.eye(n)))
     assert abs(ny.effective_dimension(wl.power_spectrum(n), mu) - tr) < 1e-10
+
+
+# ---------------------------------------------------------------- column sampling (Sec. 2.2)
+
+def test_column_sampling_equals_column_nystrom_formula():
+    # Algorithm 1 with Omega = I[:, S] is the classical column Nystrom
+    # approximation C W^{-1} C^T (C = A[:, S], W = A[S, S]) up to the shift nu
+    n, ell = 60, 12
+    A, _ = wl.dense_spd(n, seed=21)
+    S = wl.column_indices(n, ell, seed=21)
+    o = ny.rand_nystrom(lambda V: A @ V, wl.selection(n, S))
+    C, W = A[:, S], A[np.ix_(S, S)]
+    ref = C @ np.linalg.solve(W, C.T)
+    got = (o["U"] * o["lam"]) @ o["U"].T
+    assert np.linalg.norm(got - ref, 2) <= 1e-9 * np.linalg.norm(ref, 2)
+
+
+def test_column_sampling_recovers_low_rank_matrix():
+    # rank(A) = r and rank(A[:, S]) = r: the approximation is A itself (Sec. 2.2)
+    n, r, ell = 50, 5, 9
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal((n, r))
+    A = F @ F.T
+    S = wl.column_indices(n, ell, seed=4)
+    o = ny.rand_nystrom(lambda V: A @ V, wl.selection(n, S))
+    got = (o["U"] * o["lam"]) @ o["U"].T
+    assert np.linalg.norm(got - A, 2) <= 1e-9 * np.linalg.norm(A, 2)
+
+
+def test_column_indices_are_distinct_and_seeded():
+    a = wl.column_indices(1000, 200, seed=5)
+    assert len(np.unique(a)) == 200 and a.min() >= 0 and a.max() < 1000
+    assert np.array_equal(a, wl.column_indices(1000, 200, seed=5))
+    assert not np.array_equal(a, wl.column_indices(1000, 200, seed=6))
