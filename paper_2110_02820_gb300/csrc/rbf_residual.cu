@@ -190,6 +190,12 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
   __shared__ float2 vjf[EXACT ? 1 : RP_Q][RP_BJ];
   __shared__ double tab[EXACT ? EXP_TAB : 1];
   __shared__ float2 tab2[EXACT ? 1 : DFL_TAB];
+  // double-float running sums (dynamic shared memory, [RP_Q * ROWS][RP_THREADS],
+  // one column per thread): each point tile is summed locally in registers and
+  // merged here with a renormalising add, so the low word never grows past half
+  // an ulp of the high word
+  extern __shared__ float2 gacc_dyn[];
+  auto gacc = reinterpret_cast<float2(*)[RP_THREADS]>(gacc_dyn);
   if (EXACT) {
     for (int t = threadIdx.x; t < EXP_TAB; t += blockDim.x)
       tab[EXACT ? t : 0] = exp2((double)t / (double)EXP_TAB);
@@ -228,12 +234,22 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
 #pragma unroll
     for (int q = 0; q < RP_Q; ++q) {
       if (EXACT) acc[EXACT ? r : 0][EXACT ? q : 0] = 0.0;
-      else {
-        ah[EXACT ? 0 : r][EXACT ? 0 : q] = 0.f;
-        al[EXACT ? 0 : r][EXACT ? 0 : q] = 0.f;
-      }
     }
+  if (!EXACT) {
+#pragma unroll
+    for (int t = 0; t < RP_Q * ROWS; ++t)
+      gacc[t][threadIdx.x] = make_float2(0.f, 0.f);
+  }
   for (int64_t j0 = 0; j0 < n; j0 += RP_BJ) {
+    if (!EXACT) {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int q = 0; q < RP_Q; ++q) {
+          ah[EXACT ? 0 : r][EXACT ? 0 : q] = 0.f;
+          al[EXACT ? 0 : r][EXACT ? 0 : q] = 0.f;
+        }
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < RP_BJ * DMAX; e += RP_THREADS) {
       const int jj = e / DMAX, k = e - jj * DMAX;
@@ -323,6 +339,22 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
         }
       }
     }
+    if (!EXACT) {
+      // merge the tile's sums: (gh, gl) + (ah, al), renormalised
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int q = 0; q < RP_Q; ++q) {
+          if (q < nq) {
+            float2& g = gacc[q * ROWS + r][threadIdx.x];
+            float sh, se;
+            two_sum(g.x, ah[EXACT ? 0 : r][EXACT ? 0 : q], sh, se);
+            const float t = __fadd_rn(g.y, __fadd_rn(al[EXACT ? 0 : r][EXACT ? 0 : q], se));
+            const float hi = __fadd_rn(sh, t);
+            g = make_float2(hi, __fsub_rn(t, __fsub_rn(hi, sh)));
+          }
+        }
+    }
   }
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) {
@@ -332,9 +364,13 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
     for (int q = 0; q < RP_Q; ++q)
       if (q < nq) {
         const int64_t g = q0 + q;
-        double out = EXACT ? acc[EXACT ? r : 0][EXACT ? q : 0]
-                           : (double)ah[EXACT ? 0 : r][EXACT ? 0 : q] +
-                                 (double)al[EXACT ? 0 : r][EXACT ? 0 : q];
+        double out;
+        if (EXACT) {
+          out = acc[EXACT ? r : 0][EXACT ? q : 0];
+        } else {
+          const float2 g = gacc[q * ROWS + r][threadIdx.x];
+          out = (double)g.x + (double)g.y;
+        }
         if (shift) out = fma(shift == 2 ? mus[g] : mu0, v[g * n + i], out);
         y[g * nt + i] = out;
       }
@@ -383,8 +419,15 @@ void products_go(const float* tg, int64_t nt, int64_t ldt, const double* nrm_t, 
                  int64_t n, int64_t ldp, const double* nrm, int64_t d, double a, double b, int kind,
                  int shift, const double* d_mu, double mu0, int64_t nvec, const double* v,
                  double* y, const int* skip, const Exp64Consts& ec, cudaStream_t s) {
+  const int dyn = EXACT ? 0 : Q * ROWS * RP_THREADS * (int)sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(rbf_products_kernel<DMAX, ROWS, Q, EXACT>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    attr = true;
+  }
   rbf_products_kernel<DMAX, ROWS, Q, EXACT>
-      <<<dim3((unsigned)cdiv(nt, ROWS * RP_THREADS), (unsigned)cdiv(nvec, Q)), RP_THREADS, 0, s>>>(
+      <<<dim3((unsigned)cdiv(nt, ROWS * RP_THREADS), (unsigned)cdiv(nvec, Q)), RP_THREADS, dyn, s>>>(
           tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y, skip,
           ec);
   count_launch();

@@ -97,7 +97,7 @@ def test_rbf_residual_products_entrywise(ny, n, d):
     scale = oops.rbf_matmat(P, sigma, np.abs(X).T).T + 0.1 * np.abs(X)
     for q in range(2):
         err = np.abs(Y[q] - ref[q]) / scale[q]
-        assert err.max() <= 6e-14, (q, err.max())
+        assert err.max() <= 4e-14, (q, err.max())
 
 
 # ---------------------------------------------------------------- Algorithm 1
