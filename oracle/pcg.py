@@ -17,6 +17,23 @@ Algorithm 3 (Sec. 5.2) is left-preconditioned CG.  Readings:
 Batched solves (many mu values and right-hand sides sharing one factor) are
 independent recurrences, so the oracle is a loop of single solves.
 
+Block PCG (Sec. 5.2, "Block Nystrom PCG"): O'Leary's block CG for several
+right-hand sides of one shifted matrix, with the preconditioner of Eq. (5.3)
+and the orthogonalisation pre-processing of Feng, Owen & Peric (1995).  The
+paper names the two ingredients only; the readings here are:
+* pre-processing: the initial residual block is factored R_0 = Q S (thin QR),
+  block CG runs on (A + mu I) Y = Q from Y = 0, and X = X_0 + Y S;
+* the recurrence is O'Leary's with the scaling matrices gamma_k = I:
+  alpha = (P^T V)^{-1} (Z^T R), beta = (Z^T R)^{-1} (Z_new^T R_new), both s x s
+  solves by Cholesky of the symmetrised left factor;
+* column j stops being a target when ||(R S) e_j|| <= tol ||b_j|| (its
+  recurrence residual in the original scaling); the loop runs until every
+  column meets it, tested before the first iteration as well; a column that
+  meets it at the start (b_j = 0 included) leaves the block;
+* ``iterations`` counts block products (A + mu I) P; a failed Cholesky or a
+  non-finite value stops the loop with status "breakdown" for the columns not
+  yet converged.
+
 Iterative refinement (not in the paper): an FP64 outer loop
     r = b - (A + mu I) x   (FP64),  stop if ||r|| <= tol ||b||,
     d = PCG on (A + mu I) d = r in float32 to relative tolerance inner_tol,
@@ -90,6 +107,73 @@ def batched_pcg(matvec, mus, B: np.ndarray, precond_inv_for_mu, tol: float, maxi
         mu = float(mus[s])
         out.append(nys_pcg(matvec, mu, B[s], None, precond_inv_for_mu(mu), tol, maxit))
     return out
+
+
+def block_pcg(matmat, mu: float, B: np.ndarray, X0: np.ndarray | None, precond_inv, tol: float,
+              maxit: int = 500):
+    """Block Nystrom PCG (readings in the module docstring).  ``B`` and ``X0``
+    are [s][n] (system-major); ``matmat(V)`` applies A to the columns of the
+    n x k matrix V, ``precond_inv(V)`` applies P^{-1} to them.
+
+    Returns dict(X [s][n], iterations, status [s], rel_res [s], res_hist
+    (iterations+1) x s)."""
+    import scipy.linalg as sla
+    Bc = np.asarray(B, dtype=np.float64).T.copy()
+    n, s = Bc.shape
+    X = np.zeros_like(Bc) if X0 is None else np.asarray(X0, dtype=np.float64).T.copy()
+
+    def amu(V):
+        return np.asarray(matmat(V), dtype=np.float64) + mu * V
+
+    R0 = Bc - amu(X) if X0 is not None else Bc.copy()
+    thresh = tol * np.linalg.norm(Bc, axis=0)
+    res = np.linalg.norm(R0, axis=0)
+    status = [CONVERGED] * s
+    act = np.nonzero(res > thresh)[0]
+    hist = [res.copy()]
+    it = 0
+    if act.size:
+        Q, S = np.linalg.qr(R0[:, act])          # pre-processing: R_0 = Q S
+        Y = np.zeros((n, act.size))
+        R = Q
+        Z = np.asarray(precond_inv(R), dtype=np.float64)
+        P = Z.copy()
+        rho = Z.T @ R
+        broke = False
+        while True:
+            res[act] = np.linalg.norm(R @ S, axis=0)
+            if it > 0:
+                hist.append(res.copy())
+            if np.all(res[act] <= thresh[act]) or it >= maxit or broke:
+                break
+            V = amu(P)
+            G = P.T @ V
+            try:
+                alpha = sla.cho_solve(sla.cho_factor(0.5 * (G + G.T)), rho)
+            except (np.linalg.LinAlgError, ValueError):
+                broke = True
+                break
+            Y = Y + P @ alpha
+            R = R - V @ alpha
+            Z = np.asarray(precond_inv(R), dtype=np.float64)
+            rho_new = Z.T @ R
+            it += 1
+            try:
+                beta = sla.cho_solve(sla.cho_factor(0.5 * (rho + rho.T)), rho_new)
+            except (np.linalg.LinAlgError, ValueError):
+                broke = True        # this step stands; the next one cannot be formed
+                continue
+            P = Z + P @ beta
+            rho = rho_new
+            if not np.all(np.isfinite(P)):
+                broke = True
+        X[:, act] = X[:, act] + Y @ S
+        for j in act:
+            if not res[j] <= thresh[j]:
+                status[j] = BREAKDOWN if broke else MAXIT
+    bn = np.linalg.norm(Bc, axis=0)
+    rel = np.where(bn > 0, res / np.where(bn > 0, bn, 1.0), res)
+    return dict(X=X.T.copy(), iterations=it, status=status, rel_res=rel, res_hist=np.array(hist))
 
 
 def refine_solve(matvec_hi, matvec_lo, precond_inv_lo, mu: float, b: np.ndarray, tol: float,
