@@ -7,6 +7,7 @@
  *   - nys_sketch           Algorithm 1 (randomized Nystrom approximation)
  *   - nys_sketch_adaptive  Algorithm 5 with Algorithm 4 (adaptive rank)
  *   - nys_precond_apply    Eq. (5.3), the inverse preconditioner P^{-1}
+ *   - nys_block_pcg        block Nystrom PCG (Sec. 5.2) for many right-hand sides of one mu
  *   - pcg_solve            Algorithm 3 (Nystrom PCG), batched over systems,
  *                          in FP64 or mixed precision with FP64-residual
  *                          iterative refinement
@@ -175,6 +176,31 @@ typedef struct nys_pcg_result {
 int32_t pcg_solve(const nys_operator* op, const nys_factor* f, const double* mu, int64_t nsys,
                   const double* b, double* x, const nys_pcg_opts* opts,
                   nys_pcg_result* results, void* stream);
+
+/* Block Nystrom PCG (Sec. 5.2, "Block Nystrom PCG"): O'Leary's block CG for
+ * nrhs right-hand sides of ONE shifted system (A + mu I) X = B, preconditioned
+ * by Eq. (5.3) (f == NULL gives unpreconditioned block CG), after the initial
+ * residual block is orthonormalised, R_0 = Q S (Feng, Owen & Peric's
+ * pre-processing; Gram-Schmidt with one reorthogonalisation, a column with no
+ * new direction contributing through S only).  The block iterates share one
+ * Krylov space, so a column can converge in fewer products than its single
+ * solve.  Column j stops being a target when ||(R S) e_j|| <= tol ||b_j||;
+ * the loop runs until every column meets it.
+ *   mu      the shift (host scalar, >= 0; > 0 when lambda_hat_ell = 0);
+ *   nrhs    1..32 columns;
+ *   b, x    device FP64 [nrhs][n] (system-major); x is the initial guess when
+ *           opts->use_x0, else overwritten;
+ *   opts    as for pcg_solve (residual_history is ignored); NYS_PREC_MIXED
+ *           runs the FP32 block solve inside the FP64-residual refinement;
+ *   results HOST [nrhs]: status per column; iterations = block products
+ *           (A + mu I) P summed over refinement steps, the same for every
+ *           column; rel_residual as for pcg_solve.
+ * Returns the worst column status (NYS_ERR_BREAKDOWN when P^T (A + mu I) P or
+ * Z^T R stops being positive definite), or NYS_ERR_ARG / NYS_ERR_OOM /
+ * NYS_ERR_CUDA / NYS_ERR_TIMEOUT.  Synchronises `stream`. */
+int32_t nys_block_pcg(const nys_operator* op, const nys_factor* f, double mu, int64_t nrhs,
+                      const double* b, double* x, const nys_pcg_opts* opts,
+                      nys_pcg_result* results, void* stream);
 
 /* Read-only views of a factor's device arrays (valid until nys_factor_free):
  * U (n x ell row-major, FP64 when *u_dtype == NYS_F64 else FP32) and

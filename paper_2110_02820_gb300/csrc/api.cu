@@ -19,6 +19,12 @@ int32_t pcg_f64(const nys_operator* op, const nys_factor* f, const double* mu, i
 int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu, int64_t nsys,
                   const double* b, double* x, double tol, double inner_tol, int maxit,
                   int max_refine, int use_x0, double* hist, nys_pcg_result* res, cudaStream_t s);
+int32_t block_pcg_f64(const nys_operator* op, const nys_factor* f, double mu, int64_t k,
+                      const double* b, double* x, double tol, int maxit, int use_x0,
+                      nys_pcg_result* res, cudaStream_t s);
+int32_t block_pcg_mixed(const nys_operator* op, const nys_factor* f, double mu, int64_t k,
+                        const double* b, double* x, double tol, double inner_tol, int maxit,
+                        int max_refine, int use_x0, nys_pcg_result* res, cudaStream_t s);
 int32_t precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const void* v, void* z,
                       int32_t dtype, cudaStream_t s);
 
@@ -774,6 +780,42 @@ int32_t pcg_solve(const nys_operator* op, const nys_factor* f, const double* mu,
   if (st != NYS_OK) return st;
   int32_t worst = NYS_OK;
   for (int64_t q = 0; q < nsys; ++q) {
+    int32_t r = results[q].status;
+    if (r == NYS_ERR_BREAKDOWN) worst = NYS_ERR_BREAKDOWN;
+    else if (r == NYS_ERR_MAXIT && worst == NYS_OK) worst = NYS_ERR_MAXIT;
+  }
+  return worst;
+}
+
+int32_t nys_block_pcg(const nys_operator* op, const nys_factor* f, double mu, int64_t nrhs,
+                      const double* b, double* x, const nys_pcg_opts* opts,
+                      nys_pcg_result* results, void* stream) {
+  NYS_TRY(check_op(op));
+  if (nrhs < 1 || nrhs > 32 || !b || !x || !results) return NYS_ERR_ARG;
+  if (f && f->n != op->n) return NYS_ERR_ARG;
+  NYS_TRY(check_mu(f, &mu, 1));
+  nys_pcg_opts o;
+  o.tol = 1e-8;
+  o.maxit = 500;
+  o.precision = NYS_PREC_F64;
+  o.inner_tol = 1e-4;
+  o.max_refine = 20;
+  o.use_x0 = 0;
+  o.residual_history = nullptr;
+  if (opts) o = *opts;
+  if (!(o.tol >= 0.0) || o.maxit < 0 || o.max_refine < 0) return NYS_ERR_ARG;
+  if (o.precision != NYS_PREC_F64 && o.precision != NYS_PREC_MIXED) return NYS_ERR_ARG;
+  if (o.precision == NYS_PREC_MIXED && !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return NYS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t st;
+  if (o.precision == NYS_PREC_F64)
+    st = block_pcg_f64(op, f, mu, nrhs, b, x, o.tol, o.maxit, o.use_x0, results, s);
+  else
+    st = block_pcg_mixed(op, f, mu, nrhs, b, x, o.tol, o.inner_tol, o.maxit, o.max_refine,
+                         o.use_x0, results, s);
+  if (st != NYS_OK) return st;
+  int32_t worst = NYS_OK;
+  for (int64_t q = 0; q < nrhs; ++q) {
     int32_t r = results[q].status;
     if (r == NYS_ERR_BREAKDOWN) worst = NYS_ERR_BREAKDOWN;
     else if (r == NYS_ERR_MAXIT && worst == NYS_OK) worst = NYS_ERR_MAXIT;

@@ -329,6 +329,28 @@ def pcg_solve(op: Operator, f: Factor | None, mu, b: torch.Tensor, x: torch.Tens
     return xo, out, hist
 
 
+def nys_block_pcg(op: Operator, f: Factor | None, mu: float, B: torch.Tensor,
+                  X: torch.Tensor | None = None, tol: float = 1e-8, maxit: int = 500,
+                  precision: int = NYS_PREC_F64, inner_tol: float = 1e-4, max_refine: int = 20):
+    """Block Nystrom PCG for the rows of B ([nrhs][n] float64, nrhs <= 32) with
+    one shift mu.  Returns (X, [PcgResult])."""
+    fn = lib().nys_block_pcg
+    if fn.argtypes is None:
+        fn.argtypes = [C.POINTER(_Operator), C.c_void_p, C.c_double, C.c_int64, C.c_void_p,
+                       C.c_void_p, C.POINTER(_PcgOpts), C.POINTER(_PcgResult), C.c_void_p]
+        fn.restype = C.c_int32
+    nrhs = B.shape[0]
+    use_x0 = X is not None
+    XX = X.clone() if use_x0 else torch.empty_like(B)
+    opts = _PcgOpts(tol, maxit, precision, inner_tol, max_refine, int(use_x0), None)
+    res = (_PcgResult * nrhs)()
+    st = fn(op.ref, f.h if f is not None else None, float(mu), nrhs, _ptr(B), _ptr(XX),
+            C.byref(opts), res, _stream())
+    if st not in (NYS_OK, NYS_ERR_MAXIT, NYS_ERR_BREAKDOWN):
+        raise NysError(st, "nys_block_pcg")
+    return XX, [PcgResult(r.status, r.iterations, r.refinements, r.rel_residual) for r in res]
+
+
 def nys_op_matvec(op: Operator, mu: float, x: torch.Tensor, mode: int = 0) -> torch.Tensor:
     xx = x if x.dim() == 2 else x[None]
     y = torch.empty_like(xx)

@@ -527,3 +527,93 @@ def test_column_sketch_seeded_sampling_and_krr_solve(ny):
     assert res[0].status == ny.NYS_OK, res
     xs = opcg.direct_solve(oops.rbf_block(P, P, sigma), mu, b)
     assert relerr(x.cpu().numpy(), xs) <= 1e-5
+
+
+# ---------------------------------------------------------------- block PCG (Sec. 5.2)
+
+@pytest.mark.parametrize("n,ell,s", [(300, 16, 1), (1000, 32, 4), (777, 24, 7), (2048, 64, 16)])
+def test_block_pcg_f64_matches_oracle(ny, n, ell, s):
+    A, _ = wl.dense_spd(n, seed=40)
+    Om = wl.omega(n, ell, seed=40)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(Om))
+    o = onys.rand_nystrom(lambda V: A @ V, Om)
+    mu = 1e-3
+    B = wl.rhs(n, seed=41, nrhs=s)
+    X, res = ny.nys_block_pcg(op, f, mu, T(B), tol=1e-10)
+    ref = opcg.block_pcg(lambda V: A @ V, mu, B, None,
+                         lambda V: onys.precond_inverse_apply(o["U"], o["lam"], mu, V), 1e-10)
+    assert all(r.status == ny.NYS_OK for r in res), res
+    assert abs(res[0].iterations - ref["iterations"]) <= 1
+    Xg = X.cpu().numpy()
+    assert relerr(Xg, ref["X"]) <= 1e-8
+    Xs = np.linalg.solve(A + mu * np.eye(n), B.T).T
+    for j in range(s):
+        assert relerr(Xg[j], Xs[j]) <= 1e-8
+        assert abs(res[j].rel_residual - ref["rel_res"][j]) <= 1e-3 * 1e-10 + 0.5 * ref["rel_res"][j]
+
+
+def test_block_pcg_one_rhs_equals_pcg_and_fewer_products_than_singles(ny):
+    n, ell, s = 1500, 16, 8
+    A, _ = wl.dense_spd(n, seed=42)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, seed=42)))
+    mu = 1e-5
+    B = wl.rhs(n, seed=42, nrhs=s)
+    X1, r1 = ny.nys_block_pcg(op, f, mu, T(B[:1]), tol=1e-10)
+    x1, p1, _ = ny.pcg_solve(op, f, mu, T(B[0]), tol=1e-10)
+    assert abs(r1[0].iterations - p1[0].iterations) <= 1
+    assert relerr(X1[0].cpu().numpy(), x1.cpu().numpy()) <= 1e-9
+    Xb, rb = ny.nys_block_pcg(op, f, mu, T(B), tol=1e-10)
+    xs, ps, _ = ny.pcg_solve(op, f, [mu] * s, T(B), tol=1e-10)
+    assert all(r.status == ny.NYS_OK for r in rb)
+    assert rb[0].iterations < max(p.iterations for p in ps)
+    assert relerr(Xb.cpu().numpy(), xs.cpu().numpy()) <= 1e-8
+
+
+def test_block_pcg_zero_duplicate_columns_and_x0(ny):
+    n, ell = 900, 24
+    A, _ = wl.dense_spd(n, seed=43)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, seed=43)))
+    mu = 1e-3
+    b = wl.rhs(n, seed=43)
+    B = np.stack([b, np.zeros(n), b, 3.0 * wl.rhs(n, seed=44)])
+    X, res = ny.nys_block_pcg(op, f, mu, T(B), tol=1e-10)
+    assert all(r.status == ny.NYS_OK for r in res), res
+    Xg = X.cpu().numpy()
+    assert np.all(Xg[1] == 0.0)
+    Xs = np.linalg.solve(A + mu * np.eye(n), B.T).T
+    assert relerr(Xg, Xs) <= 1e-8
+    # warm start from the solution: no iterations needed
+    X2, r2 = ny.nys_block_pcg(op, f, mu, T(B), X=T(Xs), tol=1e-8)
+    assert all(r.status == ny.NYS_OK and r.iterations == 0 for r in r2)
+    # maxit
+    X3, r3 = ny.nys_block_pcg(op, None, 1e-9, T(B), tol=1e-14, maxit=3)
+    assert r3[0].iterations == 3 and r3[0].status == ny.NYS_ERR_MAXIT
+
+
+@pytest.mark.parametrize("kind", ["gram", "rbf"])
+def test_block_pcg_mixed_refinement(ny, kind):
+    s = 4
+    if kind == "gram":
+        m, n, ell = 3000, 512, 64
+        X = wl.ridge_X(m, n, seed=45)
+        op = ny.gram_operator(T(X))
+        mu = 1e-3
+        Amat = oops.gram_matmat(X, np.eye(n))
+    else:
+        n, d, ell = 2500, 8, 128
+        P = wl.gmm_points(n, d, seed=45)
+        sigma = wl.median_distance(P, seed=45)
+        op = ny.rbf_operator(T(P), sigma)
+        mu = 1e-6 * n * 100
+        Amat = oops.rbf_block(P, P, sigma)
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, seed=45)), precision=ny.NYS_PREC_MIXED)
+    B = wl.rhs(n, seed=45, nrhs=s)
+    Xb, res = ny.nys_block_pcg(op, f, mu, T(B), tol=1e-10, precision=ny.NYS_PREC_MIXED)
+    assert all(r.status == ny.NYS_OK for r in res), res
+    Xs = np.linalg.solve(Amat + mu * np.eye(n), B.T).T
+    for j in range(s):
+        assert res[j].rel_residual <= 1e-10
+        assert relerr(Xb[j].cpu().numpy(), Xs[j]) <= 1e-6
