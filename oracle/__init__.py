@@ -18,8 +18,11 @@ Nystrom Preconditioning", arXiv 2110.02820) step by step:
   preconditioner of Eq. (5.3), Algorithm 4 (randomized power error
   estimate), Algorithm 5 (adaptive rank doubling, Strategy 1) and the
   ratio rule of Strategy 2 (Sec. 5.4.2), Algorithm 2 (sketch-and-solve);
-* ``pcg``        Algorithm 3 (Nystrom PCG), its independent-batch form, and
-  FP64-residual iterative refinement around a float32 inner solve;
+* ``pcg``        Algorithm 3 (Nystrom PCG), its independent-batch form,
+  block Nystrom PCG for several right-hand sides of one shift (Sec. 5.2),
+  and FP64-residual iterative refinement around a float32 inner solve;
+* ``path``       the regularization path with warm starts and factor reuse
+  of the paper's path experiments (Sec. 6.2);
 * ``krr``        the KRR validation loss and its gradient by implicit
   differentiation (adjoint solve).
 
