@@ -8,6 +8,7 @@
  *   - nys_sketch_adaptive  Algorithm 5 with Algorithm 4 (adaptive rank)
  *   - nys_precond_apply    Eq. (5.3), the inverse preconditioner P^{-1}
  *   - nys_block_pcg        block Nystrom PCG (Sec. 5.2) for many right-hand sides of one mu
+ *   - nys_reg_path         regularization path with warm starts and factor reuse (Sec. 6.2)
  *   - pcg_solve            Algorithm 3 (Nystrom PCG), batched over systems,
  *                          in FP64 or mixed precision with FP64-residual
  *                          iterative refinement
@@ -201,6 +202,43 @@ int32_t pcg_solve(const nys_operator* op, const nys_factor* f, const double* mu,
 int32_t nys_block_pcg(const nys_operator* op, const nys_factor* f, double mu, int64_t nrhs,
                       const double* b, double* x, const nys_pcg_opts* opts,
                       nys_pcg_result* results, void* stream);
+
+typedef struct nys_path_result {
+  int32_t status;       /* PCG status at this shift (NYS_OK, NYS_ERR_MAXIT, NYS_ERR_BREAKDOWN) */
+  int32_t iterations;   /* PCG iterations at this shift (inner, summed, in mixed precision) */
+  int32_t resketched;   /* 1 when a new factor was built for this shift */
+  int32_t refinements;  /* mixed: outer refinement steps; FP64: 0 */
+  int64_t ell;          /* sketch size of the factor used */
+  double err_est;       /* Algorithm 4 estimate in force (NaN once the sketch reached ell_max) */
+  double rel_residual;  /* as pcg_result.rel_residual */
+} nys_path_result;
+
+/* Regularization path with warm starts and factor reuse (the procedure of
+ * the paper's path experiments, Sec. 6.2): (A + mu_i I) x_i = b for `count`
+ * shifts, processed in DECREASING order of mu whatever the order of `mus`.
+ * The first solve starts from zero, each later one from the previous shift's
+ * solution.  A factor is built (Algorithm 5, Strategy 1, tolerance
+ * err_factor * mu, q power steps, nu as nys_sketch_adaptive) for the first
+ * shift, and rebuilt for a later shift only when the estimate in force
+ * exceeds err_factor * mu and the sketch is still below ell_max; a rebuild
+ * starts from twice the previous sketch size (capped at ell_max) with a fresh
+ * test matrix.  The experiments use err_factor = 30, q = 5.
+ *   mus      HOST [count], each > 0;
+ *   b        device FP64 [n];  x  device FP64 [count][n], row i the solution for mus[i];
+ *   omegas   device FP64 [count][n][ell_max] or NULL: the r-th factor build uses
+ *            omegas + r n ell_max as its raw Gaussian test matrix (else drawn
+ *            from seed + r);
+ *   gs       device FP64 [count][kmax][n] or NULL, kmax = ceil(log2(ell_max / ell0)) + 1:
+ *            the power-step starts of the r-th build (else drawn);
+ *   opts     as for pcg_solve (precision applies to the sketches and the solves;
+ *            use_x0 and residual_history are ignored);
+ *   results  HOST [count], in the order of mus.
+ * Returns the worst per-shift status or an error of the sketch or the
+ * solver.  Synchronises `stream`. */
+int32_t nys_reg_path(const nys_operator* op, int64_t count, const double* mus, const double* b,
+                     double* x, int64_t ell0, int64_t ell_max, double err_factor, int32_t q,
+                     uint64_t seed, const double* omegas, const double* gs,
+                     const nys_pcg_opts* opts, nys_path_result* results, void* stream);
 
 /* Read-only views of a factor's device arrays (valid until nys_factor_free):
  * U (n x ell row-major, FP64 when *u_dtype == NYS_F64 else FP32) and

@@ -2,6 +2,7 @@
 // shifted core of Algorithm 1, the adaptive loop of Algorithm 5 with the
 // power estimate of Algorithm 4, and the PCG dispatch.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -820,6 +821,93 @@ int32_t nys_block_pcg(const nys_operator* op, const nys_factor* f, double mu, in
     if (r == NYS_ERR_BREAKDOWN) worst = NYS_ERR_BREAKDOWN;
     else if (r == NYS_ERR_MAXIT && worst == NYS_OK) worst = NYS_ERR_MAXIT;
   }
+  return worst;
+}
+
+int32_t nys_reg_path(const nys_operator* op, int64_t count, const double* mus, const double* b,
+                     double* x, int64_t ell0, int64_t ell_max, double err_factor, int32_t q,
+                     uint64_t seed, const double* omegas, const double* gs,
+                     const nys_pcg_opts* opts, nys_path_result* results, void* stream) {
+  NYS_TRY(check_op(op));
+  const int64_t n = op->n;
+  if (count < 1 || !mus || !b || !x || !results) return NYS_ERR_ARG;
+  for (int64_t i = 0; i < count; ++i)
+    if (!(mus[i] > 0.0) || !std::isfinite(mus[i])) return NYS_ERR_ARG;
+  if (ell0 < 1 || ell0 > ell_max || ell_max > n || ell_max > kMaxEll) return NYS_ERR_ARG;
+  if (!(err_factor > 0.0) || !std::isfinite(err_factor) || q < 1) return NYS_ERR_ARG;
+  nys_pcg_opts o;
+  o.tol = 1e-8;
+  o.maxit = 500;
+  o.precision = NYS_PREC_F64;
+  o.inner_tol = 1e-4;
+  o.max_refine = 20;
+  if (opts) o = *opts;
+  o.residual_history = nullptr;
+  if (o.precision != NYS_PREC_F64 && o.precision != NYS_PREC_MIXED) return NYS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int64_t> order(count);
+  for (int64_t i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t a, int64_t c) { return mus[a] > mus[c]; });
+  const int64_t kmax = (int64_t)std::ceil(std::log2((double)ell_max / (double)ell0)) + 1;
+  nys_factor* f = nullptr;
+  double E = INFINITY;
+  bool capped = false;
+  int64_t builds = 0;
+  const double* xprev = nullptr;
+  int32_t worst = NYS_OK;
+  for (int64_t idx : order) {
+    const double mu = mus[idx], tol_e = err_factor * mu;
+    int resk = 0;
+    if (!f || (!capped && !(E <= tol_e))) {
+      const int64_t start = f ? std::min<int64_t>(2 * f->ell, ell_max) : ell0;
+      const double* om = omegas ? omegas + builds * n * ell_max : nullptr;
+      const double* g = gs ? gs + builds * kmax * n : nullptr;
+      nys_factor* nf = nullptr;
+      nys_adapt_info info;
+      int32_t st = nys_sketch_adaptive(op, start, ell_max, NYS_RULE_ERR, tol_e, q, mu,
+                                       seed + (uint64_t)builds, om, g, o.precision, &nf, &info,
+                                       stream);
+      if (st != NYS_OK) {
+        if (f) nys_factor_free(f);
+        return st;
+      }
+      if (f) nys_factor_free(f);
+      f = nf;
+      E = info.err_est;
+      capped = f->ell >= ell_max;
+      ++builds;
+      resk = 1;
+    }
+    double* xi = x + idx * n;
+    if (xprev) {
+      cudaError_t ce = cudaMemcpyAsync(xi, xprev, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      if (ce != cudaSuccess) {
+        nys_factor_free(f);
+        NYS_CUDA_TRY(ce);
+      }
+    }
+    nys_pcg_opts oo = o;
+    oo.use_x0 = xprev ? 1 : 0;
+    nys_pcg_result r;
+    int32_t st = pcg_solve(op, f, &mu, 1, b, xi, &oo, &r, stream);
+    if (st != NYS_OK && st != NYS_ERR_MAXIT && st != NYS_ERR_BREAKDOWN) {
+      nys_factor_free(f);
+      return st;
+    }
+    nys_path_result& pr = results[idx];
+    pr.status = r.status;
+    pr.iterations = r.iterations;
+    pr.resketched = resk;
+    pr.refinements = r.refinements;
+    pr.ell = f->ell;
+    pr.err_est = E;
+    pr.rel_residual = r.rel_residual;
+    if (r.status == NYS_ERR_BREAKDOWN) worst = NYS_ERR_BREAKDOWN;
+    else if (r.status == NYS_ERR_MAXIT && worst == NYS_OK) worst = NYS_ERR_MAXIT;
+    xprev = xi;
+  }
+  nys_factor_free(f);
   return worst;
 }
 

@@ -351,6 +351,41 @@ def nys_block_pcg(op: Operator, f: Factor | None, mu: float, B: torch.Tensor,
     return XX, [PcgResult(r.status, r.iterations, r.refinements, r.rel_residual) for r in res]
 
 
+class _PathResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("resketched", C.c_int32),
+                ("refinements", C.c_int32), ("ell", C.c_int64), ("err_est", C.c_double),
+                ("rel_residual", C.c_double)]
+
+
+def nys_reg_path(op: Operator, mus, b: torch.Tensor, ell0: int, ell_max: int,
+                 err_factor: float = 30.0, q: int = 5, seed: int = 0,
+                 omegas: torch.Tensor | None = None, gs: torch.Tensor | None = None,
+                 tol: float = 1e-8, maxit: int = 500, precision: int = NYS_PREC_F64,
+                 inner_tol: float = 1e-4, max_refine: int = 20):
+    """Regularization path (warm starts, factor reuse) for the shifts `mus`.
+    Returns (X [count][n], [dict per shift])."""
+    fn = lib().nys_reg_path
+    if fn.argtypes is None:
+        fn.argtypes = [C.POINTER(_Operator), C.c_int64, C.POINTER(C.c_double), C.c_void_p,
+                       C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_int32, C.c_uint64,
+                       C.c_void_p, C.c_void_p, C.POINTER(_PcgOpts), C.POINTER(_PathResult),
+                       C.c_void_p]
+        fn.restype = C.c_int32
+    count = len(mus)
+    X = torch.empty((count, b.shape[-1]), dtype=torch.float64, device=b.device)
+    arr = (C.c_double * count)(*[float(m) for m in mus])
+    opts = _PcgOpts(tol, maxit, precision, inner_tol, max_refine, 0, None)
+    res = (_PathResult * count)()
+    st = fn(op.ref, count, arr, _ptr(b), _ptr(X), ell0, ell_max, float(err_factor), q, seed,
+            _ptr(omegas), _ptr(gs), C.byref(opts), res, _stream())
+    if st not in (NYS_OK, NYS_ERR_MAXIT, NYS_ERR_BREAKDOWN):
+        raise NysError(st, "nys_reg_path")
+    out = [dict(status=r.status, iterations=r.iterations, resketched=bool(r.resketched),
+                refinements=r.refinements, ell=r.ell, err_est=r.err_est,
+                rel_residual=r.rel_residual) for r in res]
+    return X, out
+
+
 def nys_op_matvec(op: Operator, mu: float, x: torch.Tensor, mode: int = 0) -> torch.Tensor:
     xx = x if x.dim() == 2 else x[None]
     y = torch.empty_like(xx)
