@@ -54,7 +54,7 @@ def parse():
                     help="time the solves only (no matvec, launch-count, e2e or CPU legs); "
                          "used for profiler launch lists")
     ap.add_argument("--workload", default="ridge",
-                    choices=["ridge", "dense", "krr", "batched", "adjoint"],
+                    choices=["ridge", "dense", "krr", "batched", "adjoint", "block", "path"],
                     help="ridge (default): the headline line; the others measure the remaining "
                          "workloads of the hot path (dense FP64; adaptive mixed kernel ridge; "
                          "batched regularisation path; differentiable kernel ridge)")
@@ -65,6 +65,8 @@ def parse():
                     help="krr workload: adaptive Gaussian sketch (default) or column-sampling "
                          "Nystrom at --cols sampled points")
     ap.add_argument("--cols", type=int, default=1024)
+    ap.add_argument("--nrhs", type=int, default=4,
+                    help="block workload: right-hand sides of the one shifted system")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="non-default workloads: multiply the number of points by this factor")
     return ap.parse_args()
@@ -565,6 +567,78 @@ def run_workload(args):
                              "status_by_mu": [[float(m), r.status, r.iterations, r.rel_residual]
                                               for m, r in list(zip(mus, res))[::4]]}
         line["phases_ms"] = dict(phase)
+    elif args.workload == "block":
+        # block Nystrom PCG: nrhs right-hand sides of one shifted Gaussian-kernel
+        # system, against the same systems solved as independent recurrences
+        n, d, ell, nrhs = int(50000 * args.scale), 16, 1024, args.nrhs
+        P = wl.gmm_points(n, d, seed=0)
+        sigma = wl.median_distance(P, seed=0)
+        op = ny.rbf_operator(T(P), sigma)
+        mu, tol = 1e-4 * n, 1e-8
+        B = T(wl.rhs(n, seed=0, nrhs=nrhs))
+        phase = {}
+
+        def step(seed):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            f = ny.nys_sketch(op, ell, seed=seed, precision=ny.NYS_PREC_MIXED)
+            e1.record()
+            X, res = ny.nys_block_pcg(op, f, mu, B, tol=tol, precision=ny.NYS_PREC_MIXED)
+            e2.record()
+            torch.cuda.synchronize()
+            phase["sketch_ms"], phase["block_pcg_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
+            f.free()
+            return res, None
+        for w in range(args.warmup):
+            step(100 + w)
+        launches0 = ny.kernel_launch_count()
+        ms, (res, _) = _events_ms(lambda: step(7), args.steps)
+        # the same systems as independent recurrences (one kernel pass per step for all)
+        f = ny.nys_sketch(op, ell, seed=7, precision=ny.NYS_PREC_MIXED)
+        ind_ms, (xi, ri, _) = _events_ms(
+            lambda: ny.pcg_solve(op, f, [mu] * nrhs, B, tol=tol, precision=ny.NYS_PREC_MIXED), 1)
+        f.free()
+        ok = [r.status == 0 for r in res]
+        line.update({"dtype": "f32",
+                     "config": {"workload": f"block PCG, Gaussian kernel n={n} d={d} "
+                                            f"GMM(10), {nrhs} right-hand sides of mu=1e-4 n, "
+                                            f"ell={ell}, mixed, tol {tol}"},
+                     "solve": {"systems": nrhs, "converged": int(sum(ok)),
+                               "block_products": res[0].iterations,
+                               "refinements": res[0].refinements,
+                               "worst_rel_residual": max(r.rel_residual for r in res)},
+                     "independent": {"pcg_ms": ind_ms,
+                                     "iterations_max": max(r.iterations for r in ri),
+                                     "converged": int(sum(r.status == 0 for r in ri))},
+                     "phases_ms": dict(phase)})
+    elif args.workload == "path":
+        # regularization path on the ridge operator: decreasing shifts, warm
+        # starts, factor reuse (err_factor 30, q 5), mixed precision
+        X, y = make_inputs(args.m, args.n)
+        Xd = T(X)
+        b = rhs_on_device(Xd, y)
+        op = ny.gram_operator(Xd)
+        mus = [10.0 ** e for e in range(1, -4, -1)]
+        ell0, ell_max, tol = 128, 2048, 1e-8
+
+        def step(seed):
+            Xs, out = ny.nys_reg_path(op, mus, b, ell0, ell_max, 30.0, 5, seed=seed, tol=tol,
+                                      precision=ny.NYS_PREC_MIXED)
+            return out, None
+        for w in range(args.warmup):
+            step(100 + w)
+        launches0 = ny.kernel_launch_count()
+        ms, (out, _) = _events_ms(lambda: step(7), args.steps)
+        ok = [o["status"] == 0 for o in out]
+        line.update({"dtype": "f32",
+                     "config": {"workload": f"regularization path, ridge {args.m}x{args.n}, "
+                                            f"mu = 10..1e-3 (5 shifts, decreasing), warm starts, "
+                                            f"factor kept while estimate <= 30 mu, ell {ell0}->"
+                                            f"{ell_max}, mixed, tol {tol}"},
+                     "solve": {"systems": len(mus), "converged": int(sum(ok)),
+                               "builds": int(sum(o["resketched"] for o in out)),
+                               "per_shift": [[m, o["ell"], o["resketched"], o["iterations"],
+                                              o["status"]] for m, o in zip(mus, out)]}})
     else:  # adjoint
         from paper_2110_02820_gb300 import krr
         n, nv, d, ell = int(200000 * args.scale), int(10000 * args.scale), 16, 2048
@@ -598,15 +672,16 @@ def run_workload(args):
                      "solve": {"loss": out[0], "dL_dmu": out[1], "dL_dsigma": out[2]},
                      "phases_ms": dict(phase)})
     sol = line.get("solve", {})
-    if args.workload == "batched":
+    if args.workload in ("batched", "block", "path"):
         line["metric"] = "converged PCG systems/sec (rel-residual 1e-8 each)"
         line["unit"] = "systems/s"
-        line["value_note"] = "value = converged systems / batched solve time"
+        line["value_note"] = "value = converged systems / solve time"
     if sol.get("status", 0) != 0 or sol.get("converged", 1) == 0:
         sys.stderr.write(f"bench: the {args.workload} solve did not converge: {sol}\n")
         sys.exit(3)
     line["ms_per_step"] = ms
-    line["value"] = (sol["converged"] if args.workload == "batched" else 1) * 1e3 / ms
+    line["value"] = (sol["converged"] if args.workload in ("batched", "block", "path")
+                     else 1) * 1e3 / ms
     line["gpu_launches"] = int(ny.kernel_launch_count() - launches0)
     print(json.dumps(line), flush=True)
 
