@@ -391,6 +391,154 @@ __global__ void init_state_kernel(const T* __restrict__ b, int64_t n, SysState* 
   }
 }
 
+// -------------------------------------------------------------- shared-U preconditioner
+//
+// For many systems sharing one factor, the two passes over U of Eq. (5.3)
+// serve a group of MUKM systems at once (U read once per group, not once per
+// system): W = U^T R for the group, w'_s = coefficient_s * W_s, and
+// z_s = r_s + U w'_s with the r^T z partials.  The residual update, the
+// ||r||^2 test and alpha / beta bookkeeping stay in the per-system kernels.
+template <typename T>
+struct MuGroup {
+  static constexpr int KM = sizeof(T) == 4 ? 16 : 8;  // systems per group
+};
+constexpr int MU_TR = 64;    // rows per tile of the U^T R pass
+constexpr int MU_LC = 256;   // columns of U per staged chunk of the z pass
+
+// wpart[bx][l][q] = sum over this block's row tiles of U[i][l] r[s0 + q][i]
+template <typename T, typename TU>
+__global__ void __launch_bounds__(PC_THREADS)
+mutr_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, T* __restrict__ wpart) {
+  constexpr int KM = MuGroup<T>::KM;
+  __shared__ __align__(16) T rs[MU_TR][KM];
+  const int64_t l = (int64_t)blockIdx.y * PC_THREADS + threadIdx.x;
+  T acc[KM];
+#pragma unroll
+  for (int q = 0; q < KM; ++q) acc[q] = T(0);
+  for (int64_t r0 = (int64_t)blockIdx.x * MU_TR; r0 < a.n; r0 += (int64_t)gridDim.x * MU_TR) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < KM * MU_TR; e += PC_THREADS) {
+      const int q = e / MU_TR, r = e - q * MU_TR;
+      rs[r][q] = (q < ks && r0 + r < a.n) ? a.r[(s0 + q) * a.n + r0 + r] : T(0);
+    }
+    __syncthreads();
+    if (l < a.ell) {
+      const int rows = (int)((a.n - r0 < MU_TR) ? a.n - r0 : MU_TR);
+      for (int r = 0; r < rows; ++r) {
+        const T u = (T)a.U[(r0 + r) * a.ell + l];
+#pragma unroll
+        for (int q = 0; q < KM; ++q) acc[q] = fma(u, rs[r][q], acc[q]);
+      }
+    }
+  }
+  if (l < a.ell)
+#pragma unroll
+    for (int q = 0; q < KM; ++q) wpart[((int64_t)blockIdx.x * a.ell + l) * KM + q] = acc[q];
+}
+
+// w'[s0 + q][l] = ((lam_ell + mu) / (lam_l + mu) - 1) sum_b wpart[b][l][q]
+template <typename T, typename TU>
+__global__ void mw_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, const T* __restrict__ wpart,
+                          int nb) {
+  constexpr int KM = MuGroup<T>::KM;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.ell * KM) return;
+  const int64_t l = e / KM;
+  const int q = (int)(e - l * KM);
+  if (q >= ks) return;
+  const SysState* st = a.st + s0 + q;
+  if (st->done) return;
+  double sum = 0.0;
+  for (int b = 0; b < nb; ++b) sum += (double)wpart[((int64_t)b * a.ell + l) * KM + q];
+  const double coef = st->lam_ell_mu / (a.lam[l] + st->mu) - 1.0;
+  a.w[(s0 + q) * a.ell + l] = (T)(coef * sum);
+}
+
+// z[s0 + q] = r + U w'[s0 + q] (one thread per row, w' staged in chunks of
+// MU_LC columns), r^T z partials into dpart[s][blockIdx.x].
+template <typename T, typename TU>
+__global__ void __launch_bounds__(PC_THREADS)
+mz_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, int setup) {
+  constexpr int KM = MuGroup<T>::KM;
+  __shared__ __align__(16) T ws[MU_LC][KM];
+  __shared__ double red[PC_WARPS][KM];
+  __shared__ int act[KM];
+  if (threadIdx.x < KM)
+    act[threadIdx.x] = threadIdx.x < ks && (setup || !a.st[s0 + threadIdx.x].done);
+  double rzq[KM];
+#pragma unroll
+  for (int q = 0; q < KM; ++q) rzq[q] = 0.0;
+  for (int64_t i0 = (int64_t)blockIdx.x * PC_THREADS; i0 < a.n;
+       i0 += (int64_t)gridDim.x * PC_THREADS) {
+    const int64_t i = i0 + threadIdx.x;
+    T acc[KM];
+#pragma unroll
+    for (int q = 0; q < KM; ++q) acc[q] = T(0);
+    for (int64_t c0 = 0; c0 < a.ell; c0 += MU_LC) {
+      const int lc = (int)((a.ell - c0 < MU_LC) ? a.ell - c0 : MU_LC);
+      __syncthreads();
+      for (int e = threadIdx.x; e < KM * MU_LC; e += PC_THREADS) {
+        const int q = e / MU_LC, c = e - q * MU_LC;
+        ws[c][q] = (q < ks && c < lc) ? a.w[(s0 + q) * a.ell + c0 + c] : T(0);
+      }
+      __syncthreads();
+      if (i < a.n) {
+        const TU* urow = a.U + i * a.ell + c0;
+        for (int c = 0; c < lc; ++c) {
+          const T u = (T)urow[c];
+#pragma unroll
+          for (int q = 0; q < KM; ++q) acc[q] = fma(u, ws[c][q], acc[q]);
+        }
+      }
+    }
+    if (i < a.n) {
+#pragma unroll
+      for (int q = 0; q < KM; ++q) {
+        if (q < ks && act[q]) {
+          const T ri = a.r[(s0 + q) * a.n + i];
+          const T zi = (T)((double)ri + (double)acc[q]);
+          a.z[(s0 + q) * a.n + i] = zi;
+          rzq[q] += (double)ri * (double)zi;
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < KM; ++q) {
+    const double v = warp_sum(rzq[q]);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < ks && act[threadIdx.x]) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < PC_WARPS; ++w) t += red[w][threadIdx.x];
+    a.dpart[(s0 + threadIdx.x) * a.npart + blockIdx.x] = t;
+  }
+}
+
+// r^T z from the mz partials (fixed order); beta and rz as z_kernel's last block.
+template <typename T, typename TU>
+__global__ void __launch_bounds__(PC_THREADS)
+mrz_kernel(PcgArgs<T, TU> a, int nbz, int setup) {
+  const int64_t sidx = blockIdx.x;
+  SysState* st = a.st + sidx;
+  if (st->done && !setup) return;
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nbz; b += PC_THREADS) t += a.dpart[sidx * a.npart + b];
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) {
+    if (setup) {
+      st->rz = t;
+    } else {
+      st->beta = t / st->rz;
+      st->rz = t;
+    }
+  }
+}
+
 // -------------------------------------------------------------- host driver
 
 template <typename T, typename TU>
@@ -429,6 +577,10 @@ struct PcgLaunch {
   bool vec;
   size_t usm, zsm;
   dim3 g_u, g_w, g_d;
+  // shared-U passes for many systems (multi): groups of MuGroup<T>::KM systems
+  bool multi = false;
+  T* mwpart = nullptr;
+  int nbu_m = 0, nbz_m = 0;
   int32_t setup(PcgArgs<T, TU>& a, int64_t nsys) {
     constexpr int VE = 16 / sizeof(TU);
     vec = a.U && (a.ell % VE == 0) && (((uintptr_t)a.U & 15u) == 0);
@@ -446,8 +598,44 @@ struct PcgLaunch {
     }
     return NYS_OK;
   }
+  // Multi-system mode: the U passes run per group of systems.  `wpart` must
+  // hold multi_wpart_elems(a) values of T.
+  static size_t multi_wpart_elems(const PcgArgs<T, TU>& a) {
+    return (size_t)multi_nbu(a) * a.ell * MuGroup<T>::KM;
+  }
+  static int multi_nbu(const PcgArgs<T, TU>& a) {
+    const int64_t t = cdiv(a.n, MU_TR);
+    const int64_t cap = num_sms();
+    return (int)(t < cap ? t : cap);
+  }
+  void enable_multi(const PcgArgs<T, TU>& a, T* wpart) {
+    multi = true;
+    mwpart = wpart;
+    nbu_m = multi_nbu(a);
+    const int64_t t = cdiv(a.n, PC_THREADS);
+    nbz_m = (int)(t < a.npart ? t : a.npart);
+  }
   void update(PcgArgs<T, TU>& a, int do_update, cudaStream_t s) {
     constexpr int VE = 16 / sizeof(TU);
+    if (multi) {
+      // x, r update and ||r||^2 per system (no U), then U^T R per group
+      PcgArgs<T, TU> b = a;
+      b.U = nullptr;
+      update_kernel<T, TU, 1><<<g_u, PC_THREADS, usm, s>>>(b, do_update); count_launch();
+      wreduce_kernel<T, TU><<<dim3(1, (unsigned)a.nsys), PC_THREADS, 0, s>>>(b, do_update);
+      count_launch();
+      constexpr int KM = MuGroup<T>::KM;
+      for (int64_t s0 = 0; s0 < a.nsys; s0 += KM) {
+        const int ks = (int)((a.nsys - s0 < KM) ? a.nsys - s0 : KM);
+        mutr_kernel<T, TU><<<dim3((unsigned)nbu_m, (unsigned)cdiv(a.ell, PC_THREADS)),
+                             PC_THREADS, 0, s>>>(a, s0, ks, mwpart);
+        count_launch();
+        mw_kernel<T, TU><<<(unsigned)cdiv(a.ell * KM, 256), 256, 0, s>>>(a, s0, ks, mwpart,
+                                                                         nbu_m);
+        count_launch();
+      }
+      return;
+    }
     if (vec)
       update_kernel<T, TU, VE><<<g_u, PC_THREADS, usm, s>>>(a, do_update);
     else
@@ -457,6 +645,17 @@ struct PcgLaunch {
   }
   void z(PcgArgs<T, TU>& a, int setup_flag, cudaStream_t s) {
     constexpr int VE = 16 / sizeof(TU);
+    if (multi) {
+      constexpr int KM = MuGroup<T>::KM;
+      for (int64_t s0 = 0; s0 < a.nsys; s0 += KM) {
+        const int ks = (int)((a.nsys - s0 < KM) ? a.nsys - s0 : KM);
+        mz_kernel<T, TU><<<(unsigned)nbz_m, PC_THREADS, 0, s>>>(a, s0, ks, setup_flag);
+        count_launch();
+      }
+      mrz_kernel<T, TU><<<(unsigned)a.nsys, PC_THREADS, 0, s>>>(a, nbz_m, setup_flag);
+      count_launch();
+      return;
+    }
     if (vec)
       z_kernel<T, TU, VE><<<g_u, PC_THREADS, zsm, s>>>(a, setup_flag);
     else
@@ -526,6 +725,12 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   }
   PcgLaunch<T, TU> L;
   NYS_TRY(L.setup(a, nsys));
+  if (U && nsys >= 4) {
+    // many systems share U: read it once per group of systems, not per system
+    T* mw;
+    NYS_TRY(B.get((void**)&mw, PcgLaunch<T, TU>::multi_wpart_elems(a) * sizeof(T)));
+    L.enable_multi(a, mw);
+  }
 
   // ---- setup: state, r0, z0 = P^{-1} r0, p0 = z0, r0^T z0
   init_state_kernel<T><<<(unsigned)nsys, 256, 0, s>>>(b_T, n, a.st, B.d_mu, lam_ell, tol, maxit);
