@@ -574,7 +574,7 @@ def run_workload(args):
         P = wl.gmm_points(n, d, seed=0)
         sigma = wl.median_distance(P, seed=0)
         op = ny.rbf_operator(T(P), sigma)
-        mu, tol = 1e-4 * n, 1e-8
+        mu, tol = 2e-7 * n, 1e-8
         B = T(wl.rhs(n, seed=0, nrhs=nrhs))
         phase = {}
 
@@ -601,7 +601,7 @@ def run_workload(args):
         ok = [r.status == 0 for r in res]
         line.update({"dtype": "f32",
                      "config": {"workload": f"block PCG, Gaussian kernel n={n} d={d} "
-                                            f"GMM(10), {nrhs} right-hand sides of mu=1e-4 n, "
+                                            f"GMM(10), {nrhs} right-hand sides of mu=2e-7 n, "
                                             f"ell={ell}, mixed, tol {tol}"},
                      "solve": {"systems": nrhs, "converged": int(sum(ok)),
                                "block_products": res[0].iterations,

@@ -629,10 +629,10 @@ static int32_t adaptive_impl(const nys_operator* op, int64_t ell0, int64_t ell_m
       if (m > 0) {
         st = add_block(m);
         if (st == NYS_OK) st = compute();
+        E = std::nan("");  // the enlarged factor has no estimate
       } else {
-        --doublings;
+        --doublings;       // the sketch is already at ell_max: its estimate stands
       }
-      E = std::nan("");
       break;
     }
   }
