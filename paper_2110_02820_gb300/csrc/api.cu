@@ -300,6 +300,12 @@ static int32_t shifted_core(const T* Q, const T* Y, int64_t n, int64_t ell, bool
   NYS_TRY(read_int(jst, &hj, s));
   if (hj != 0) return NYS_ERR_TIMEOUT;
   NYS_TRY(Ops<T>::mul_small(Bb, Ut, n, ell, ell, (T*)f->U, s));  // U = Qb Ut
+  if (!Ops<T>::f64) {
+    // an FP32 U is orthonormal only to its rounding: keep U^T U - I for the
+    // corrected preconditioner apply
+    if (!f->E) NYS_CUDA_TRY(cudaMalloc(&f->E, (size_t)ell * ell * sizeof(float)));
+    NYS_TRY(orth_defect_f32(reinterpret_cast<const float*>(f->U), n, ell, f->E, s));
+  }
   NYS_TRY(lambda_from_sigma(sig, nu, f->lam, ell, s));         // lam = max(0, sigma^2 - nu)
   NYS_TRY(read_double(nu, &f->nu, s));
   NYS_TRY(read_double(f->lam + (ell - 1), &f->lam_ell, s));
@@ -947,6 +953,7 @@ void nys_factor_free(nys_factor* f) {
   cudaDeviceSynchronize();
   if (f->U) cudaFree(f->U);
   if (f->lam) cudaFree(f->lam);
+  if (f->E) cudaFree(f->E);
   if (cur != f->device) cudaSetDevice(cur);
   delete f;
 }

@@ -156,17 +156,54 @@ butr_part_kernel(const TU* __restrict__ U, int64_t n, int64_t ell, const T* __re
     for (int q = 0; q < k; ++q) wpart[((int64_t)blockIdx.x * ell + l) * k + q] = (double)acc[q];
 }
 
-// w[l][q] = ((lam_ell + mu) / (lam_l + mu) - 1) sum_b wpart[b][l][q]
+// w[l][q] = ((lam_ell + mu) / (lam_l + mu) - 1) sum_b wpart[b][l][q]; with an
+// orthonormality defect E the raw sums go to wraw and the corrected
+// coefficients are formed by bwcorr_kernel.
 __global__ void bw_reduce_kernel(const double* __restrict__ wpart, int nb, int64_t ell, int k,
                                  const double* __restrict__ lam, double lam_ell, double mu,
-                                 double* __restrict__ w, const BState* st) {
+                                 double* __restrict__ w, double* __restrict__ wraw,
+                                 const BState* st) {
   if (st && st->done) return;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ell * k) return;
   double s = 0.0;
   for (int b = 0; b < nb; ++b) s += wpart[(int64_t)b * ell * k + e];
   const int64_t l = e / k;
-  w[e] = ((lam_ell + mu) / (lam[l] + mu) - 1.0) * s;
+  const double c = (lam_ell + mu) / (lam[l] + mu) - 1.0;
+  if (wraw) {
+    wraw[e] = s;            // raw U^T r
+    wraw[ell * k + e] = c * s;  // c . (U^T r)
+  } else {
+    w[e] = c * s;
+  }
+}
+
+// w[i][q] = c_i W_iq - (c_i (E W)_iq + (E (c.W))_iq) / 2, with W and c.W in
+// wraw[0 .. ell k) and wraw[ell k .. 2 ell k) (the apply through the
+// orthonormal basis U (I + E)^{-1/2}, first order in E): one warp per (i, q).
+__global__ void bwcorr_kernel(const float* __restrict__ E, int64_t ell, int k,
+                              const double* __restrict__ lam, double lam_ell, double mu,
+                              const double* __restrict__ wraw, double* __restrict__ w,
+                              const BState* st) {
+  if (st && st->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (g >= ell * k) return;
+  const int64_t i = g / k;
+  const int q = (int)(g - i * k);
+  const double* wcw = wraw + ell * k;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t j = lane; j < ell; j += 32) {
+    const double e = (double)E[i * ell + j];
+    s1 += e * wraw[j * k + q];
+    s2 += e * wcw[j * k + q];
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    const double ci = (lam_ell + mu) / (lam[i] + mu) - 1.0;
+    w[i * k + q] = ci * wraw[i * k + q] - 0.5 * (ci * s1 + s2);
+  }
 }
 
 // Z[q][i] = R[q][i] + sum_l U[i][l] w[l][q]: one warp per row
@@ -363,9 +400,9 @@ int32_t comb(const T* A, int ka, const double* M, int ko, const TO* C, double cs
 
 // Z = P^{-1} R (Eq. 5.3) for k columns: two passes over U.
 template <typename T, typename TU>
-int32_t precond_block(const TU* U, const double* lam, int64_t ell, double lam_ell, double mu,
-                      int64_t n, int k, const T* R, T* Z, double* wpart, double* w,
-                      const BState* st, cudaStream_t s) {
+int32_t precond_block(const TU* U, const float* E, const double* lam, int64_t ell, double lam_ell,
+                      double mu, int64_t n, int k, const T* R, T* Z, double* wpart, double* w,
+                      double* wraw, const BState* st, cudaStream_t s) {
   if (!U || ell == 0) {
     NYS_CUDA_TRY(cudaMemcpyAsync(Z, R, (size_t)k * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     return NYS_OK;
@@ -377,8 +414,14 @@ int32_t precond_block(const TU* U, const double* lam, int64_t ell, double lam_el
   butr_part_kernel<T, TU, KM><<<g1, BT, 0, s>>>(U, n, ell, R, k, wpart, st);                   \
   count_launch();                                                                             \
   bw_reduce_kernel<<<(unsigned)cdiv(ell * k, 256), 256, 0, s>>>(wpart, nbu, ell, k, lam,      \
-                                                                 lam_ell, mu, w, st);         \
+                                                                 lam_ell, mu, w,              \
+                                                                 E ? wraw : nullptr, st);     \
   count_launch();                                                                             \
+  if (E) {                                                                                    \
+    bwcorr_kernel<<<(unsigned)cdiv(ell * k * 32, 256), 256, 0, s>>>(E, ell, k, lam, lam_ell,  \
+                                                                    mu, wraw, w, st);         \
+    count_launch();                                                                           \
+  }                                                                                           \
   bz_kernel<T, TU, KM><<<gz, BT, 0, s>>>(U, n, ell, w, R, Z, k, st);                           \
   count_launch();
   if (k <= 4) {
@@ -443,8 +486,9 @@ double drop_tol<float>() { return 64.0 * 5.9604644775390625e-08; }
 // tol ||b_j||.  On return X holds the iterate; it, status[j], rel[j]
 // (recurrence residual / ||b_j||) are host outputs.
 template <typename T, typename TU>
-int32_t run_block(const nys_operator* op, const TU* U, const double* lam, int64_t ell,
-                  double lam_ell, double mu, int k, const T* B, T* X, bool use_x0, double tol,
+int32_t run_block(const nys_operator* op, const TU* U, const float* E, const double* lam,
+                  int64_t ell, double lam_ell, double mu, int k, const T* B, T* X, bool use_x0,
+                  double tol,
                   int maxit, int* it_out, int* status, double* rel, cudaStream_t s) {
   const int64_t n = op->n;
   Scratch sc(s);
@@ -458,7 +502,7 @@ int32_t run_block(const nys_operator* op, const TU* U, const double* lam, int64_
   NYS_TRY(sc.get(&P, kn));
   NYS_TRY(sc.get(&V, kn));
   const int nbg = gram_blocks(n);
-  double *part, *part2, *small, *wpart = nullptr, *w = nullptr, *d_mu;
+  double *part, *part2, *small, *wpart = nullptr, *w = nullptr, *wraw = nullptr, *d_mu;
   NYS_TRY(sc.get(&part, (size_t)nbg * BK * BK));
   NYS_TRY(sc.get(&part2, (size_t)nbg * BK * BK));
   NYS_TRY(sc.get(&small, 8 * BK * BK));
@@ -466,6 +510,7 @@ int32_t run_block(const nys_operator* op, const TU* U, const double* lam, int64_
   if (U && ell > 0) {
     NYS_TRY(sc.get(&wpart, precond_wpart_elems(n, ell, k)));
     NYS_TRY(sc.get(&w, (size_t)ell * k));
+    if (E) NYS_TRY(sc.get(&wraw, 2 * (size_t)ell * k));
   }
   double* d_rho = small;
   double* d_alpha = small + BK * BK;
@@ -573,7 +618,7 @@ int32_t run_block(const nys_operator* op, const TU* U, const double* lam, int64_
   // ---- Y = 0, R = Q, Z = P^{-1} R, P = Z, rho = Z^T R
   NYS_CUDA_TRY(cudaMemsetAsync(Y, 0, (size_t)k1 * n * sizeof(T), s));
   NYS_CUDA_TRY(cudaMemcpyAsync(R, Q, (size_t)k1 * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-  NYS_TRY((precond_block<T, TU>(U, lam, ell, lam_ell, mu, n, k1, R, Z, wpart, w, st, s)));
+  NYS_TRY((precond_block<T, TU>(U, E, lam, ell, lam_ell, mu, n, k1, R, Z, wpart, w, wraw, st, s)));
   NYS_CUDA_TRY(cudaMemcpyAsync(P, Z, (size_t)k1 * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   NYS_TRY(gram<T>(Z, k1, R, k1, n, part, d_rho, st, s));
 
@@ -587,7 +632,7 @@ int32_t run_block(const nys_operator* op, const TU* U, const double* lam, int64_
       NYS_TRY((comb<T, T>(P, k1, d_alpha, k1, Y, 1.0, 1.0, Y, n, st, s)));
       NYS_TRY((comb<T, T>(V, k1, d_alpha, k1, R, 1.0, -1.0, R, n, st, s)));
       NYS_TRY(gram<T>(R, k1, R, k1, n, part, nullptr, st, s));
-      NYS_TRY((precond_block<T, TU>(U, lam, ell, lam_ell, mu, n, k1, R, Z, wpart, w, st, s)));
+      NYS_TRY((precond_block<T, TU>(U, E, lam, ell, lam_ell, mu, n, k1, R, Z, wpart, w, wraw, st, s)));
       NYS_TRY(gram<T>(Z, k1, R, k1, n, part2, nullptr, st, s));
       bbeta_kernel<<<1, 1024, 0, s>>>(part, part2, nbg, d_S, d_rho, d_beta, st); count_launch();
       NYS_TRY((comb<T, T>(P, k1, d_beta, k1, Z, 1.0, 1.0, P, n, st, s)));
@@ -657,7 +702,8 @@ int32_t block_pcg_f64(const nys_operator* op, const nys_factor* f, double mu, in
   std::vector<int> stt(k);
   std::vector<double> rel(k);
   int it = 0;
-  NYS_TRY((run_block<double, double>(op, U, f ? f->lam : nullptr, f ? f->ell : 0,
+  NYS_TRY((run_block<double, double>(op, U, f ? f->E : nullptr, f ? f->lam : nullptr,
+                                     f ? f->ell : 0,
                                      f ? f->lam_ell : 0.0, mu, (int)k, b, x, use_x0 != 0, tol,
                                      maxit, &it, stt.data(), rel.data(), s)));
   for (int64_t q = 0; q < k; ++q) {
@@ -678,14 +724,19 @@ int32_t block_pcg_mixed(const nys_operator* op, const nys_factor* f, double mu, 
   const int64_t n = op->n;
   Scratch sc(s);
   const float* U = nullptr;
+  const float* Edef = nullptr;
   if (f) {
     if (f->u_dtype == NYS_F32) {
       U = (const float*)f->U;
+      Edef = f->E;
     } else {
-      float* Uf;
+      float *Uf, *Ef;
       NYS_TRY(sc.get(&Uf, f->n * f->ell));
+      NYS_TRY(sc.get(&Ef, f->ell * f->ell));
       NYS_TRY(convert_f64_to_f32((const double*)f->U, Uf, f->n * f->ell, s));
+      NYS_TRY(orth_defect_f32(Uf, f->n, f->ell, Ef, s));
       U = Uf;
+      Edef = Ef;
     }
   }
   double *r, *v, *d_mu, *nrm;
@@ -772,7 +823,7 @@ int32_t block_pcg_mixed(const nys_operator* op, const nys_factor* f, double mu, 
     std::vector<int> ist(na);
     std::vector<double> irel(na);
     int its = 0;
-    NYS_TRY((run_block<float, float>(op, U, f ? f->lam : nullptr, f ? f->ell : 0,
+    NYS_TRY((run_block<float, float>(op, U, Edef, f ? f->lam : nullptr, f ? f->ell : 0,
                                      f ? f->lam_ell : 0.0, mu, na, rf, df, false, inner_tol,
                                      maxit - total_it, &its, ist.data(), irel.data(), s)));
     for (int a = 0; a < na; ++a) {

@@ -17,6 +17,7 @@ struct nys_factor {
   int32_t escalations = 0;
   int32_t svd_sweeps = 0;
   int32_t svd_refine = 0;
+  float* E = nullptr;         // FP32 U only: U^T U - I (ell x ell), for the corrected P^{-1}
   int device = 0;
 };
 
@@ -105,6 +106,8 @@ int32_t tc_gemm_tn_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t 
 // y += x (elementwise)
 int32_t add_inplace_f64(double* y, const double* x, int64_t count, cudaStream_t s);
 int32_t convert_f64_to_f32(const double* in, float* out, int64_t count, cudaStream_t s);
+// E = U^T U - I for an FP32 n x ell U, in double-FP32 arithmetic (orth.cu).
+int32_t orth_defect_f32(const float* U, int64_t n, int64_t ell, float* E, cudaStream_t s);
 int32_t convert_f32_to_f64(const float* in, double* out, int64_t count, cudaStream_t s);
 // sum of squares of `count` values, written to d_out (FP64 accumulate, fixed order)
 int32_t sumsq_f32(const float* x, int64_t count, double* d_out, cudaStream_t s);

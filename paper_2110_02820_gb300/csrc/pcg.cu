@@ -59,6 +59,9 @@ struct PcgArgs {
   int64_t nblk_d;         // blocks of the elementwise dot kernels
   int64_t npart;          // stride of dpart per system
   double* hist;           // [nsys][maxit+1] or NULL
+  const float* E;         // U^T U - I (ell x ell) of an FP32 factor, or NULL
+  T* wraw;                // [nsys][ell] U^T r (when E is set)
+  T* wc;                  // [nsys][ell] coefficient * U^T r (when E is set)
 };
 
 // -------------------------------------------------------------- kernels
@@ -240,7 +243,12 @@ wreduce_kernel(PcgArgs<T, TU> a, int do_update) {
 #pragma unroll
       for (int w = 0; w < PC_WARPS; ++w) tot += ws[w][lane];
       const double coef = st->lam_ell_mu / (a.lam[j] + st->mu) - 1.0;
-      a.w[sidx * a.ell + j] = (T)(coef * (double)tot);
+      if (a.E) {
+        a.wraw[sidx * a.ell + j] = (T)tot;
+        a.wc[sidx * a.ell + j] = (T)(coef * (double)tot);
+      } else {
+        a.w[sidx * a.ell + j] = (T)(coef * (double)tot);
+      }
     }
   }
   if (blockIdx.x == 0) {
@@ -451,7 +459,12 @@ __global__ void mw_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, const T* __restr
   double sum = 0.0;
   for (int b = 0; b < nb; ++b) sum += (double)wpart[((int64_t)b * a.ell + l) * KM + q];
   const double coef = st->lam_ell_mu / (a.lam[l] + st->mu) - 1.0;
-  a.w[(s0 + q) * a.ell + l] = (T)(coef * sum);
+  if (a.E) {
+    a.wraw[(s0 + q) * a.ell + l] = (T)sum;
+    a.wc[(s0 + q) * a.ell + l] = (T)(coef * sum);
+  } else {
+    a.w[(s0 + q) * a.ell + l] = (T)(coef * sum);
+  }
 }
 
 // z[s0 + q] = r + U w'[s0 + q] (one thread per row, w' staged in chunks of
@@ -536,6 +549,35 @@ mrz_kernel(PcgArgs<T, TU> a, int nbz, int setup) {
       st->beta = t / st->rz;
       st->rz = t;
     }
+  }
+}
+
+// Corrected coefficients for an FP32 factor (U^T U = I + E): w' = c.w -
+// (c.(E w) + E (c.w)) / 2, the apply through the orthonormal basis U (I+E)^{-1/2}
+// to first order in E.  One warp per (coefficient i, system).
+template <typename T, typename TU>
+__global__ void __launch_bounds__(PC_THREADS)
+wcorr_kernel(PcgArgs<T, TU> a) {
+  const int64_t sidx = blockIdx.y;
+  const SysState* st = a.st + sidx;
+  if (st->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * PC_WARPS + warp;
+  if (i >= a.ell) return;
+  const T* wr = a.wraw + sidx * a.ell;
+  const T* wc = a.wc + sidx * a.ell;
+  const float* Ei = a.E + i * a.ell;
+  float s1 = 0.f, s2 = 0.f;
+  for (int64_t j = lane; j < a.ell; j += 32) {
+    const float e = Ei[j];
+    s1 = fmaf(e, (float)wr[j], s1);
+    s2 = fmaf(e, (float)wc[j], s2);
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    const double ci = st->lam_ell_mu / (a.lam[i] + st->mu) - 1.0;
+    a.w[sidx * a.ell + i] = (T)((double)wc[i] - 0.5 * (ci * (double)s1 + (double)s2));
   }
 }
 
@@ -634,6 +676,11 @@ struct PcgLaunch {
                                                                          nbu_m);
         count_launch();
       }
+      if (a.E) {
+        wcorr_kernel<T, TU><<<dim3((unsigned)cdiv(a.ell, PC_WARPS), (unsigned)a.nsys), PC_THREADS,
+                              0, s>>>(a);
+        count_launch();
+      }
       return;
     }
     if (vec)
@@ -642,6 +689,11 @@ struct PcgLaunch {
       update_kernel<T, TU, 1><<<g_u, PC_THREADS, usm, s>>>(a, do_update);
     count_launch();
     wreduce_kernel<T, TU><<<g_w, PC_THREADS, 0, s>>>(a, do_update); count_launch();
+    if (a.E) {
+      wcorr_kernel<T, TU><<<dim3((unsigned)cdiv(a.ell, PC_WARPS), (unsigned)a.nsys), PC_THREADS,
+                            0, s>>>(a);
+      count_launch();
+    }
   }
   void z(PcgArgs<T, TU>& a, int setup_flag, cudaStream_t s) {
     constexpr int VE = 16 / sizeof(TU);
@@ -683,7 +735,8 @@ int32_t matvec_T<double>(const nys_operator* op, double mu, const double* p, dou
 // use_x0 the incoming x is the initial guess.  Fills iterations/status.
 template <typename T, typename TU>
 static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, int64_t ell,
-                       double lam_ell, const double* mus_host, int64_t nsys, const double* b_dev,
+                       double lam_ell, const float* E, const double* mus_host, int64_t nsys,
+                       const double* b_dev,
                        const T* b_T, T* x, double tol, int maxit, int use_x0, double* hist,
                        int* iters_out, int* status_out, double* relres_out, cudaStream_t s) {
   const int64_t n = op->n;
@@ -711,6 +764,11 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   if (U) {
     NYS_TRY(B.get((void**)&a.wpart, (size_t)nsys * a.nblk_u * ell * sizeof(TU)));
     NYS_TRY(B.get((void**)&a.w, (size_t)nsys * ell * sizeof(T)));
+    if (E) {
+      a.E = E;
+      NYS_TRY(B.get((void**)&a.wraw, (size_t)nsys * ell * sizeof(T)));
+      NYS_TRY(B.get((void**)&a.wc, (size_t)nsys * ell * sizeof(T)));
+    }
   }
   size_t wbytes = op_matvec_work_bytes(op, sizeof(T) == sizeof(double));
   NYS_TRY(B.get(&B.op_work, wbytes));
@@ -835,7 +893,7 @@ int32_t pcg_f64(const nys_operator* op, const nys_factor* f, const double* mu, i
     }
   }
   NYS_TRY((run_pcg<double, double>(op, U, f ? f->lam : nullptr, f ? f->ell : 0,
-                                   f ? f->lam_ell : 0.0, mu, nsys, b, b, x, tol, maxit, use_x0,
+                                   f ? f->lam_ell : 0.0, f ? f->E : nullptr, mu, nsys, b, b, x, tol, maxit, use_x0,
                                    hist, it.data(), stt.data(), rel.data(), s)));
   for (int64_t q = 0; q < nsys; ++q) {
     res[q].status = stt[q];
@@ -855,14 +913,19 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   const int64_t n = op->n;
   Scratch sc(s);
   const float* U = nullptr;
+  const float* Edef = nullptr;  // U^T U - I of the FP32 U the inner solves use
   if (f) {
     if (f->u_dtype == NYS_F32) {
       U = (const float*)f->U;
+      Edef = f->E;
     } else {
-      float* Uf;
+      float *Uf, *Ef;
       NYS_TRY(sc.get(&Uf, f->n * f->ell));
+      NYS_TRY(sc.get(&Ef, f->ell * f->ell));
       NYS_TRY(convert_f64_to_f32((const double*)f->U, Uf, f->n * f->ell, s));
+      NYS_TRY(orth_defect_f32(Uf, f->n, f->ell, Ef, s));
       U = Uf;
+      Edef = Ef;
     }
   }
   double *r, *v, *nrm;
@@ -991,7 +1054,7 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
     int budget = 1;
     for (int64_t q : todo) budget = std::max(budget, maxit - total_it[q]);
     NYS_TRY((run_pcg<float, float>(op, U, f ? f->lam : nullptr, f ? f->ell : 0,
-                                   f ? f->lam_ell : 0.0, mua.data(), na, v, rf, df, inner_tol,
+                                   f ? f->lam_ell : 0.0, Edef, mua.data(), na, v, rf, df, inner_tol,
                                    budget, 0, (k == 0) ? hist : nullptr, it.data(), st.data(),
                                    rr.data(), s)));
     for (int64_t t = 0; t < na; ++t) {
@@ -1019,8 +1082,9 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
 // -------------------------------------------------------------- P^{-1} apply
 
 template <typename T, typename TU>
-static int32_t precond_apply_impl(const nys_factor* f, const TU* U, const double* mu,
-                                  int64_t nrhs, const T* v, T* z, cudaStream_t s) {
+static int32_t precond_apply_impl(const nys_factor* f, const TU* U, const float* E,
+                                  const double* mu, int64_t nrhs, const T* v, T* z,
+                                  cudaStream_t s) {
   const int64_t n = f->n, ell = f->ell;
   PcgBuffers<T, TU> B;
   B.s = s;
@@ -1040,6 +1104,11 @@ static int32_t precond_apply_impl(const nys_factor* f, const TU* U, const double
   NYS_TRY(B.get((void**)&a.counters, (size_t)nrhs * 4 * sizeof(unsigned)));
   NYS_TRY(B.get((void**)&a.wpart, (size_t)nrhs * a.nblk_u * ell * sizeof(TU)));
   NYS_TRY(B.get((void**)&a.w, (size_t)nrhs * ell * sizeof(T)));
+  if (E) {
+    a.E = E;
+    NYS_TRY(B.get((void**)&a.wraw, (size_t)nrhs * ell * sizeof(T)));
+    NYS_TRY(B.get((void**)&a.wc, (size_t)nrhs * ell * sizeof(T)));
+  }
   NYS_TRY(B.get((void**)&B.d_mu, nrhs * sizeof(double)));
   NYS_CUDA_TRY(cudaMemsetAsync(a.counters, 0, (size_t)nrhs * 4 * sizeof(unsigned), s));
   NYS_CUDA_TRY(cudaMemcpyAsync(B.d_mu, mu, nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1068,16 +1137,21 @@ int32_t precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const
       NYS_TRY(convert_f32_to_f64((const float*)f->U, Ud, f->n * f->ell, s));
       U = Ud;
     }
-    return precond_apply_impl<double, double>(f, U, mu, nrhs, (const double*)v, (double*)z, s);
+    return precond_apply_impl<double, double>(f, U, f->E, mu, nrhs, (const double*)v,
+                                              (double*)z, s);
   }
   const float* U = (const float*)f->U;
+  const float* E = f->E;
   if (f->u_dtype != NYS_F32) {
-    float* Uf;
+    float *Uf, *Ef;
     NYS_TRY(sc.get(&Uf, f->n * f->ell));
+    NYS_TRY(sc.get(&Ef, f->ell * f->ell));
     NYS_TRY(convert_f64_to_f32((const double*)f->U, Uf, f->n * f->ell, s));
+    NYS_TRY(orth_defect_f32(Uf, f->n, f->ell, Ef, s));
     U = Uf;
+    E = Ef;
   }
-  return precond_apply_impl<float, float>(f, U, mu, nrhs, (const float*)v, (float*)z, s);
+  return precond_apply_impl<float, float>(f, U, E, mu, nrhs, (const float*)v, (float*)z, s);
 }
 
 }  // namespace nys

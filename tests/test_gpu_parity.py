@@ -302,8 +302,10 @@ def test_pcg_batched_columns_equal_single_solves(ny):
     X, res, _ = ny.pcg_solve(op, f, mus, T(B), tol=1e-10)
     for s in range(6):
         x1, r1, _ = ny.pcg_solve(op, f, mus[s], T(B[s]), tol=1e-10)
-        assert r1[0].iterations == res[s].iterations
-        assert torch.equal(x1, X[s])
+        # the same recurrence; with >= 4 systems the two passes over U serve a
+        # group of systems at once, so the sums round in another order
+        assert abs(r1[0].iterations - res[s].iterations) <= 1
+        assert relerr(X[s].cpu().numpy(), x1.cpu().numpy()) <= 1e-10 * (1 + 1 / mus[s])
         xs = opcg.direct_solve(A, mus[s], B[s])
         assert relerr(X[s].cpu().numpy(), xs) <= 1e-10 * (1 + 1 / mus[s]) * 10
 
@@ -340,6 +342,49 @@ def test_mixed_preconditioner_keeps_fp64_iteration_count(ny):
     U = fm.U().double()
     assert (U.T @ U - torch.eye(ell, dtype=torch.float64, device=U.device)).abs().max() <= 2e-6
     f64 = ny.nys_sketch(op, ell, omega=Om)
+    _, r64, _ = ny.pcg_solve(op, f64, mu, T(b), tol=1e-8)
+    _, rm, _ = ny.pcg_solve(op, fm, mu, T(b), tol=1e-8, precision=ny.NYS_PREC_MIXED)
+    assert r64[0].status == ny.NYS_OK and rm[0].status == ny.NYS_OK, (r64, rm)
+    assert rm[0].iterations <= 2 * r64[0].iterations + 10, (r64, rm)
+
+
+def test_precond_apply_orthonormalises_fp32_factor(ny):
+    # An FP32 U has U^T U = I + E.  The apply uses the orthonormal basis
+    # V = U (I + E)^{-1/2} of the same range (to first order in E): compared in
+    # FP64 with Eq. (5.3) built on the exactly orthonormalised V, the error is
+    # second order in ||E||, while the formula taken with U itself is off by ~||E||.
+    m, n, ell, mu = 4000, 1024, 256, 1e-3
+    X = wl.ridge_X(m, n, seed=60)
+    op = ny.gram_operator(T(X))
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, 60)), precision=ny.NYS_PREC_MIXED)
+    U = f.U().double().cpu().numpy()
+    lam = f.lam().cpu().numpy()
+    G = U.T @ U
+    w, Q = np.linalg.eigh(G)
+    V = U @ (Q * w ** -0.5) @ Q.T
+    v = wl.rhs(n, seed=60, nrhs=3)
+    z = ny.nys_precond_apply(f, mu, T(v)).cpu().numpy()
+    ref = onys.precond_inverse_apply(V, lam, mu, v.T).T
+    naive = onys.precond_inverse_apply(U, lam, mu, v.T).T
+    e_fix, e_naive = relerr(z, ref), relerr(naive, ref)
+    assert np.abs(G - np.eye(ell)).max() > 1e-8          # the defect is there
+    assert e_fix <= 1e-9, (e_fix, e_naive)
+    assert e_naive > 10 * e_fix, (e_fix, e_naive)
+
+
+def test_mixed_pcg_with_lambda_ratio_below_fp32_orthogonality(ny):
+    # (lambda_ell + mu) / lambda_1 ~ 1e-7 sits below the FP32 defect ||U^T U - I||
+    # (~ 1e-7 sqrt(ell)); with the orthonormalised apply the mixed solve keeps
+    # the FP64 iteration count.
+    m, n, ell, mu = 20000, 4096, 1024, 1e-4
+    X = wl.ridge_X(m, n, seed=61)
+    b = wl.rhs(n, seed=61)
+    op = ny.gram_operator(T(X))
+    Om = T(wl.omega(n, ell, 61))
+    fm = ny.nys_sketch(op, ell, omega=Om, precision=ny.NYS_PREC_MIXED)
+    f64 = ny.nys_sketch(op, ell, omega=Om)
+    lam = f64.lam().cpu().numpy()
+    assert (lam[-1] + mu) / lam[0] < 1e-6
     _, r64, _ = ny.pcg_solve(op, f64, mu, T(b), tol=1e-8)
     _, rm, _ = ny.pcg_solve(op, fm, mu, T(b), tol=1e-8, precision=ny.NYS_PREC_MIXED)
     assert r64[0].status == ny.NYS_OK and rm[0].status == ny.NYS_OK, (r64, rm)
