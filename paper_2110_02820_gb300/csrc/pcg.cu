@@ -416,8 +416,11 @@ constexpr int MU_LC = 256;   // columns of U per staged chunk of the z pass
 // wpart[bx][l][q] = sum over this block's row tiles of U[i][l] r[s0 + q][i]
 template <typename T, typename TU>
 __global__ void __launch_bounds__(PC_THREADS)
-mutr_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, T* __restrict__ wpart) {
+mutr_kernel(PcgArgs<T, TU> a, T* __restrict__ wpart_all) {
   constexpr int KM = MuGroup<T>::KM;
+  const int64_t s0 = (int64_t)blockIdx.z * KM;
+  const int ks = (int)((a.nsys - s0 < KM) ? a.nsys - s0 : KM);
+  T* wpart = wpart_all + (int64_t)blockIdx.z * gridDim.x * a.ell * KM;
   __shared__ __align__(16) T rs[MU_TR][KM];
   const int64_t l = (int64_t)blockIdx.y * PC_THREADS + threadIdx.x;
   T acc[KM];
@@ -446,9 +449,11 @@ mutr_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, T* __restrict__ wpart) {
 
 // w'[s0 + q][l] = ((lam_ell + mu) / (lam_l + mu) - 1) sum_b wpart[b][l][q]
 template <typename T, typename TU>
-__global__ void mw_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, const T* __restrict__ wpart,
-                          int nb) {
+__global__ void mw_kernel(PcgArgs<T, TU> a, const T* __restrict__ wpart_all, int nb) {
   constexpr int KM = MuGroup<T>::KM;
+  const int64_t s0 = (int64_t)blockIdx.y * KM;
+  const int ks = (int)((a.nsys - s0 < KM) ? a.nsys - s0 : KM);
+  const T* wpart = wpart_all + (int64_t)blockIdx.y * nb * a.ell * KM;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.ell * KM) return;
   const int64_t l = e / KM;
@@ -469,10 +474,12 @@ __global__ void mw_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, const T* __restr
 
 // z[s0 + q] = r + U w'[s0 + q] (one thread per row, w' staged in chunks of
 // MU_LC columns), r^T z partials into dpart[s][blockIdx.x].
-template <typename T, typename TU>
+template <typename T, typename TU, int VE>
 __global__ void __launch_bounds__(PC_THREADS)
-mz_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, int setup) {
+mz_kernel(PcgArgs<T, TU> a, int setup) {
   constexpr int KM = MuGroup<T>::KM;
+  const int64_t s0 = (int64_t)blockIdx.y * KM;
+  const int ks = (int)((a.nsys - s0 < KM) ? a.nsys - s0 : KM);
   __shared__ __align__(16) T ws[MU_LC][KM];
   __shared__ double red[PC_WARPS][KM];
   __shared__ int act[KM];
@@ -497,10 +504,13 @@ mz_kernel(PcgArgs<T, TU> a, int64_t s0, int ks, int setup) {
       __syncthreads();
       if (i < a.n) {
         const TU* urow = a.U + i * a.ell + c0;
-        for (int c = 0; c < lc; ++c) {
-          const T u = (T)urow[c];
+        // VE consecutive U entries per load (16 bytes when the rows allow it)
+        for (int c = 0; c < lc; c += VE) {
+          const UVec<TU, VE> u = load_uvec<TU, VE>(urow + c);
 #pragma unroll
-          for (int q = 0; q < KM; ++q) acc[q] = fma(u, ws[c][q], acc[q]);
+          for (int k = 0; k < VE; ++k)
+#pragma unroll
+            for (int q = 0; q < KM; ++q) acc[q] = fma((T)u.e[k], ws[c + k][q], acc[q]);
         }
       }
     }
@@ -620,7 +630,7 @@ struct PcgLaunch {
   size_t usm, zsm;
   dim3 g_u, g_w, g_d;
   // shared-U passes for many systems (multi): groups of MuGroup<T>::KM systems
-  bool multi = false;
+  bool multi = false, vec_m = false;
   T* mwpart = nullptr;
   int nbu_m = 0, nbz_m = 0;
   int32_t setup(PcgArgs<T, TU>& a, int64_t nsys) {
@@ -643,7 +653,7 @@ struct PcgLaunch {
   // Multi-system mode: the U passes run per group of systems.  `wpart` must
   // hold multi_wpart_elems(a) values of T.
   static size_t multi_wpart_elems(const PcgArgs<T, TU>& a) {
-    return (size_t)multi_nbu(a) * a.ell * MuGroup<T>::KM;
+    return (size_t)cdiv(a.nsys, MuGroup<T>::KM) * multi_nbu(a) * a.ell * MuGroup<T>::KM;
   }
   static int multi_nbu(const PcgArgs<T, TU>& a) {
     const int64_t t = cdiv(a.n, MU_TR);
@@ -653,6 +663,9 @@ struct PcgLaunch {
   void enable_multi(const PcgArgs<T, TU>& a, T* wpart) {
     multi = true;
     mwpart = wpart;
+    // 16-byte loads of U in the z pass: rows of whole vectors, aligned base
+    constexpr int VE = 16 / sizeof(TU);
+    vec_m = (a.ell % VE == 0) && (((uintptr_t)a.U & 15u) == 0);
     nbu_m = multi_nbu(a);
     const int64_t t = cdiv(a.n, PC_THREADS);
     nbz_m = (int)(t < a.npart ? t : a.npart);
@@ -667,15 +680,13 @@ struct PcgLaunch {
       wreduce_kernel<T, TU><<<dim3(1, (unsigned)a.nsys), PC_THREADS, 0, s>>>(b, do_update);
       count_launch();
       constexpr int KM = MuGroup<T>::KM;
-      for (int64_t s0 = 0; s0 < a.nsys; s0 += KM) {
-        const int ks = (int)((a.nsys - s0 < KM) ? a.nsys - s0 : KM);
-        mutr_kernel<T, TU><<<dim3((unsigned)nbu_m, (unsigned)cdiv(a.ell, PC_THREADS)),
-                             PC_THREADS, 0, s>>>(a, s0, ks, mwpart);
-        count_launch();
-        mw_kernel<T, TU><<<(unsigned)cdiv(a.ell * KM, 256), 256, 0, s>>>(a, s0, ks, mwpart,
-                                                                         nbu_m);
-        count_launch();
-      }
+      const unsigned groups = (unsigned)cdiv(a.nsys, KM);
+      mutr_kernel<T, TU><<<dim3((unsigned)nbu_m, (unsigned)cdiv(a.ell, PC_THREADS), groups),
+                           PC_THREADS, 0, s>>>(a, mwpart);
+      count_launch();
+      mw_kernel<T, TU><<<dim3((unsigned)cdiv(a.ell * KM, 256), groups), 256, 0, s>>>(a, mwpart,
+                                                                                    nbu_m);
+      count_launch();
       if (a.E) {
         wcorr_kernel<T, TU><<<dim3((unsigned)cdiv(a.ell, PC_WARPS), (unsigned)a.nsys), PC_THREADS,
                               0, s>>>(a);
@@ -699,11 +710,12 @@ struct PcgLaunch {
     constexpr int VE = 16 / sizeof(TU);
     if (multi) {
       constexpr int KM = MuGroup<T>::KM;
-      for (int64_t s0 = 0; s0 < a.nsys; s0 += KM) {
-        const int ks = (int)((a.nsys - s0 < KM) ? a.nsys - s0 : KM);
-        mz_kernel<T, TU><<<(unsigned)nbz_m, PC_THREADS, 0, s>>>(a, s0, ks, setup_flag);
-        count_launch();
-      }
+      const dim3 gz((unsigned)nbz_m, (unsigned)cdiv(a.nsys, KM));
+      if (vec_m)
+        mz_kernel<T, TU, 16 / sizeof(TU)><<<gz, PC_THREADS, 0, s>>>(a, setup_flag);
+      else
+        mz_kernel<T, TU, 1><<<gz, PC_THREADS, 0, s>>>(a, setup_flag);
+      count_launch();
       mrz_kernel<T, TU><<<(unsigned)a.nsys, PC_THREADS, 0, s>>>(a, nbz_m, setup_flag);
       count_launch();
       return;
