@@ -67,6 +67,11 @@ def parse():
     ap.add_argument("--cols", type=int, default=1024)
     ap.add_argument("--nrhs", type=int, default=4,
                     help="block workload: right-hand sides of the one shifted system")
+    ap.add_argument("--block-ell", type=int, default=1024,
+                    help="block workload: sketch size of the preconditioner")
+    ap.add_argument("--matvec-mode", type=int, default=1, choices=[1, 2],
+                    help="--matvec-only: 1 the FP32 product, 2 the FP64-accurate residual "
+                         "product (double-FP32 for the ridge and Gaussian operators)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="non-default workloads: multiply the number of points by this factor")
     return ap.parse_args()
@@ -570,7 +575,7 @@ def run_workload(args):
     elif args.workload == "block":
         # block Nystrom PCG: nrhs right-hand sides of one shifted Gaussian-kernel
         # system, against the same systems solved as independent recurrences
-        n, d, ell, nrhs = int(50000 * args.scale), 16, 1024, args.nrhs
+        n, d, ell, nrhs = int(50000 * args.scale), 16, args.block_ell, args.nrhs
         P = wl.gmm_points(n, d, seed=0)
         sigma = wl.median_distance(P, seed=0)
         op = ny.rbf_operator(T(P), sigma)
@@ -706,13 +711,20 @@ def run_matvec_only(args):
         op = ny.rbf_operator(torch.tensor(P, device=dev), wl.median_distance(P, SEED))
         v = torch.tensor(wl.rhs(n, SEED), device=dev)
         mu, what = 1e-6 * n, f"Gaussian matvec n={n} d=32"
+    mode = args.matvec_mode
     for _ in range(args.warmup):
-        ny.nys_op_matvec(op, mu, v, mode=1)
-    ny.timing_start(max(args.steps, 1))
-    for _ in range(args.steps):
-        y = ny.nys_op_matvec(op, mu, v, mode=1)
-    ms, cnt = ny.timing_stop()
-    print(json.dumps({"matvec_only": what, "ms_per_matvec": ms / max(cnt, 1), "timed": cnt,
+        ny.nys_op_matvec(op, mu, v, mode=mode)
+    if mode == 1:
+        ny.timing_start(max(args.steps, 1))
+        for _ in range(args.steps):
+            y = ny.nys_op_matvec(op, mu, v, mode=mode)
+        ms, cnt = ny.timing_stop()
+        ms_per = ms / max(cnt, 1)
+    else:
+        # the residual product is not among the event-timed FP32 products
+        ms_per, y = _events_ms(lambda: ny.nys_op_matvec(op, mu, v, mode=mode), args.steps)
+        cnt = args.steps
+    print(json.dumps({"matvec_only": what, "mode": mode, "ms_per_matvec": ms_per, "timed": cnt,
                       "checksum": float(y.abs().sum())}), flush=True)
 
 

@@ -100,4 +100,39 @@ __device__ __forceinline__ bool last_block_arrived(unsigned int* counter,
 template <typename T>
 struct TypeName;
 
+// Bounded grid barrier for a cooperative launch.  Returns false (and sets
+// *status = NYS_ERR_TIMEOUT) if the wait did not end within the spin limit
+// or another block already failed; the caller then returns.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* status) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = gen;
+    volatile int* vstat = status;
+    unsigned int g = *vgen;
+    __threadfence();
+    unsigned int nb = gridDim.x;
+    if (atomicAdd(count, 1u) == nb - 1) {
+      *count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (*vstat != 0) { ok = 0; break; }
+        if (++spins > (1ll << 26)) {  // ~ seconds: far beyond any legal wait
+          atomicCAS(status, 0, (int)NYS_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 }  // namespace nys
