@@ -152,7 +152,10 @@ typedef struct nys_pcg_opts {
   double tol;                 /* stop when ||r||_2 <= tol ||b||_2 (default 1e-8) */
   int32_t maxit;              /* iteration cap per system (default 500); in mixed precision
                                  the cap on a system's inner iterations summed over all
-                                 refinement steps */
+                                 refinement steps.  Mixed precision also ends a system with
+                                 NYS_ERR_MAXIT when, with FP64-accurate residuals, its true
+                                 residual fails to halve over two consecutive inner solves
+                                 (kappa times the FP32 product error is then near 1) */
   int32_t precision;          /* nys_precision */
   double inner_tol;           /* mixed: relative tolerance of each inner solve (default 1e-4) */
   int32_t max_refine;         /* mixed: cap on outer refinement steps (default 20) */

@@ -121,33 +121,37 @@ __global__ void __launch_bounds__(1024)
 chol_coop_kernel(double* M, int64_t ell, int* info, unsigned int* bar, int* bstat) {
   __shared__ double D[CH_NB][CH_NB + 1];
   __shared__ double Pi[CH_NB][33], Pj[CH_NB][33];
-  __shared__ int bad;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   volatile int* vinfo = info;
   for (int64_t k = 0; k < ell; k += CH_NB) {
     const int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
-    // ---- diagonal block (block 0)
-    if (blockIdx.x == 0) {
-      if (tx == 0 && ty == 0) bad = 0;
-      if (ty < nb && tx < nb) D[ty][tx] = M[(k + ty) * ell + k + tx];
-      __syncthreads();
+    // ---- diagonal block: one warp of block 0 (warp-level syncs only)
+    if (blockIdx.x == 0 && ty == 0) {
+      for (int r = 0; r < nb; ++r) D[r][tx] = (tx < nb) ? M[(k + r) * ell + k + tx] : 0.0;
+      __syncwarp();
+      int badw = 0;
       for (int j = 0; j < nb; ++j) {
-        if (tx == 0 && ty == 0) {
-          const double d = D[j][j];
-          if (!(d > 0.0) || !isfinite(d)) bad = (int)(k + j + 1);
-          else D[j][j] = sqrt(d);
+        const double d = D[j][j];
+        if (!(d > 0.0) || !isfinite(d)) {
+          badw = (int)(k + j + 1);
+          break;
         }
-        __syncthreads();
-        if (bad) break;
-        if (ty == 0 && tx > j && tx < nb) D[j][tx] = D[j][tx] / D[j][j];
-        __syncthreads();
-        if (ty > j && tx >= ty && tx < nb) D[ty][tx] -= D[j][ty] * D[j][tx];
-        __syncthreads();
+        const double piv = sqrt(d);
+        __syncwarp();
+        // row j of the factor; lane r > j then updates row r of the trailing block
+        if (tx > j && tx < nb) D[j][tx] = D[j][tx] / piv;
+        if (tx == j) D[j][j] = piv;
+        __syncwarp();
+        if (tx > j && tx < nb) {
+          const double cjr = D[j][tx];
+          for (int c = tx; c < nb; ++c) D[tx][c] -= cjr * D[j][c];
+        }
+        __syncwarp();
       }
-      if (bad) {
-        if (tx == 0 && ty == 0) atomicCAS(info, 0, bad);
-      } else if (ty < nb && tx < nb) {
-        M[(k + ty) * ell + k + tx] = (tx >= ty) ? D[ty][tx] : 0.0;
+      if (badw) {
+        if (tx == 0) atomicCAS(info, 0, badw);
+      } else if (tx < nb) {
+        for (int r = 0; r < nb; ++r) M[(k + r) * ell + k + tx] = (tx >= r) ? D[r][tx] : 0.0;
       }
     }
     if (!grid_barrier(bar, bar + 1, bstat)) {
@@ -222,8 +226,8 @@ int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
     NYS_TRY(sc.get(&bar, 4));
     NYS_CUDA_TRY(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned int), s));
     int* bstat = reinterpret_cast<int*>(bar + 2);
-    const int64_t want = std::max<int64_t>(1, cdiv(ell, 32));
-    int blocks = (int)std::min<int64_t>((int64_t)num_sms(), want);
+    // one block per SM: the trailing tiles of a step spread over the whole GPU
+    int blocks = num_sms();
     void* args[] = {&M, &ell, &d_info, &bar, &bstat};
     NYS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)chol_coop_kernel, dim3(blocks), dim3(1024),
                                              args, 0, s));

@@ -960,6 +960,13 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   NYS_CUDA_TRY(cudaMemcpyAsync(bn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
   std::vector<int> active(nsys, 1), total_it(nsys, 0), outer(nsys, 0), stt(nsys, NYS_ERR_MAXIT);
   std::vector<double> rel(nsys, 1.0), prev(nsys, 0.0);
+  // Stagnation: with FP64-accurate residuals, a system whose true residual
+  // fails to halve over two consecutive inner solves has reached what an FP32
+  // inner solve can refine (kappa eps_32 >~ 1); it stops with NYS_ERR_MAXIT
+  // instead of spending the rest of its budget.
+  std::vector<int> stag(nsys, 0);
+  std::vector<double> before(nsys, 0.0);
+  bool retaken = false;
   const unsigned gb = (unsigned)cdiv(n, 256) > 1024 ? 1024 : (unsigned)cdiv(n, 256);
   // The refinement residual starts in double-FP32 arithmetic (kernel and ridge
   // operators, ~1e-13 relative per product).  Its floor relative to ||b|| is
@@ -1037,21 +1044,28 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       } else if (!std::isfinite(rel[q])) {
         active[q] = 0;
         stt[q] = NYS_ERR_BREAKDOWN;
-      } else if (total_it[q] >= maxit) {
-        active[q] = 0;  // its iteration budget is spent: NYS_ERR_MAXIT
-      } else if (k < max_refine) {
-        // maxit bounds a system's inner iterations over all refinements
-        todo.push_back(q);
+      } else {
+        if (exact && !retaken && outer[q] > 0)
+          stag[q] = (rel[q] > 0.5 * before[q]) ? stag[q] + 1 : 0;
+        if (stag[q] >= 2 || total_it[q] >= maxit) {
+          active[q] = 0;  // stagnated or budget spent: NYS_ERR_MAXIT
+        } else if (k < max_refine) {
+          // maxit bounds a system's inner iterations over all refinements
+          todo.push_back(q);
+        }
       }
     }
     if (todo.empty()) break;
     bool stalled = false;
     for (int64_t t : todo) stalled |= k > 0 && rel[t] > 0.5 * prev[t];
     for (int64_t q = 0; q < nsys; ++q) prev[q] = rel[q];
+    retaken = false;
     if (stalled && may_escalate && !exact) {
       exact = true;
+      retaken = true;
       continue;  // the same iterate, its residual retaken in FP64
     }
+    for (int64_t t : todo) before[t] = rel[t];
     // inner solves for the systems still active (batched over them)
     int64_t na = (int64_t)todo.size();
     std::vector<double> mua(na);

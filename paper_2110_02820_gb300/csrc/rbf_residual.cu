@@ -20,6 +20,7 @@
 // (and their norm terms) in shared memory, up to RP_Q right-hand sides per
 // launch in registers.
 
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -181,7 +182,8 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
                     double inv_s3, int kind, int64_t nvec, int shift,
                     const double* __restrict__ mus, double mu0, const double* __restrict__ v,
                     double* __restrict__ y, const int* __restrict__ skip,
-                    const __grid_constant__ Exp64Consts ec) {
+                    const __grid_constant__ Exp64Consts ec, int64_t jchunk,
+                    double* __restrict__ ypart) {
   if (skip && *skip) return;
   __shared__ __align__(16) float xs[RP_BJ][DMAX];
   __shared__ double njs[EXACT ? RP_BJ : 1];
@@ -240,7 +242,10 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
     for (int t = 0; t < RP_Q * ROWS; ++t)
       gacc[t][threadIdx.x] = make_float2(0.f, 0.f);
   }
-  for (int64_t j0 = 0; j0 < n; j0 += RP_BJ) {
+  // this block's slice of the points (grid.z splits them; partial sums go to ypart)
+  const int64_t jb = (int64_t)blockIdx.z * jchunk;
+  const int64_t je = (n < jb + jchunk) ? n : jb + jchunk;
+  for (int64_t j0 = jb; j0 < je; j0 += RP_BJ) {
     if (!EXACT) {
 #pragma unroll
       for (int r = 0; r < ROWS; ++r)
@@ -253,10 +258,10 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
     __syncthreads();
     for (int e = threadIdx.x; e < RP_BJ * DMAX; e += RP_THREADS) {
       const int jj = e / DMAX, k = e - jj * DMAX;
-      xs[jj][k] = (j0 + jj < n && k < d) ? pts[(j0 + jj) * ld + k] : 0.f;
+      xs[jj][k] = (j0 + jj < je && k < d) ? pts[(j0 + jj) * ld + k] : 0.f;
     }
     for (int jj = threadIdx.x; jj < RP_BJ; jj += RP_THREADS) {
-      const double bj = j0 + jj < n ? neg_inv_2s2 * nrm[j0 + jj] : 0.0;
+      const double bj = j0 + jj < je ? neg_inv_2s2 * nrm[j0 + jj] : 0.0;
       if (EXACT) {
         njs[EXACT ? jj : 0] = bj;
       } else {
@@ -265,7 +270,7 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
       }
 #pragma unroll
       for (int q = 0; q < RP_Q; ++q) {
-        const double vv = (q < nq && j0 + jj < n) ? v[(q0 + q) * n + j0 + jj] : 0.0;
+        const double vv = (q < nq && j0 + jj < je) ? v[(q0 + q) * n + j0 + jj] : 0.0;
         if (EXACT) {
           vjd[EXACT ? q : 0][jj] = vv;
         } else {
@@ -275,7 +280,7 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
       }
     }
     __syncthreads();
-    const int jn = (int)((n - j0 < RP_BJ) ? n - j0 : RP_BJ);
+    const int jn = (int)((je - j0 < RP_BJ) ? je - j0 : RP_BJ);
     for (int jj = 0; jj < jn; ++jj) {
       // inner products <t_i, x_j> in double-float (exact FP32 products)
       float dh[ROWS], dl[ROWS];
@@ -371,10 +376,29 @@ rbf_products_kernel(const float* __restrict__ tg, int64_t nt, int64_t ldt,
           const float2 g = gacc[q * ROWS + r][threadIdx.x];
           out = (double)g.x + (double)g.y;
         }
-        if (shift) out = fma(shift == 2 ? mus[g] : mu0, v[g * n + i], out);
-        y[g * nt + i] = out;
+        if (ypart) {
+          ypart[((int64_t)blockIdx.z * nvec + g) * nt + i] = out;
+        } else {
+          if (shift) out = fma(shift == 2 ? mus[g] : mu0, v[g * n + i], out);
+          y[g * nt + i] = out;
+        }
       }
   }
+}
+
+// y[g][i] = sum_z ypart[z][g][i] (fixed order) + shift
+__global__ void products_sum_kernel(const double* __restrict__ ypart, int nz, int64_t nt,
+                                    int64_t nvec, int shift, const double* __restrict__ mus,
+                                    double mu0, const double* __restrict__ v, int64_t n,
+                                    double* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nvec * nt) return;
+  const int64_t g = e / nt, i = e - g * nt;
+  double out = 0.0;
+  for (int z = 0; z < nz; ++z) out += ypart[(int64_t)z * nvec * nt + e];
+  if (shift) out = fma(shift == 2 ? mus[g] : mu0, v[g * n + i], out);
+  y[e] = out;
 }
 
 static Exp64Consts exp64_consts() {
@@ -415,10 +439,22 @@ int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_
 namespace {
 
 template <int DMAX, int ROWS, int Q, bool EXACT>
-void products_go(const float* tg, int64_t nt, int64_t ldt, const double* nrm_t, const float* pts,
-                 int64_t n, int64_t ldp, const double* nrm, int64_t d, double a, double b, int kind,
-                 int shift, const double* d_mu, double mu0, int64_t nvec, const double* v,
-                 double* y, const int* skip, const Exp64Consts& ec, cudaStream_t s) {
+int32_t products_go(const float* tg, int64_t nt, int64_t ldt, const double* nrm_t,
+                    const float* pts, int64_t n, int64_t ldp, const double* nrm, int64_t d,
+                    double a, double b, int kind, int shift, const double* d_mu, double mu0,
+                    int64_t nvec, const double* v, double* y, const int* skip,
+                    const Exp64Consts& ec, cudaStream_t s) {
+  // split the points over grid.z until the grid has ~4 blocks per SM, each
+  // slice at least 4 point tiles; partial sums are added in a fixed order
+  const int64_t bx = cdiv(nt, ROWS * RP_THREADS), by = cdiv(nvec, Q);
+  const int64_t target = 4 * (int64_t)num_sms();
+  int64_t nz = (bx * by >= target) ? 1 : cdiv(target, bx * by);
+  nz = std::min<int64_t>(nz, std::max<int64_t>(1, n / (4 * RP_BJ)));
+  const int64_t jchunk = cdiv(cdiv(n, nz), RP_BJ) * RP_BJ;
+  nz = cdiv(n, jchunk);
+  Scratch sc(s);
+  double* ypart = nullptr;
+  if (nz > 1) NYS_TRY(sc.get(&ypart, (size_t)nz * nvec * nt));
   const int dyn = EXACT ? 0 : Q * ROWS * RP_THREADS * (int)sizeof(float2);
   static bool attr = false;
   if (!attr) {
@@ -427,10 +463,17 @@ void products_go(const float* tg, int64_t nt, int64_t ldt, const double* nrm_t, 
     attr = true;
   }
   rbf_products_kernel<DMAX, ROWS, Q, EXACT>
-      <<<dim3((unsigned)cdiv(nt, ROWS * RP_THREADS), (unsigned)cdiv(nvec, Q)), RP_THREADS, dyn, s>>>(
+      <<<dim3((unsigned)bx, (unsigned)by, (unsigned)nz), RP_THREADS, dyn, s>>>(
           tg, nt, ldt, nrm_t, pts, n, d, ldp, nrm, a, b, kind, nvec, shift, d_mu, mu0, v, y, skip,
-          ec);
+          ec, jchunk, ypart);
   count_launch();
+  if (ypart) {
+    products_sum_kernel<<<(unsigned)cdiv(nvec * nt, 256), 256, 0, s>>>(
+        ypart, (int)nz, nt, nvec, shift, d_mu, mu0, v, n, y, skip);
+    count_launch();
+  }
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
 }
 
 template <bool EXACT>
@@ -441,9 +484,9 @@ int32_t products_launch(const float* tg, int64_t nt, int64_t ldt, const double* 
                         cudaStream_t s) {
   const double a = -1.0 / (2.0 * sigma * sigma), b = 1.0 / (sigma * sigma * sigma);
   const Exp64Consts ec = exp64_consts();
-#define NYS_PRODUCTS(DM, R, Q)                                                                  \
-  products_go<DM, R, Q, EXACT>(tg, nt, ldt, nrm_t, pts, n, ldp, nrm, d, a, b, kind, shift, d_mu, \
-                               mu0, nvec, v, y, skip, ec, s)
+#define NYS_PRODUCTS(DM, R, Q)                                                             \
+  NYS_TRY((products_go<DM, R, Q, EXACT>(tg, nt, ldt, nrm_t, pts, n, ldp, nrm, d, a, b, kind, \
+                                        shift, d_mu, mu0, nvec, v, y, skip, ec, s)))
   if (nvec <= 8) {
     if (d <= 16) NYS_PRODUCTS(16, 2, 8);
     else if (d <= 32) NYS_PRODUCTS(32, 2, 8);
