@@ -58,8 +58,7 @@ struct Scratch {
 
 // In-place upper Cholesky M = C^T C of a symmetric ell x ell matrix (upper
 // triangle read); on return the strict lower triangle is zero.  *d_info
-// (device int) is 0 on success, k+1 if the k-th pivot was not positive, -1
-// if a grid-barrier wait of the one-launch factorisation expired.
+// (device int) is 0 on success, k+1 if the k-th pivot was not positive.
 int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s);
 // X = C^{-1} for upper-triangular C (ell x ell); X upper triangular.
 int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s);

@@ -21,37 +21,34 @@ namespace nys {
 constexpr int CH_NB = 32;
 
 // Factor the diagonal block D = M[k:k+nb, k:k+nb] in place: D = C_kk^T C_kk.
+// One warp: lane r owns row r of the block in shared memory; the steps need
+// only warp-level syncs.
 __global__ void chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb, int* info) {
   if (*info != 0) return;
   __shared__ double D[CH_NB][CH_NB + 1];
-  __shared__ int bad;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
-  if (tx == 0 && ty == 0) bad = 0;
-  if (ty < nb && tx < nb) D[ty][tx] = M[(k + ty) * ell + k + tx];
-  __syncthreads();
+  const int tx = threadIdx.x;  // 32 threads
+  for (int r = 0; r < nb; ++r) D[r][tx] = (tx < nb) ? M[(k + r) * ell + k + tx] : 0.0;
+  __syncwarp();
   for (int j = 0; j < nb; ++j) {
-    if (tx == 0 && ty == 0) {
-      double d = D[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = (int)(k + j + 1);
-      } else {
-        D[j][j] = sqrt(d);
-      }
+    const double d = D[j][j];
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (tx == 0) atomicCAS(info, 0, (int)(k + j + 1));
+      return;
     }
-    __syncthreads();
-    if (bad) break;
-    // row j right of the diagonal
-    if (ty == 0 && tx > j && tx < nb) D[j][tx] = D[j][tx] / D[j][j];
-    __syncthreads();
-    // trailing update of the upper triangle r <= c, r, c > j
-    if (ty > j && tx >= ty && tx < nb) D[ty][tx] -= D[j][ty] * D[j][tx];
-    __syncthreads();
+    const double piv = sqrt(d);
+    __syncwarp();
+    // row j of the factor, then lane r > j updates row r of the trailing block
+    if (tx > j && tx < nb) D[j][tx] = D[j][tx] / piv;
+    if (tx == j) D[j][j] = piv;
+    __syncwarp();
+    if (tx > j && tx < nb) {
+      const double cjr = D[j][tx];
+      for (int c = tx; c < nb; ++c) D[tx][c] -= cjr * D[j][c];
+    }
+    __syncwarp();
   }
-  if (bad) {
-    if (tx == 0 && ty == 0) atomicCAS(info, 0, bad);
-    return;
-  }
-  if (ty < nb && tx < nb) M[(k + ty) * ell + k + tx] = (tx >= ty) ? D[ty][tx] : 0.0;
+  if (tx < nb)
+    for (int r = 0; r < nb; ++r) M[(k + r) * ell + k + tx] = (tx >= r) ? D[r][tx] : 0.0;
 }
 
 // Row panel: C[k:k+nb, c] = C_kk^{-T} M[k:k+nb, c] for c >= k + nb (forward
@@ -110,133 +107,11 @@ __global__ void zero_lower_kernel(double* M, int64_t ell) {
   if (j < i) M[e] = 0.0;
 }
 
-// The whole blocked factorisation in one cooperative launch (one block of
-// 32 x 32 threads per SM): for each 32-column step, block 0 factors the
-// diagonal block, every block then solves its share of the row panel (one
-// warp per column), then updates its share of the trailing upper-triangle
-// tiles, with a bounded grid barrier between the phases.  Three barriers per
-// step replace three kernel launches.  *info as chol_upper; -1 if a barrier
-// wait expired.
-__global__ void __launch_bounds__(1024)
-chol_coop_kernel(double* M, int64_t ell, int* info, unsigned int* bar, int* bstat) {
-  __shared__ double D[CH_NB][CH_NB + 1];
-  __shared__ double Pi[CH_NB][33], Pj[CH_NB][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  volatile int* vinfo = info;
-  for (int64_t k = 0; k < ell; k += CH_NB) {
-    const int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
-    // ---- diagonal block: one warp of block 0 (warp-level syncs only)
-    if (blockIdx.x == 0 && ty == 0) {
-      for (int r = 0; r < nb; ++r) D[r][tx] = (tx < nb) ? M[(k + r) * ell + k + tx] : 0.0;
-      __syncwarp();
-      int badw = 0;
-      for (int j = 0; j < nb; ++j) {
-        const double d = D[j][j];
-        if (!(d > 0.0) || !isfinite(d)) {
-          badw = (int)(k + j + 1);
-          break;
-        }
-        const double piv = sqrt(d);
-        __syncwarp();
-        // row j of the factor; lane r > j then updates row r of the trailing block
-        if (tx > j && tx < nb) D[j][tx] = D[j][tx] / piv;
-        if (tx == j) D[j][j] = piv;
-        __syncwarp();
-        if (tx > j && tx < nb) {
-          const double cjr = D[j][tx];
-          for (int c = tx; c < nb; ++c) D[tx][c] -= cjr * D[j][c];
-        }
-        __syncwarp();
-      }
-      if (badw) {
-        if (tx == 0) atomicCAS(info, 0, badw);
-      } else if (tx < nb) {
-        for (int r = 0; r < nb; ++r) M[(k + r) * ell + k + tx] = (tx >= r) ? D[r][tx] : 0.0;
-      }
-    }
-    if (!grid_barrier(bar, bar + 1, bstat)) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(info, 0, -1);
-      return;
-    }
-    if (*vinfo != 0) return;
-    const int64_t rest = ell - k - nb;
-    if (rest > 0) {
-      // ---- row panel: C[k:k+nb, c] = C_kk^{-T} M[k:k+nb, c], one warp per column
-      for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        const int r = e / nb, c = e - r * nb;
-        D[r][c] = M[(k + r) * ell + k + c];
-      }
-      __syncthreads();
-      for (int64_t c = k + nb + (int64_t)blockIdx.x * 32 + ty; c < ell;
-           c += (int64_t)gridDim.x * 32) {
-        double m = (tx < nb) ? M[(k + tx) * ell + c] : 0.0;
-        for (int r = 0; r < nb; ++r) {
-          double xr = (tx == r) ? m / D[r][r] : 0.0;
-          xr = __shfl_sync(0xffffffffu, xr, r);
-          if (tx == r) m = xr;
-          else if (tx > r && tx < nb) m -= D[r][tx] * xr;
-        }
-        if (tx < nb) M[(k + tx) * ell + c] = m;
-      }
-      if (!grid_barrier(bar, bar + 1, bstat)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(info, 0, -1);
-        return;
-      }
-      // ---- trailing update of the upper-triangle tiles (ti <= tj)
-      const int64_t base = k + nb, T = (rest + 31) / 32;
-      for (int64_t t = blockIdx.x; t < T * T; t += gridDim.x) {
-        const int64_t bi = t / T, bj = t - bi * T;
-        if (bj < bi) continue;
-        const int64_t ti = base + bi * 32, tj = base + bj * 32;
-        __syncthreads();
-        if (ty < nb) {
-          Pi[ty][tx] = (ti + tx < ell) ? M[(k + ty) * ell + ti + tx] : 0.0;
-          Pj[ty][tx] = (tj + tx < ell) ? M[(k + ty) * ell + tj + tx] : 0.0;
-        }
-        __syncthreads();
-        const int64_t i = ti + ty, j = tj + tx;
-        if (i < ell && j < ell && j >= i) {
-          double acc = 0.0;
-          for (int r = 0; r < nb; ++r) acc += Pi[r][ty] * Pj[r][tx];
-          M[i * ell + j] -= acc;
-        }
-      }
-      if (!grid_barrier(bar, bar + 1, bstat)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(info, 0, -1);
-        return;
-      }
-    }
-  }
-  // zero the strict lower triangle
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ell * ell;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / ell, j = e - i * ell;
-    if (j < i) M[e] = 0.0;
-  }
-}
-
 int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
   NYS_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
-  // one block per SM (cooperative: every block must be resident)
-  int per_sm = 0;
-  NYS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_coop_kernel, 1024, 0));
-  if (per_sm >= 1) {
-    Scratch sc(s);
-    unsigned int* bar;
-    NYS_TRY(sc.get(&bar, 4));
-    NYS_CUDA_TRY(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned int), s));
-    int* bstat = reinterpret_cast<int*>(bar + 2);
-    // one block per SM: the trailing tiles of a step spread over the whole GPU
-    int blocks = num_sms();
-    void* args[] = {&M, &ell, &d_info, &bar, &bstat};
-    NYS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)chol_coop_kernel, dim3(blocks), dim3(1024),
-                                             args, 0, s));
-    count_launch();
-    return NYS_OK;
-  }
   for (int64_t k = 0; k < ell; k += CH_NB) {
     int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
-    chol_diag_kernel<<<1, dim3(32, 32), 0, s>>>(M, ell, k, nb, d_info); count_launch();
+    chol_diag_kernel<<<1, 32, 0, s>>>(M, ell, k, nb, d_info); count_launch();
     int64_t rest = ell - k - nb;
     if (rest > 0) {
       chol_panel_kernel<<<(unsigned)cdiv(rest, 8), 256, 0, s>>>(M, ell, k, nb, d_info); count_launch();
