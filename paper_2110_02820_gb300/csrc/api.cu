@@ -166,7 +166,6 @@ static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool r
     NYS_TRY(chol_upper(G, ell, info, s));
     int h_info = 0;
     NYS_TRY(read_int(info, &h_info, s));
-    if (h_info < 0) return NYS_ERR_TIMEOUT;
     if (h_info != 0) {
       if (pass > 0) return NYS_ERR_NOT_PSD;
       // shifted CholeskyQR: G + s I with s = 11 (n ell + ell (ell + 1)) u max_i G_ii
@@ -181,7 +180,6 @@ static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool r
       NYS_TRY(add_diag(G, ell, shift, s));
       NYS_TRY(chol_upper(G, ell, info, s));
       NYS_TRY(read_int(info, &h_info, s));
-      if (h_info < 0) return NYS_ERR_TIMEOUT;
       if (h_info != 0) return NYS_ERR_NOT_PSD;
       passes = passes0 + 1;
     }
@@ -285,7 +283,6 @@ static int32_t shifted_core(const T* Q, const T* Y, int64_t n, int64_t ell, bool
     NYS_TRY(chol_upper(M, ell, info, s));                // C^T C = Q^T Y_nu
     int h = 0;
     NYS_TRY(read_int(info, &h, s));
-    if (h < 0) return NYS_ERR_TIMEOUT;
     if (h == 0) break;
     if (esc >= kMaxEscalations) return NYS_ERR_NOT_PSD;
     scale_scalar_kernel<<<1, 1, 0, s>>>(nu, 10.0); count_launch();
