@@ -21,34 +21,37 @@ namespace nys {
 constexpr int CH_NB = 32;
 
 // Factor the diagonal block D = M[k:k+nb, k:k+nb] in place: D = C_kk^T C_kk.
-// One warp: lane r owns row r of the block in shared memory; the steps need
-// only warp-level syncs.
 __global__ void chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb, int* info) {
   if (*info != 0) return;
   __shared__ double D[CH_NB][CH_NB + 1];
-  const int tx = threadIdx.x;  // 32 threads
-  for (int r = 0; r < nb; ++r) D[r][tx] = (tx < nb) ? M[(k + r) * ell + k + tx] : 0.0;
-  __syncwarp();
+  __shared__ int bad;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
+  if (tx == 0 && ty == 0) bad = 0;
+  if (ty < nb && tx < nb) D[ty][tx] = M[(k + ty) * ell + k + tx];
+  __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    const double d = D[j][j];
-    if (!(d > 0.0) || !isfinite(d)) {
-      if (tx == 0) atomicCAS(info, 0, (int)(k + j + 1));
-      return;
+    if (tx == 0 && ty == 0) {
+      double d = D[j][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = (int)(k + j + 1);
+      } else {
+        D[j][j] = sqrt(d);
+      }
     }
-    const double piv = sqrt(d);
-    __syncwarp();
-    // row j of the factor, then lane r > j updates row r of the trailing block
-    if (tx > j && tx < nb) D[j][tx] = D[j][tx] / piv;
-    if (tx == j) D[j][j] = piv;
-    __syncwarp();
-    if (tx > j && tx < nb) {
-      const double cjr = D[j][tx];
-      for (int c = tx; c < nb; ++c) D[tx][c] -= cjr * D[j][c];
-    }
-    __syncwarp();
+    __syncthreads();
+    if (bad) break;
+    // row j right of the diagonal
+    if (ty == 0 && tx > j && tx < nb) D[j][tx] = D[j][tx] / D[j][j];
+    __syncthreads();
+    // trailing update of the upper triangle r <= c, r, c > j
+    if (ty > j && tx >= ty && tx < nb) D[ty][tx] -= D[j][ty] * D[j][tx];
+    __syncthreads();
   }
-  if (tx < nb)
-    for (int r = 0; r < nb; ++r) M[(k + r) * ell + k + tx] = (tx >= r) ? D[r][tx] : 0.0;
+  if (bad) {
+    if (tx == 0 && ty == 0) atomicCAS(info, 0, bad);
+    return;
+  }
+  if (ty < nb && tx < nb) M[(k + ty) * ell + k + tx] = (tx >= ty) ? D[ty][tx] : 0.0;
 }
 
 // Row panel: C[k:k+nb, c] = C_kk^{-T} M[k:k+nb, c] for c >= k + nb (forward
@@ -111,7 +114,7 @@ int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
   NYS_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   for (int64_t k = 0; k < ell; k += CH_NB) {
     int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
-    chol_diag_kernel<<<1, 32, 0, s>>>(M, ell, k, nb, d_info); count_launch();
+    chol_diag_kernel<<<1, dim3(32, 32), 0, s>>>(M, ell, k, nb, d_info); count_launch();
     int64_t rest = ell - k - nb;
     if (rest > 0) {
       chol_panel_kernel<<<(unsigned)cdiv(rest, 8), 256, 0, s>>>(M, ell, k, nb, d_info); count_launch();
