@@ -157,9 +157,7 @@ typedef struct nys_pcg_opts {
                                  residual fails to halve over two consecutive inner solves
                                  (kappa times the FP32 product error is then near 1) */
   int32_t precision;          /* nys_precision */
-  double inner_tol;           /* mixed: relative tolerance of each inner solve (default 1e-4);
-                                 a step whose remaining reduction tol / ||r|| is >= 1e-6 uses
-                                 0.3 tol / ||r|| instead (nys_pcg_solve only) */
+  double inner_tol;           /* mixed: relative tolerance of each inner solve (default 1e-4) */
   int32_t max_refine;         /* mixed: cap on outer refinement steps (default 20) */
   int32_t use_x0;             /* nonzero: x holds the initial guess; zero: start from x = 0 */
   double* residual_history;   /* optional device buffer [nsys][maxit+1] FP64: recurrence

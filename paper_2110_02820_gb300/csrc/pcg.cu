@@ -917,9 +917,6 @@ int32_t pcg_f64(const nys_operator* op, const nys_factor* f, const double* mu, i
   return NYS_OK;
 }
 
-// Smallest inner tolerance the final refinement step may ask of an FP32 solve.
-constexpr double kInnerFloor = 1e-6;
-
 // Mixed precision: FP64 outer loop r = b - (A + mu I) x (FP64-accurate
 // matvec), inner Algorithm 3 on FP32 vectors for the correction.
 int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu, int64_t nsys,
@@ -1082,18 +1079,8 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
     std::vector<double> rr(na);
     int budget = 1;
     for (int64_t q : todo) budget = std::max(budget, maxit - total_it[q]);
-    // The last step aims at tol: when the reduction still needed, tol / ||r||, is
-    // within what an FP32 inner solve reaches (>= kInnerFloor), the inner
-    // tolerance tightens to 0.3 tol / ||r|| (for every system of the batch,
-    // the strictest of them), sparing one more FP64-accurate residual pass.
-    double itol = inner_tol;
-    {
-      double need = inner_tol;
-      for (int64_t q : todo) need = std::min(need, 0.3 * tol / rel[q]);
-      if (need >= kInnerFloor) itol = need;
-    }
     NYS_TRY((run_pcg<float, float>(op, U, f ? f->lam : nullptr, f ? f->ell : 0,
-                                   f ? f->lam_ell : 0.0, Edef, mua.data(), na, v, rf, df, itol,
+                                   f ? f->lam_ell : 0.0, Edef, mua.data(), na, v, rf, df, inner_tol,
                                    budget, 0, (k == 0) ? hist : nullptr, it.data(), st.data(),
                                    rr.data(), s)));
     for (int64_t t = 0; t < na; ++t) {

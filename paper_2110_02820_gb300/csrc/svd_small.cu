@@ -44,8 +44,6 @@ namespace {
 
 constexpr int kMaxSweeps = 30;
 constexpr int kMaxRefine = 8;
-// Rotation threshold of the FP32 sweeps when the FP64 refinement follows.
-constexpr double kJacobiTolRefined = 1e-4;
 constexpr double kOaCap = 1e-2;
 constexpr size_t kBjSmemMax = 200 * 1024;
 
@@ -469,10 +467,6 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, bool
   const double ru = 5.960464477539063e-08;
   double tol = 2.0 * ru * (double)(ellp / 32 + 8);
   if (tol < 32.0 * ru) tol = 32.0 * ru;
-  // With the FP64 refinement to follow, the rotations only need to bring the
-  // columns within its quadratic convergence: the last sweeps before ~1e-6
-  // (about three of thirteen) are left to one more refinement step.
-  if (refine && tol < kJacobiTolRefined) tol = kJacobiTolRefined;
   a.tol = (float)tol;
   a.bar = aux->bar;
   a.rot = aux->rot;
