@@ -21,37 +21,47 @@ namespace nys {
 constexpr int CH_NB = 32;
 
 // Factor the diagonal block D = M[k:k+nb, k:k+nb] in place: D = C_kk^T C_kk.
-__global__ void chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb, int* info) {
+// One warp, registers only: lane c holds column c (rows 0..31); step j
+// broadcasts the pivot and row j by shuffles, and lane c updates rows
+// j < r <= c of its column.  Loops are unrolled so the column stays in
+// registers.
+__global__ void __launch_bounds__(32) chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb,
+                                                       int* info) {
   if (*info != 0) return;
-  __shared__ double D[CH_NB][CH_NB + 1];
-  __shared__ int bad;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
-  if (tx == 0 && ty == 0) bad = 0;
-  if (ty < nb && tx < nb) D[ty][tx] = M[(k + ty) * ell + k + tx];
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (tx == 0 && ty == 0) {
-      double d = D[j][j];
+  const int c = threadIdx.x;
+  double col[CH_NB];
+#pragma unroll
+  for (int r = 0; r < CH_NB; ++r)
+    col[r] = (r < nb && c < nb) ? M[(k + r) * ell + k + c] : (r == c ? 1.0 : 0.0);
+  int bad = 0;
+#pragma unroll
+  for (int j = 0; j < CH_NB; ++j) {
+    if (j < nb && !bad) {
+      const double d = __shfl_sync(0xffffffffu, col[j], j);  // D[j][j] (lane j)
       if (!(d > 0.0) || !isfinite(d)) {
         bad = (int)(k + j + 1);
       } else {
-        D[j][j] = sqrt(d);
+        const double piv = sqrt(d);
+        if (c == j) col[j] = piv;
+        else if (c > j) col[j] = col[j] / piv;             // C[j][c]
+        // C[j][r] for r > j sits in lane r at index j: rows r <= c of this column
+#pragma unroll
+        for (int r = j + 1; r < CH_NB; ++r) {
+          const double cjr = __shfl_sync(0xffffffffu, col[j], r);
+          if (r <= c && c < nb) col[r] -= cjr * col[j];
+        }
       }
     }
-    __syncthreads();
-    if (bad) break;
-    // row j right of the diagonal
-    if (ty == 0 && tx > j && tx < nb) D[j][tx] = D[j][tx] / D[j][j];
-    __syncthreads();
-    // trailing update of the upper triangle r <= c, r, c > j
-    if (ty > j && tx >= ty && tx < nb) D[ty][tx] -= D[j][ty] * D[j][tx];
-    __syncthreads();
   }
   if (bad) {
-    if (tx == 0 && ty == 0) atomicCAS(info, 0, bad);
+    if (c == 0) atomicCAS(info, 0, bad);
     return;
   }
-  if (ty < nb && tx < nb) M[(k + ty) * ell + k + tx] = (tx >= ty) ? D[ty][tx] : 0.0;
+  if (c < nb) {
+#pragma unroll
+    for (int r = 0; r < CH_NB; ++r)
+      if (r < nb) M[(k + r) * ell + k + c] = (c >= r) ? col[r] : 0.0;
+  }
 }
 
 // Row panel: C[k:k+nb, c] = C_kk^{-T} M[k:k+nb, c] for c >= k + nb (forward
@@ -114,7 +124,7 @@ int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
   NYS_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   for (int64_t k = 0; k < ell; k += CH_NB) {
     int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
-    chol_diag_kernel<<<1, dim3(32, 32), 0, s>>>(M, ell, k, nb, d_info); count_launch();
+    chol_diag_kernel<<<1, 32, 0, s>>>(M, ell, k, nb, d_info); count_launch();
     int64_t rest = ell - k - nb;
     if (rest > 0) {
       chol_panel_kernel<<<(unsigned)cdiv(rest, 8), 256, 0, s>>>(M, ell, k, nb, d_info); count_launch();
