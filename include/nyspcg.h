@@ -7,6 +7,7 @@
  *   - nys_sketch           Algorithm 1 (randomized Nystrom approximation)
  *   - nys_sketch_adaptive  Algorithm 5 with Algorithm 4 (adaptive rank)
  *   - nys_precond_apply    Eq. (5.3), the inverse preconditioner P^{-1}
+ *   - nys_sketch_solve     Algorithm 2 (Nystrom sketch-and-solve), the accuracy contrast
  *   - nys_block_pcg        block Nystrom PCG (Sec. 5.2) for many right-hand sides of one mu
  *   - nys_reg_path         regularization path with warm starts and factor reuse (Sec. 6.2)
  *   - pcg_solve            Algorithm 3 (Nystrom PCG), batched over systems,
@@ -147,6 +148,17 @@ int32_t nys_sketch_adaptive(const nys_operator* op, int64_t ell0, int64_t ell_ma
  * of nrhs n-vectors of type `dtype` (may not alias).  Asynchronous. */
 int32_t nys_precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const void* v,
                           void* z, int32_t dtype, void* stream);
+
+/* Algorithm 2 (Nystrom sketch-and-solve, Sec. 4, Eq. (4.1)): solves the
+ * approximated system (U Lam U^T + mu_s I) x_s = b_s directly,
+ *   x_s = U (Lam + mu_s I)^{-1} U^T b_s + (b_s - U U^T b_s) / mu_s,
+ * for s < nrhs.  This is the paper's accuracy contrast to PCG: x_s solves the
+ * Nystrom approximation, not (A + mu_s I) x = b_s.  `mu` is a HOST array of nrhs
+ * shifts, each > 0; b and x are device arrays [nrhs][n] of `dtype` (may not
+ * alias).  An FP32 factor is applied through its orthonormalised basis, as in
+ * nys_precond_apply.  Synchronises `stream`. */
+int32_t nys_sketch_solve(const nys_factor* f, const double* mu, int64_t nrhs, const void* b,
+                         void* x, int32_t dtype, void* stream);
 
 typedef struct nys_pcg_opts {
   double tol;                 /* stop when ||r||_2 <= tol ||b||_2 (default 1e-8) */

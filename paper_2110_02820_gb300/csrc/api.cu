@@ -28,6 +28,8 @@ int32_t block_pcg_mixed(const nys_operator* op, const nys_factor* f, double mu, 
                         int max_refine, int use_x0, nys_pcg_result* res, cudaStream_t s);
 int32_t precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const void* v, void* z,
                       int32_t dtype, cudaStream_t s);
+int32_t sketch_solve(const nys_factor* f, const double* mu, int64_t nrhs, const void* b, void* x,
+                     int32_t dtype, cudaStream_t s);
 
 constexpr int64_t kMaxEll = 4096;
 constexpr int kMaxEscalations = 6;
@@ -756,6 +758,16 @@ int32_t nys_precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, c
   if (v == z) return NYS_ERR_ARG;
   NYS_TRY(check_mu(f, mu, nrhs));
   return precond_apply(f, mu, nrhs, v, z, dtype, (cudaStream_t)stream);
+}
+
+int32_t nys_sketch_solve(const nys_factor* f, const double* mu, int64_t nrhs, const void* b,
+                         void* x, int32_t dtype, void* stream) {
+  if (!f || !b || !x || nrhs < 1 || !mu) return NYS_ERR_ARG;
+  if (dtype != NYS_F64 && dtype != NYS_F32) return NYS_ERR_ARG;
+  if (b == x) return NYS_ERR_ARG;
+  for (int64_t q = 0; q < nrhs; ++q)
+    if (!(mu[q] > 0.0) || !std::isfinite(mu[q])) return NYS_ERR_ARG;
+  return sketch_solve(f, mu, nrhs, b, x, dtype, (cudaStream_t)stream);
 }
 
 int32_t pcg_solve(const nys_operator* op, const nys_factor* f, const double* mu, int64_t nsys,

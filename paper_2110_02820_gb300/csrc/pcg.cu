@@ -1110,7 +1110,7 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
 template <typename T, typename TU>
 static int32_t precond_apply_impl(const nys_factor* f, const TU* U, const float* E,
                                   const double* mu, int64_t nrhs, const T* v, T* z,
-                                  cudaStream_t s) {
+                                  double lam_ell, cudaStream_t s) {
   const int64_t n = f->n, ell = f->ell;
   PcgBuffers<T, TU> B;
   B.s = s;
@@ -1139,7 +1139,7 @@ static int32_t precond_apply_impl(const nys_factor* f, const TU* U, const float*
   NYS_CUDA_TRY(cudaMemsetAsync(a.counters, 0, (size_t)nrhs * 4 * sizeof(unsigned), s));
   NYS_CUDA_TRY(cudaMemcpyAsync(B.d_mu, mu, nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
   // states: tol = 0 (never "converged"), cap never reached
-  init_state_kernel<T><<<(unsigned)nrhs, 256, 0, s>>>(v, n, a.st, B.d_mu, f->lam_ell, 0.0,
+  init_state_kernel<T><<<(unsigned)nrhs, 256, 0, s>>>(v, n, a.st, B.d_mu, lam_ell, 0.0,
                                                        1 << 30);
   count_launch();
   PcgLaunch<T, TU> L;
@@ -1152,9 +1152,27 @@ static int32_t precond_apply_impl(const nys_factor* f, const TU* U, const float*
   return NYS_OK;
 }
 
-int32_t precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const void* v, void* z,
-                      int32_t dtype, cudaStream_t s) {
+template <typename T>
+__global__ void scale_rows_kernel(T* z, int64_t n, const double* __restrict__ scale) {
+  const int64_t q = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    z[q * n + i] = (T)((double)z[q * n + i] * scale[q]);
+}
+
+// z_s = P_s^{-1} v_s with lam_ell as the top coefficient (f->lam_ell for Eq. (5.3),
+// 0 for sketch-and-solve), then z_s /= mu_s when `solve`.
+static int32_t apply_impl(const nys_factor* f, const double* mu, int64_t nrhs, const void* v,
+                          void* z, int32_t dtype, double lam_ell, bool solve, cudaStream_t s) {
   Scratch sc(s);
+  double* inv = nullptr;
+  if (solve) {
+    std::vector<double> h(nrhs);
+    for (int64_t q = 0; q < nrhs; ++q) h[q] = 1.0 / mu[q];
+    NYS_TRY(sc.get(&inv, nrhs));
+    NYS_CUDA_TRY(cudaMemcpyAsync(inv, h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  const dim3 gs((unsigned)std::min<int64_t>(cdiv(f->n, 256), 1024), (unsigned)nrhs);
   if (dtype == NYS_F64) {
     const double* U = (const double*)f->U;
     if (f->u_dtype != NYS_F64) {
@@ -1163,8 +1181,13 @@ int32_t precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const
       NYS_TRY(convert_f32_to_f64((const float*)f->U, Ud, f->n * f->ell, s));
       U = Ud;
     }
-    return precond_apply_impl<double, double>(f, U, f->E, mu, nrhs, (const double*)v,
-                                              (double*)z, s);
+    NYS_TRY((precond_apply_impl<double, double>(f, U, f->E, mu, nrhs, (const double*)v,
+                                                (double*)z, lam_ell, s)));
+    if (solve) {
+      scale_rows_kernel<double><<<gs, 256, 0, s>>>((double*)z, f->n, inv); count_launch();
+      NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return NYS_OK;
   }
   const float* U = (const float*)f->U;
   const float* E = f->E;
@@ -1177,7 +1200,26 @@ int32_t precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const
     U = Uf;
     E = Ef;
   }
-  return precond_apply_impl<float, float>(f, U, E, mu, nrhs, (const float*)v, (float*)z, s);
+  NYS_TRY((precond_apply_impl<float, float>(f, U, E, mu, nrhs, (const float*)v, (float*)z,
+                                            lam_ell, s)));
+  if (solve) {
+    scale_rows_kernel<float><<<gs, 256, 0, s>>>((float*)z, f->n, inv); count_launch();
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return NYS_OK;
+}
+
+int32_t precond_apply(const nys_factor* f, const double* mu, int64_t nrhs, const void* v, void* z,
+                      int32_t dtype, cudaStream_t s) {
+  return apply_impl(f, mu, nrhs, v, z, dtype, f->lam_ell, false, s);
+}
+
+// Algorithm 2: x = U (Lam + mu I)^{-1} U^T b + (b - U U^T b) / mu
+//             = (1/mu) [b + U (mu / (Lam + mu) - 1) U^T b],
+// the Eq. (5.3) apply with lam_ell replaced by 0, scaled by 1/mu.
+int32_t sketch_solve(const nys_factor* f, const double* mu, int64_t nrhs, const void* b, void* x,
+                     int32_t dtype, cudaStream_t s) {
+  return apply_impl(f, mu, nrhs, b, x, dtype, 0.0, true, s);
 }
 
 }  // namespace nys

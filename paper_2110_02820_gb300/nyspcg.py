@@ -295,6 +295,23 @@ def nys_precond_apply(f: Factor, mu, v: torch.Tensor) -> torch.Tensor:
     return z if v.dim() == 2 else z[0]
 
 
+def nys_sketch_solve(f: Factor, mu, b: torch.Tensor) -> torch.Tensor:
+    """Algorithm 2: x = (U Lam U^T + mu I)^{-1} b for each row of b ([nrhs][n] or [n])."""
+    fn = lib().nys_sketch_solve
+    if fn.argtypes is None:
+        fn.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.c_void_p, C.c_void_p,
+                       C.c_int32, C.c_void_p]
+        fn.restype = C.c_int32
+    bb = b if b.dim() == 2 else b[None]
+    nrhs = bb.shape[0]
+    mus = [float(mu)] * nrhs if not hasattr(mu, "__len__") else [float(m) for m in mu]
+    x = torch.empty_like(bb)
+    dt = NYS_F64 if bb.dtype == torch.float64 else NYS_F32
+    arr = (C.c_double * nrhs)(*mus)
+    _check(fn(f.h, arr, nrhs, _ptr(bb), _ptr(x), dt, _stream()), "nys_sketch_solve")
+    return x if b.dim() == 2 else x[0]
+
+
 @dataclass
 class PcgResult:
     status: int

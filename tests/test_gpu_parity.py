@@ -709,3 +709,28 @@ def test_regularization_path_mixed_gaussian(ny):
         xs = np.linalg.solve(K + mu * np.eye(n), b)
         assert relerr(X[i].cpu().numpy(), xs) <= 1e-6
     assert out[0]["resketched"]
+
+
+# ---------------------------------------------------------------- Algorithm 2 (sketch-and-solve)
+
+def test_sketch_solve_matches_oracle_and_contrasts_with_pcg(ny):
+    n, ell, mu = 1500, 48, 1e-3
+    A, _ = wl.dense_spd(n, seed=70)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, 70)))
+    U, lam = f.U().cpu().numpy(), f.lam().cpu().numpy()
+    B = wl.rhs(n, seed=70, nrhs=3)
+    X = ny.nys_sketch_solve(f, mu, T(B)).cpu().numpy()
+    ref = np.stack([onys.sketch_and_solve(U, lam, mu, B[q]) for q in range(3)])
+    assert relerr(X, ref) <= 1e-12
+    # x solves the Nystrom system (U Lam U^T + mu I) x = b
+    R = (U * lam) @ (U.T @ X.T) + mu * X.T - B.T
+    assert np.linalg.norm(R) <= 1e-10 * np.linalg.norm(B)
+    # the accuracy contrast of Algorithm 2 against PCG on the true system
+    xs = np.linalg.solve(A + mu * np.eye(n), B[0])
+    xp, res, _ = ny.pcg_solve(op, f, mu, T(B[0]), tol=1e-10)
+    e_ss, e_pcg = relerr(X[0], xs), relerr(xp.cpu().numpy(), xs)
+    assert e_ss > 100 * e_pcg, (e_ss, e_pcg)
+    # FP32 vectors
+    X32 = ny.nys_sketch_solve(f, mu, T(B, torch.float32)).cpu().numpy()
+    assert relerr(X32, ref) <= 1e-5
