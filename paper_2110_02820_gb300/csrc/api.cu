@@ -986,8 +986,18 @@ int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const dou
     for (int64_t q = 0; q < nvec; ++q)
       NYS_TRY(op_matvec_f64(op, mu, x + q * n, y + q * n, nullptr, work, s));
   } else if (mode == 2) {
-    for (int64_t q = 0; q < nvec; ++q)
-      NYS_TRY(op_matvec_residual(op, mu, x + q * n, y + q * n, nullptr, work, s));
+    if (op->kind == NYS_OP_RBF && op->d <= 64) {
+      // all vectors in one pass over the kernel
+      std::vector<double> mus(nvec, mu);
+      double* d_mu;
+      NYS_TRY(sc.get(&d_mu, nvec));
+      NYS_CUDA_TRY(cudaMemcpyAsync(d_mu, mus.data(), nvec * sizeof(double),
+                                   cudaMemcpyHostToDevice, s));
+      NYS_TRY(rbf_residual_products(op, d_mu, nvec, x, y, s));
+    } else {
+      for (int64_t q = 0; q < nvec; ++q)
+        NYS_TRY(op_matvec_residual(op, mu, x + q * n, y + q * n, nullptr, work, s));
+    }
   } else {
     float *xf, *yf;
     NYS_TRY(sc.get(&xf, nvec * n));

@@ -427,13 +427,259 @@ __global__ void sq_norms_kernel(const float* __restrict__ pts, int64_t n, int64_
   nrm[i] = s;
 }
 
+// ---------------------------------------------------------------- symmetric products
+//
+// y_q = (K + mu_q I) v_q for the points against themselves with every kernel
+// entry computed once.  Row tiles I and column tiles J >= I of BR points form
+// the units of the grid; a unit adds K_IJ v_J to the rows of I and, for
+// J > I, K_IJ^T v_I to the rows of J (column sums reduced across the warp and
+// then across the block's warps in a fixed order, in double-float).  Each
+// contribution (tile t, row i) has a slot of its own, part[t][q][i], and the
+// final sum over t runs in a fixed order: the result is reproducible.
+template <int DMAX, int ROWS, int SQ>
+__global__ void __launch_bounds__(RP_THREADS)
+rbf_sym_products_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld,
+                        const double* __restrict__ nrm, double neg_inv_2s2, int64_t nvec,
+                        const double* __restrict__ v, double* __restrict__ part, int64_t nbr,
+                        const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int BR = ROWS * RP_THREADS;
+  constexpr int NW = RP_THREADS / 32;
+  __shared__ __align__(16) float xs[RP_BJ][DMAX];
+  __shared__ float2 bjs[RP_BJ];
+  __shared__ float2 vjf[SQ][RP_BJ];
+  __shared__ float2 tab2[DFL_TAB];
+  __shared__ float2 cacc[NW][SQ][RP_BJ];
+  // unit -> (I, J >= I): units before row tile a number a nbr - a (a - 1) / 2
+  const int64_t u = blockIdx.x;
+  const double tb = 2.0 * (double)nbr + 1.0;
+  int64_t I = (int64_t)floor((tb - sqrt(fmax(tb * tb - 8.0 * (double)u, 0.0))) * 0.5);
+  if (I < 0) I = 0;
+  if (I > nbr - 1) I = nbr - 1;
+  while (I > 0 && I * nbr - I * (I - 1) / 2 > u) --I;
+  while (I + 1 < nbr && (I + 1) * nbr - (I + 1) * I / 2 <= u) ++I;
+  const int64_t J = I + (u - (I * nbr - I * (I - 1) / 2));
+  const bool diag = (I == J);
+  const int64_t q0 = (int64_t)blockIdx.y * SQ;
+  const int nq = (int)((nvec - q0 < SQ) ? nvec - q0 : SQ);
+  for (int t = threadIdx.x; t < DFL_TAB; t += blockDim.x) {
+    const dfl T = dfl_from_double(exp2((double)t / (double)DFL_TAB));
+    tab2[t] = make_float2(T.hi, T.lo);
+  }
+  const dfl c2 = dfl_from_double(-2.0 * neg_inv_2s2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the rows of tile I (with v at those rows, for the column sums)
+  float xi[ROWS][DMAX];
+  dfl aid[ROWS];
+  float2 vi[ROWS][SQ];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int64_t i = I * BR + (int64_t)r * RP_THREADS + threadIdx.x;
+    const bool ok = i < n;
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) xi[r][k] = (ok && k < d) ? pts[i * ld + k] : 0.f;
+    aid[r] = ok ? dfl_from_double(neg_inv_2s2 * nrm[i]) : dfl_make(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < SQ; ++q) {
+      const dfl t = (ok && q < nq) ? dfl_from_double(v[(q0 + q) * n + i]) : dfl_make(0.f, 0.f);
+      vi[r][q] = make_float2(t.hi, t.lo);
+    }
+  }
+  float gh[ROWS][SQ], gl[ROWS][SQ];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int q = 0; q < SQ; ++q) gh[r][q] = gl[r][q] = 0.f;
+  const int64_t jt0 = J * BR, jt1 = (n < jt0 + BR) ? n : jt0 + BR;
+  for (int64_t j0 = jt0; j0 < jt1; j0 += RP_BJ) {
+    float ah[ROWS][SQ], al[ROWS][SQ];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int q = 0; q < SQ; ++q) ah[r][q] = al[r][q] = 0.f;
+    __syncthreads();
+    for (int e = threadIdx.x; e < RP_BJ * DMAX; e += RP_THREADS) {
+      const int jj = e / DMAX, k = e - jj * DMAX;
+      xs[jj][k] = (j0 + jj < jt1 && k < d) ? pts[(j0 + jj) * ld + k] : 0.f;
+    }
+    for (int jj = threadIdx.x; jj < RP_BJ; jj += RP_THREADS) {
+      const bool ok = j0 + jj < jt1;
+      const dfl t = dfl_from_double(ok ? neg_inv_2s2 * nrm[j0 + jj] : 0.0);
+      bjs[jj] = make_float2(t.hi, t.lo);
+#pragma unroll
+      for (int q = 0; q < SQ; ++q) {
+        const dfl w = dfl_from_double((ok && q < nq) ? v[(q0 + q) * n + j0 + jj] : 0.0);
+        vjf[q][jj] = make_float2(w.hi, w.lo);
+      }
+    }
+    __syncthreads();
+    const int jn = (int)((jt1 - j0 < RP_BJ) ? jt1 - j0 : RP_BJ);
+    for (int jj = 0; jj < jn; ++jj) {
+      float dh[ROWS], dl[ROWS];
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) dh[r] = dl[r] = 0.f;
+      const float4* xr = reinterpret_cast<const float4*>(xs[jj]);
+#pragma unroll
+      for (int k4 = 0; k4 < DMAX / 4; ++k4) {
+        const float4 xj = xr[k4];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          dfl_acc_prod(xi[r][4 * k4 + 0], xj.x, dh[r], dl[r]);
+          dfl_acc_prod(xi[r][4 * k4 + 1], xj.y, dh[r], dl[r]);
+          dfl_acc_prod(xi[r][4 * k4 + 2], xj.z, dh[r], dl[r]);
+          dfl_acc_prod(xi[r][4 * k4 + 3], xj.w, dh[r], dl[r]);
+        }
+      }
+      dfl Kr[ROWS];
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const dfl dot = dfl_norm(dh[r], dl[r]);
+        const float mh = __fmul_rn(dot.hi, c2.hi);
+        float ml = __fmaf_rn(dot.hi, c2.hi, -mh);
+        ml = __fmaf_rn(dot.hi, c2.lo, ml);
+        ml = __fmaf_rn(dot.lo, c2.hi, ml);
+        const float2 bj = bjs[jj];
+        float s1, e1, s2, e2;
+        two_sum(aid[r].hi, bj.x, s1, e1);
+        two_sum(s1, mh, s2, e2);
+        const float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(aid[r].lo, bj.y), ml));
+        dfl ex = dfl_norm(s2, lo);
+        if (ex.hi > 0.f) ex = dfl_make(0.f, 0.f);
+        Kr[r] = dfl_exp_neg(ex, tab2);
+#pragma unroll
+        for (int q = 0; q < SQ; ++q) {
+          const float2 vv = vjf[q][jj];
+          const float p = __fmul_rn(Kr[r].hi, vv.x);
+          float e = __fmaf_rn(Kr[r].hi, vv.x, -p);
+          e = __fmaf_rn(Kr[r].hi, vv.y, e);
+          e = __fmaf_rn(Kr[r].lo, vv.x, e);
+          float sum, e3;
+          two_sum(ah[r][q], p, sum, e3);
+          ah[r][q] = sum;
+          al[r][q] = __fadd_rn(al[r][q], __fadd_rn(e3, e));
+        }
+      }
+      if (!diag) {
+        // column sums over the block's rows of tile I: K_ij v_i, this thread's
+        // rows, then a butterfly across the warp (lane 0 keeps the total)
+#pragma unroll
+        for (int q = 0; q < SQ; ++q) {
+          float sh = 0.f, sl = 0.f;
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) {
+            const float2 vv = vi[r][q];
+            const float p = __fmul_rn(Kr[r].hi, vv.x);
+            float e = __fmaf_rn(Kr[r].hi, vv.x, -p);
+            e = __fmaf_rn(Kr[r].hi, vv.y, e);
+            e = __fmaf_rn(Kr[r].lo, vv.x, e);
+            float sum, e3;
+            two_sum(sh, p, sum, e3);
+            sh = sum;
+            sl = __fadd_rn(sl, __fadd_rn(e3, e));
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, off);
+            const float ol = __shfl_xor_sync(0xffffffffu, sl, off);
+            float sum, e3;
+            two_sum(sh, oh, sum, e3);
+            sh = sum;
+            sl = __fadd_rn(sl, __fadd_rn(ol, e3));
+          }
+          if (lane == 0) cacc[warp][q][jj] = make_float2(sh, sl);
+        }
+      }
+    }
+    // merge the chunk's row sums into the running sums, renormalised
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int q = 0; q < SQ; ++q) {
+        float sh, se;
+        two_sum(gh[r][q], ah[r][q], sh, se);
+        const float t = __fadd_rn(gl[r][q], __fadd_rn(al[r][q], se));
+        const float h = __fadd_rn(sh, t);
+        gl[r][q] = __fsub_rn(t, __fsub_rn(h, sh));
+        gh[r][q] = h;
+      }
+    if (!diag) {
+      __syncthreads();
+      // the chunk's column sums: warps added in a fixed order; slot I of the rows of J
+      for (int e = threadIdx.x; e < SQ * RP_BJ; e += RP_THREADS) {
+        const int q = e / RP_BJ, jj = e - q * RP_BJ;
+        if (q < nq && jj < jn) {
+          float2 a = cacc[0][q][jj];
+#pragma unroll
+          for (int w = 1; w < NW; ++w) {
+            const float2 b = cacc[w][q][jj];
+            float sum, e3;
+            two_sum(a.x, b.x, sum, e3);
+            a = make_float2(sum, __fadd_rn(a.y, __fadd_rn(b.y, e3)));
+          }
+          part[(I * nvec + q0 + q) * n + j0 + jj] = (double)a.x + (double)a.y;
+        }
+      }
+    }
+  }
+  // row sums: slot J of the rows of I
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int64_t i = I * BR + (int64_t)r * RP_THREADS + threadIdx.x;
+    if (i >= n) continue;
+#pragma unroll
+    for (int q = 0; q < SQ; ++q)
+      if (q < nq) part[(J * nvec + q0 + q) * n + i] = (double)gh[r][q] + (double)gl[r][q];
+  }
+}
+
+namespace {
+
+template <int DMAX, int ROWS, int SQ>
+int32_t sym_go(const float* pts, int64_t n, int64_t ld, int64_t d, double sigma,
+               const double* d_mu, int64_t nvec, const double* v, double* y, cudaStream_t s) {
+  constexpr int BR = ROWS * RP_THREADS;
+  const int64_t nbr = cdiv(n, BR);
+  const int64_t units = nbr * (nbr + 1) / 2;
+  if (units > 0x7fffffffll) return NYS_ERR_ARG;
+  Scratch sc(s);
+  double *nrm, *part;
+  NYS_TRY(sc.get(&nrm, n));
+  NYS_TRY(sc.get(&part, (size_t)nbr * nvec * n));
+  sq_norms_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(pts, n, d, ld, nrm);
+  count_launch();
+  const double a = -1.0 / (2.0 * sigma * sigma);
+  rbf_sym_products_kernel<DMAX, ROWS, SQ>
+      <<<dim3((unsigned)units, (unsigned)cdiv(nvec, SQ)), RP_THREADS, 0, s>>>(
+          pts, n, d, ld, nrm, a, nvec, v, part, nbr, nullptr);
+  count_launch();
+  products_sum_kernel<<<(unsigned)cdiv(nvec * n, 256), 256, 0, s>>>(
+      part, (int)nbr, n, nvec, d_mu ? 2 : 0, d_mu, 0.0, v, n, y, nullptr);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+}  // namespace
+
 // y_q = (K + mu_q I) v_q for q < nvec (device FP64 arrays), FP64-accurate.
+// Up to 4 vectors take the symmetric products (each entry once); more take
+// the row-block products.
 int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_t nvec,
                               const double* v, double* y, cudaStream_t s) {
   if (op->kind != NYS_OP_RBF || op->d > RR_DMAX) return NYS_ERR_ARG;
   const float* pts = (const float*)op->data;
-  return rbf_dfl_products(pts, op->n, op->ld, pts, op->n, op->ld, op->d, op->sigma, 0, d_mu, nvec,
-                          v, y, s);
+  const int64_t n = op->n, d = op->d, ld = op->ld;
+  if (nvec == 1) {
+    if (d <= 16) return sym_go<16, 2, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
+    if (d <= 32) return sym_go<32, 2, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
+    return sym_go<64, 1, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
+  }
+  if (nvec <= 4) {
+    if (d <= 16) return sym_go<16, 2, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
+    if (d <= 32) return sym_go<32, 2, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
+    return sym_go<64, 1, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
+  }
+  return rbf_dfl_products(pts, n, ld, pts, n, ld, d, op->sigma, 0, d_mu, nvec, v, y, s);
 }
 
 namespace {
