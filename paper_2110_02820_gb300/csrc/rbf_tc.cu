@@ -100,6 +100,9 @@ struct RtArgs {
   const int* done0;    // done0[s * done_stride] != 0: vector s needs no product (or NULL)
   int64_t done_stride;
   int* err;
+  int tile_chunk;      // one vector: tiles of points per grid.y slice (0: all)
+  float* ypart;        // one vector: [slices][npad] partial sums (NULL: write y directly)
+  int64_t part_stride;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -618,7 +621,9 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * RT_BM;
   const int64_t q0 = a.vec;
-  const int T = a.ntiles;
+  // this CTA's slice of the point tiles (grid.y splits them; see ypart)
+  const int t0 = a.tile_chunk > 0 ? (int)blockIdx.y * a.tile_chunk : 0;
+  const int T = a.tile_chunk > 0 ? min(a.ntiles - t0, a.tile_chunk) : a.ntiles;
 
   if (threadIdx.x == 0) {
     s_skip = (a.done0 && a.done0[q0 * a.done_stride]) ? 1 : 0;
@@ -662,7 +667,7 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
         }
         if (*(volatile int*)&s_fail) break;
         unsigned char* st = sSt + s * GV_STAGE;
-        const int j0 = t * GV_BN;
+        const int j0 = (t0 + t) * GV_BN;
         mbar_arrive_expect_tx(&full[s], (uint32_t)GV_TX);
         tma_load_2d(st, &tmX, 0, j0, &full[s]);
         tma_load_2d(st + GV_XJ / 2, &tmX, 0, j0 + 64, &full[s]);
@@ -781,9 +786,13 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
       double tot = 0.0;
 #pragma unroll
       for (int h = 0; h < GV_G; ++h) tot += sD[h * RT_BM + r];
-      float val = (float)tot;
-      if (a.v) val = fmaf(a.mus ? (float)a.mus[q0] : a.mu0, a.v[q0 * a.ldv + row], val);
-      a.y[q0 * a.ldy + row] = val;
+      if (a.ypart) {
+        a.ypart[(int64_t)blockIdx.y * a.part_stride + row] = (float)tot;
+      } else {
+        float val = (float)tot;
+        if (a.v) val = fmaf(a.mus ? (float)a.mus[q0] : a.mu0, a.v[q0 * a.ldv + row], val);
+        a.y[q0 * a.ldy + row] = val;
+      }
     }
   }
   __syncwarp();
@@ -791,6 +800,19 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
   __syncthreads();
   if (warp == 1) tmem_dealloc(tmem, RT_TMEM_COLS);
   if (threadIdx.x == 0 && s_fail) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
+}
+
+// y[q][row] = sum_z part[z][row] (fixed order) + shift, for the one-vector
+// product split over point slices.
+__global__ void gv_sum_kernel(const float* __restrict__ part, int nz, int64_t stride, RtArgs a) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t q0 = a.vec;
+  if (row >= a.n) return;
+  if (a.done0 && a.done0[q0 * a.done_stride]) return;
+  float val = 0.f;
+  for (int z = 0; z < nz; ++z) val += part[(int64_t)z * stride + row];
+  if (a.v) val = fmaf(a.mus ? (float)a.mus[q0] : a.mu0, a.v[q0 * a.ldv + row], val);
+  a.y[q0 * a.ldy + row] = val;
 }
 
 // max |x_jk| over the points (bit pattern of a non-negative float).
@@ -954,6 +976,9 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
   a.done0 = done0;
   a.done_stride = done_stride;
   a.err = err;
+  a.tile_chunk = 0;
+  a.ypart = nullptr;
+  a.part_stride = 0;
   if (S == 1) {
     // FP16 split layout of the points (in the FP32 layout's space), then one
     // launch per vector (nvec <= 2), each reading its own padded copy
@@ -972,15 +997,40 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
     if (!tmap_f16_2d(&tx16, XS16, npad, 64, 64, 64, 64)) return NYS_ERR_CUDA;
     NYS_CUDA_TRY(
         cudaFuncSetAttribute(rbf_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GV_SMEM));
+    // One CTA per SM runs at a time; split the points into slices (grid.y)
+    // when that fills the last wave of CTAs better (fixed-order partial sums).
+    const int64_t ctas = npad / RT_BM, ntiles = npad / GV_BN, sms = num_sms();
+    int nz = 1;
+    double best = 0.0;
+    for (int z = 1; z <= 4; ++z) {
+      const double waves = (double)(ctas * z) / (double)sms;
+      const double eff = waves / std::ceil(waves);
+      if (eff > best + 0.02) {
+        best = eff;
+        nz = z;
+      }
+    }
+    const int chunk = (int)cdiv(ntiles, nz);
+    nz = (int)cdiv(ntiles, chunk);
+    Scratch sp(s);
+    float* part = nullptr;
+    if (nz > 1) NYS_TRY(sp.get(&part, (size_t)nz * npad));
     for (int64_t q = 0; q < nvec; ++q) {
       RtArgs aq = a;
       aq.vec = q;
       aq.vj = VS + q * npad;
-      aq.ntiles = (int)(npad / GV_BN);
+      aq.ntiles = (int)ntiles;
       aq.ksteps = (int)cdiv(d, 16);
       aq.m2c_dev = m2c_dev;
-      rbf_gemv_kernel<<<(unsigned)(npad / RT_BM), GV_THREADS, GV_SMEM, s>>>(tx16, aq);
+      aq.tile_chunk = nz > 1 ? chunk : 0;
+      aq.ypart = part;
+      aq.part_stride = npad;
+      rbf_gemv_kernel<<<dim3((unsigned)ctas, (unsigned)nz), GV_THREADS, GV_SMEM, s>>>(tx16, aq);
       count_launch();
+      if (part) {
+        gv_sum_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, nz, npad, aq);
+        count_launch();
+      }
       NYS_CUDA_TRY(cudaGetLastError());
     }
     return NYS_OK;
