@@ -139,27 +139,6 @@ int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
 
 // ============================================================ triangular inverse
 
-// Row j of X^T (= column j of X = C^{-1} e_j) by back substitution; one warp
-// per column.  XT[j][i] = X[i][j]; entries i > j are zero.
-__global__ void tri_inv_cols_kernel(const double* C, double* XT, int64_t ell) {
-  const int lane = threadIdx.x & 31;
-  const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= ell) return;
-  double* x = XT + j * ell;
-  for (int64_t i = lane; i < ell; i += 32) x[i] = 0.0;
-  __syncwarp();
-  if (lane == 0) x[j] = 1.0 / C[j * ell + j];
-  __syncwarp();
-  for (int64_t i = j - 1; i >= 0; --i) {
-    const double* Ci = C + i * ell;
-    double acc = 0.0;
-    for (int64_t t = i + 1 + lane; t <= j; t += 32) acc += Ci[t] * x[t];
-    acc = warp_sum(acc);
-    if (lane == 0) x[i] = -acc / Ci[i];
-    __syncwarp();
-  }
-}
-
 __global__ void transpose_kernel(const double* in, double* out, int64_t rows, int64_t cols) {
   __shared__ double tile[32][33];
   int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
