@@ -966,35 +966,29 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   // instead of spending the rest of its budget.
   std::vector<int> stag(nsys, 0);
   std::vector<double> before(nsys, 0.0);
-  bool retaken = false;
+  std::vector<char> bex(nsys, 0);
   const unsigned gb = (unsigned)cdiv(n, 256) > 1024 ? 1024 : (unsigned)cdiv(n, 256);
   // The refinement residual starts in double-FP32 arithmetic (kernel and ridge
-  // operators, ~1e-13 relative per product).  Its floor relative to ||b|| is
-  // about that times ||A|| ||x|| / ||b||, which for a nearly flat kernel
-  // (||K|| / mu ~ 1e6) reaches 1e-7.  So when the residual of a system stops
-  // halving while it is still above tol, the remaining passes take the
-  // residual of the systems still active in native FP64 (slower on this part,
-  // exact to FP64 rounding).
-  bool exact = op->kind == NYS_OP_DENSE;
-  const bool may_escalate = !exact;
-  // The Gaussian residual runs as one pass over the kernel for all systems
-  // still active (gathered into contiguous buffers when some are done).
+  // operators, a few units of 2^-46 relative per product).  Its floor relative
+  // to ||b|| is about that times ||A|| ||x|| / ||b||, which for a nearly flat
+  // kernel and a small shift can sit above tol.  So a system whose residual
+  // stops halving while still above tol takes its remaining residuals in
+  // native FP64 (slower on this part, exact to FP64 rounding); the others
+  // keep the double-FP32 products.
+  std::vector<char> exq(nsys, op->kind == NYS_OP_DENSE ? 1 : 0);
+  const bool may_escalate = op->kind != NYS_OP_DENSE;
+  // The Gaussian residual runs as one pass over the kernel for a set of
+  // systems (gathered into contiguous buffers unless it is all of them).
   double *xa = nullptr, *va = nullptr, *d_musa = nullptr;
   std::vector<double> musa;
-  std::vector<int64_t> act;
-  for (int k = 0; k <= max_refine; ++k) {
-    const bool rbf_pass = op->kind == NYS_OP_RBF && op->d <= 64;
-    if (k == 0 && !use_x0) {
-      // x = 0: the residual is b itself, no product needed
-      NYS_CUDA_TRY(cudaMemsetAsync(v, 0, nsys * n * sizeof(double), s));
-    } else if (rbf_pass) {
-      act.clear();
-      for (int64_t q = 0; q < nsys; ++q)
-        if (active[q]) act.push_back(q);
-      const int64_t na = (int64_t)act.size();
+  auto residual_pass = [&](const std::vector<int64_t>& set, bool ex) -> int32_t {
+    if (set.empty()) return NYS_OK;
+    const int64_t na = (int64_t)set.size();
+    if (op->kind == NYS_OP_RBF && op->d <= 64) {
       const double *xs = x, *ms = d_mus;
       double* vs = v;
-      if (na < nsys) {
+      const bool gather = na < nsys;
+      if (gather) {
         if (!xa) {
           NYS_TRY(sc.get(&xa, nsys * n));
           NYS_TRY(sc.get(&va, nsys * n));
@@ -1002,8 +996,8 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
         }
         musa.resize(na);
         for (int64_t t = 0; t < na; ++t) {
-          musa[t] = mu[act[t]];
-          NYS_CUDA_TRY(cudaMemcpyAsync(xa + t * n, x + act[t] * n, n * sizeof(double),
+          musa[t] = mu[set[t]];
+          NYS_CUDA_TRY(cudaMemcpyAsync(xa + t * n, x + set[t] * n, n * sizeof(double),
                                        cudaMemcpyDeviceToDevice, s));
         }
         NYS_CUDA_TRY(cudaMemcpyAsync(d_musa, musa.data(), na * sizeof(double),
@@ -1013,27 +1007,42 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
         vs = va;
       }
       const float* pts = (const float*)op->data;
-      if (exact)
+      if (ex)
         NYS_TRY(rbf_exact_products(pts, n, op->ld, pts, n, op->ld, op->d, op->sigma, 0, 2, ms, 0.0,
                                    na, xs, vs, nullptr, s));
       else
         NYS_TRY(rbf_residual_products(op, ms, na, xs, vs, s));
-      if (na < nsys)
+      if (gather)
         for (int64_t t = 0; t < na; ++t)
-          NYS_CUDA_TRY(cudaMemcpyAsync(v + act[t] * n, va + t * n, n * sizeof(double),
+          NYS_CUDA_TRY(cudaMemcpyAsync(v + set[t] * n, va + t * n, n * sizeof(double),
                                        cudaMemcpyDeviceToDevice, s));
-    } else if (exact) {
-      for (int64_t q = 0; q < nsys; ++q)
-        if (active[q]) NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
     } else {
-      for (int64_t q = 0; q < nsys; ++q)
-        if (active[q])
-          NYS_TRY(op_matvec_residual(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+      for (int64_t q : set) {
+        if (ex) NYS_TRY(op_matvec_f64(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+        else NYS_TRY(op_matvec_residual(op, mu[q], x + q * n, v + q * n, nullptr, work, s));
+      }
     }
+    return NYS_OK;
+  };
+  auto residual_norms = [&]() -> int32_t {
     sub_kernel<<<gb, 256, 0, s>>>(b, v, r, nsys * n); count_launch();
     sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(r, n, nrm); count_launch();
     NYS_CUDA_TRY(cudaMemcpyAsync(rn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
     NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    return NYS_OK;
+  };
+  for (int k = 0; k <= max_refine; ++k) {
+    if (k == 0 && !use_x0) {
+      // x = 0: the residual is b itself, no product needed
+      NYS_CUDA_TRY(cudaMemsetAsync(v, 0, nsys * n * sizeof(double), s));
+    } else {
+      std::vector<int64_t> set_dfl, set_ex;
+      for (int64_t q = 0; q < nsys; ++q)
+        if (active[q]) (exq[q] ? set_ex : set_dfl).push_back(q);
+      NYS_TRY(residual_pass(set_dfl, false));
+      NYS_TRY(residual_pass(set_ex, true));
+    }
+    NYS_TRY(residual_norms());
     std::vector<int64_t> todo;
     for (int64_t q = 0; q < nsys; ++q) {
       if (!active[q]) continue;  // its residual was not retaken
@@ -1045,7 +1054,7 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
         active[q] = 0;
         stt[q] = NYS_ERR_BREAKDOWN;
       } else {
-        if (exact && !retaken && outer[q] > 0)
+        if (exq[q] && bex[q] && outer[q] > 0)
           stag[q] = (rel[q] > 0.5 * before[q]) ? stag[q] + 1 : 0;
         if (stag[q] >= 2 || total_it[q] >= maxit) {
           active[q] = 0;  // stagnated or budget spent: NYS_ERR_MAXIT
@@ -1056,16 +1065,37 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       }
     }
     if (todo.empty()) break;
-    bool stalled = false;
-    for (int64_t t : todo) stalled |= k > 0 && rel[t] > 0.5 * prev[t];
+    // systems whose residual stopped halving: the same iterate, its residual
+    // retaken in FP64, and FP64 residuals from now on
+    std::vector<int64_t> newly;
+    if (may_escalate && k > 0)
+      for (int64_t t : todo)
+        if (!exq[t] && rel[t] > 0.5 * prev[t]) newly.push_back(t);
     for (int64_t q = 0; q < nsys; ++q) prev[q] = rel[q];
-    retaken = false;
-    if (stalled && may_escalate && !exact) {
-      exact = true;
-      retaken = true;
-      continue;  // the same iterate, its residual retaken in FP64
+    if (!newly.empty()) {
+      for (int64_t t : newly) exq[t] = 1;
+      NYS_TRY(residual_pass(newly, true));
+      NYS_TRY(residual_norms());
+      std::vector<int64_t> keep;
+      for (int64_t q : todo) {
+        if (exq[q] && std::find(newly.begin(), newly.end(), q) != newly.end()) {
+          rel[q] = bn2[q] > 0 ? sqrt(rn2[q] / bn2[q]) : sqrt(rn2[q]);
+          prev[q] = rel[q];
+          if (rel[q] <= tol) {
+            active[q] = 0;
+            stt[q] = NYS_OK;
+            continue;
+          }
+        }
+        keep.push_back(q);
+      }
+      todo.swap(keep);
+      if (todo.empty()) break;
     }
-    for (int64_t t : todo) before[t] = rel[t];
+    for (int64_t t : todo) {
+      before[t] = rel[t];
+      bex[t] = exq[t];
+    }
     // inner solves for the systems still active (batched over them)
     int64_t na = (int64_t)todo.size();
     std::vector<double> mua(na);
