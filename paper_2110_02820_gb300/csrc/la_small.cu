@@ -166,6 +166,11 @@ tri_inv_cols2_kernel(const double* __restrict__ CT, const double* __restrict__ C
                      int64_t ell) {
   extern __shared__ double rsm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // 1 / C_ii for every i, once per block: each step of the chain below then
+  // waits on shared memory only, not on an L2 load of the diagonal
+  double* dinv = rsm + (int64_t)TI_WARPS * ell;
+  for (int64_t i = threadIdx.x; i < ell; i += blockDim.x) dinv[i] = 1.0 / C[i * ell + i];
+  __syncthreads();
   const int64_t j = (int64_t)blockIdx.x * TI_WARPS + wib;
   if (j >= ell) return;
   double* r = rsm + (int64_t)wib * ell;
@@ -175,7 +180,7 @@ tri_inv_cols2_kernel(const double* __restrict__ CT, const double* __restrict__ C
     x[i] = 0.0;
   }
   __syncwarp();
-  double xt = 1.0 / C[j * ell + j];
+  double xt = dinv[j];
   if (lane == 0) x[j] = xt;
   double pf[TI_PF];
   {
@@ -200,7 +205,7 @@ tri_inv_cols2_kernel(const double* __restrict__ CT, const double* __restrict__ C
     for (int64_t i = lane + 32 * TI_PF; i < t; i += 32) r[i] = fma(row[i], xt, r[i]);
     __syncwarp();
     const int64_t i1 = t - 1;
-    xt = -r[i1] / C[i1 * ell + i1];
+    xt = -r[i1] * dinv[i1];
     if (lane == 0) x[i1] = xt;
 #pragma unroll
     for (int q = 0; q < TI_PF; ++q) pf[q] = nxt[q];
@@ -215,7 +220,7 @@ int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s) {
   NYS_TRY(sc.get(&CT, ell * ell));
   dim3 g((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 32));
   transpose_kernel<<<g, dim3(32, 8), 0, s>>>(C, CT, ell, ell); count_launch();
-  const size_t sh = (size_t)TI_WARPS * ell * sizeof(double);
+  const size_t sh = (size_t)(TI_WARPS + 1) * ell * sizeof(double);
   if (sh > 48 * 1024)
     NYS_CUDA_TRY(cudaFuncSetAttribute(tri_inv_cols2_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
