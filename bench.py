@@ -65,6 +65,9 @@ def parse():
                     help="krr workload: adaptive Gaussian sketch (default) or column-sampling "
                          "Nystrom at --cols sampled points")
     ap.add_argument("--cols", type=int, default=1024)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"],
+                    help="krr / batched workloads: mixed (FP32 inner solves, FP64-accurate "
+                         "residual refinement; the default) or plain FP64 PCG, for comparison")
     ap.add_argument("--nrhs", type=int, default=4,
                     help="block workload: right-hand sides of the one shifted system")
     ap.add_argument("--block-ell", type=int, default=1024,
@@ -495,6 +498,7 @@ def run_workload(args):
         P = wl.gmm_points(n, d, seed=0)
         sigma = wl.median_distance(P, seed=0)
         op = ny.rbf_operator(T(P), sigma)
+        prec = ny.NYS_PREC_F64 if args.precision == "f64" else ny.NYS_PREC_MIXED
         if args.workload == "krr":
             mu, tol = 1e-6 * n, 1e-8
             b = T(wl.rhs(n, seed=0))
@@ -505,13 +509,13 @@ def run_workload(args):
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record()
                 if args.sketch == "columns":
-                    f = ny.nys_sketch_columns(op, args.cols, seed=seed, precision=ny.NYS_PREC_MIXED)
+                    f = ny.nys_sketch_columns(op, args.cols, seed=seed, precision=prec)
                     info = None
                 else:
                     f, info = ny.nys_sketch_adaptive(op, ell0, ell_max, ny.NYS_RULE_RATIO, 40.0, 0,
-                                                     mu, seed=seed, precision=ny.NYS_PREC_MIXED)
+                                                     mu, seed=seed, precision=prec)
                 e1.record()
-                x, res, _ = ny.pcg_solve(op, f, mu, b, tol=tol, precision=ny.NYS_PREC_MIXED)
+                x, res, _ = ny.pcg_solve(op, f, mu, b, tol=tol, precision=prec)
                 e2.record()
                 torch.cuda.synchronize()
                 phase["sketch_ms"], phase["pcg_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
@@ -520,7 +524,8 @@ def run_workload(args):
             sk = (f"column sampling, ell={args.cols} uniform points" if args.sketch == "columns"
                   else f"adaptive ratio rule 40, ell {ell0}->{ell_max}")
             cfg = (f"kernel ridge n={n} d={d} GMM(10), sigma=median dist={sigma:.3f}, mu=1e-6 n, "
-                   f"{sk}, mixed + FP64 refinement, tol {tol}")
+                   f"{sk}, {'FP64 PCG' if args.precision == 'f64' else 'mixed + FP64 refinement'}, "
+                   f"tol {tol}")
         else:
             mus = list(np.repeat(wl.regularization_path(32, 1e-8 * n, 1e-1 * n), 4))
             B = T(np.tile(wl.rhs(n, seed=0, nrhs=4), (32, 1)))
@@ -531,16 +536,17 @@ def run_workload(args):
             def step(seed):
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record()
-                f = ny.nys_sketch(op, ell, seed=seed, precision=ny.NYS_PREC_MIXED)
+                f = ny.nys_sketch(op, ell, seed=seed, precision=prec)
                 e1.record()
-                x, res, _ = ny.pcg_solve(op, f, mus, B, tol=tol, precision=ny.NYS_PREC_MIXED)
+                x, res, _ = ny.pcg_solve(op, f, mus, B, tol=tol, precision=prec)
                 e2.record()
                 torch.cuda.synchronize()
                 phase["sketch_ms"], phase["pcg_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
                 f.free()
                 return res, None
             cfg = (f"batched regularisation path n={n} d={d}, 32 shifts log-spaced in "
-                   f"[1e-8, 1e-1] n x 4 rhs = 128 systems, ell={ell}, mixed, tol {tol} each")
+                   f"[1e-8, 1e-1] n x 4 rhs = 128 systems, ell={ell}, {args.precision}, "
+                   f"tol {tol} each")
         for w in range(args.warmup):
             step(100 + w)
         launches0 = ny.kernel_launch_count()
@@ -550,7 +556,10 @@ def run_workload(args):
         mv_ms = mv_total / max(mv_cnt, 1)
         kern = ("rbf_gemv_kernel (tensor-core distances, one vector)" if args.workload == "krr"
                 else "rbf_tc_kernel<64,3> (tensor cores, 64 systems per CTA)")
-        line.update({"dtype": "f32", "config": {"workload": cfg},
+        if args.precision == "f64":
+            kern = "rbf_products_kernel (FP64 entries and sums; not event-timed)"
+        line.update({"dtype": "f64" if args.precision == "f64" else "f32",
+                     "config": {"workload": cfg},
                      "dominant_kernel": {"kernel": kern, "ms_per_launch": mv_ms,
                                          "launches_timed": mv_cnt,
                                          "kernel_entries_per_s": n * n / (mv_ms * 1e-3)}})
