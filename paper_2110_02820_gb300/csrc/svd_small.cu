@@ -159,17 +159,22 @@ __global__ void __launch_bounds__(32 * WB) bjacobi_kernel(BJArgs a) {
             be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
             ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
           }
-          al = warp_sum(al);
-          be = warp_sum(be);
-          ga = warp_sum(ga);
-          if (fabsf(ga) > a.tol * sqrtf(al) * sqrtf(be)) {
+          // the three sums share one butterfly (three independent shuffles per level)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga += __shfl_xor_sync(0xffffffffu, ga, o);
+          }
+          // |gamma| > tol sqrt(alpha beta), without the square roots
+          if (ga * ga > a.tol * a.tol * (al * be)) {
             // 2 x 2 rotation that zeroes the inner product (Hestenes):
             // zeta = (beta - alpha) / (2 gamma), t = tan of the angle.
             const float zeta = (be - al) / (2.0f * ga);
             const float az = fabsf(zeta);
             const float t = az > 1e18f ? 0.5f / zeta
                                        : copysignf(1.0f, zeta) / (az + sqrtf(1.0f + zeta * zeta));
-            const float cs = 1.0f / sqrtf(1.0f + t * t);
+            const float cs = rsqrtf(1.0f + t * t);
             const float sn = cs * t;
             for (int c = lane; c < rq; c += 32) {
               const float4 x = P[c], y = Q[c];
