@@ -562,7 +562,8 @@ def run_workload(args):
                      "config": {"workload": cfg},
                      "dominant_kernel": {"kernel": kern, "ms_per_launch": mv_ms,
                                          "launches_timed": mv_cnt,
-                                         "kernel_entries_per_s": n * n / (mv_ms * 1e-3)}})
+                                         "kernel_entries_per_s":
+                                             n * n / (mv_ms * 1e-3) if mv_ms > 0 else None}})
         if args.workload == "krr":
             line["solve"] = {"iterations": res.iterations, "refinements": res.refinements,
                              "rel_residual": res.rel_residual, "status": res.status,
