@@ -66,7 +66,7 @@ def parse():
                          "Nystrom at --cols sampled points")
     ap.add_argument("--cols", type=int, default=1024)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"],
-                    help="krr / batched workloads: mixed (FP32 inner solves, FP64-accurate "
+                    help="krr / batched / adjoint workloads: mixed (FP32 inner solves, FP64-accurate "
                          "residual refinement; the default) or plain FP64 PCG, for comparison")
     ap.add_argument("--nrhs", type=int, default=4,
                     help="block workload: right-hand sides of the one shifted system")
@@ -670,7 +670,9 @@ def run_workload(args):
             m = torch.tensor(1e-6 * n, dtype=torch.float64, device=dev, requires_grad=True)
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record()
-            L = krr.validation_loss(Pt, y, Vt, yv, sg, m, ell, precision=ny.NYS_PREC_MIXED,
+            L = krr.validation_loss(Pt, y, Vt, yv, sg, m, ell,
+                                    precision=ny.NYS_PREC_F64 if args.precision == "f64"
+                                    else ny.NYS_PREC_MIXED,
                                     tol=1e-8, seed=seed)
             e1.record()
             L.backward()
@@ -682,8 +684,9 @@ def run_workload(args):
             step(100 + w)
         launches0 = ny.kernel_launch_count()
         ms, out = _events_ms(lambda: step(7), args.steps)
-        line.update({"dtype": "f32", "config": {"workload": f"differentiable KRR n_train={n} "
-                                                            f"n_val={nv} d={d} ell={ell} mixed"},
+        line.update({"dtype": "f64" if args.precision == "f64" else "f32",
+                     "config": {"workload": f"differentiable KRR n_train={n} n_val={nv} d={d} "
+                                            f"ell={ell} {args.precision}"},
                      "solve": {"loss": out[0], "dL_dmu": out[1], "dL_dsigma": out[2]},
                      "phases_ms": dict(phase)})
     sol = line.get("solve", {})
