@@ -25,39 +25,49 @@ namespace nys {
 
 // ============================================================ dense
 
+// One warp per row; blocks of DM_WARPS rows so that every block of a 2048-row
+// matrix is resident at once (no tail wave).  Eight 16-byte loads and eight
+// independent accumulators per step keep the L2 loads in flight; the FP64
+// FMA rate of the part, not bandwidth, is the bound (A is L2-resident).
+constexpr int DM_WARPS = 4;
 template <typename P, typename V>
-__global__ void dense_matvec_kernel(const double* __restrict__ A, int64_t n, int64_t ld,
-                                    const P* __restrict__ p, double mu, V* __restrict__ v,
-                                    const int* __restrict__ skip) {
+__global__ void __launch_bounds__(32 * DM_WARPS)
+dense_matvec_kernel(const double* __restrict__ A, int64_t n, int64_t ld,
+                    const P* __restrict__ p, double mu, V* __restrict__ v,
+                    const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t row = (int64_t)blockIdx.x * DM_WARPS + (threadIdx.x >> 5);
   if (row >= n) return;
   const double* a = A + row * ld;
-  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+  double acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = 0.0;
   int64_t j0 = 0;
   if (((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0)) {
-    // 16-byte loads, four independent accumulators (loads stay in flight)
     const double2* a2 = reinterpret_cast<const double2*>(a);
     const int64_t n2 = n >> 1;
     int64_t c = lane;
-    for (; c + 96 < n2; c += 128) {
-      const double2 x0 = a2[c], x1 = a2[c + 32], x2 = a2[c + 64], x3 = a2[c + 96];
-      acc0 = fma(x0.x, (double)p[2 * c], fma(x0.y, (double)p[2 * c + 1], acc0));
-      acc1 = fma(x1.x, (double)p[2 * c + 64], fma(x1.y, (double)p[2 * c + 65], acc1));
-      acc2 = fma(x2.x, (double)p[2 * c + 128], fma(x2.y, (double)p[2 * c + 129], acc2));
-      acc3 = fma(x3.x, (double)p[2 * c + 192], fma(x3.y, (double)p[2 * c + 193], acc3));
+    for (; c + 7 * 32 < n2; c += 8 * 32) {
+      double2 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = a2[c + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j = 2 * (c + 32 * u);
+        acc[u] = fma(x[u].x, (double)p[j], fma(x[u].y, (double)p[j + 1], acc[u]));
+      }
     }
     for (; c < n2; c += 32) {
       const double2 x0 = a2[c];
-      acc0 = fma(x0.x, (double)p[2 * c], fma(x0.y, (double)p[2 * c + 1], acc0));
+      acc[0] = fma(x0.x, (double)p[2 * c], fma(x0.y, (double)p[2 * c + 1], acc[0]));
     }
     j0 = n2 << 1;
   }
-  for (int64_t j = j0 + lane; j < n; j += 32) acc0 = fma(a[j], (double)p[j], acc0);
-  double acc = (acc0 + acc1) + (acc2 + acc3);
-  acc = warp_sum(acc);
-  if (lane == 0) v[row] = (V)(acc + mu * (double)p[row]);
+  for (int64_t j = j0 + lane; j < n; j += 32) acc[0] = fma(a[j], (double)p[j], acc[0]);
+  double t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  t = warp_sum(t);
+  if (lane == 0) v[row] = (V)(t + mu * (double)p[row]);
 }
 
 // ============================================================ gram (fused single pass)
@@ -1006,7 +1016,7 @@ int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* 
   MatvecTimer timer(s);
   const int64_t n = op->n;
   if (op->kind == NYS_OP_DENSE) {
-    dense_matvec_kernel<float, float><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(
+    dense_matvec_kernel<float, float><<<(unsigned)cdiv(n, DM_WARPS), 32 * DM_WARPS, 0, s>>>(
         (const double*)op->data, n, op->ld, p, mu, v, skip); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     return NYS_OK;
@@ -1032,7 +1042,7 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
                       const int* skip, void* work, cudaStream_t s) {
   const int64_t n = op->n;
   if (op->kind == NYS_OP_DENSE) {
-    dense_matvec_kernel<double, double><<<(unsigned)cdiv(n, 8), 256, 0, s>>>(
+    dense_matvec_kernel<double, double><<<(unsigned)cdiv(n, DM_WARPS), 32 * DM_WARPS, 0, s>>>(
         (const double*)op->data, n, op->ld, p, mu, v, skip); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
     return NYS_OK;
