@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"],
                     help="krr / batched / adjoint workloads: mixed (FP32 inner solves, FP64-accurate "
                          "residual refinement; the default) or plain FP64 PCG, for comparison")
+    ap.add_argument("--pcg-launch", default="graph", choices=["graph", "stream"],
+                    help="PCG iterations replayed from a captured CUDA graph (default) or "
+                         "launched kernel by kernel on the stream")
     ap.add_argument("--nrhs", type=int, default=4,
                     help="block workload: right-hand sides of the one shifted system")
     ap.add_argument("--block-ell", type=int, default=1024,
@@ -283,6 +286,7 @@ def run_ours(args):
     import torch
 
     from paper_2110_02820_gb300 import nyspcg as ny
+    ny.pcg_graphs(args.pcg_launch == "graph")
     rank, world, local = dist_init(args)
     dev = torch.device("cuda", torch.cuda.current_device())
     m, n, ell = args.m, args.n, args.ell
@@ -396,6 +400,7 @@ def run_ours(args):
             "cpu_baseline": cb,
             "e2e": e2e,
             "gpu_launches": int(launches_timed),
+            "pcg_launch": args.pcg_launch,
             "clocks": clk,
             "solve": {"inner_iterations": iters[-1][0], "refinements": iters[-1][1],
                       "rel_residual": iters[-1][2], "status": iters[-1][3]},
@@ -472,6 +477,7 @@ def run_workload(args):
 
     from paper_2110_02820_gb300 import nyspcg as ny
     from paper_2110_02820_gb300 import workloads as wl
+    ny.pcg_graphs(args.pcg_launch == "graph")
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)  # noqa: E731
@@ -714,6 +720,7 @@ def run_workload(args):
     line["value"] = (sol["converged"] if args.workload in ("batched", "block", "path")
                      else 1) * 1e3 / ms
     line["gpu_launches"] = int(ny.kernel_launch_count() - launches0)
+    line["pcg_launch"] = args.pcg_launch
     print(json.dumps(line), flush=True)
 
 

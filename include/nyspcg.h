@@ -278,6 +278,23 @@ const char* nys_status_str(int32_t status);
  * number of kernels that call launched.  No paper counterpart. */
 uint64_t nys_kernel_launch_count(void);
 
+/* PCG launch mode (no counterpart in the paper).  With `on` = 1 (the
+ * default, unless the environment sets NYS_PCG_GRAPH=0 before the first
+ * solve) pcg_solve, the inner solves of the mixed path and the batched
+ * solves capture four PCG iterations (Algorithm 3's loop body, every kernel
+ * of it) once per solve as a CUDA graph and replay it between the host's
+ * convergence checks; 0 launches the same kernels one by one on the stream.
+ * Both modes run the same kernels in the same order and give bit-identical
+ * results.  Where a capture is refused the solve falls back to plain
+ * launches.  Returns the previous mode; any other `on` only queries it.
+ * Process-wide; set it between solves, not during one. */
+int32_t nys_pcg_graphs(int32_t on);
+
+/* Number of PCG iteration graphs replayed in this process (a diagnostic:
+ * zero growth across a solve in graph mode means its capture was refused and
+ * it ran on plain launches). */
+uint64_t nys_pcg_graph_replays(void);
+
 /* Diagnostics (no counterpart in the paper): CUDA-event timing of the FP32
  * operator products that mixed-precision PCG runs (the ridge or Gaussian
  * matvec), recorded on the stream each product is launched on.

@@ -671,6 +671,10 @@ extern "C" {
 
 uint64_t nys_kernel_launch_count(void) { return (uint64_t)nys::launch_count(); }
 
+int32_t nys_pcg_graphs(int32_t on) { return nys::pcg_graphs(on); }
+
+uint64_t nys_pcg_graph_replays(void) { return (uint64_t)nys::pcg_graph_replays(); }
+
 const char* nys_status_str(int32_t st) {
   switch (st) {
     case NYS_OK: return "ok";

@@ -28,6 +28,10 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+void count_launches(long long k) {
+  g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed);
+}
+
 int num_sms() {
   static int cached[64] = {0};
   int dev = 0;

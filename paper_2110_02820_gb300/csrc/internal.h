@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/nyspcg.h"
 
 struct nys_factor {
@@ -25,6 +27,12 @@ namespace nys {
 
 // Kernel launches made by this library since the process started.
 unsigned long long launch_count();
+// Adds k (may be negative) to the launch count: a graph replay adds the
+// launches it holds; a capture takes back the launches it only recorded.
+void count_launches(long long k);
+// PCG graph mode switch behind nys_pcg_graphs (pcg.cu).
+int32_t pcg_graphs(int32_t on);
+unsigned long long pcg_graph_replays();
 
 // ---------------------------------------------------------------- workspace
 
@@ -150,6 +158,19 @@ int32_t op_matvec_f32(const nys_operator* op, double mu, const float* p, float* 
                       void* work, cudaStream_t s);
 // Opt-in event timing of op_matvec_f32 (operators.cu).
 int32_t timing_start(int32_t max_products);
+// Event timing of products launched inside a stream capture (operators.cu):
+// timing_capture_begin() before the capture, timing_graph_nodes() on the
+// captured graph, timing_graph_rebind() before every replay of its
+// executable.  A graph captured with timing off carries no timing nodes.
+struct GraphTiming {
+  std::vector<cudaGraphNode_t> nodes;
+  std::vector<int> index;               // placeholder index of each node
+  std::vector<cudaEvent_t> placeholders;
+  int products = 0;
+};
+void timing_capture_begin();
+int32_t timing_graph_nodes(cudaGraph_t g, GraphTiming* gt);
+int32_t timing_graph_rebind(cudaGraphExec_t ge, const GraphTiming& gt);
 int32_t timing_stop(double* total_ms, int64_t* products);
 // v = (A + mu I) p in FP64 arithmetic (FP64 PCG).
 int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double* v,

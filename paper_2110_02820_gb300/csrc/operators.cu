@@ -956,29 +956,106 @@ size_t op_matvec_work_bytes(const nys_operator* op, bool accurate) {
 //
 // Opt-in CUDA-event timing of the FP32 operator products (the inner PCG
 // matvec): a pool of event pairs recorded on the launching stream around each
-// product while enabled, summed when timing stops.
+// product while enabled, summed when timing stops.  Inside a stream capture
+// the pair is recorded as two external event-record nodes of the graph on
+// placeholder events; before each replay timing_graph_rebind() points those
+// nodes at fresh pairs of the pool, so graph replays are timed product by
+// product like plain launches.
 namespace {
 std::mutex g_tm_mutex;
 bool g_tm_on = false;
-std::vector<cudaEvent_t> g_tm_ev;  // 2 per product
+std::vector<cudaEvent_t> g_tm_ev;   // 2 per product
 size_t g_tm_used = 0;
+std::vector<cudaEvent_t> g_tm_ph;   // placeholders of the capture in progress
+size_t g_tm_ph_used = 0;
 
 struct MatvecTimer {
   cudaStream_t s;
   int slot = -1;
+  bool captured = false;
   explicit MatvecTimer(cudaStream_t st) : s(st) {
     std::lock_guard<std::mutex> lk(g_tm_mutex);
-    if (g_tm_on && g_tm_used + 2 <= g_tm_ev.size()) {
+    if (!g_tm_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return;
+    if (cs == cudaStreamCaptureStatusActive) {
+      while (g_tm_ph.size() < g_tm_ph_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        g_tm_ph.push_back(e);
+      }
+      slot = (int)g_tm_ph_used;
+      g_tm_ph_used += 2;
+      captured = true;
+      cudaEventRecordWithFlags(g_tm_ph[slot], s, cudaEventRecordExternal);
+    } else if (g_tm_used + 2 <= g_tm_ev.size()) {
       slot = (int)g_tm_used;
       g_tm_used += 2;
       cudaEventRecord(g_tm_ev[slot], s);
     }
   }
   ~MatvecTimer() {
-    if (slot >= 0) cudaEventRecord(g_tm_ev[slot + 1], s);
+    if (slot < 0) return;
+    if (captured)
+      cudaEventRecordWithFlags(g_tm_ph[slot + 1], s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(g_tm_ev[slot + 1], s);
   }
 };
 }  // namespace
+
+void timing_capture_begin() {
+  std::lock_guard<std::mutex> lk(g_tm_mutex);
+  g_tm_ph_used = 0;
+}
+
+int32_t timing_graph_nodes(cudaGraph_t g, GraphTiming* gt) {
+  gt->nodes.clear();
+  gt->index.clear();
+  gt->products = 0;
+  std::lock_guard<std::mutex> lk(g_tm_mutex);
+  if (g_tm_ph_used == 0) return NYS_OK;
+  size_t cnt = 0;
+  NYS_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &cnt));
+  std::vector<cudaGraphNode_t> nodes(cnt);
+  NYS_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &cnt));
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    NYS_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t e;
+    NYS_CUDA_TRY(cudaGraphEventRecordNodeGetEvent(nd, &e));
+    for (size_t k = 0; k < g_tm_ph_used; ++k)
+      if (g_tm_ph[k] == e) {
+        gt->nodes.push_back(nd);
+        gt->index.push_back((int)k);
+      }
+  }
+  // both events of every pair must be present, else the graph is not timed
+  if (gt->nodes.size() != g_tm_ph_used) {
+    gt->nodes.clear();
+    gt->index.clear();
+    return NYS_OK;
+  }
+  gt->products = (int)(g_tm_ph_used / 2);
+  gt->placeholders.assign(g_tm_ph.begin(), g_tm_ph.begin() + g_tm_ph_used);
+  return NYS_OK;
+}
+
+int32_t timing_graph_rebind(cudaGraphExec_t ge, const GraphTiming& gt) {
+  if (gt.products == 0) return NYS_OK;
+  std::lock_guard<std::mutex> lk(g_tm_mutex);
+  const size_t need = 2 * (size_t)gt.products;
+  const bool pool = g_tm_on && g_tm_used + need <= g_tm_ev.size();
+  const size_t base = g_tm_used;
+  for (size_t k = 0; k < gt.nodes.size(); ++k) {
+    const int i = gt.index[k];
+    cudaEvent_t e = pool ? g_tm_ev[base + i] : gt.placeholders[i];
+    NYS_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(ge, gt.nodes[k], e));
+  }
+  if (pool) g_tm_used += need;
+  return NYS_OK;
+}
 
 int32_t timing_start(int32_t max_products) {
   std::lock_guard<std::mutex> lk(g_tm_mutex);

@@ -18,9 +18,11 @@
 // returns at once, so the host enqueues several iterations between checks.
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -742,6 +744,95 @@ int32_t matvec_T<double>(const nys_operator* op, double mu, const double* p, dou
   return op_matvec_f64(op, mu, p, v, skip, work, s);
 }
 
+// Iterations per captured graph; the host check interval (4, 8, then 16
+// iterations) is a multiple of it.  Iterations past convergence or the cap
+// return at once on the device `done` words, so a replay may overrun both.
+constexpr int kGraphIters = 4;
+
+// Graph mode: NYS_PCG_GRAPH=0 in the environment turns it off at start-up;
+// nys_pcg_graphs() switches it at run time.
+static std::atomic<int> g_pcg_graphs{-1};
+static bool pcg_graphs_enabled() {
+  int v = g_pcg_graphs.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("NYS_PCG_GRAPH");
+    int want = (e && e[0] == '0') ? 0 : 1;
+    g_pcg_graphs.compare_exchange_strong(v, want);
+    v = g_pcg_graphs.load(std::memory_order_relaxed);
+  }
+  return v == 1;
+}
+
+static std::atomic<unsigned long long> g_graph_replays{0};
+unsigned long long pcg_graph_replays() { return g_graph_replays.load(std::memory_order_relaxed); }
+
+int32_t pcg_graphs(int32_t on) {
+  const int32_t prev = pcg_graphs_enabled() ? 1 : 0;
+  if (on == 0 || on == 1) g_pcg_graphs.store(on, std::memory_order_relaxed);
+  return prev;
+}
+
+// A CUDA graph of kGraphIters PCG iterations.  Captured on a private stream
+// (the caller's may be the legacy default stream, which cannot be captured)
+// and replayed on the caller's.  Kernel parameters are captured by value:
+// the graph is valid while the buffers of its solve live.
+struct IterGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  GraphTiming timing;
+  long long launches = 0;  // kernels per replay
+  ~IterGraph() {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+  }
+  bool ok() const { return ge != nullptr; }
+  template <typename F>
+  void build(F& iteration) {
+    // one capture stream per thread and device, kept for the process
+    thread_local cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+      cudaGetLastError();
+      return;
+    }
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+      streams[dev] = nullptr;
+      cudaGetLastError();
+      return;
+    }
+    cudaStream_t cs = streams[dev];
+    const unsigned long long c0 = launch_count();
+    timing_capture_begin();
+    int32_t st = NYS_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      for (int c = 0; c < kGraphIters && st == NYS_OK; ++c) st = iteration(cs);
+      cudaGraph_t cg = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(cs, &cg);
+      if (st == NYS_OK && e == cudaSuccess && cg) {
+        g = cg;
+        if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess ||
+            timing_graph_nodes(g, &timing) != NYS_OK) {
+          if (ge) cudaGraphExecDestroy(ge);
+          ge = nullptr;
+        }
+      } else if (cg) {
+        cudaGraphDestroy(cg);
+      }
+    }
+    cudaGetLastError();  // a refused capture leaves no sticky error
+    // the capture recorded these launches without running them
+    launches = (long long)(launch_count() - c0);
+    count_launches(-launches);
+  }
+  int32_t replay(cudaStream_t s) {
+    NYS_TRY(timing_graph_rebind(ge, timing));
+    NYS_CUDA_TRY(cudaGraphLaunch(ge, s));
+    count_launches(launches);
+    g_graph_replays.fetch_add(1, std::memory_order_relaxed);
+    return NYS_OK;
+  }
+};
+
 // Runs Algorithm 3 on T vectors.  x (device, T, [nsys][n]) receives the
 // solution; b_dev (device FP64 [nsys][n]) is the right-hand side; with
 // use_x0 the incoming x is the initial guess.  Fills iterations/status.
@@ -817,25 +908,38 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
 
   // ---- iterations, checked every `chunk`
   const bool batched_rbf = std::is_same<T, float>::value && nsys > 1 && op->kind == NYS_OP_RBF;
+  auto iteration = [&](cudaStream_t st) -> int32_t {
+    if (batched_rbf) {
+      // one pass over the kernel matrix for all systems
+      NYS_TRY(op_matvec_batched_f32(op, B.d_mu, nsys, (const float*)a.p, (float*)a.v,
+                                    &a.st[0].done, (int64_t)(sizeof(SysState) / sizeof(int)),
+                                    reinterpret_cast<int*>(B.op_work), st));
+    } else {
+      for (int64_t q = 0; q < nsys; ++q)
+        NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work,
+                            st));
+    }
+    pv_alpha_kernel<T, TU><<<L.g_d, PC_THREADS, 0, st>>>(a); count_launch();
+    L.update(a, 1, st);
+    L.z(a, 0, st);
+    p_kernel<T, TU><<<L.g_d, 256, 0, st>>>(a, 0); count_launch();
+    NYS_CUDA_TRY(cudaGetLastError());
+    return NYS_OK;
+  };
+  // The launches of kGraphIters iterations are captured once as a CUDA graph
+  // and replayed between host checks (one launch instead of ~7 per
+  // iteration).  Falls back to plain launches when capture is not possible.
+  IterGraph graph;
+  if (maxit > 0 && pcg_graphs_enabled()) graph.build(iteration);
   std::vector<SysState> hst(nsys);
   int64_t launched = 0;
   int chunk = 4;
   while (true) {
-    for (int c = 0; c < chunk && launched < maxit; ++c, ++launched) {
-      if (batched_rbf) {
-        // one pass over the kernel matrix for all systems
-        NYS_TRY(op_matvec_batched_f32(op, B.d_mu, nsys, (const float*)a.p, (float*)a.v,
-                                      &a.st[0].done, (int64_t)(sizeof(SysState) / sizeof(int)),
-                                      reinterpret_cast<int*>(B.op_work), s));
-      } else {
-        for (int64_t q = 0; q < nsys; ++q)
-          NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work,
-                              s));
-      }
-      pv_alpha_kernel<T, TU><<<L.g_d, PC_THREADS, 0, s>>>(a); count_launch();
-      L.update(a, 1, s);
-      L.z(a, 0, s);
-      p_kernel<T, TU><<<L.g_d, 256, 0, s>>>(a, 0); count_launch();
+    if (graph.ok()) {
+      for (int c = 0; c < chunk && launched < maxit; c += kGraphIters, launched += kGraphIters)
+        NYS_TRY(graph.replay(s));
+    } else {
+      for (int c = 0; c < chunk && launched < maxit; ++c, ++launched) NYS_TRY(iteration(s));
     }
     NYS_CUDA_TRY(cudaGetLastError());
     NYS_CUDA_TRY(cudaMemcpyAsync(hst.data(), a.st, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s));

@@ -97,6 +97,10 @@ def lib() -> C.CDLL:
         L.nys_gemm_tf32_tn.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
         L.nys_kernel_launch_count.argtypes = []
         L.nys_kernel_launch_count.restype = C.c_uint64
+        L.nys_pcg_graphs.argtypes = [i32]
+        L.nys_pcg_graphs.restype = i32
+        L.nys_pcg_graph_replays.argtypes = []
+        L.nys_pcg_graph_replays.restype = C.c_uint64
         L.nys_rbf_cross_matvec.argtypes = [vp, i64, i64, vp, i64, i64, i64, dbl, i64, vp, vp, i32,
                                            vp]
         for name in EXPORTS:
@@ -110,6 +114,18 @@ def lib() -> C.CDLL:
 def kernel_launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(lib().nys_kernel_launch_count())
+
+
+def pcg_graphs(on: int | None = None) -> bool:
+    """PCG launch mode: with `on` True/False, capture (or not) the iteration
+    loop as a CUDA graph; returns the previous mode.  None only queries."""
+    arg = -1 if on is None else (1 if on else 0)
+    return bool(lib().nys_pcg_graphs(arg))
+
+
+def pcg_graph_replays() -> int:
+    """PCG iteration graphs replayed so far in this process."""
+    return int(lib().nys_pcg_graph_replays())
 
 
 def status_str(status: int) -> str:
