@@ -290,6 +290,33 @@ uint64_t nys_kernel_launch_count(void);
  * Process-wide; set it between solves, not during one. */
 int32_t nys_pcg_graphs(int32_t on);
 
+/* Launch-shape autotuner (no counterpart in the paper).  Where a kernel has
+ * several correct launch shapes for one problem size (today: the number of
+ * slices the points of a Gaussian kernel-matrix product are split into, for
+ * one vector and for a batch of vectors), the first product of that size
+ * times each shape with CUDA events and the fastest is used from then on.
+ * Choices are kept per process and, when the environment names a file in
+ * NYS_TUNE_CACHE, saved there as a JSON object {"key": choice, ...} and read
+ * back by later processes.  Shapes that split a sum round its last bits
+ * differently; every shape meets the same accuracy.
+ *
+ * nys_autotune: `on` = 1 times unseen sizes (the default unless NYS_TUNE=0),
+ * 0 uses each launcher's own rule for them (cached choices still apply);
+ * returns the previous mode, any other `on` only queries it.
+ * nys_autotune_dump: writes the current choices as a NUL-terminated JSON
+ * object into buf (at most cap bytes, truncated) and returns the full
+ * length; buf may be NULL to query the length.
+ * nys_autotune_clear: forgets every choice (the file is left alone and not
+ * read again by this process).
+ * nys_autotune_set: pins `choice` for `key` (a key as nys_autotune_dump
+ * prints it); a choice that is not a candidate of the key is ignored at
+ * launch and the sizes are timed again.  NYS_ERR_ARG for a NULL or empty
+ * key. */
+int32_t nys_autotune(int32_t on);
+int64_t nys_autotune_dump(char* buf, int64_t cap);
+void nys_autotune_clear(void);
+int32_t nys_autotune_set(const char* key, int32_t choice);
+
 /* Number of PCG iteration graphs replayed in this process (a diagnostic:
  * zero growth across a solve in graph mode means its capture was refused and
  * it ran on plain launches). */

@@ -675,6 +675,14 @@ int32_t nys_pcg_graphs(int32_t on) { return nys::pcg_graphs(on); }
 
 uint64_t nys_pcg_graph_replays(void) { return (uint64_t)nys::pcg_graph_replays(); }
 
+int32_t nys_autotune(int32_t on) { return nys::tune_switch(on); }
+
+int64_t nys_autotune_dump(char* buf, int64_t cap) { return nys::tune_dump(buf, cap); }
+
+void nys_autotune_clear(void) { nys::tune_clear(); }
+
+int32_t nys_autotune_set(const char* key, int32_t choice) { return nys::tune_set(key, choice); }
+
 const char* nys_status_str(int32_t st) {
   switch (st) {
     case NYS_OK: return "ok";

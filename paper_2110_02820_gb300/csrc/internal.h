@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+#include <string>
 #include <vector>
 
 #include "../../include/nyspcg.h"
@@ -30,6 +32,20 @@ unsigned long long launch_count();
 // Adds k (may be negative) to the launch count: a graph replay adds the
 // launches it holds; a capture takes back the launches it only recorded.
 void count_launches(long long k);
+// Launch-shape autotuner (tune.cu).  tune_pick() returns in *choice the
+// fastest of `cands` for `key` (cached per process and in the JSON file named
+// by NYS_TUNE_CACHE); run(c) must launch the work with candidate c on `s`.
+// With tuning off or `s` capturing, an uncached key gets `fallback`.
+bool tune_enabled();
+int32_t tune_switch(int32_t on);
+bool tune_cached(const std::string& key, int* choice);
+int32_t tune_pick(const std::string& key, const std::vector<int>& cands, int fallback,
+                  const std::function<int32_t(int)>& run, cudaStream_t s, int* choice);
+int64_t tune_dump(char* buf, int64_t cap);
+void tune_clear();
+int32_t tune_set(const char* key, int32_t choice);
+unsigned long long tune_timed();
+
 // PCG graph mode switch behind nys_pcg_graphs (pcg.cu).
 int32_t pcg_graphs(int32_t on);
 unsigned long long pcg_graph_replays();
@@ -211,6 +227,10 @@ int32_t rbf_cross_matvec(const float* tg, int64_t nt, int64_t ldt, const float* 
 // word is the device error word (err defaults to it; NYS_ERR_TIMEOUT is
 // written there if a bounded wait expired).
 bool rbf_tc_supported(int64_t d);
+// True when the next product of this shape would time its launch shapes
+// (the tuner is on and has no entry for it): a solve runs one product
+// before it captures its iteration graph, where nothing can be timed.
+bool rbf_tc_tune_pending(int64_t n, int64_t d, int64_t nvec, int passes);
 size_t rbf_tc_work_bytes(int64_t n, int64_t nvec, int passes);
 int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, double sigma,
                         int64_t nvec, const float* V, int64_t ldv, int shift, const double* d_mu,

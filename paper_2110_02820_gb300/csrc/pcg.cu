@@ -908,17 +908,20 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
 
   // ---- iterations, checked every `chunk`
   const bool batched_rbf = std::is_same<T, float>::value && nsys > 1 && op->kind == NYS_OP_RBF;
-  auto iteration = [&](cudaStream_t st) -> int32_t {
+  auto products = [&](cudaStream_t st) -> int32_t {
     if (batched_rbf) {
       // one pass over the kernel matrix for all systems
-      NYS_TRY(op_matvec_batched_f32(op, B.d_mu, nsys, (const float*)a.p, (float*)a.v,
-                                    &a.st[0].done, (int64_t)(sizeof(SysState) / sizeof(int)),
-                                    reinterpret_cast<int*>(B.op_work), st));
-    } else {
-      for (int64_t q = 0; q < nsys; ++q)
-        NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work,
-                            st));
+      return op_matvec_batched_f32(op, B.d_mu, nsys, (const float*)a.p, (float*)a.v,
+                                   &a.st[0].done, (int64_t)(sizeof(SysState) / sizeof(int)),
+                                   reinterpret_cast<int*>(B.op_work), st);
     }
+    for (int64_t q = 0; q < nsys; ++q)
+      NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work,
+                          st));
+    return NYS_OK;
+  };
+  auto iteration = [&](cudaStream_t st) -> int32_t {
+    NYS_TRY(products(st));
     pv_alpha_kernel<T, TU><<<L.g_d, PC_THREADS, 0, st>>>(a); count_launch();
     L.update(a, 1, st);
     L.z(a, 0, st);
@@ -930,7 +933,15 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   // and replayed between host checks (one launch instead of ~7 per
   // iteration).  Falls back to plain launches when capture is not possible.
   IterGraph graph;
-  if (maxit > 0 && pcg_graphs_enabled()) graph.build(iteration);
+  if (maxit > 0 && pcg_graphs_enabled()) {
+    // the tuner times launch shapes on a live stream only: let it see this
+    // solve's product once before the capture (v is recomputed by the first
+    // iteration)
+    if (std::is_same<T, float>::value && op->kind == NYS_OP_RBF &&
+        rbf_tc_tune_pending(n, op->d, batched_rbf ? nsys : 1, 3))
+      NYS_TRY(products(s));
+    graph.build(iteration);
+  }
   std::vector<SysState> hst(nsys);
   int64_t launched = 0;
   int chunk = 4;

@@ -41,6 +41,10 @@
 
 #include <cuda_fp16.h>
 
+#include <cmath>
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 #include "ptx.cuh"
@@ -100,8 +104,10 @@ struct RtArgs {
   const int* done0;    // done0[s * done_stride] != 0: vector s needs no product (or NULL)
   int64_t done_stride;
   int* err;
-  int tile_chunk;      // one vector: tiles of points per grid.y slice (0: all)
-  float* ypart;        // one vector: [slices][npad] partial sums (NULL: write y directly)
+  int tile_chunk;      // tiles of points per slice (0: all); slices are grid.y for one
+                       // vector, grid.z for many
+  float* ypart;        // partial sums (NULL: write y directly): one vector [slices][npad],
+                       // many [slices][nvec][part_stride], no shift term
   int64_t part_stride;
 };
 
@@ -214,6 +220,17 @@ __device__ __forceinline__ bool promote(uint32_t tmem, uint32_t lane_base, int c
   return true;
 }
 
+// Many vectors: y[sv][row] = val (+ mu_sv v[sv][row]), or, with point
+// slices, the slice's partial sum (the shift is added once, by rt_sum_kernel).
+__device__ __forceinline__ void rt_store(const RtArgs& a, int64_t sv, int64_t row, float val) {
+  if (a.ypart) {
+    a.ypart[((int64_t)blockIdx.z * a.nvec + sv) * a.part_stride + row] = val;
+    return;
+  }
+  if (a.v) val = fmaf(a.mus ? (float)a.mus[sv] : a.mu0, a.v[sv * a.ldv + row], val);
+  a.y[sv * a.ldy + row] = val;
+}
+
 template <int S, int P2>
 __global__ void __launch_bounds__(RT_THREADS, 1)
 rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV,
@@ -242,7 +259,9 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * RT_BM;
   const int64_t s0 = Cfg::GEMV ? a.vec : (int64_t)blockIdx.y * S;
-  const int T = a.ntiles;
+  // this CTA's slice of the point tiles, [t0, t0 + T) (grid.z; see ypart)
+  const int t0 = a.tile_chunk > 0 ? (int)blockIdx.z * a.tile_chunk : 0;
+  const int T = a.tile_chunk > 0 ? min(a.ntiles - t0, a.tile_chunk) : a.ntiles;
 
   if (threadIdx.x == 0) {
     int skip = 0;
@@ -303,7 +322,7 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         }
         if (*(volatile int*)&s_fail) break;
         unsigned char* st = sSt + s * Cfg::STAGE;
-        const int j0 = t * RT_BN;
+        const int j0 = (t0 + t) * RT_BN;
         mbar_arrive_expect_tx(&full[s], (uint32_t)Cfg::TX);
         tma_load_2d(st, &tmX, 0, j0, &full[s]);
         tma_load_2d(st + Cfg::XJ_BYTES, &tmX, RT_DP, j0, &full[s]);
@@ -514,12 +533,8 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         if (ok) ok = promote<S>(tmem, lane_base, (T - 1) / RT_CH, ycf, ycfree, sY, r, lane);
         if (!ok) atomicOr(&s_fail, 1);
         if (ok && row < a.n) {
-          for (int sv = 0; sv < S && s0 + sv < a.nvec; ++sv) {
-            float val = sY[sv * RT_BM + r];
-            const int64_t gv = s0 + sv;
-            if (a.v) val = fmaf(a.mus ? (float)a.mus[gv] : a.mu0, a.v[gv * a.ldv + row], val);
-            a.y[gv * a.ldy + row] = val;
-          }
+          for (int sv = 0; sv < S && s0 + sv < a.nvec; ++sv)
+            rt_store(a, s0 + sv, row, sY[sv * RT_BM + r]);
         }
       } else {
         if (ok) ok = mbar_wait_bounded(yfull, 0u, 1ll << 26);
@@ -534,11 +549,7 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 #pragma unroll
               for (int jj = 0; jj < 16; ++jj) {
                 const int64_t sv = s0 + c0 + jj;
-                if (sv < a.nvec) {
-                  float val = __uint_as_float(v[jj]);
-                  if (a.v) val = fmaf(a.mus ? (float)a.mus[sv] : a.mu0, a.v[sv * a.ldv + row], val);
-                  a.y[sv * a.ldy + row] = val;
-                }
+                if (sv < a.nvec) rt_store(a, sv, row, __uint_as_float(v[jj]));
               }
             }
           }
@@ -815,6 +826,21 @@ __global__ void gv_sum_kernel(const float* __restrict__ part, int nz, int64_t st
   a.y[q0 * a.ldy + row] = val;
 }
 
+// y[sv][row] = sum_z part[z][sv][row] (fixed order) + shift, for the
+// many-vector product split over point slices; vectors whose `done` word is
+// set are left alone, as the product kernel leaves them.
+__global__ void rt_sum_kernel(const float* __restrict__ part, int nz, RtArgs a) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= a.n) return;
+  for (int64_t sv = blockIdx.y; sv < a.nvec; sv += gridDim.y) {
+    if (a.done0 && a.done0[sv * a.done_stride]) continue;
+    float val = 0.f;
+    for (int z = 0; z < nz; ++z) val += part[((int64_t)z * a.nvec + sv) * a.part_stride + row];
+    if (a.v) val = fmaf(a.mus ? (float)a.mus[sv] : a.mu0, a.v[sv * a.ldv + row], val);
+    a.y[sv * a.ldy + row] = val;
+  }
+}
+
 // max |x_jk| over the points (bit pattern of a non-negative float).
 __global__ void rt_absmax_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t ld,
                                  unsigned int* out) {
@@ -891,15 +917,107 @@ __global__ void rt_prep_vecs_kernel(const float* __restrict__ V, int64_t nvec, i
 }
 
 template <int S, int P2>
-int32_t rt_launch(const CUtensorMap& tx, const CUtensorMap& tv, const RtArgs& a, int64_t npad,
-                  int64_t nblk_y, cudaStream_t s) {
+int32_t rt_launch(const CUtensorMap& tx, const CUtensorMap& tv, const RtArgs& a0, int64_t npad,
+                  int64_t nblk_y, int nz, cudaStream_t s) {
   using Cfg = RtCfg<S, P2>;
   auto kern = rbf_tc_kernel<S, P2>;
   NYS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
-  kern<<<dim3((unsigned)(npad / RT_BM), (unsigned)nblk_y), RT_THREADS, Cfg::SMEM, s>>>(tx, tv, a);
+  RtArgs a = a0;
+  Scratch sp(s);
+  if (nz > 1) {
+    const int chunk = (int)cdiv(a.ntiles, nz);
+    nz = (int)cdiv(a.ntiles, chunk);
+    a.tile_chunk = chunk;
+    a.part_stride = npad;
+    NYS_TRY(sp.get(&a.ypart, (size_t)nz * a.nvec * npad));
+  }
+  kern<<<dim3((unsigned)(npad / RT_BM), (unsigned)nblk_y, (unsigned)nz), RT_THREADS, Cfg::SMEM,
+         s>>>(tx, tv, a);
   count_launch();
+  if (a.ypart) {
+    const unsigned gy = (unsigned)(a.nvec < 65535 ? a.nvec : 65535);
+    rt_sum_kernel<<<dim3((unsigned)cdiv(a.n, 256), gy), 256, 0, s>>>(a.ypart, nz, a);
+    count_launch();
+  }
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
+}
+
+// One vector at a time (nvec <= 2), the points split into nz slices.
+int32_t gv_run(const CUtensorMap& tx16, const RtArgs& a, const float* VS, const float* m2c_dev,
+               int64_t npad, int64_t ntiles, int64_t d, int64_t nvec, int nz, cudaStream_t s) {
+  const int64_t ctas = npad / RT_BM;
+  const int chunk = (int)cdiv(ntiles, nz);
+  nz = (int)cdiv(ntiles, chunk);
+  Scratch sp(s);
+  float* part = nullptr;
+  if (nz > 1) NYS_TRY(sp.get(&part, (size_t)nz * npad));
+  for (int64_t q = 0; q < nvec; ++q) {
+    RtArgs aq = a;
+    aq.vec = q;
+    aq.vj = VS + q * npad;
+    aq.ntiles = (int)ntiles;
+    aq.ksteps = (int)cdiv(d, 16);
+    aq.m2c_dev = m2c_dev;
+    aq.tile_chunk = nz > 1 ? chunk : 0;
+    aq.ypart = part;
+    aq.part_stride = npad;
+    rbf_gemv_kernel<<<dim3((unsigned)ctas, (unsigned)nz), GV_THREADS, GV_SMEM, s>>>(tx16, aq);
+    count_launch();
+    if (part) {
+      gv_sum_kernel<<<(unsigned)cdiv(a.n, 256), 256, 0, s>>>(part, nz, npad, aq);
+      count_launch();
+    }
+    NYS_CUDA_TRY(cudaGetLastError());
+  }
+  return NYS_OK;
+}
+
+// Slice counts worth timing.  One vector: 1..4 (the partial sums are a few
+// n-vectors).  Many vectors: only while the grid is under 8 waves (beyond
+// that the last wave costs little), each slice at least 4 tiles, and the
+// partial sums (slices x nvec x npad floats) at most 256 MB.
+std::vector<int> gv_slice_candidates(int64_t ntiles) {
+  std::vector<int> c;
+  for (int z = 1; z <= 4; ++z)
+    if (z == 1 || ntiles >= 2 * z) c.push_back(z);
+  return c;
+}
+
+std::vector<int> rt_slice_candidates(int64_t npad, int64_t nvec, int64_t ctas, int64_t sms) {
+  std::vector<int> c{1};
+  if (ctas >= 8 * sms) return c;
+  const int64_t ntiles = npad / RT_BN;
+  for (int z = 2; z <= 4; ++z)
+    if (ntiles >= 4 * z && (double)z * nvec * npad * 4.0 <= 256.0 * (1 << 20)) c.push_back(z);
+  return c;
+}
+
+// The untimed rule: the candidate whose last wave of CTAs (one per SM) is
+// fullest, a smaller slice count unless a larger one fills 2 % more.
+int wave_fill_rule(int64_t ctas, const std::vector<int>& cands, int64_t sms) {
+  int pick = cands.empty() ? 1 : cands[0];
+  double best = 0.0;
+  for (int z : cands) {
+    const double waves = (double)(ctas * z) / (double)sms;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best + 0.02) {
+      best = eff;
+      pick = z;
+    }
+  }
+  return pick;
+}
+
+std::string gv_tune_key(int64_t npad, int64_t d, int64_t nvec) {
+  return "rbf_gemv npad=" + std::to_string(npad) + " d=" + std::to_string(d) +
+         " nvec=" + std::to_string(nvec) + " sms=" + std::to_string(num_sms());
+}
+
+std::string rt_tune_key(int S, int passes, int64_t npad, int64_t d, int64_t nblk_y) {
+  return "rbf_tc S=" + std::to_string(S) + " passes=" + std::to_string(passes) +
+         " npad=" + std::to_string(npad) + " d=" + std::to_string(d) +
+         " blocks=" + std::to_string(nblk_y) + " sms=" + std::to_string(num_sms());
 }
 
 // Vectors per CTA: 1 (FP32 products on the exp warps) for one or two
@@ -912,6 +1030,19 @@ int rt_block(int64_t nvec, int passes) {
 }  // namespace
 
 bool rbf_tc_supported(int64_t d) { return d >= 1 && d <= RT_DP; }
+
+bool rbf_tc_tune_pending(int64_t n, int64_t d, int64_t nvec, int passes) {
+  if (!tune_enabled() || !rbf_tc_supported(d) || n < 1 || nvec < 1) return false;
+  const int64_t npad = cdiv(n, RT_BM) * RT_BM;
+  const int S = rt_block(nvec, passes);
+  if (S == 1) {
+    const std::vector<int> c = gv_slice_candidates(npad / GV_BN);
+    return c.size() > 1 && !tune_cached(gv_tune_key(npad, d, nvec), nullptr);
+  }
+  const int64_t nblk_y = cdiv(nvec, S);
+  const std::vector<int> c = rt_slice_candidates(npad, nvec, (npad / RT_BM) * nblk_y, num_sms());
+  return c.size() > 1 && !tune_cached(rt_tune_key(S, passes, npad, d, nblk_y), nullptr);
+}
 
 size_t rbf_tc_work_bytes(int64_t n, int64_t nvec, int passes) {
   const int64_t npad = cdiv(n, RT_BM) * RT_BM;
@@ -997,46 +1128,32 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
     if (!tmap_f16_2d(&tx16, XS16, npad, 64, 64, 64, 64)) return NYS_ERR_CUDA;
     NYS_CUDA_TRY(
         cudaFuncSetAttribute(rbf_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GV_SMEM));
-    // One CTA per SM runs at a time; split the points into slices (grid.y)
-    // when that fills the last wave of CTAs better (fixed-order partial sums).
+    // One CTA per SM runs at a time; the points may be split into slices
+    // (grid.y, fixed-order partial sums) so that the last wave of CTAs is
+    // fuller.  The tuner times 1..4 slices; its fallback rule takes the
+    // best last-wave fill.
     const int64_t ctas = npad / RT_BM, ntiles = npad / GV_BN, sms = num_sms();
+    const std::vector<int> cands = gv_slice_candidates(ntiles);
     int nz = 1;
-    double best = 0.0;
-    for (int z = 1; z <= 4; ++z) {
-      const double waves = (double)(ctas * z) / (double)sms;
-      const double eff = waves / std::ceil(waves);
-      if (eff > best + 0.02) {
-        best = eff;
-        nz = z;
-      }
-    }
-    const int chunk = (int)cdiv(ntiles, nz);
-    nz = (int)cdiv(ntiles, chunk);
-    Scratch sp(s);
-    float* part = nullptr;
-    if (nz > 1) NYS_TRY(sp.get(&part, (size_t)nz * npad));
-    for (int64_t q = 0; q < nvec; ++q) {
-      RtArgs aq = a;
-      aq.vec = q;
-      aq.vj = VS + q * npad;
-      aq.ntiles = (int)ntiles;
-      aq.ksteps = (int)cdiv(d, 16);
-      aq.m2c_dev = m2c_dev;
-      aq.tile_chunk = nz > 1 ? chunk : 0;
-      aq.ypart = part;
-      aq.part_stride = npad;
-      rbf_gemv_kernel<<<dim3((unsigned)ctas, (unsigned)nz), GV_THREADS, GV_SMEM, s>>>(tx16, aq);
-      count_launch();
-      if (part) {
-        gv_sum_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(part, nz, npad, aq);
-        count_launch();
-      }
-      NYS_CUDA_TRY(cudaGetLastError());
-    }
-    return NYS_OK;
+    NYS_TRY(tune_pick(gv_tune_key(npad, d, nvec), cands, wave_fill_rule(ctas, cands, sms),
+                      [&](int z) -> int32_t {
+                        return gv_run(tx16, a, VS, m2c_dev, npad, ntiles, d, nvec, z, s);
+                      },
+                      s, &nz));
+    return gv_run(tx16, a, VS, m2c_dev, npad, ntiles, d, nvec, nz, s);
   }
-  if (S == 64) return rt_launch<64, 3>(tx, tv, a, npad, spad / S, s);
-  return rt_launch<128, 1>(tx, tv, a, npad, spad / S, s);
+  // many vectors: point slices over grid.z where the grid is only a few waves
+  const int64_t nblk_y = spad / S;
+  const int64_t ctas = (npad / RT_BM) * nblk_y, sms = num_sms();
+  const std::vector<int> cands = rt_slice_candidates(npad, nvec, ctas, sms);
+  auto run = [&](int z) -> int32_t {
+    return S == 64 ? rt_launch<64, 3>(tx, tv, a, npad, nblk_y, z, s)
+                   : rt_launch<128, 1>(tx, tv, a, npad, nblk_y, z, s);
+  };
+  int nz = 1;
+  NYS_TRY(tune_pick(rt_tune_key(S, passes, npad, d, nblk_y), cands,
+                    wave_fill_rule(ctas, cands, sms), run, s, &nz));
+  return run(nz);
 }
 
 }  // namespace nys

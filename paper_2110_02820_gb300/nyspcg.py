@@ -101,6 +101,14 @@ def lib() -> C.CDLL:
         L.nys_pcg_graphs.restype = i32
         L.nys_pcg_graph_replays.argtypes = []
         L.nys_pcg_graph_replays.restype = C.c_uint64
+        L.nys_autotune.argtypes = [i32]
+        L.nys_autotune.restype = i32
+        L.nys_autotune_dump.argtypes = [C.c_char_p, i64]
+        L.nys_autotune_dump.restype = i64
+        L.nys_autotune_clear.argtypes = []
+        L.nys_autotune_clear.restype = None
+        L.nys_autotune_set.argtypes = [C.c_char_p, i32]
+        L.nys_autotune_set.restype = i32
         L.nys_rbf_cross_matvec.argtypes = [vp, i64, i64, vp, i64, i64, i64, dbl, i64, vp, vp, i32,
                                            vp]
         for name in EXPORTS:
@@ -126,6 +134,32 @@ def pcg_graphs(on: int | None = None) -> bool:
 def pcg_graph_replays() -> int:
     """PCG iteration graphs replayed so far in this process."""
     return int(lib().nys_pcg_graph_replays())
+
+
+def autotune(on: bool | None = None) -> bool:
+    """Launch-shape autotuner: with `on` True/False, time (or not) the launch
+    shapes of unseen problem sizes; returns the previous mode."""
+    arg = -1 if on is None else (1 if on else 0)
+    return bool(lib().nys_autotune(arg))
+
+
+def autotune_choices() -> dict:
+    """The tuner's current choices, {key: launch shape}."""
+    import json
+    n = int(lib().nys_autotune_dump(None, 0))
+    buf = C.create_string_buffer(n + 1)
+    lib().nys_autotune_dump(buf, n + 1)
+    return json.loads(buf.value.decode())
+
+
+def autotune_clear() -> None:
+    """Forget every tuned choice of this process."""
+    lib().nys_autotune_clear()
+
+
+def autotune_set(key: str, choice: int) -> None:
+    """Pin the launch shape `choice` for `key` (a key of autotune_choices())."""
+    _check(lib().nys_autotune_set(key.encode(), int(choice)), "nys_autotune_set")
 
 
 def status_str(status: int) -> str:
