@@ -60,9 +60,11 @@ def test_every_slice_count_gives_the_product(ny, n, d, nvec, prefix):
         y = ny.nys_op_matvec(op, mu, T(V), mode=1).cpu().numpy()
         assert relerr(y, ref) <= 1e-5, z
         outs.append(y)
-    # the shapes differ only in how the FP32 sum over the points is grouped
+    # the shapes differ only in how the FP32 sum over the points (N(0,1)
+    # vectors: the terms cancel) is grouped, each within the 1e-5 of the
+    # oracle above; a dropped or doubled slice would be off by O(1 / slices)
     for y in outs[1:]:
-        assert relerr(y, outs[0]) <= 1e-6
+        assert relerr(y, outs[0]) <= 1e-5
     ny.autotune_clear()
 
 
