@@ -324,7 +324,9 @@ uint64_t nys_pcg_graph_replays(void);
 
 /* Diagnostics (no counterpart in the paper): CUDA-event timing of the FP32
  * operator products that mixed-precision PCG runs (the ridge or Gaussian
- * matvec), recorded on the stream each product is launched on.
+ * matvec) and of the dense products in FP64 and FP32, recorded on the stream
+ * each product is launched on (inside a PCG iteration graph as event nodes
+ * that every replay points at fresh events).
  * nys_timing_start allocates events for up to max_products products
  * (NYS_ERR_ARG if < 1; later products are not timed) and enables the
  * recording; nys_timing_stop waits for the recorded events, returns the

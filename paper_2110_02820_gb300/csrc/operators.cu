@@ -955,7 +955,7 @@ size_t op_matvec_work_bytes(const nys_operator* op, bool accurate) {
 // ---------------------------------------------------------------- matvec timing
 //
 // Opt-in CUDA-event timing of the FP32 operator products (the inner PCG
-// matvec): a pool of event pairs recorded on the launching stream around each
+// matvec) and of the dense products in either precision: a pool of event pairs recorded on the launching stream around each
 // product while enabled, summed when timing stops.  Inside a stream capture
 // the pair is recorded as two external event-record nodes of the graph on
 // placeholder events; before each replay timing_graph_rebind() points those
@@ -1119,6 +1119,7 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
                       const int* skip, void* work, cudaStream_t s) {
   const int64_t n = op->n;
   if (op->kind == NYS_OP_DENSE) {
+    MatvecTimer timer(s);  // the dense products are timed in either precision
     dense_matvec_kernel<double, double><<<(unsigned)cdiv(n, DM_WARPS), 32 * DM_WARPS, 0, s>>>(
         (const double*)op->data, n, op->ld, p, mu, v, skip); count_launch();
     NYS_CUDA_TRY(cudaGetLastError());
