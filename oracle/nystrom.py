@@ -211,6 +211,14 @@ def adaptive_nystrom(matmat, n: int, ell0: int, ell_max: int, tol: float, q: int
                 doublings=len(history) - 1)
 
 
+def adaptive_tau0(tau: float) -> float:
+    """Theorem 5.6 (3): with the error tolerance tau mu of Algorithm 5, PCG
+    contracts by tau0 = (sqrt(1 + 12 tau / 11) - 1) / (sqrt(1 + 12 tau / 11) + 1)
+    per iteration."""
+    r = math.sqrt(1.0 + 12.0 * tau / 11.0)
+    return (r - 1.0) / (r + 1.0)
+
+
 def kappa_estimate(lam_ell: float, mu: float, E: float) -> float:
     """Posterior bound of Eq. (5.6): kappa <= (lam_ell + mu + ||E||) / mu."""
     return (lam_ell + mu + E) / mu

@@ -207,6 +207,20 @@ def refine_solve(matvec_hi, matvec_lo, precond_inv_lo, mu: float, b: np.ndarray,
                 true_res_hist=np.array(hist))
 
 
+def cg_rate(kappa: float) -> float:
+    """Per-iteration contraction of the CG error in the energy norm for a
+    system of condition number kappa, (sqrt(kappa) - 1) / (sqrt(kappa) + 1):
+    the standard CG bound behind the convergence corollaries of Sec. 1 and
+    Sec. 5.3 (delta_t < 2 rate^t)."""
+    r = float(np.sqrt(kappa))
+    return (r - 1.0) / (r + 1.0)
+
+
+def iterations_to(rate: float, eps: float) -> int:
+    """Smallest t with 2 rate^t <= eps: ceil(log(2/eps) / log(1/rate))."""
+    return int(np.ceil(np.log(2.0 / eps) / np.log(1.0 / rate)))
+
+
 def direct_solve(A: np.ndarray, mu: float, b: np.ndarray) -> np.ndarray:
     """x_star = (A + mu I)^{-1} b by dense Cholesky (the plain definition)."""
     import scipy.linalg as sla

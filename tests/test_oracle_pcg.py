@@ -111,7 +111,7 @@ def test_cg_error_bound_in_energy_norm():
     Pinv = lambda r: ny.precond_inverse_apply(f["U"], f["lam"], mu, r)
     ev = ny.preconditioned_spectrum(A, f["U"], f["lam"], mu)
     kap = ev.max() / ev.min()
-    rho = (math.sqrt(kap) - 1) / (math.sqrt(kap) + 1)
+    rho = pcg.cg_rate(kap)
     Am = A + mu * np.eye(n)
     xs = np.linalg.solve(Am, b)
     en = lambda e: math.sqrt(e @ Am @ e)
