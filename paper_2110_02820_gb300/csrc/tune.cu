@@ -25,6 +25,8 @@
 #include <mutex>
 #include <string>
 
+#include <unistd.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -75,7 +77,9 @@ void load_locked() {
 void save_locked() {
   const char* path = cache_path();
   if (!path) return;
-  const std::string tmp = std::string(path) + ".tmp";
+  // one temporary per process: ranks sharing a cache file each write their
+  // own and rename it into place (the last rename wins, whole)
+  const std::string tmp = std::string(path) + ".tmp." + std::to_string((long)getpid());
   FILE* f = fopen(tmp.c_str(), "wb");
   if (!f) return;
   fputs("{\n", f);
