@@ -294,6 +294,58 @@ def test_sketch_and_solve_woodbury_identity():
                                np.linalg.solve(Ahat + mu * np.eye(60), b), rtol=1e-10)
 
 
+def _sketch_solve_case(n, seed):
+    # fast spectral decay, so that the Theorem 4.2 bounds sit well below 1/mu
+    lam_true = np.exp(-np.arange(n) / 2.0)
+    A, _ = spd_with_spectrum(n, lam_true, seed)
+    return A, lam_true
+
+
+def test_sketch_and_solve_inverse_error_theorem_4_2():
+    # Eq. (4.2): E||(A + mu I)^-1 - (A_nys + mu I)^-1|| <=
+    #   (3 + 4 e^2 sr_p(A) / p) lambda_p / (mu (lambda_p + mu)),  ell = 2p - 1.
+    # sr_p is taken with the sum from j = p on (the larger of the paper's two
+    # statements of the p-stable rank).  A dropped (I - U U^T) / mu term would
+    # leave an error ~ 1 / mu = 10, far above the bound (0.42 at p = 16).
+    n, p, mu = 150, 16, 0.1
+    ell = 2 * p - 1
+    A, lam_true = _sketch_solve_case(n, 61)
+    lam_p = lam_true[p - 1]
+    sr_p = lam_true[p - 1:].sum() / lam_p
+    bound = (3 + 4 * math.e ** 2 * sr_p / p) * lam_p / (mu * (lam_p + mu))
+    assert bound < 0.1 / mu
+    inv = np.linalg.inv(A + mu * np.eye(n))
+    errs = []
+    for seed in range(20):
+        out = ny.rand_nystrom(lambda V: A @ V, wl.omega(n, ell, 100 + seed))
+        approx = np.column_stack([ny.sketch_and_solve(out["U"], out["lam"], mu, e)
+                                  for e in np.eye(n)])
+        errs.append(np.linalg.norm(inv - approx, 2))
+    assert np.mean(errs) <= bound
+
+
+def test_sketch_and_solve_solution_error_theorem_4_2():
+    # Eq. (4.3): with ell = 2 ceil(1.5 d_eff(eps mu)) + 1 the relative error of
+    # the sketch-and-solve solution is at most 26 eps in expectation.  Without
+    # the (b - U U^T b) / mu term the error exceeds that bound.
+    n, mu, eps = 150, 0.1, 0.02
+    A, lam_true = _sketch_solve_case(n, 62)
+    ell = 2 * math.ceil(1.5 * ny.effective_dimension(lam_true, eps * mu)) + 1
+    assert ell < n
+    b = wl.rhs(n, 62)
+    xs = np.linalg.solve(A + mu * np.eye(n), b)
+    errs, errs_no_tail = [], []
+    for seed in range(20):
+        out = ny.rand_nystrom(lambda V: A @ V, wl.omega(n, ell, 200 + seed))
+        U, lam = out["U"], out["lam"]
+        xh = ny.sketch_and_solve(U, lam, mu, b)
+        errs.append(np.linalg.norm(xh - xs) / np.linalg.norm(xs))
+        head = U @ ((U.T @ b) / (lam + mu))
+        errs_no_tail.append(np.linalg.norm(head - xs) / np.linalg.norm(xs))
+    assert np.mean(errs) <= 26 * eps
+    assert np.mean(errs_no_tail) > 26 * eps
+
+
 def test_effective_dimension_is_trace_formula():
     n, mu = 50, 0.1
     A, _ = spd_with_spectrum(n, wl.power_spectrum(n), 2)
