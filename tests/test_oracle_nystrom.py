@@ -246,6 +246,11 @@ def test_condition_number_bounds_prop_5_3_every_draw(seed):
     lower = max((lh + mu) / (lam_n + mu), 1.0)
     upper = (lh + mu + E) * min(1.0 / mu, (lh + lam_n + 2 * mu) / ((lh + mu) * (lam_n + mu)))
     assert lower * (1 - 1e-8) <= kappa <= upper * (1 + 1e-8)
+    # the posterior estimate of Sec. 5.4.1 is the first factor of the upper
+    # bound times 1/mu, so it bounds kappa too (and is at least the upper bound)
+    est = ny.kappa_estimate(lh, mu, E)
+    assert upper * (1 - 1e-12) <= est
+    assert kappa <= est * (1 + 1e-8)
 
 
 def test_expected_condition_number_below_28_thm_5_1():
