@@ -117,3 +117,42 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(ny, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(ny.NysLibraryMissing):
         ny.lib()
+
+
+def test_newer_entry_points_reject_bad_arguments(L):
+    # column sketch, block PCG, regularization path and sketch-and-solve check
+    # their arguments on the host and return NYS_ERR_ARG before any device work
+    from paper_2110_02820_gb300 import nyspcg as ny
+    i64, dbl, vp, u64, i32 = C.c_int64, C.c_double, C.c_void_p, C.c_uint64, C.c_int32
+    op = _op()
+    h = C.c_void_p()
+    cols = L.nys_sketch_columns
+    assert cols(C.byref(op), i64(4), u64(0), None, i32(0), None, None) == ny.NYS_ERR_ARG
+    assert cols(C.byref(op), i64(65), u64(0), None, i32(0), C.byref(h), None) == ny.NYS_ERR_ARG
+    assert cols(C.byref(op), i64(0), u64(0), None, i32(0), C.byref(h), None) == ny.NYS_ERR_ARG
+    assert cols(C.byref(op), i64(4), u64(0), None, i32(7), C.byref(h), None) == ny.NYS_ERR_ARG
+
+    res = (ny._PcgResult * 40)()
+    b, x = vp(0x2000), vp(0x3000)
+    blk = L.nys_block_pcg
+    for nrhs, mu in ((0, 1e-3), (33, 1e-3), (4, -1.0), (4, float("nan"))):
+        assert blk(C.byref(op), None, dbl(mu), i64(nrhs), b, x, None, res, None) == ny.NYS_ERR_ARG
+    assert blk(C.byref(op), None, dbl(1e-3), i64(4), None, x, None, res, None) == ny.NYS_ERR_ARG
+
+    pres = (ny._PathResult * 4)()
+    path = L.nys_reg_path
+    good = (C.c_double * 3)(1e-1, 1e-2, 1e-3)
+    bad = (C.c_double * 3)(1e-1, 0.0, 1e-3)
+
+    def call(count=3, mus=good, ell0=4, ell_max=16, err_factor=30.0, q=5):
+        return path(C.byref(op), i64(count), mus, b, x, i64(ell0), i64(ell_max), dbl(err_factor),
+                    i32(q), u64(0), None, None, None, pres, None)
+    assert call(count=0) == ny.NYS_ERR_ARG
+    assert call(mus=bad) == ny.NYS_ERR_ARG
+    assert call(ell0=32, ell_max=16) == ny.NYS_ERR_ARG
+    assert call(ell_max=65) == ny.NYS_ERR_ARG
+    assert call(err_factor=0.0) == ny.NYS_ERR_ARG
+    assert call(q=0) == ny.NYS_ERR_ARG
+
+    mu1 = (C.c_double * 1)(1e-3)
+    assert L.nys_sketch_solve(None, mu1, i64(1), b, x, i32(0), None) == ny.NYS_ERR_ARG
