@@ -15,7 +15,9 @@
 // Scalars live on the device in FP64.  Every reduction runs in a fixed order
 // (per-block partials summed in index order), so results do not depend on
 // scheduling.  Once a system's `done` word is set every kernel of that system
-// returns at once, so the host enqueues several iterations between checks.
+// returns at once, so the host enqueues several iterations between checks:
+// by default it captures four iterations once per solve as a CUDA graph and
+// replays that graph (IterGraph below).
 
 #include <cstdio>
 #include <cstdlib>
