@@ -351,7 +351,7 @@ static int32_t sketch_impl(const nys_operator* op, int64_t ell, uint64_t seed, c
     if (st == NYS_OK) st = sc.get(&Y, n * ell);
     if (st == NYS_OK && !omega) {
       st = sc.get(&raw, n * ell);
-      if (st == NYS_OK) st = philox_gaussian_f64(raw, n * ell, seed, 0x4f6d656761ull, s);
+      if (st == NYS_OK) st = philox_gaussian_f64(raw, n * ell, seed, NYS_STREAM_OMEGA, s);
     }
     if (st == NYS_OK) st = Ops<T>::from_f64(omega ? omega : raw, Q, n * ell, s);
     if (st == NYS_OK) st = orthonormalize<T>(Q, n, ell, s);
@@ -583,7 +583,7 @@ static int32_t adaptive_impl(const nys_operator* op, int64_t ell0, int64_t ell_m
       copy_cols_kernel<<<(unsigned)cdiv(n * mm, 256), 256, 0, s>>>(omega, ell_max, ell_tot, raw, n,
                                                                   mm); count_launch();
     } else {
-      NYS_TRY(philox_gaussian_f64(raw, n * mm, seed, 0x4164610000ull + (uint64_t)ell_tot, s));
+      NYS_TRY(philox_gaussian_f64(raw, n * mm, seed, NYS_STREAM_ADAPTIVE + (uint64_t)ell_tot, s));
     }
     NYS_TRY(Ops<T>::from_f64(raw, blk, n * mm, s));
     NYS_TRY(orthonormalize<T>(blk, n, mm, s));
@@ -616,7 +616,7 @@ static int32_t adaptive_impl(const nys_operator* op, int64_t ell0, int64_t ell_m
     if (rule == NYS_RULE_ERR) {
       const double* gp = g ? g + (int64_t)k_est * n : nullptr;
       if (!gp) {
-        st = philox_gaussian_f64(gk, n, seed, 0x4573740000ull + (uint64_t)k_est, s);
+        st = philox_gaussian_f64(gk, n, seed, NYS_STREAM_ESTIMATE + (uint64_t)k_est, s);
         if (st != NYS_OK) break;
         gp = gk;
       }
@@ -1060,6 +1060,26 @@ int32_t nys_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_
   NYS_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   NYS_CUDA_TRY(cudaStreamSynchronize(s));
   return h ? NYS_ERR_TIMEOUT : NYS_OK;
+}
+
+int32_t nys_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t count, uint32_t* out,
+                          void* stream) {
+  if (count < 0 || (count > 0 && (!ctr || !key || !out))) return NYS_ERR_ARG;
+  if (count > ((int64_t)1 << 40)) return NYS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  NYS_TRY(philox_blocks(ctr, key, count, out, s));
+  NYS_CUDA_TRY(cudaStreamSynchronize(s));
+  return NYS_OK;
+}
+
+int32_t nys_random_stream(uint64_t seed, uint64_t stream_id, int64_t first, int64_t count,
+                          uint32_t* words, double* gauss, void* stream) {
+  if (first < 0 || count < 0 || (count > 0 && !words && !gauss)) return NYS_ERR_ARG;
+  if (first > ((int64_t)1 << 60) || count > ((int64_t)1 << 40)) return NYS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  NYS_TRY(philox_stream(words, gauss, first, count, seed, stream_id, s));
+  NYS_CUDA_TRY(cudaStreamSynchronize(s));
+  return NYS_OK;
 }
 
 int32_t nys_power_err_est(const nys_operator* op, const nys_factor* f, const double* g, int32_t q,

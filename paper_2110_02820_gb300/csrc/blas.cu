@@ -433,39 +433,83 @@ __device__ __forceinline__ Philox4 philox4x32_10(Philox4 c, uint32_t k0, uint32_
   return c;
 }
 
-// Element e of stream (seed, stream_id): counter = (e / 4, stream lo, stream hi, 0);
-// the four 32-bit outputs give two Box-Muller pairs.
-__global__ void philox_gaussian_kernel(double* out, int64_t count, uint64_t seed,
-                                       uint64_t stream_id) {
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g * 4 < count; g += stride) {
+// Element e of stream (seed, stream_id) is word e mod 4 of the block of
+// counter (g, (g >> 32) ^ stream lo, stream hi, 0x6e79), g = e / 4, under key
+// (seed lo, seed hi).  Uniforms u = ((w >> 9) + 1/2) 2^-23 take 23 bits of a
+// word, so they are exact in FP32 (and equal to the FP64 value); Box-Muller
+// pairs elements (0, 1) and (2, 3) of a block: sqrt(-2 ln u_even) times
+// cos (even element) and sin (odd element) of 2 pi u_odd, the angle through
+// sincospif so that 2 u is exact.  Elements [first, first + count) go to
+// words[e - first] and gauss[e - first] (either may be NULL).
+__global__ void philox_stream_kernel(uint32_t* words, double* gauss, int64_t first, int64_t count,
+                                     uint64_t seed, uint64_t stream_id) {
+  const int64_t g0 = first / 4, g1 = (first + count - 1) / 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= g1; g += stride) {
     Philox4 c;
     c.v[0] = (uint32_t)g;
-    c.v[1] = (uint32_t)(g >> 32) ^ (uint32_t)stream_id;
+    c.v[1] = (uint32_t)((uint64_t)g >> 32) ^ (uint32_t)stream_id;
     c.v[2] = (uint32_t)(stream_id >> 32);
     c.v[3] = 0x6e79u;  // fixed tag
-    Philox4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
-    const float two_pi = 6.28318530717958647692f;
+    const Philox4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     float z[4];
+    if (gauss) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float u1 = ((float)r.v[2 * h] + 0.5f) * 2.3283064365386963e-10f;  // (0, 1)
-      float u2 = ((float)r.v[2 * h + 1] + 0.5f) * 2.3283064365386963e-10f;
-      float rad = sqrtf(-2.0f * logf(u1));
-      float sn, cs;
-      sincosf(two_pi * u2, &sn, &cs);
-      z[2 * h] = rad * cs;
-      z[2 * h + 1] = rad * sn;
+      for (int h = 0; h < 2; ++h) {
+        const float u1 = ((float)(r.v[2 * h] >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
+        const float u2 = ((float)(r.v[2 * h + 1] >> 9) + 0.5f) * 1.1920928955078125e-07f;
+        const float rad = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        z[2 * h] = rad * cs;
+        z[2 * h + 1] = rad * sn;
+      }
     }
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (g * 4 + t < count) out[g * 4 + t] = (double)z[t];
+    for (int t = 0; t < 4; ++t) {
+      const int64_t e = g * 4 + t;
+      if (e < first || e >= first + count) continue;
+      if (words) words[e - first] = r.v[t];
+      if (gauss) gauss[e - first] = (double)z[t];
+    }
   }
+}
+
+int32_t philox_stream(uint32_t* words, double* gauss, int64_t first, int64_t count, uint64_t seed,
+                      uint64_t stream_id, cudaStream_t s) {
+  if (count <= 0) return NYS_OK;
+  const int64_t blocks = (first + count - 1) / 4 - first / 4 + 1;
+  philox_stream_kernel<<<grid_for(blocks), 256, 0, s>>>(words, gauss, first, count, seed,
+                                                        stream_id);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
 }
 
 int32_t philox_gaussian_f64(double* out, int64_t count, uint64_t seed, uint64_t stream_id,
                             cudaStream_t s) {
-  philox_gaussian_kernel<<<grid_for(cdiv(count, 4)), 256, 0, s>>>(out, count, seed, stream_id); count_launch();
+  return philox_stream(nullptr, out, 0, count, seed, stream_id, s);
+}
+
+// The bare bijection on caller-given counters and keys (known-answer checks).
+__global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr,
+                                     const uint32_t* __restrict__ key, int64_t count,
+                                     uint32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  Philox4 c;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) c.v[t] = ctr[4 * i + t];
+  const Philox4 r = philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) out[4 * i + t] = r.v[t];
+}
+
+int32_t philox_blocks(const uint32_t* ctr, const uint32_t* key, int64_t count, uint32_t* out,
+                      cudaStream_t s) {
+  if (count <= 0) return NYS_OK;
+  philox_blocks_kernel<<<(unsigned)cdiv(count, 256), 256, 0, s>>>(ctr, key, count, out);
+  count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
