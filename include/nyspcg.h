@@ -86,7 +86,8 @@ typedef struct nys_operator {
 typedef struct nys_factor nys_factor;
 
 /* Algorithm 1.  Draws Omega (n x ell) with the library's Philox4x32-10 +
- * Box-Muller generator from `seed`, unless `omega` (device, n x ell FP64,
+ * Box-Muller generator from `seed` (elements [0, n ell) of stream
+ * (seed, NYS_STREAM_OMEGA), see nys_random_stream), unless `omega` (device, n x ell FP64,
  * row-major, raw Gaussian before the thin QR) is given; orthonormalises it
  * (thin QR of step 2, computed by CholeskyQR2); forms Y = A Omega; shifts by
  * nu = eps(||Y||_F) (FP64) or the FP32 spacing (mixed); factors
@@ -163,11 +164,15 @@ int32_t nys_sketch_solve(const nys_factor* f, const double* mu, int64_t nrhs, co
 typedef struct nys_pcg_opts {
   double tol;                 /* stop when ||r||_2 <= tol ||b||_2 (default 1e-8) */
   int32_t maxit;              /* iteration cap per system (default 500); in mixed precision
-                                 the cap on a system's inner iterations summed over all
-                                 refinement steps.  Mixed precision also ends a system with
-                                 NYS_ERR_MAXIT when, with FP64-accurate residuals, its true
-                                 residual fails to halve over two consecutive inner solves
-                                 (kappa times the FP32 product error is then near 1) */
+                                 the cap on a system's FP32 inner iterations summed over all
+                                 refinement steps.  A mixed-precision system whose true
+                                 residual (FP64-accurate) fails to halve over one FP32 inner
+                                 solve, or that spends this budget, is escalated: its later
+                                 inner solves run on FP64 vectors with FP64-accurate
+                                 products (the FP32 products' error is then comparable to
+                                 mu), under a second budget of maxit iterations.  An
+                                 escalated system whose true residual fails to halve over
+                                 two consecutive inner solves ends with NYS_ERR_MAXIT */
   int32_t precision;          /* nys_precision */
   double inner_tol;           /* mixed: relative tolerance of each inner solve (default 1e-4) */
   int32_t max_refine;         /* mixed: cap on outer refinement steps (default 20) */
@@ -180,7 +185,9 @@ typedef struct nys_pcg_result {
   int32_t status;             /* per system: NYS_OK, NYS_ERR_MAXIT or NYS_ERR_BREAKDOWN */
   int32_t iterations;         /* A-matvecs inside the PCG loop (summed over inner solves) */
   int32_t refinements;        /* mixed: outer steps taken; FP64: 0 */
-  int32_t reserved;
+  int32_t escalated;          /* mixed: 1 when the system's later inner solves ran on FP64
+                                 vectors with FP64-accurate products (see nys_pcg_opts.maxit);
+                                 otherwise 0 */
   double rel_residual;        /* FP64: recurrence ||r||/||b||; mixed: true FP64 ||b - A_mu x||/||b|| */
 } nys_pcg_result;
 
@@ -331,6 +338,9 @@ uint64_t nys_pcg_graph_replays(void);
  * (NYS_ERR_ARG if < 1; later products are not timed) and enables the
  * recording; nys_timing_stop waits for the recorded events, returns the
  * summed duration in ms and the number of products timed, and disables it.
+ * Products shorter than a quarter of the median are left out of both: they
+ * are launches for systems that had already converged (a replayed PCG
+ * iteration past convergence), which return at once on the done word.
  * Not for concurrent use from several host threads. */
 int32_t nys_timing_start(int32_t max_products);
 int32_t nys_timing_stop(double* total_ms, int64_t* products);
@@ -365,6 +375,37 @@ int32_t nys_rbf_cross_matvec(const float* targets, int64_t nt, int64_t ldt, cons
                              int64_t n, int64_t ldp, int64_t d, double sigma, int64_t nvec,
                              const double* v, double* out, int32_t kind, void* stream);
 
+/* Kernel ridge regression objective (Sec. 6.5, Eq. (6.3): KRR with the
+ * Gaussian kernel, here with the validation mean squared error as the
+ * objective) for alpha = (K + mu I)^{-1} b on the training points:
+ *   pred = K_v alpha,   (K_v)_ij = exp(-||v_i - x_j||^2 / (2 sigma^2)),
+ *   *loss (host) = mean_i (pred_i - yv_i)^2,
+ *   g   = (2/m)(pred - yv)            (device FP64 [m], dL/dpred),
+ *   ktg = K_v^T g                     (device FP64 [n], dL/dalpha: the
+ *                                      right-hand side of the adjoint solve).
+ * points: n x d FP32 (row stride ldp), vpoints: m x d FP32 (row stride ldv),
+ * 1 <= d <= 64; alpha, yv: device FP64 [n], [m].  Products in double-FP32
+ * arithmetic (~2^-44 relative), sums in FP64 in a fixed order.  g and ktg
+ * must not alias each other or alpha.  Synchronises `stream`. */
+int32_t nys_krr_validation(const float* points, int64_t n, int64_t ldp, const float* vpoints,
+                           int64_t m, int64_t ldv, int64_t d, double sigma, const double* alpha,
+                           const double* yv, double* loss, double* g, double* ktg, void* stream);
+
+/* Gradient scalars of the KRR objective by implicit differentiation of the
+ * training solve (the paper does not differentiate it): with
+ * lam = (K + mu I)^{-1} dL/dalpha (the adjoint solve, which reuses the
+ * training solve's Nystrom factor),
+ *   out[0] = dL/dmu    = -lam^T alpha,
+ *   out[1] = dL/dsigma = g^T (dK_v/dsigma) alpha - lam^T (dK/dsigma) alpha,
+ *            dK_ij/dsigma = K_ij ||x_i - x_j||^2 / sigma^3,
+ * (dL/db = lam itself).  vpoints may be NULL (g ignored): the objective then
+ * depends on sigma only through alpha and out[1] = -lam^T (dK/dsigma) alpha.
+ * Arrays as in nys_krr_validation; lam, alpha: device FP64 [n], g: device
+ * FP64 [m]; out: HOST [2].  Synchronises `stream`. */
+int32_t nys_krr_gradients(const float* points, int64_t n, int64_t ldp, const float* vpoints,
+                          int64_t m, int64_t ldv, int64_t d, double sigma, const double* alpha,
+                          const double* lam, const double* g, double* out, void* stream);
+
 /* D = A B^T on the 5th-generation tensor cores: TF32 products (the low 13
  * mantissa bits of each FP32 operand are ignored), FP32 accumulation.  A is
  * M x K, B is N x K, D is M x N, all device FP32 row-major with leading
@@ -376,6 +417,44 @@ int32_t nys_rbf_cross_matvec(const float* targets, int64_t nt, int64_t ldt, cons
 int32_t nys_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                          const float* B, int64_t ldb, float* D, int64_t ldd, void* stream);
 
+/* Stream identifiers of the library's own random draws (see
+ * nys_random_stream): Algorithm 1's Omega in nys_sketch; block k of
+ * Algorithm 5 uses NYS_STREAM_ADAPTIVE + (the sketch size reached before
+ * the block); the k-th start vector of Algorithm 4 inside
+ * nys_sketch_adaptive uses NYS_STREAM_ESTIMATE + k. */
+#define NYS_STREAM_OMEGA 0x4f6d656761ull
+#define NYS_STREAM_ADAPTIVE 0x4164610000ull
+#define NYS_STREAM_ESTIMATE 0x4573740000ull
+
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), the counter-based
+ * generator behind Algorithm 1's Gaussian test matrix (step 1), applied to
+ * caller-given blocks: out[4i..4i+3] = Philox4x32-10 of the counter
+ * ctr[4i..4i+3] under the key key[2i..2i+1], for i < count.  ctr, key and
+ * out are device uint32 arrays ([count][4], [count][2], [count][4]).
+ * Exposed so that the bijection can be checked against the authors'
+ * known-answer vectors.  NYS_ERR_ARG for count < 0 or a NULL array.
+ * Synchronises `stream`. */
+int32_t nys_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t count, uint32_t* out,
+                          void* stream);
+
+/* Elements [first, first + count) of the library's random stream
+ * (seed, stream_id), the draw behind Algorithm 1 step 1 (Omega with i.i.d.
+ * N(0, 1) entries) and the other NYS_STREAM_* draws.  Element e is word
+ * e mod 4 of the Philox4x32-10 block of counter
+ * (g mod 2^32, (g >> 32) ^ (stream_id mod 2^32), stream_id >> 32, 0x6e79)
+ * under key (seed mod 2^32, seed >> 32), g = e / 4.  words (device uint32
+ * [count]) receives those raw words; gauss (device FP64 [count]) receives
+ * the Box-Muller values: with u(w) = ((w >> 9) + 1/2) 2^-23 (exact in FP32)
+ * and a block's words w0..w3, element 0 is sqrt(-2 ln u(w0)) cos(2 pi u(w1)),
+ * element 1 the same radius times sin(2 pi u(w1)), elements 2 and 3 likewise
+ * from w2, w3; computed in FP32 (logf, sqrtf, sincospif) and widened, within
+ * 4e-6 of the exact transform of the same words.  Either output may be
+ * NULL, not both.  nys_sketch(seed) uses elements [0, n ell) of stream
+ * (seed, NYS_STREAM_OMEGA) as its row-major n x ell Omega.
+ * NYS_ERR_ARG for first < 0 or count < 0.  Synchronises `stream`. */
+int32_t nys_random_stream(uint64_t seed, uint64_t stream_id, int64_t first, int64_t count,
+                          uint32_t* words, double* gauss, void* stream);
+
 /* Allocation-free ridge matvec: y = (X^T X + mu I) x in FP32 for an
  * NYS_OP_GRAM operator, computed by the same fused single-pass kernel as the
  * mixed-precision PCG matvec.  The paper has no counterpart; this exists for
@@ -386,18 +465,22 @@ int32_t nys_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_
  * x and y (device FP32 [n], 16-byte aligned, distinct); everything else the
  * kernel needs lives in one file-scope device array of 4 MiB + 256 bytes,
  * which every GPU that loads this library holds until the process exits.
- * Limit: (number of SMs) x n <= 2^20 floats, and n <= 6400 with n a multiple
- * of 4 (the kernel's two-stage shared-memory pipeline); X must be
- * row-contiguous (ld == n) and 16-byte aligned.
+ * Limit: n <= 6400 with n a multiple of 4 (the kernel's two-stage
+ * shared-memory pipeline holds 2 x 4 rows of X in 200 KiB); X must be
+ * row-contiguous (ld == n) and 16-byte aligned.  The partials also need
+ * (number of SMs) x n <= 2^20 floats, which n <= 6400 implies on GPUs of up
+ * to 163 SMs (the check stays for larger ones).
  * Larger or unsupported shapes return NYS_ERR_ARG without touching the GPU.
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it; make that first call before any stream
- * capture.  Every call shares the array and leaves its contents behind: the
- * timeout word is cleared at the start of each call and the partials are
- * fully overwritten, but calls that overlap on the GPU (several streams or
- * threads at once) race on the array and give wrong results.  Calls no
- * cudaMalloc, cudaFree or allocating library routine.  Synchronises
- * `stream`; NYS_ERR_TIMEOUT if a bounded device wait expired. */
+ * capture.  cudaDeviceReset destroys the array with the device's context:
+ * do not call this entry point after it in the same process.  Every call
+ * shares the array and leaves its contents behind: the timeout word is
+ * cleared at the start of each call and the partials are fully overwritten,
+ * but calls that overlap on the GPU (several streams or threads at once)
+ * race on the array and give wrong results.  Calls no cudaMalloc, cudaFree
+ * or allocating library routine.  Synchronises `stream`; NYS_ERR_TIMEOUT if
+ * a bounded device wait expired, in which case y is left unchanged. */
 int32_t nys_gram_matvec_f32_noalloc(const nys_operator* op, double mu, const float* x, float* y,
                                     void* stream);
 

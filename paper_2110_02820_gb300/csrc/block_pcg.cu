@@ -104,24 +104,22 @@ bcomb_kernel(const T* A, int ka, const double* __restrict__ M, int ko, const TO*
   __shared__ Acc Ms[KM * KM];
   for (int e = threadIdx.x; e < ka * ko; e += BT) Ms[e] = (Acc)(ms * M[e]);
   __syncthreads();
+  // the column loop is unrolled only for narrow blocks (a fully unrolled
+  // 32 x 32 body costs minutes of compilation for no measurable gain)
+  constexpr int QU = KM <= 16 ? KM : 1;
   for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < n; i += (int64_t)gridDim.x * BT) {
     Acc a[KM];
 #pragma unroll
     for (int j = 0; j < KM; ++j) a[j] = j < ka ? (Acc)A[j * n + i] : (Acc)0;
-    Acc o[KM];
+    // every A[.][i] is in registers before the first store of row i
+#pragma unroll QU
+    for (int q = 0; q < ko; ++q) {
+      Acc v = C ? (Acc)(cs * (double)C[q * n + i]) : (Acc)0;
 #pragma unroll
-    for (int q = 0; q < KM; ++q) {
-      if (q < ko) {
-        Acc v = C ? (Acc)(cs * (double)C[q * n + i]) : (Acc)0;
-#pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < ka) v += a[j] * Ms[j * ko + q];
-        o[q] = v;
-      }
+      for (int j = 0; j < KM; ++j)
+        if (j < ka) v += a[j] * Ms[j * ko + q];
+      out[q * n + i] = (TO)v;
     }
-#pragma unroll
-    for (int q = 0; q < KM; ++q)
-      if (q < ko) out[q * n + i] = (TO)o[q];
   }
 }
 
@@ -710,7 +708,7 @@ int32_t block_pcg_f64(const nys_operator* op, const nys_factor* f, double mu, in
     res[q].status = stt[q];
     res[q].iterations = it;
     res[q].refinements = 0;
-    res[q].reserved = 0;
+    res[q].escalated = 0;
     res[q].rel_residual = rel[q];
   }
   return NYS_OK;
@@ -843,7 +841,7 @@ int32_t block_pcg_mixed(const nys_operator* op, const nys_factor* f, double mu, 
     res[q].status = stt[q];
     res[q].iterations = total_it;
     res[q].refinements = outer;
-    res[q].reserved = 0;
+    res[q].escalated = 0;
     res[q].rel_residual = rel[q];
   }
   NYS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -144,6 +144,10 @@ int32_t shift_add_f64(const double* Y, const double* Q, double* Ynu, int64_t cou
 // Philox4x32-10 + Box-Muller N(0,1) draws; element e of the stream (seed, stream_id)
 int32_t philox_gaussian_f64(double* out, int64_t count, uint64_t seed, uint64_t stream_id,
                             cudaStream_t s);
+int32_t philox_stream(uint32_t* words, double* gauss, int64_t first, int64_t count, uint64_t seed,
+                      uint64_t stream_id, cudaStream_t s);
+int32_t philox_blocks(const uint32_t* ctr, const uint32_t* key, int64_t count, uint32_t* out,
+                      cudaStream_t s);
 // nu = 2^(floor(log2(scale * sqrt(d_sumsq[0]))) - mantissa_bits), written to d_nu
 int32_t compute_nu(const double* d_sumsq, double scale, int mantissa_bits, double* d_nu,
                    cudaStream_t s);
@@ -199,8 +203,10 @@ int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_
                               int* err, cudaStream_t s);
 // y_q = (K + mu_q I) v_q, q < nvec, FP64-accurate in double-FP32 arithmetic
 // (rbf_residual.cu).  d_mu: device [nvec].  NYS_ERR_ARG unless RBF, d <= 64.
+// skip (device, may be NULL): nothing is computed while *skip is nonzero.
 int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_t nvec,
-                              const double* v, double* y, cudaStream_t s);
+                              const double* v, double* y, cudaStream_t s,
+                              const int* skip = nullptr);
 // Double-FP32 Gaussian products between targets (nt x d) and points (n x d):
 // kind 0 y_q = K(t, x) v_q, kind 1 y_q = dK/dsigma v_q; d_mu (device [nvec],
 // or NULL) adds mu_q v_q and requires targets == points.

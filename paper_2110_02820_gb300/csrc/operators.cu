@@ -1073,15 +1073,32 @@ int32_t timing_start(int32_t max_products) {
 int32_t timing_stop(double* total_ms, int64_t* products) {
   std::lock_guard<std::mutex> lk(g_tm_mutex);
   g_tm_on = false;
-  double tot = 0.0;
+  std::vector<float> dur;
   for (size_t i = 0; i + 1 < g_tm_used; i += 2) {
     NYS_CUDA_TRY(cudaEventSynchronize(g_tm_ev[i + 1]));
     float ms = 0.f;
     NYS_CUDA_TRY(cudaEventElapsedTime(&ms, g_tm_ev[i], g_tm_ev[i + 1]));
-    tot += ms;
+    dur.push_back(ms);
+  }
+  // A product launched for a system that has already converged (a graph
+  // replay that runs past convergence) returns at once on the system's done
+  // word: a few microseconds against the hundreds of a product that ran.
+  // Products below a quarter of the median are such launches and are left
+  // out of the total and the count.
+  double tot = 0.0;
+  int64_t cnt = 0;
+  if (!dur.empty()) {
+    std::vector<float> srt(dur);
+    std::nth_element(srt.begin(), srt.begin() + srt.size() / 2, srt.end());
+    const float cut = 0.25f * srt[srt.size() / 2];
+    for (float ms : dur)
+      if (ms >= cut) {
+        tot += ms;
+        ++cnt;
+      }
   }
   if (total_ms) *total_ms = tot;
-  if (products) *products = (int64_t)(g_tm_used / 2);
+  if (products) *products = cnt;
   for (cudaEvent_t e : g_tm_ev) cudaEventDestroy(e);
   g_tm_ev.clear();
   g_tm_used = 0;
@@ -1344,7 +1361,10 @@ void* g_noalloc_addr[128] = {nullptr};
 
 // Device address of g_noalloc_scratch on the current device.  In host code
 // the symbol itself is only a host-side stand-in, so the address is looked
-// up once per device (with that device current) and cached.
+// up once per device (with that device current) and cached.  The cache is
+// valid for the life of the device's primary context: cudaDeviceReset
+// destroys the array with the context, and this entry point must not be
+// called after it.
 int32_t noalloc_scratch_address(void** out) {
   int dev = 0;
   NYS_CUDA_TRY(cudaGetDevice(&dev));
@@ -1384,8 +1404,10 @@ extern "C" int32_t nys_gram_matvec_f32_noalloc(const nys_operator* op, double mu
     case 4: NYS_TRY((gram_fused_launch<float, float, 4>(op, g, x, part, err, nullptr, s))); break;
     default: NYS_TRY((gram_fused_launch<float, float, 8>(op, g, x, part, err, nullptr, s))); break;
   }
+  // the timeout word doubles as the reduction's skip word: after an expired
+  // wait y is left as it was instead of summing incomplete partials
   gram_reduce_kernel<float, float, float><<<(unsigned)cdiv(op->n, 32), 256, 0, s>>>(
-      part, g.grid, op->n, mu, x, y, nullptr); count_launch();
+      part, g.grid, op->n, mu, x, y, err); count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   int h_err = 0;
   NYS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));

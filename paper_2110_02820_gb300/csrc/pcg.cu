@@ -595,6 +595,17 @@ wcorr_kernel(PcgArgs<T, TU> a) {
   }
 }
 
+// flag[g] = 1 when every system of group g (systems [g*gs, min((g+1)*gs, nsys)))
+// is done: a product shared by the group is skipped once none of them needs it.
+__global__ void group_done_kernel(const SysState* st, int64_t nsys, int gs, int* flag) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t q0 = (int64_t)g * gs;
+  if (q0 >= nsys) return;
+  int all = 1;
+  for (int64_t q = q0; q < q0 + gs && q < nsys; ++q) all &= (st[q].done != 0);
+  flag[g] = all;
+}
+
 // -------------------------------------------------------------- host driver
 
 template <typename T, typename TU>
@@ -843,7 +854,13 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
                        double lam_ell, const float* E, const double* mus_host, int64_t nsys,
                        const double* b_dev,
                        const T* b_T, T* x, double tol, int maxit, int use_x0, double* hist,
-                       int* iters_out, int* status_out, double* relres_out, cudaStream_t s) {
+                       int* iters_out, int* status_out, double* relres_out, cudaStream_t s,
+                       bool accurate = false) {
+  // accurate (FP64 vectors only): the operator products are the FP64-accurate
+  // ones of the refinement residual (double-FP32 for the ridge and Gaussian
+  // operators) instead of op_matvec_f64; Gaussian systems share one pass over
+  // the kernel per group of up to 4
+  if (accurate && !std::is_same<T, double>::value) return NYS_ERR_ARG;
   const int64_t n = op->n;
   PcgBuffers<T, TU> B;
   B.s = s;
@@ -910,7 +927,29 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
 
   // ---- iterations, checked every `chunk`
   const bool batched_rbf = std::is_same<T, float>::value && nsys > 1 && op->kind == NYS_OP_RBF;
+  constexpr int kAccGroup = 4;
+  const bool acc_rbf = accurate && op->kind == NYS_OP_RBF;
+  int* gflag = nullptr;
+  if (acc_rbf) NYS_TRY(B.get((void**)&gflag, (size_t)cdiv(nsys, kAccGroup) * sizeof(int)));
   auto products = [&](cudaStream_t st) -> int32_t {
+    if (accurate) {
+      if (acc_rbf) {
+        const int ng = (int)cdiv(nsys, kAccGroup);
+        group_done_kernel<<<(unsigned)cdiv(ng, 128), 128, 0, st>>>(a.st, nsys, kAccGroup, gflag);
+        count_launch();
+        for (int g = 0; g < ng; ++g) {
+          const int64_t q0 = (int64_t)g * kAccGroup;
+          const int64_t cnt = std::min<int64_t>(kAccGroup, nsys - q0);
+          NYS_TRY(rbf_residual_products(op, B.d_mu + q0, cnt, (const double*)(a.p + q0 * n),
+                                        (double*)(a.v + q0 * n), st, gflag + g));
+        }
+        return NYS_OK;
+      }
+      for (int64_t q = 0; q < nsys; ++q)
+        NYS_TRY(op_matvec_residual(op, mus_host[q], (const double*)(a.p + q * n),
+                                   (double*)(a.v + q * n), &a.st[q].done, B.op_work, st));
+      return NYS_OK;
+    }
     if (batched_rbf) {
       // one pass over the kernel matrix for all systems
       return op_matvec_batched_f32(op, B.d_mu, nsys, (const float*)a.p, (float*)a.v,
@@ -939,7 +978,7 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
     // the tuner times launch shapes on a live stream only: let it see this
     // solve's product once before the capture (v is recomputed by the first
     // iteration)
-    if (std::is_same<T, float>::value && op->kind == NYS_OP_RBF &&
+    if (!accurate && std::is_same<T, float>::value && op->kind == NYS_OP_RBF &&
         rbf_tc_tune_pending(n, op->d, batched_rbf ? nsys : 1, 3))
       NYS_TRY(products(s));
     graph.build(iteration);
@@ -1028,7 +1067,7 @@ int32_t pcg_f64(const nys_operator* op, const nys_factor* f, const double* mu, i
     res[q].status = stt[q];
     res[q].iterations = it[q];
     res[q].refinements = 0;
-    res[q].reserved = 0;
+    res[q].escalated = 0;
     res[q].rel_residual = rel[q];
   }
   return NYS_OK;
@@ -1077,11 +1116,21 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   NYS_CUDA_TRY(cudaMemcpyAsync(bn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
   std::vector<int> active(nsys, 1), total_it(nsys, 0), outer(nsys, 0), stt(nsys, NYS_ERR_MAXIT);
   std::vector<double> rel(nsys, 1.0), prev(nsys, 0.0);
-  // Stagnation: with FP64-accurate residuals, a system whose true residual
-  // fails to halve over two consecutive inner solves has reached what an FP32
-  // inner solve can refine (kappa eps_32 >~ 1); it stops with NYS_ERR_MAXIT
-  // instead of spending the rest of its budget.
-  std::vector<int> stag(nsys, 0);
+  // Escalation of the inner solve: with FP64-accurate residuals, a system
+  // whose true residual fails to halve over one inner solve, or that has
+  // spent its FP32 iteration budget, has reached what an FP32 inner solve can
+  // refine (the FP32 products' error is then comparable to mu: refinement
+  // contracts by about ||(A + mu I)^{-1} dA||).  Its later inner solves run on
+  // FP64 vectors with the FP64-accurate products of the residual (double-FP32
+  // for the ridge and Gaussian operators, error ~2^-46 relative), with a
+  // budget of maxit iterations of their own.  A system whose true residual
+  // then still fails to halve over two consecutive inner solves stops with
+  // NYS_ERR_MAXIT.
+  std::vector<int> stag(nsys, 0), acc_it(nsys, 0);
+  std::vector<char> acc(nsys, 0);
+  const double* U64 = nullptr;
+  const float* E64 = nullptr;
+  double *ra = nullptr, *dd = nullptr;
   std::vector<double> before(nsys, 0.0);
   std::vector<char> bex(nsys, 0);
   const unsigned gb = (unsigned)cdiv(n, 256) > 1024 ? 1024 : (unsigned)cdiv(n, 256);
@@ -1173,7 +1222,12 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       } else {
         if (exq[q] && bex[q] && outer[q] > 0)
           stag[q] = (rel[q] > 0.5 * before[q]) ? stag[q] + 1 : 0;
-        if (stag[q] >= 2 || total_it[q] >= maxit) {
+        if (!acc[q] && ((exq[q] && stag[q] >= 1) || total_it[q] >= maxit)) {
+          acc[q] = 1;  // FP64-accurate inner solves (and FP64 residuals) from now on
+          exq[q] = 1;
+          stag[q] = 0;
+        }
+        if (stag[q] >= 2 || (acc[q] ? acc_it[q] >= maxit : total_it[q] >= maxit)) {
           active[q] = 0;  // stagnated or budget spent: NYS_ERR_MAXIT
         } else if (k < max_refine) {
           // maxit bounds a system's inner iterations over all refinements
@@ -1213,6 +1267,53 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       before[t] = rel[t];
       bex[t] = exq[t];
     }
+    std::vector<int64_t> todo_acc, todo_f32;
+    for (int64_t q : todo) (acc[q] ? todo_acc : todo_f32).push_back(q);
+    if (!todo_acc.empty()) {
+      const int64_t nb = (int64_t)todo_acc.size();
+      if (!ra) {
+        NYS_TRY(sc.get(&ra, nsys * n));
+        NYS_TRY(sc.get(&dd, nsys * n));
+        if (f) {
+          if (f->u_dtype == NYS_F64) {
+            U64 = (const double*)f->U;
+          } else {
+            double* Ud;
+            NYS_TRY(sc.get(&Ud, f->n * f->ell));
+            NYS_TRY(convert_f32_to_f64((const float*)f->U, Ud, f->n * f->ell, s));
+            U64 = Ud;
+            E64 = f->E;
+          }
+        }
+      }
+      std::vector<double> mub(nb);
+      for (int64_t t = 0; t < nb; ++t) {
+        mub[t] = mu[todo_acc[t]];
+        NYS_CUDA_TRY(cudaMemcpyAsync(ra + t * n, r + todo_acc[t] * n, n * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+      }
+      std::vector<int> it(nb), st(nb);
+      std::vector<double> rr(nb);
+      int budget = 1;
+      for (int64_t q : todo_acc) budget = std::max(budget, maxit - acc_it[q]);
+      NYS_TRY((run_pcg<double, double>(op, U64, f ? f->lam : nullptr, f ? f->ell : 0,
+                                       f ? f->lam_ell : 0.0, E64, mub.data(), nb, ra, ra, dd,
+                                       inner_tol, budget, 0, nullptr, it.data(), st.data(),
+                                       rr.data(), s, true)));
+      for (int64_t t = 0; t < nb; ++t) {
+        const int64_t q = todo_acc[t];
+        axpy_to_f64_kernel<double><<<gb, 256, 0, s>>>(x + q * n, dd + t * n, n); count_launch();
+        acc_it[q] += it[t];
+        outer[q] += 1;
+        if (st[t] == NYS_ERR_BREAKDOWN) {
+          active[q] = 0;
+          stt[q] = NYS_ERR_BREAKDOWN;
+        }
+      }
+      NYS_CUDA_TRY(cudaGetLastError());
+    }
+    todo.swap(todo_f32);
+    if (todo.empty()) continue;
     // inner solves for the systems still active (batched over them)
     int64_t na = (int64_t)todo.size();
     std::vector<double> mua(na);
@@ -1244,9 +1345,9 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   }
   for (int64_t q = 0; q < nsys; ++q) {
     res[q].status = stt[q];
-    res[q].iterations = total_it[q];
+    res[q].iterations = total_it[q] + acc_it[q];
     res[q].refinements = outer[q];
-    res[q].reserved = 0;
+    res[q].escalated = acc[q];
     res[q].rel_residual = rel[q];
   }
   return NYS_OK;

@@ -636,7 +636,8 @@ namespace {
 
 template <int DMAX, int ROWS, int SQ>
 int32_t sym_go(const float* pts, int64_t n, int64_t ld, int64_t d, double sigma,
-               const double* d_mu, int64_t nvec, const double* v, double* y, cudaStream_t s) {
+               const double* d_mu, int64_t nvec, const double* v, double* y, const int* skip,
+               cudaStream_t s) {
   constexpr int BR = ROWS * RP_THREADS;
   const int64_t nbr = cdiv(n, BR);
   const int64_t units = nbr * (nbr + 1) / 2;
@@ -650,37 +651,16 @@ int32_t sym_go(const float* pts, int64_t n, int64_t ld, int64_t d, double sigma,
   const double a = -1.0 / (2.0 * sigma * sigma);
   rbf_sym_products_kernel<DMAX, ROWS, SQ>
       <<<dim3((unsigned)units, (unsigned)cdiv(nvec, SQ)), RP_THREADS, 0, s>>>(
-          pts, n, d, ld, nrm, a, nvec, v, part, nbr, nullptr);
+          pts, n, d, ld, nrm, a, nvec, v, part, nbr, skip);
   count_launch();
   products_sum_kernel<<<(unsigned)cdiv(nvec * n, 256), 256, 0, s>>>(
-      part, (int)nbr, n, nvec, d_mu ? 2 : 0, d_mu, 0.0, v, n, y, nullptr);
+      part, (int)nbr, n, nvec, d_mu ? 2 : 0, d_mu, 0.0, v, n, y, skip);
   count_launch();
   NYS_CUDA_TRY(cudaGetLastError());
   return NYS_OK;
 }
 
 }  // namespace
-
-// y_q = (K + mu_q I) v_q for q < nvec (device FP64 arrays), FP64-accurate.
-// Up to 4 vectors take the symmetric products (each entry once); more take
-// the row-block products.
-int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_t nvec,
-                              const double* v, double* y, cudaStream_t s) {
-  if (op->kind != NYS_OP_RBF || op->d > RR_DMAX) return NYS_ERR_ARG;
-  const float* pts = (const float*)op->data;
-  const int64_t n = op->n, d = op->d, ld = op->ld;
-  if (nvec == 1) {
-    if (d <= 16) return sym_go<16, 2, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
-    if (d <= 32) return sym_go<32, 2, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
-    return sym_go<64, 1, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
-  }
-  if (nvec <= 4) {
-    if (d <= 16) return sym_go<16, 2, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
-    if (d <= 32) return sym_go<32, 2, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
-    return sym_go<64, 1, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, s);
-  }
-  return rbf_dfl_products(pts, n, ld, pts, n, ld, d, op->sigma, 0, d_mu, nvec, v, y, s);
-}
 
 namespace {
 
@@ -781,6 +761,29 @@ int32_t rbf_exact_products(const float* tg, int64_t nt, int64_t ldt, const float
                            const int* skip, cudaStream_t s) {
   return products(true, tg, nt, ldt, pts, n, ldp, d, sigma, kind, shift, d_mu, mu0, nvec, v, y,
                   skip, s);
+}
+
+// y_q = (K + mu_q I) v_q for q < nvec (device FP64 arrays), FP64-accurate.
+// Up to 4 vectors take the symmetric products (each entry once); more take
+// the row-block products.  skip (device, may be NULL): nothing is computed
+// while *skip is nonzero.
+int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_t nvec,
+                              const double* v, double* y, cudaStream_t s, const int* skip) {
+  if (op->kind != NYS_OP_RBF || op->d > RR_DMAX) return NYS_ERR_ARG;
+  const float* pts = (const float*)op->data;
+  const int64_t n = op->n, d = op->d, ld = op->ld;
+  if (nvec == 1) {
+    if (d <= 16) return sym_go<16, 2, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+    if (d <= 32) return sym_go<32, 2, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+    return sym_go<64, 1, 1>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+  }
+  if (nvec <= 4) {
+    if (d <= 16) return sym_go<16, 2, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+    if (d <= 32) return sym_go<32, 2, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+    return sym_go<64, 1, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+  }
+  return products(false, pts, n, ld, pts, n, ld, d, op->sigma, 0, d_mu ? 2 : 0, d_mu, 0.0, nvec,
+                  v, y, skip, s);
 }
 
 }  // namespace nys

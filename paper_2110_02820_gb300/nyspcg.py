@@ -57,7 +57,7 @@ class _PcgOpts(C.Structure):
 
 class _PcgResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("refinements", C.c_int32),
-                ("reserved", C.c_int32), ("rel_residual", C.c_double)]
+                ("escalated", C.c_int32), ("rel_residual", C.c_double)]
 
 
 _lib = None
@@ -528,3 +528,84 @@ def nys_rbf_cross_matvec(targets: torch.Tensor, points: torch.Tensor, sigma: flo
                                       points.stride(0), d, float(sigma), vv.shape[0], _ptr(vv),
                                       _ptr(out), kind, _stream()), "nys_rbf_cross_matvec")
     return out if v.dim() == 2 else out[0]
+
+
+# stream identifiers of the library's own draws (NYS_STREAM_* in the header)
+NYS_STREAM_OMEGA = 0x4F6D656761
+NYS_STREAM_ADAPTIVE = 0x4164610000
+NYS_STREAM_ESTIMATE = 0x4573740000
+
+
+def nys_philox4x32_10(ctr: torch.Tensor, key: torch.Tensor) -> torch.Tensor:
+    """Philox4x32-10 blocks: ctr [count, 4] and key [count, 2] int32 CUDA
+    tensors holding uint32 bit patterns; returns [count, 4] int32 (bits)."""
+    f = lib().nys_philox4x32_10
+    if f.argtypes is None:
+        f.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        f.restype = C.c_int32
+    if ctr.dtype != torch.int32 or key.dtype != torch.int32:
+        raise ValueError("ctr and key must be int32 tensors of uint32 bit patterns")
+    ctr, key = ctr.contiguous(), key.contiguous()
+    count = ctr.shape[0]
+    assert ctr.shape == (count, 4) and key.shape == (count, 2)
+    out = torch.empty((count, 4), dtype=torch.int32, device=ctr.device)
+    _check(f(_ptr(ctr), _ptr(key), count, _ptr(out), _stream()), "nys_philox4x32_10")
+    return out
+
+
+def nys_random_stream(seed: int, stream_id: int, first: int, count: int, words: bool = True,
+                      gauss: bool = True, device=None):
+    """Elements [first, first + count) of the library's random stream: the raw
+    words (int32 tensor of uint32 bit patterns) and the Box-Muller values
+    (float64 tensor); either is None when not asked for."""
+    f = lib().nys_random_stream
+    if f.argtypes is None:
+        f.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                      C.c_void_p]
+        f.restype = C.c_int32
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    w = torch.empty(count, dtype=torch.int32, device=dev) if words else None
+    g = torch.empty(count, dtype=torch.float64, device=dev) if gauss else None
+    _check(f(seed, stream_id, first, count, _ptr(w), _ptr(g), _stream()), "nys_random_stream")
+    return w, g
+
+
+def nys_krr_validation(points: torch.Tensor, vpoints: torch.Tensor, sigma: float,
+                       alpha: torch.Tensor, yv: torch.Tensor):
+    """KRR validation objective: returns (loss, g, ktg) with loss the mean
+    squared error of K_v alpha against yv (host float), g = dL/dpred and
+    ktg = K_v^T g (FP64 CUDA tensors)."""
+    f = lib().nys_krr_validation
+    if f.argtypes is None:
+        vp, i64 = C.c_void_p, C.c_int64
+        f.argtypes = [vp, i64, i64, vp, i64, i64, i64, C.c_double, vp, vp, C.POINTER(C.c_double),
+                      vp, vp, vp]
+        f.restype = C.c_int32
+    n, d = points.shape
+    m = vpoints.shape[0]
+    g = torch.empty(m, dtype=torch.float64, device=alpha.device)
+    ktg = torch.empty(n, dtype=torch.float64, device=alpha.device)
+    loss = C.c_double()
+    _check(f(_ptr(points), n, points.stride(0), _ptr(vpoints), m, vpoints.stride(0), d,
+             float(sigma), _ptr(alpha), _ptr(yv), C.byref(loss), _ptr(g), _ptr(ktg), _stream()),
+           "nys_krr_validation")
+    return loss.value, g, ktg
+
+
+def nys_krr_gradients(points: torch.Tensor, vpoints: torch.Tensor | None, sigma: float,
+                      alpha: torch.Tensor, lam: torch.Tensor, g: torch.Tensor | None):
+    """(dL/dmu, dL/dsigma) of the KRR objective from the training solution
+    alpha and the adjoint solution lam (see nys_krr_gradients in the header)."""
+    f = lib().nys_krr_gradients
+    if f.argtypes is None:
+        vp, i64 = C.c_void_p, C.c_int64
+        f.argtypes = [vp, i64, i64, vp, i64, i64, i64, C.c_double, vp, vp, vp,
+                      C.POINTER(C.c_double), vp]
+        f.restype = C.c_int32
+    n, d = points.shape
+    m = vpoints.shape[0] if vpoints is not None else 0
+    ldv = vpoints.stride(0) if vpoints is not None else 0
+    out = (C.c_double * 2)()
+    _check(f(_ptr(points), n, points.stride(0), _ptr(vpoints), m, ldv, d, float(sigma),
+             _ptr(alpha), _ptr(lam), _ptr(g), out, _stream()), "nys_krr_gradients")
+    return out[0], out[1]

@@ -130,7 +130,10 @@ def test_sketch_exact_recovery_on_gpu(ny):
     assert np.all(lam[r:] <= 1e-10)
 
 
-def test_sketch_generated_omega_is_gaussian_and_seeded(ny):
+def test_sketch_generated_omega_is_seeded_and_interlaces(ny):
+    # the drawn Omega itself is compared with the oracle's generator in
+    # test_gpu_philox.py; here: same seed, same factor; another seed, another
+    # factor; lambda_hat_j <= lambda_j (Lemma 2.1) for the drawn Omega
     n, ell = 500, 20
     A, _ = wl.dense_spd(n, seed=1)
     op = ny.dense_operator(T(A))
@@ -267,6 +270,30 @@ def test_pcg_integer_case_iteration_count_identical(ny):
     ref = opcg.nys_pcg(lambda v: A @ v, 1.0, b, None, lambda r: r.copy(), 1e-10, 50)
     assert res[0].iterations == ref["iterations"]
     assert relerr(x.cpu().numpy(), ref["x"]) <= 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n,ell,rank", [(8, 3, None), (12, 4, 6), (16, 5, None)])
+def test_pcg_integer_case_nystrom_iteration_counts_identical(ny, seed, n, ell, rank):
+    # integer-valued A = G^T G, b and raw Omega: Algorithm 1's factor and
+    # Algorithm 3 with the Eq. (5.3) preconditioner give the oracle's
+    # iteration count exactly (finite termination leaves the residual far
+    # from the stopping threshold at every step but the last)
+    mu = 1.0
+    A = wl.integer_spd(n, seed=seed, rank=rank)
+    b = wl.integer_vector(n, seed=seed)
+    Om = wl.integer_omega(n, ell, seed=seed)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(Om))
+    x, res, _ = ny.pcg_solve(op, f, mu, T(b), tol=1e-10)
+    o = onys.rand_nystrom(lambda V: A @ V, Om)
+    ref = opcg.nys_pcg(lambda v: A @ v, mu, b, None,
+                       lambda r: onys.precond_inverse_apply(o["U"], o["lam"], mu, r), 1e-10, 50)
+    assert res[0].status == ny.NYS_OK and ref["status"] == opcg.CONVERGED
+    assert res[0].iterations == ref["iterations"], (res[0].iterations, ref["iterations"])
+    assert res[0].iterations <= n
+    assert relerr(x.cpu().numpy(), ref["x"]) <= 1e-10
+    assert np.abs(f.lam().cpu().numpy() - o["lam"]).max() <= 1e-10 * o["lam"][0]
 
 
 def test_pcg_plain_cg_and_maxit(ny):
@@ -422,13 +449,18 @@ def test_pcg_rbf_mixed_refinement(ny):
     assert relerr(x.cpu().numpy(), xs) <= 1e-5
 
 
-def test_batched_rbf_regularization_path(ny):
-    # 8 shifts log-spaced in [1e-6, 1e-1] n times 4 right-hand sides = 32 systems
-    # sharing one factor; the batched FP32 kernel matvec serves all of them.
-    n, d, ell = 2000, 16, 200
+@pytest.mark.parametrize("n,ell", [(2000, 400), (3001, 512)])
+def test_batched_rbf_regularization_path(ny, n, ell):
+    # the regularisation-path recipe over its full range: 8 shifts log-spaced
+    # in [1e-8, 1e-1] n times 4 right-hand sides = 32 systems sharing one
+    # factor; the batched FP32 kernel matvec serves all of them.  At the
+    # smallest shifts the FP32 products' error is comparable to mu, so those
+    # systems escalate to FP64-accurate inner solves; every system must reach
+    # 1e-8 and match the direct solution.
+    d = 16
     P = wl.gmm_points(n, d, seed=41)
     sigma = wl.median_distance(P, seed=41)
-    mus = np.repeat(wl.regularization_path(8, 1e-6 * n, 1e-1 * n), 4)
+    mus = np.repeat(wl.regularization_path(8, 1e-8 * n, 1e-1 * n), 4)
     B = wl.rhs(n, seed=41, nrhs=4)
     B = np.tile(B, (8, 1))
     op = ny.rbf_operator(T(P), sigma)
@@ -436,12 +468,49 @@ def test_batched_rbf_regularization_path(ny):
     X, res, _ = ny.pcg_solve(op, f, list(mus), T(B), tol=1e-8, precision=ny.NYS_PREC_MIXED)
     K = oops.rbf_block(P, P, sigma)
     Xg = X.cpu().numpy()
-    for s in [0, 5, 13, 22, 31]:
-        assert res[s].status == ny.NYS_OK, (s, res[s])
-        xs = opcg.direct_solve(K, mus[s], B[s])
-        assert relerr(Xg[s], xs) <= 1e-5
+    for s in range(len(mus)):
+        assert res[s].status == ny.NYS_OK, (s, mus[s], res[s])
+        assert res[s].rel_residual <= 1e-8
+    for m in range(8):
+        xs = opcg.direct_solve(K, mus[4 * m], B[4 * m:4 * m + 4].T).T
+        for j in range(4):
+            assert relerr(Xg[4 * m + j], xs[j]) <= 1e-5, (m, j)
+    # the largest shifts stay on FP32 inner solves, the smallest escalate
+    assert not any(r.escalated for r in res[-8:])
+    assert all(r.escalated for r in res[:4])
     # systems converge unevenly: larger shifts need fewer iterations
     assert res[31].iterations < res[0].iterations
+
+
+def test_kernel_ridge_recipe_n5000_matches_oracle(ny):
+    # the kernel-ridge workload (Sec. 6.5 recipe: 10-component Gaussian
+    # mixture in d = 32, sigma = median pairwise distance, shift 1e-6 n) at a
+    # seeded n = 5000 subsample: Strategy 2 (ratio rule lambda_ell / mu <= 40,
+    # Sec. 5.4.2) from ell0 = 128 up to 2048 in mixed precision, then PCG with
+    # FP64-residual refinement to 1e-8, against the oracle's Algorithm 5 on the
+    # same Omega and its direct solve
+    n, d, ell0, ell_max = 5000, 32, 128, 2048
+    P = wl.gmm_points(n, d, seed=0)
+    sigma = wl.median_distance(P, seed=0)
+    mu = 1e-6 * n
+    b = wl.rhs(n, seed=0)
+    Om = wl.omega(n, ell_max, 50)
+    op = ny.rbf_operator(T(P), sigma)
+    f, info = ny.nys_sketch_adaptive(op, ell0, ell_max, ny.NYS_RULE_RATIO, 40.0, 0, mu,
+                                     omega=T(Om), precision=ny.NYS_PREC_MIXED)
+    K = oops.rbf_block(P, P, sigma)
+    o = onys.adaptive_nystrom(lambda V: K @ V, n, ell0, ell_max, 40.0, 0, Om, None, rule="ratio",
+                              mu=mu, mantissa_bits=23)
+    assert info.ell == o["ell"] and info.doublings == o["doublings"]
+    lam = f.lam().cpu().numpy()
+    assert np.abs(lam - o["lam"]).max() <= 1e-5 * o["lam"][0]
+    x, res, _ = ny.pcg_solve(op, f, mu, T(b), tol=1e-8, precision=ny.NYS_PREC_MIXED)
+    assert res[0].status == ny.NYS_OK and res[0].rel_residual <= 1e-8, res
+    xs = opcg.direct_solve(K, mu, b)
+    assert relerr(x.cpu().numpy(), xs) <= 1e-5
+    # the true residual of the returned x, recomputed in FP64 on the CPU
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(b - (K @ xg + mu * xg)) <= 1.5e-8 * np.linalg.norm(b)
 
 
 # ---------------------------------------------------------------- Algorithms 4 and 5
