@@ -220,6 +220,36 @@ def test_precond_times_inverse_is_identity_and_spd():
         assert np.linalg.eigvalsh(Pinv).min() > 0
 
 
+def test_float32_precond_apply_exact_case_equals_fp64():
+    # U with entries +-1/2 (columns of a 4 x 4 Hadamard matrix over 2), small
+    # integer v and shifts for which every coefficient (lam_ell + mu) / (lam + mu)
+    # - 1 is a dyadic number: the float32 emulation is exact and must equal the
+    # FP64 Eq. (5.3) bit for bit
+    H = 0.5 * np.array([[1, 1, 1, 1], [1, -1, 1, -1], [1, 1, -1, -1], [1, -1, -1, 1]], float)
+    U = H[:, :2]
+    lam = np.array([7.0, 3.0])
+    mu = 1.0
+    v = np.array([3.0, -1.0, 2.0, 5.0])
+    z32 = ny.precond_inverse_apply_f32(U.astype(np.float32), lam, mu, v.astype(np.float32))
+    z64 = ny.precond_inverse_apply(U, lam, mu, v)
+    assert np.array_equal(z32.astype(np.float64), z64)
+    # and the closed form: P^{-1} u_1 = (lam_2 + mu)/(lam_1 + mu) u_1 = u_1 / 2
+    z = ny.precond_inverse_apply_f32(U.astype(np.float32), lam, mu, U[:, 0].astype(np.float32))
+    assert np.array_equal(z.astype(np.float64), 0.5 * U[:, 0])
+
+
+def test_float32_precond_apply_matches_fp64_to_float32_rounding():
+    rs = np.random.default_rng(3)
+    n, ell, mu = 300, 12, 1e-2
+    U = np.linalg.qr(rs.standard_normal((n, ell)))[0]
+    lam = np.sort(rs.uniform(0.1, 10.0, ell))[::-1]
+    U32 = U.astype(np.float32)
+    v32 = rs.standard_normal(n).astype(np.float32)
+    z32 = ny.precond_inverse_apply_f32(U32, lam, mu, v32)
+    z64 = ny.precond_inverse_apply(U32.astype(np.float64), lam, mu, v32.astype(np.float64))
+    assert np.linalg.norm(z32 - z64) <= 1e-6 * np.linalg.norm(z64)
+
+
 def test_preconditioned_condition_number_with_exact_eigenpairs():
     # With U, Lam the exact top-ell eigenpairs, P^{-1} A_mu has eigenvalues
     # lam_ell + mu (on range U) and lam_j + mu (j > ell): kappa = (lam_ell+mu)/(lam_n+mu).
