@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 M, N, ELL, MU, TOL = 200_000, 4096, 512, 1e-3, 1e-8
+RATED_HBM_GBS = 7900.0  # GB300 HBM3e, rated
 INNER_TOL = 1e-4
 SEED = 0
 
@@ -50,6 +51,9 @@ def parse():
     ap.add_argument("--ell", type=int, default=ELL)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the dense, kernel-ridge, regularisation-path and adjoint "
+                         "records that follow the headline")
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no matvec, launch-count, e2e or CPU legs); "
                          "used for profiler launch lists")
@@ -374,14 +378,12 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = []
     launches0 = ny.kernel_launch_count()
-    ny.timing_start(8192)  # CUDA events around each FP32 ridge matvec of the timed solves
     ev0.record()
     for k in range(args.steps):
         x, res = solve_once(ny, op, b, ell, seed=k)
         iters.append((res.iterations, res.refinements, res.rel_residual, res.status))
     ev1.record()
     torch.cuda.synchronize()
-    mv_total_ms, mv_count = ny.timing_stop()
     launches_timed = ny.kernel_launch_count() - launches0
     barrier(world)
     clk = clocks.stop()
@@ -400,7 +402,13 @@ def run_ours(args):
         return
 
     # dominant kernel: the fused ridge matvec (gram_fused_kernel + its fixed-order
-    # reduction), its average duration over the matvecs of the timed solves
+    # reduction), its average duration over the products of two more solves run
+    # with CUDA events around each product (kept out of the timed region)
+    ny.timing_start(8192)
+    for k in range(2):
+        solve_once(ny, op, b, ell, seed=k)
+    torch.cuda.synchronize()
+    mv_total_ms, mv_count = ny.timing_stop()
     mv_ms = mv_total_ms / max(mv_count, 1)
     bytes_mv = float(m) * n * 4  # X read once per matvec
     achieved = bytes_mv / (mv_ms * 1e-3) / 1e9
@@ -424,6 +432,22 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(m, n, ell, max(2000, m // 4))
 
+    # the other workloads, one record each (one GPU, rank 0 only): the dense
+    # FP64 solve, kernel ridge regression, the batched regularisation path and
+    # the differentiable-KRR step, each with its dominant kernel's roofline
+    peaks, legs = None, None
+    if rank == 0 and world == 1 and not args.no_legs:
+        del Xd, op
+        torch.cuda.empty_cache()
+        peaks = measured_peaks(ny)
+        legs = {}
+        for name, st, wu in [("dense", 5, 3), ("krr", 2, 1), ("batched", 1, 1), ("adjoint", 1, 1)]:
+            try:
+                legs[name] = workload_record(args, name, st, wu, peaks)
+            except Exception as e:  # one workload failing does not hide the others
+                legs[name] = {"workload": name, "error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+
     if rank == 0:
         line = {
             "metric": "PCG solves/sec to rel-residual 1e-8 and kernel-matvec TFLOP/s vs roofline, 1xGB300",
@@ -436,6 +460,9 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "gram_fused_kernel (+reduce)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
+                         "peak_note": "peak = measured copy (read + write) bandwidth; this "
+                                      "kernel only reads X, so frac can exceed 1",
+                         "rated_peak": RATED_HBM_GBS, "frac_of_rated": achieved / RATED_HBM_GBS,
                          "traffic": measured_traffic() if (m, n) == (M, N) else None,
                          "bytes_per_launch": bytes_mv, "ms_per_launch": mv_ms,
                          "launches_timed": int(mv_count)},
@@ -447,6 +474,8 @@ def run_ours(args):
             "solve": {"inner_iterations": iters[-1][0], "refinements": iters[-1][1],
                       "rel_residual": iters[-1][2], "status": iters[-1][3]},
             "phases_ms": phases,
+            "configs": legs,
+            "unit_peaks": peaks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -512,51 +541,121 @@ def _events_ms(fn, reps):
     return e0.elapsed_time(e1) / reps, out
 
 
-def run_workload(args):
-    """One JSON line for a non-default workload (solves/sec, per-phase times,
-    the dominant kernel's throughput).  Inputs are resident on the device."""
+def _events_steps(fn, reps, flush=None):
+    """Mean ms per call of fn over reps calls, CUDA events on the current
+    stream; `flush` (if given) runs between calls, outside the timed spans."""
+    import torch
+    tot, out = 0.0, None
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps, out
+
+
+class L2Flush:
+    """Writes a buffer twice the size of L2 (129 MB on GB300) between timed
+    steps whose inputs fit in L2."""
+
+    def __init__(self, device):
+        import torch
+        self.buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB
+
+    def __call__(self):
+        self.buf.fill_(1.0)
+
+
+def measured_peaks(ny):
+    """Denominators of the roofline fractions: HBM copy bandwidth and BF16
+    tensor rate from MEASURED_PEAKS.json (TF32 = BF16 x the nominal 1.1/2.25
+    ratio), and the FP64 FMA, FP32 FMA and MUFU ex2 rates measured here by the
+    library's unit probes."""
+    p = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        j = json.load(open(path))
+        p.update(hbm_gbs=j["hbm_gbs"], bf16_tflops=j["bf16_tflops"],
+                 bf16_tflops_sustained=j.get("bf16_tflops_sustained"), source="measured")
+    else:
+        p.update(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0,
+                 source="fallback")
+    p["tf32_tflops"] = p["bf16_tflops"] * 1.1 / 2.25
+    p["tf32_tflops_sustained"] = (p["bf16_tflops_sustained"] or p["bf16_tflops"]) * 1.1 / 2.25
+    p["fp64_fma_tflops"] = ny.nys_unit_peak(ny.UNIT_FP64_FMA) / 1e12
+    p["fp32_fma_tflops"] = ny.nys_unit_peak(ny.UNIT_FP32_FMA) / 1e12
+    p["mufu_ex2_gops"] = ny.nys_unit_peak(ny.UNIT_MUFU_EX2) / 1e9
+    return p
+
+
+def workload_record(args, name, steps, warmup, peaks=None):
+    """One record (dict) for the workload `name`: solves/sec (or converged
+    systems/sec), per-phase times and the dominant kernel against its
+    roofline.  Inputs are resident on the device; between timed steps whose
+    inputs fit in L2 a 256 MB buffer is written."""
     import torch
 
     from paper_2110_02820_gb300 import nyspcg as ny
     from paper_2110_02820_gb300 import workloads as wl
     ny.pcg_graphs(args.pcg_launch == "graph")
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)  # noqa: E731
-    line = {"metric": "PCG solves/sec to rel-residual target", "unit": "solves/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "data": "synthetic", "workload": args.workload}
-    launches0 = ny.kernel_launch_count()
-    if args.workload == "dense":
+    flush = L2Flush(dev)
+    line = {"metric": "PCG solves/sec to rel-residual target", "unit": "solves/s",
+            "steps": steps, "warmup": warmup, "higher_is_better": True,
+            "data": "synthetic", "workload": name, "l2": "256 MB written between timed steps"}
+    clocks = ClockSampler(torch.cuda.current_device())
+    if name == "dense":
         n, ell, mu, tol = 2048, 64, 1e-4, 1e-10
         A, _ = wl.dense_spd(n, seed=0)
         b = T(wl.rhs(n, seed=0))
         op = ny.dense_operator(T(A))
 
+        phase = {}
+
         def step(seed):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
             f = ny.nys_sketch(op, ell, seed=seed)
+            e1.record()
             x, res, _ = ny.pcg_solve(op, f, mu, b, tol=tol)
+            e2.record()
+            torch.cuda.synchronize()
+            phase["sketch_ms"], phase["pcg_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
             f.free()
             return res[0]
-        for w in range(args.warmup):
+        for w in range(warmup):
             step(100 + w)
+        clocks.start()
         launches0 = ny.kernel_launch_count()
         # CUDA events around every dense product of the timed solves (recorded
         # on the launching stream, inside the PCG graph as event nodes)
         ny.timing_start(65536)
-        ms, res = _events_ms(lambda: step(7), args.steps)
+        ms, res = _events_steps(lambda: step(7), steps, flush)
         mv_total, mv_cnt = ny.timing_stop()
         mv_ms = mv_total / max(mv_cnt, 1)
         line["solve"] = {"iterations": res.iterations, "rel_residual": res.rel_residual,
                          "status": res.status}
+        line["phases_ms"] = dict(phase)
+        gfl = 2 * n * n / (mv_ms * 1e6)
         line.update({"dtype": "f64", "config": {"workload": f"dense FP64 n={n}, lambda_i=(i+1)^-1.5, "
                                                             f"mu={mu}, ell={ell}, tol={tol}"},
                      "dominant_kernel": {"kernel": "dense_matvec_kernel<double>",
                                          "ms_per_launch": mv_ms, "launches_timed": int(mv_cnt),
-                                         "gflops_fp64": 2 * n * n / (mv_ms * 1e6),
-                                         "l2_resident_bytes": n * n * 8}})
-    elif args.workload in ("krr", "batched"):
-        if args.workload == "krr":
+                                         "gflops_fp64": gfl, "l2_resident_bytes": n * n * 8}})
+        if peaks:
+            line["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": gfl / 1e3,
+                                "peak": peaks["fp64_fma_tflops"],
+                                "frac": gfl / 1e3 / peaks["fp64_fma_tflops"],
+                                "work": "2 n^2 FP64 FLOP per product (A read from L2)",
+                                "peak_source": "FP64 FMA pipe measured by nys_unit_peak"}
+    elif name in ("krr", "batched"):
+        if name == "krr":
             n, d, ell0, ell_max = int(100000 * args.scale), 32, 128, 2048
         else:
             n, d, ell = int(50000 * args.scale), 16, 1024
@@ -564,11 +663,10 @@ def run_workload(args):
         sigma = wl.median_distance(P, seed=0)
         op = ny.rbf_operator(T(P), sigma)
         prec = ny.NYS_PREC_F64 if args.precision == "f64" else ny.NYS_PREC_MIXED
-        if args.workload == "krr":
+        phase = {}
+        if name == "krr":
             mu, tol = 1e-6 * n, 1e-8
             b = T(wl.rhs(n, seed=0))
-
-            phase = {}
 
             def step(seed):
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -596,8 +694,6 @@ def run_workload(args):
             B = T(np.tile(wl.rhs(n, seed=0, nrhs=4), (32, 1)))
             tol = 1e-8
 
-            phase = {}
-
             def step(seed):
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record()
@@ -612,14 +708,15 @@ def run_workload(args):
             cfg = (f"batched regularisation path n={n} d={d}, 32 shifts log-spaced in "
                    f"[1e-8, 1e-1] n x 4 rhs = 128 systems, ell={ell}, {args.precision}, "
                    f"tol {tol} each")
-        for w in range(args.warmup):
+        for w in range(warmup):
             step(100 + w)
+        clocks.start()
         launches0 = ny.kernel_launch_count()
         ny.timing_start(65536)
-        ms, (res, info) = _events_ms(lambda: step(7), args.steps)
+        ms, (res, info) = _events_steps(lambda: step(7), steps, flush)
         mv_total, mv_cnt = ny.timing_stop()
         mv_ms = mv_total / max(mv_cnt, 1)
-        kern = ("rbf_gemv_kernel (tensor-core distances, one vector)" if args.workload == "krr"
+        kern = ("rbf_gemv_kernel (tensor-core distances, one vector)" if name == "krr"
                 else "rbf_tc_kernel<64,3> (tensor cores, 64 systems per CTA)")
         if args.precision == "f64":
             kern = "rbf_products_kernel (FP64 entries and sums; not event-timed)"
@@ -629,25 +726,50 @@ def run_workload(args):
                                          "launches_timed": mv_cnt,
                                          "kernel_entries_per_s":
                                              n * n / (mv_ms * 1e-3) if mv_ms > 0 else None}})
-        if args.workload == "krr":
+        if name == "krr":
             line["solve"] = {"iterations": res.iterations, "refinements": res.refinements,
                              "rel_residual": res.rel_residual, "status": res.status,
+                             "escalated": res.escalated,
                              "ell": info.ell if info else args.cols,
                              "doublings": info.doublings if info else None,
                              "lambda_ell": info.lambda_ell if info else None}
+            if peaks and mv_ms > 0 and args.precision != "f64":
+                eps = n * n / (mv_ms * 1e-3) / 1e9
+                line["roofline"] = {"bound": "alu", "unit": "Gop/s (ex2)", "achieved": eps,
+                                    "peak": peaks["mufu_ex2_gops"],
+                                    "frac": eps / peaks["mufu_ex2_gops"],
+                                    "work": "one MUFU ex2 per kernel entry, n^2 entries per product",
+                                    "peak_source": "MUFU ex2 rate measured by nys_unit_peak"}
         else:
             its = [r.iterations for r in res]
             ok = [r.status == 0 for r in res]
-            # systems that reach the target; the smallest shifts (1e-8 n) need more
-            # than the 500-iteration cap at ell = 1024 in any precision
             line["solve"] = {"systems": len(res), "converged": int(sum(ok)),
+                             "escalated": int(sum(r.escalated for r in res)),
                              "iterations_min": min(its), "iterations_max": max(its),
                              "worst_rel_residual_converged":
                                  max([r.rel_residual for r in res if r.status == 0] or [None]),
                              "status_by_mu": [[float(m), r.status, r.iterations, r.rel_residual]
                                               for m, r in list(zip(mus, res))[::4]]}
+            if peaks and args.precision != "f64":
+                # the full 128-vector product alone (3xTF32 passes on the TF32 pipe)
+                V = T(np.tile(wl.rhs(n, seed=1, nrhs=4), (32, 1)))
+                ny.nys_op_matvec(op, 1e-6 * n, V, mode=1)
+                pms, _ = _events_steps(lambda: ny.nys_op_matvec(op, 1e-6 * n, V, mode=1), 3)
+                alg = 2.0 * n * n * (V.shape[0] + d)
+                exe = 3.0 * 2.0 * n * n * (V.shape[0] + 2 * d)
+                line["roofline"] = {"bound": "tensor", "unit": "TFLOP/s",
+                                    "achieved": alg / (pms * 1e-3) / 1e12,
+                                    "peak": peaks["tf32_tflops"],
+                                    "frac": alg / (pms * 1e-3) / 1e12 / peaks["tf32_tflops"],
+                                    "executed_tflops": exe / (pms * 1e-3) / 1e12,
+                                    "tensor_pipe_frac": exe / (pms * 1e-3) / 1e12 / peaks["tf32_tflops"],
+                                    "ms_per_launch": pms,
+                                    "work": "algorithmic 2 n^2 (nvec + d) FLOP for 128 vectors; "
+                                            "executed = 3 TF32 passes of the distance GEMM per "
+                                            "64-vector group and of the kernel-times-vectors GEMM",
+                                    "peak_source": "TF32 = measured BF16 x 1.1/2.25 (nominal ratio)"}
         line["phases_ms"] = dict(phase)
-    elif args.workload == "block":
+    elif name == "block":
         # block Nystrom PCG: nrhs right-hand sides of one shifted Gaussian-kernel
         # system, against the same systems solved as independent recurrences
         n, d, ell, nrhs = int(50000 * args.scale), 16, args.block_ell, args.nrhs
@@ -669,13 +791,14 @@ def run_workload(args):
             phase["sketch_ms"], phase["block_pcg_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
             f.free()
             return res, None
-        for w in range(args.warmup):
+        for w in range(warmup):
             step(100 + w)
+        clocks.start()
         launches0 = ny.kernel_launch_count()
-        ms, (res, _) = _events_ms(lambda: step(7), args.steps)
+        ms, (res, _) = _events_steps(lambda: step(7), steps, flush)
         # the same systems as independent recurrences (one kernel pass per step for all)
         f = ny.nys_sketch(op, ell, seed=7, precision=ny.NYS_PREC_MIXED)
-        ind_ms, (xi, ri, _) = _events_ms(
+        ind_ms, (xi, ri, _) = _events_steps(
             lambda: ny.pcg_solve(op, f, [mu] * nrhs, B, tol=tol, precision=ny.NYS_PREC_MIXED), 1)
         f.free()
         ok = [r.status == 0 for r in res]
@@ -691,7 +814,7 @@ def run_workload(args):
                                      "iterations_max": max(r.iterations for r in ri),
                                      "converged": int(sum(r.status == 0 for r in ri))},
                      "phases_ms": dict(phase)})
-    elif args.workload == "path":
+    elif name == "path":
         # regularization path on the ridge operator: decreasing shifts, warm
         # starts, factor reuse (err_factor 30, q 5), mixed precision
         X, y = make_inputs(args.m, args.n)
@@ -705,12 +828,13 @@ def run_workload(args):
             Xs, out = ny.nys_reg_path(op, mus, b, ell0, ell_max, 30.0, 5, seed=seed, tol=tol,
                                       precision=ny.NYS_PREC_MIXED)
             return out, None
-        for w in range(args.warmup):
+        for w in range(warmup):
             step(100 + w)
+        clocks.start()
         launches0 = ny.kernel_launch_count()
-        ms, (out, _) = _events_ms(lambda: step(7), args.steps)
+        ms, (out, _) = _events_steps(lambda: step(7), steps)
         ok = [o["status"] == 0 for o in out]
-        line.update({"dtype": "f32",
+        line.update({"dtype": "f32", "l2": "inputs larger than L2 (X 3.3 GB)",
                      "config": {"workload": f"regularization path, ridge {args.m}x{args.n}, "
                                             f"mu = 10..1e-3 (5 shifts, decreasing), warm starts, "
                                             f"factor kept while estimate <= 30 mu, ell {ell0}->"
@@ -745,28 +869,57 @@ def run_workload(args):
             torch.cuda.synchronize()
             phase["forward_ms"], phase["backward_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
             return float(L.detach()), float(m.grad), float(sg.grad)
-        for w in range(args.warmup):
+        for w in range(warmup):
             step(100 + w)
+        clocks.start()
         launches0 = ny.kernel_launch_count()
-        ms, out = _events_ms(lambda: step(7), args.steps)
+        ny.timing_start(65536)
+        ms, out = _events_steps(lambda: step(7), steps, flush)
+        mv_total, mv_cnt = ny.timing_stop()
+        mv_ms = mv_total / max(mv_cnt, 1)
         line.update({"dtype": "f64" if args.precision == "f64" else "f32",
                      "config": {"workload": f"differentiable KRR n_train={n} n_val={nv} d={d} "
-                                            f"ell={ell} {args.precision}"},
+                                            f"ell={ell} {args.precision}, loss + dL/dmu + dL/dsigma"},
                      "solve": {"loss": out[0], "dL_dmu": out[1], "dL_dsigma": out[2]},
+                     "dominant_kernel": {"kernel": "rbf_gemv_kernel (one vector, inside the "
+                                                   "forward and adjoint solves)",
+                                         "ms_per_launch": mv_ms, "launches_timed": mv_cnt},
                      "phases_ms": dict(phase)})
+        if peaks and mv_ms > 0 and args.precision != "f64":
+            eps = n * n / (mv_ms * 1e-3) / 1e9
+            line["roofline"] = {"bound": "alu", "unit": "Gop/s (ex2)", "achieved": eps,
+                                "peak": peaks["mufu_ex2_gops"],
+                                "frac": eps / peaks["mufu_ex2_gops"],
+                                "work": "one MUFU ex2 per kernel entry, n^2 entries per product",
+                                "peak_source": "MUFU ex2 rate measured by nys_unit_peak"}
+    line["clocks"] = clocks.stop()
     sol = line.get("solve", {})
-    if args.workload in ("batched", "block", "path"):
+    if name in ("batched", "block", "path"):
         line["metric"] = "converged PCG systems/sec (rel-residual 1e-8 each)"
         line["unit"] = "systems/s"
         line["value_note"] = "value = converged systems / solve time"
-    if sol.get("status", 0) != 0 or sol.get("converged", 1) == 0:
-        sys.stderr.write(f"bench: the {args.workload} solve did not converge: {sol}\n")
-        sys.exit(3)
+    line["converged"] = not (sol.get("status", 0) != 0 or
+                             sol.get("converged", sol.get("systems", 1)) != sol.get("systems", 1))
     line["ms_per_step"] = ms
-    line["value"] = (sol["converged"] if args.workload in ("batched", "block", "path")
-                     else 1) * 1e3 / ms
+    line["value"] = (sol["converged"] if name in ("batched", "block", "path") else 1) * 1e3 / ms
     line["gpu_launches"] = int(ny.kernel_launch_count() - launches0)
     line["pcg_launch"] = args.pcg_launch
+    return line
+
+
+def run_workload(args):
+    """One JSON line for a non-default workload."""
+    import torch
+
+    from paper_2110_02820_gb300 import nyspcg as ny
+    torch.cuda.set_device(0)
+    peaks = measured_peaks(ny)
+    line = workload_record(args, args.workload, args.steps, args.warmup, peaks)
+    line["n_gpus"] = 1
+    line["unit_peaks"] = peaks
+    if not line["converged"] and line.get("solve", {}).get("converged", 1) == 0:
+        sys.stderr.write(f"bench: the {args.workload} solve did not converge: {line['solve']}\n")
+        sys.exit(3)
     print(json.dumps(line), flush=True)
 
 

@@ -297,6 +297,28 @@ uint64_t nys_kernel_launch_count(void);
  * Process-wide; set it between solves, not during one. */
 int32_t nys_pcg_graphs(int32_t on);
 
+/* Mixed-precision solves of ONE system with a dense or ridge operator (no
+ * counterpart in the paper; Gaussian-kernel systems always take the
+ * refinement loop).  With `on` = 1 (the default, unless the environment sets
+ * NYS_PCG_RELIABLE=0 before the first solve) pcg_solve runs a single FP32
+ * recurrence of
+ * Algorithm 3 with reliable updates: the iterate is kept in FP64, and each
+ * time the recurrence residual has fallen by a factor 1e-3 (or met the
+ * tolerance) the FP32 correction is folded into it, the true residual
+ * b - (A + mu I) x is formed with FP64-accurate products and replaces the
+ * recurrence residual, while the search direction is kept (residual
+ * replacement).  Unlike restarted refinement this keeps the Krylov space, so
+ * the solve takes about as many products as an FP64 one.  A replacement
+ * that differs from the recurrence residual by more than a factor of two
+ * restarts the search direction.  If the true residual stops halving between
+ * replacements, or maxit iterations are spent, the system continues in the
+ * escalating refinement loop described under nys_pcg_opts.maxit.
+ * nys_pcg_result.refinements then counts the true-residual evaluations.
+ * With 0, single systems take the refinement loop like batches do.  Returns
+ * the previous mode; any other `on` only queries it.  Process-wide; set it
+ * between solves. */
+int32_t nys_pcg_reliable(int32_t on);
+
 /* Launch-shape autotuner (no counterpart in the paper).  Where a kernel has
  * several correct launch shapes for one problem size (today: the number of
  * slices the points of a Gaussian kernel-matrix product are split into, for
@@ -454,6 +476,16 @@ int32_t nys_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t coun
  * NYS_ERR_ARG for first < 0 or count < 0.  Synchronises `stream`. */
 int32_t nys_random_stream(uint64_t seed, uint64_t stream_id, int64_t first, int64_t count,
                           uint32_t* words, double* gauss, void* stream);
+
+/* Measured throughput of one execution unit on the current device (no
+ * counterpart in the paper; the denominator of the roofline fractions of the
+ * ALU-bound kernels): unit 0 = FP64 FMA pipe, 1 = FP32 FMA pipe (both in
+ * FLOP/s, an FMA counting 2), 2 = MUFU ex2.approx (operations/s).  Runs
+ * independent register-resident dependency chains on every SM, one untimed
+ * launch then one timed with CUDA events on `stream` (tens of ms).
+ * *ops_per_s (host) receives the rate.  NYS_ERR_ARG for another unit.
+ * Synchronises `stream`. */
+int32_t nys_unit_peak(int32_t unit, double* ops_per_s, void* stream);
 
 /* Allocation-free ridge matvec: y = (X^T X + mu I) x in FP32 for an
  * NYS_OP_GRAM operator, computed by the same fused single-pass kernel as the

@@ -3,6 +3,7 @@
 // of squares, the shift of Algorithm 1 (steps 4-5) and the Philox4x32-10 +
 // Box-Muller Gaussian generator of step 1.
 
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -259,6 +260,147 @@ int32_t gemm_f32_out64(bool ta, int64_t M, int64_t N, int64_t K, const float* A,
 int32_t gemm_f64(bool ta, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
                  const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
   return gemm_launch<double, double, 64, 64, 8, 4, 4>(ta, M, N, K, A, lda, B, ldb, C, ldc, s);
+}
+
+// ---------------------------------------------------------------- double-FP32 GEMM
+
+// C = opA(A) B for FP64 matrices computed on the FP32 pipes in double-float
+// arithmetic (Dekker 1971): each FP64 operand is split into an FP32 pair
+// (hi, lo) as it is staged in shared memory; a term a b is the exact product
+// hi_a hi_b (FMA two-product) plus hi_a lo_b + lo_a hi_b (lo_a lo_b, below
+// 2^-48 |a b|, is dropped), and the terms are summed into a (hi, lo) pair
+// with Knuth's TwoSum on the high parts.  Result within a few units of
+// 2^-48 of sum |a| |b| (FP64 products would give 2^-53), at a fraction of
+// the time of FP64 products on GB300.  sym: C is symmetric (A^T A-type
+// products): only the tiles on or above the diagonal are computed, and
+// the caller mirrors them.
+constexpr int DG_BM = 64, DG_BN = 64, DG_BK = 8, DG_TM = 4, DG_TN = 4;
+constexpr int DG_NT = (DG_BM / DG_TM) * (DG_BN / DG_TN);
+
+__device__ __forceinline__ float2 dg_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+template <bool TA>
+__global__ void __launch_bounds__(DG_NT)
+gemm_dfl_kernel(int64_t M, int64_t N, int64_t K, const double* __restrict__ A, int64_t lda,
+                const double* __restrict__ B, int64_t ldb, double* __restrict__ Cp, int64_t ldc,
+                int64_t kchunk, int64_t split_stride, int sym) {
+  const int64_t i0 = (int64_t)blockIdx.y * DG_BM, j0 = (int64_t)blockIdx.x * DG_BN;
+  if (sym && i0 > j0 + DG_BN - 1) return;  // tile strictly below the diagonal
+  __shared__ float2 As[DG_BK][DG_BM + 1];
+  __shared__ float2 Bs[DG_BK][DG_BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % (DG_BN / DG_TN), ty = tid / (DG_BN / DG_TN);
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
+  double* C = Cp + (int64_t)blockIdx.z * split_stride;
+  float sh[DG_TM][DG_TN], sl[DG_TM][DG_TN];
+#pragma unroll
+  for (int a = 0; a < DG_TM; ++a)
+#pragma unroll
+    for (int b = 0; b < DG_TN; ++b) sh[a][b] = sl[a][b] = 0.f;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += DG_BK) {
+    __syncthreads();
+    for (int e = tid; e < DG_BM * DG_BK; e += DG_NT) {
+      int i, k;
+      if (TA) { k = e / DG_BM; i = e % DG_BM; } else { i = e / DG_BK; k = e % DG_BK; }
+      const int64_t gi = i0 + i, gk = k0 + k;
+      double v = 0.0;
+      if (gi < M && gk < kend) v = TA ? A[gk * lda + gi] : A[gi * lda + gk];
+      As[k][i] = dg_split(v);
+    }
+    for (int e = tid; e < DG_BN * DG_BK; e += DG_NT) {
+      const int k = e / DG_BN, j = e % DG_BN;
+      const int64_t gk = k0 + k, gj = j0 + j;
+      Bs[k][j] = dg_split((gk < kend && gj < N) ? B[gk * ldb + gj] : 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < DG_BK; ++kk) {
+      float2 a[DG_TM], b[DG_TN];
+#pragma unroll
+      for (int t = 0; t < DG_TM; ++t) a[t] = As[kk][ty * DG_TM + t];
+#pragma unroll
+      for (int t = 0; t < DG_TN; ++t) b[t] = Bs[kk][tx * DG_TN + t];
+#pragma unroll
+      for (int x = 0; x < DG_TM; ++x)
+#pragma unroll
+        for (int y = 0; y < DG_TN; ++y) {
+          const float p = __fmul_rn(a[x].x, b[y].x);
+          float e = __fmaf_rn(a[x].x, b[y].x, -p);
+          e = __fmaf_rn(a[x].x, b[y].y, e);
+          e = __fmaf_rn(a[x].y, b[y].x, e);
+          const float s0 = __fadd_rn(sh[x][y], p);
+          const float bb = __fsub_rn(s0, sh[x][y]);
+          const float err = __fadd_rn(__fsub_rn(sh[x][y], __fsub_rn(s0, bb)), __fsub_rn(p, bb));
+          sl[x][y] = __fadd_rn(sl[x][y], __fadd_rn(err, e));
+          sh[x][y] = s0;
+        }
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < DG_TM; ++x) {
+    const int64_t gi = i0 + ty * DG_TM + x;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int y = 0; y < DG_TN; ++y) {
+      const int64_t gj = j0 + tx * DG_TN + y;
+      if (gj < N) C[gi * ldc + gj] = (double)sh[x][y] + (double)sl[x][y];
+    }
+  }
+}
+
+// C[j][i] = C[i][j] for i < j (upper triangle mirrored down)
+__global__ void mirror_upper_kernel(double* C, int64_t n, int64_t ldc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int64_t i = e / n, j = e - i * n;
+  if (j < i) C[i * ldc + j] = C[j * ldc + i];
+}
+
+int32_t gemm_dfl(bool ta, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                 const double* B, int64_t ldb, double* C, int64_t ldc, bool sym,
+                 cudaStream_t s) {
+  if (M <= 0 || N <= 0) return NYS_OK;
+  if (sym && M != N) return NYS_ERR_ARG;
+  const int64_t tiles = cdiv(M, DG_BM) * cdiv(N, DG_BN);
+  const int64_t target = 2 * (int64_t)num_sms();
+  int64_t splits = 1;
+  if (tiles < target && K > 16 * DG_BK) {
+    splits = std::min<int64_t>(cdiv(target, tiles), std::max<int64_t>(1, K / 64));
+    splits = std::min<int64_t>(splits, 32);
+  }
+  int64_t kchunk = cdiv(cdiv(K, splits), DG_BK) * DG_BK;
+  if (kchunk < 1) kchunk = DG_BK;
+  splits = K > 0 ? cdiv(K, kchunk) : 1;
+  const dim3 grid((unsigned)cdiv(N, DG_BN), (unsigned)cdiv(M, DG_BM), (unsigned)splits);
+  double* P = C;
+  int64_t ldp = ldc;
+  Scratch sc(s);
+  if (splits > 1) {
+    NYS_TRY(sc.get(&P, (size_t)splits * M * N));
+    ldp = N;
+  }
+  if (ta)
+    gemm_dfl_kernel<true><<<grid, DG_NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, ldp, kchunk,
+                                                 splits > 1 ? M * N : 0, sym ? 1 : 0);
+  else
+    gemm_dfl_kernel<false><<<grid, DG_NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, ldp, kchunk,
+                                                  splits > 1 ? M * N : 0, sym ? 1 : 0);
+  count_launch();
+  if (splits > 1) {
+    split_reduce_kernel<double, double><<<(unsigned)cdiv(M * N, 256), 256, 0, s>>>(
+        P, splits, M, N, C, ldc);
+    count_launch();
+  }
+  if (sym) {
+    mirror_upper_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, s>>>(C, M, ldc);
+    count_launch();
+  }
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
 }
 
 // ---------------------------------------------------------------- elementwise

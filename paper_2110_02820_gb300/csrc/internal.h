@@ -48,6 +48,8 @@ unsigned long long tune_timed();
 
 // PCG graph mode switch behind nys_pcg_graphs (pcg.cu).
 int32_t pcg_graphs(int32_t on);
+// Reliable-update mode of single-system mixed solves behind nys_pcg_reliable (pcg.cu).
+int32_t pcg_reliable(int32_t on);
 unsigned long long pcg_graph_replays();
 
 // ---------------------------------------------------------------- workspace
@@ -114,6 +116,10 @@ int32_t gemm_f64(bool trans_a, int64_t M, int64_t N, int64_t K, const double* A,
                  const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
 
 // D = sum over z of P[z] (M x N each), fixed order.
+// C = opA(A) B for FP64 matrices in double-FP32 arithmetic (~2^-48 relative
+// to sum |a||b|); sym: C symmetric, only the upper tiles computed and mirrored.
+int32_t gemm_dfl(bool trans_a, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                 const double* B, int64_t ldb, double* C, int64_t ldc, bool sym, cudaStream_t s);
 int32_t split_reduce_f32(const float* P, int64_t splits, int64_t M, int64_t N, float* D,
                          int64_t ldd, cudaStream_t s);
 // out (cols x rows, row stride rows) = transpose of in (rows x cols, row stride ld_in).

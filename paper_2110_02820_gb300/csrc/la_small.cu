@@ -20,11 +20,36 @@ namespace nys {
 
 constexpr int CH_NB = 32;
 
+// 1/sqrt(d) for finite d > 0 in FP64 without a division or a square root:
+// d = m 4^e with m in [1, 4) (exact exponent arithmetic), a single-precision
+// estimate of 1/sqrt(m) (about 2^-22 relative), then two Newton-Raphson steps
+// for f(y) = y^-2 - m, y <- y + y (1 - m y^2) / 2, each of which squares the
+// relative error (2^-44, then below the FP64 rounding), and the scale 2^-e.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  int ex;
+  double m = frexp(d, &ex);  // d = m 2^ex, m in [0.5, 1)
+  if (ex & 1) {
+    m *= 2.0;  // m in [1, 2), ex even after the shift
+    ex -= 1;
+  } else {
+    m *= 4.0;  // m in [2, 4)
+    ex -= 2;
+  }
+  double y = (double)rsqrtf((float)m);
+  double h = fma(-m * y, y, 1.0);
+  y = fma(0.5 * y, h, y);
+  h = fma(-m * y, y, 1.0);
+  y = fma(0.5 * y, h, y);
+  return ldexp(y, -ex / 2);
+}
+
 // Factor the diagonal block D = M[k:k+nb, k:k+nb] in place: D = C_kk^T C_kk.
 // One warp, registers only: lane c holds column c (rows 0..31); step j
 // broadcasts the pivot and row j by shuffles, and lane c updates rows
 // j < r <= c of its column.  Loops are unrolled so the column stays in
-// registers.
+// registers.  The pivot's reciprocal square root comes from rsqrt_newton
+// (GB300 runs FP64 division and square root as long dependent chains): the
+// row is scaled by it and the pivot is d times it.
 __global__ void __launch_bounds__(32) chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb,
                                                        int* info) {
   if (*info != 0) return;
@@ -41,9 +66,9 @@ __global__ void __launch_bounds__(32) chol_diag_kernel(double* M, int64_t ell, i
       if (!(d > 0.0) || !isfinite(d)) {
         bad = (int)(k + j + 1);
       } else {
-        const double piv = sqrt(d);
-        if (c == j) col[j] = piv;
-        else if (c > j) col[j] = col[j] / piv;             // C[j][c]
+        const double rp = rsqrt_newton(d);
+        if (c == j) col[j] = d * rp;                       // sqrt(d)
+        else if (c > j) col[j] = col[j] * rp;              // C[j][c]
         // C[j][r] for r > j sits in lane r at index j: rows r <= c of this column
 #pragma unroll
         for (int r = j + 1; r < CH_NB; ++r) {
@@ -71,9 +96,17 @@ __global__ void __launch_bounds__(32) chol_diag_kernel(double* M, int64_t ell, i
 __global__ void chol_panel_kernel(double* M, int64_t ell, int64_t k, int nb, const int* info) {
   if (*info != 0) return;
   __shared__ double Ck[CH_NB][CH_NB + 1];
+  __shared__ double dinv[CH_NB];
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int r = e / nb, c = e % nb;
     Ck[r][c] = M[(k + r) * ell + k + c];
+  }
+  __syncthreads();
+  // reciprocal pivots once per block: the substitution then multiplies
+  if (threadIdx.x < nb) {
+    const double dd = Ck[threadIdx.x][threadIdx.x];
+    const double rs = rsqrt_newton(dd);
+    dinv[threadIdx.x] = rs * rs;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -81,7 +114,7 @@ __global__ void chol_panel_kernel(double* M, int64_t ell, int64_t k, int nb, con
   if (c >= ell) return;
   double m = (lane < nb) ? M[(k + lane) * ell + c] : 0.0;
   for (int r = 0; r < nb; ++r) {
-    double xr = (lane == r) ? m / Ck[r][r] : 0.0;
+    double xr = (lane == r) ? m * dinv[r] : 0.0;
     xr = __shfl_sync(0xffffffffu, xr, r);
     if (lane == r) m = xr;
     else if (lane > r && lane < nb) m -= Ck[r][lane] * xr;

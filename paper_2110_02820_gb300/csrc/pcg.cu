@@ -859,7 +859,7 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   // accurate (FP64 vectors only): the operator products are the FP64-accurate
   // ones of the refinement residual (double-FP32 for the ridge and Gaussian
   // operators) instead of op_matvec_f64; Gaussian systems share one pass over
-  // the kernel per group of up to 4
+  // the kernel per group of up to 8
   if (accurate && !std::is_same<T, double>::value) return NYS_ERR_ARG;
   const int64_t n = op->n;
   PcgBuffers<T, TU> B;
@@ -927,7 +927,7 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
 
   // ---- iterations, checked every `chunk`
   const bool batched_rbf = std::is_same<T, float>::value && nsys > 1 && op->kind == NYS_OP_RBF;
-  constexpr int kAccGroup = 4;
+  constexpr int kAccGroup = 8;
   const bool acc_rbf = accurate && op->kind == NYS_OP_RBF;
   int* gflag = nullptr;
   if (acc_rbf) NYS_TRY(B.get((void**)&gflag, (size_t)cdiv(nsys, kAccGroup) * sizeof(int)));
@@ -1073,6 +1073,305 @@ int32_t pcg_f64(const nys_operator* op, const nys_factor* f, const double* mu, i
   return NYS_OK;
 }
 
+// Reliable-update mode of single-system mixed solves: NYS_PCG_RELIABLE=0 in
+// the environment turns it off at start-up; nys_pcg_reliable() switches it.
+static std::atomic<int> g_pcg_reliable{-1};
+static bool pcg_reliable_enabled() {
+  int v = g_pcg_reliable.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("NYS_PCG_RELIABLE");
+    v = (e && e[0] == '0') ? 0 : 1;
+    g_pcg_reliable.store(v, std::memory_order_relaxed);
+  }
+  return v == 1;
+}
+
+int32_t pcg_reliable(int32_t on) {
+  const int32_t prev = pcg_reliable_enabled() ? 1 : 0;
+  if (on == 0 || on == 1) g_pcg_reliable.store(on, std::memory_order_relaxed);
+  return prev;
+}
+
+// Reduction of the recurrence residual between two replacements.
+static double reliable_delta() {
+  static double d = [] {
+    const char* e = getenv("NYS_PCG_RELIABLE_DELTA");
+    const double v = e ? atof(e) : 0.0;
+    return (v > 0.0 && v < 1.0) ? v : 1e-3;
+  }();
+  return d;
+}
+
+// Contraction of the true residual over one FP32 inner solve above which a
+// system of the refinement loop takes FP64-accurate inner solves
+// (NYS_PCG_ESCALATE in the environment overrides it).
+static double escalation_ratio() {
+  static double r = [] {
+    const char* e = getenv("NYS_PCG_ESCALATE");
+    const double v = e ? atof(e) : 0.0;
+    return (v > 0.0 && v <= 1.0) ? v : 0.5;
+  }();
+  return r;
+}
+
+// Reopens a system after a residual replacement: its recurrence continues.
+__global__ void reopen_state_kernel(SysState* st) {
+  st->done = 0;
+  st->conv = 0;
+  st->status = NYS_OK;
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out,
+                                  int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+
+// x += (double) xl; xl = 0
+__global__ void fold_kernel(double* __restrict__ x, float* __restrict__ xl, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    x[e] += (double)xl[e];
+    xl[e] = 0.f;
+  }
+}
+
+// Mixed-precision Algorithm 3 for one system with reliable updates (residual
+// replacement; van der Vorst and Ye, SIAM J. Sci. Comput. 22, 2000): one FP32
+// recurrence runs on while the iterate is kept in FP64.  Each time the
+// recurrence residual has fallen by `delta` since the last replacement (or
+// has met the tolerance), the FP32 correction is folded into x, the true
+// residual b - (A + mu I) x is formed with FP64-accurate products, and it
+// replaces the recurrence residual (z and r^T z are recomputed; the search
+// direction is kept while the two residuals agree to a factor of two; a
+// larger gap means the FP32 products, not rounding, set it, and the
+// recurrence restarts from p = z).  Unlike refinement with restarts, the
+// Krylov space is not thrown away at each correction, so the FP32 solve takes
+// about as many iterations as an FP64 one.  Returns *stalled = true (x holds the best
+// iterate) when the true residual stops halving between replacements, so
+// that the caller continues with its escalating refinement loop.
+static int32_t pcg_reliable_one(const nys_operator* op, const float* U, const double* lam,
+                                int64_t ell, double lam_ell, const float* E, double mu,
+                                const double* b, double* x, double bn2, double tol, int maxit,
+                                int use_x0, double delta, bool* exq_io, int* iters, int* updates,
+                                double* rel_out, int* status_out, bool* stalled, double* hist,
+                                cudaStream_t s) {
+  const int64_t n = op->n;
+  *stalled = false;
+  PcgBuffers<float, float> B;
+  B.s = s;
+  PcgArgs<float, float>& a = B.a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.ell = U ? ell : 0;
+  a.nsys = 1;
+  a.U = U;
+  a.lam = lam;
+  plan_geometry(a);
+  const size_t vec = (size_t)n * sizeof(float);
+  NYS_TRY(B.get((void**)&a.x, vec));
+  NYS_TRY(B.get((void**)&a.r, vec));
+  NYS_TRY(B.get((void**)&a.z, vec));
+  NYS_TRY(B.get((void**)&a.p, vec));
+  NYS_TRY(B.get((void**)&a.v, vec));
+  NYS_TRY(B.get((void**)&a.st, sizeof(SysState)));
+  NYS_TRY(B.get((void**)&a.dpart, (size_t)a.npart * sizeof(double)));
+  NYS_TRY(B.get((void**)&a.counters, 4 * sizeof(unsigned)));
+  NYS_TRY(B.get((void**)&B.d_mu, sizeof(double)));
+  if (U) {
+    NYS_TRY(B.get((void**)&a.wpart, (size_t)a.nblk_u * ell * sizeof(float)));
+    NYS_TRY(B.get((void**)&a.w, (size_t)ell * sizeof(float)));
+    if (E) {
+      a.E = E;
+      NYS_TRY(B.get((void**)&a.wraw, (size_t)ell * sizeof(float)));
+      NYS_TRY(B.get((void**)&a.wc, (size_t)ell * sizeof(float)));
+    }
+  }
+  double *rt, *vt, *nrm;
+  NYS_TRY(B.get((void**)&rt, (size_t)n * sizeof(double)));
+  NYS_TRY(B.get((void**)&vt, (size_t)n * sizeof(double)));
+  NYS_TRY(B.get((void**)&nrm, sizeof(double)));
+  NYS_TRY(B.get(&B.op_work, op_matvec_work_bytes(op, false)));
+  void* rwork = nullptr;
+  NYS_TRY(B.get(&rwork, op_matvec_work_bytes(op, true)));
+  NYS_CUDA_TRY(cudaMemsetAsync(B.op_work, 0, 256, s));
+  NYS_CUDA_TRY(cudaMemsetAsync(rwork, 0, 256, s));
+  NYS_CUDA_TRY(cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned), s));
+  NYS_CUDA_TRY(cudaMemcpyAsync(B.d_mu, &mu, sizeof(double), cudaMemcpyHostToDevice, s));
+  if (hist) {
+    std::vector<double> nanbuf((size_t)maxit + 1, std::nan(""));
+    NYS_CUDA_TRY(cudaMemcpyAsync(hist, nanbuf.data(), nanbuf.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    a.hist = hist;
+  }
+  PcgLaunch<float, float> L;
+  NYS_TRY(L.setup(a, 1));
+  const unsigned gb = (unsigned)std::min<int64_t>(cdiv(n, 256), 1024);
+
+  // true residual of x in FP64-accurate arithmetic; rel = ||rt|| / ||b||
+  auto true_residual = [&](double* rel) -> int32_t {
+    if (*exq_io) {
+      if (op->kind == NYS_OP_RBF && op->d <= 64) {
+        const float* pts = (const float*)op->data;
+        NYS_TRY(rbf_exact_products(pts, n, op->ld, pts, n, op->ld, op->d, op->sigma, 0, 2,
+                                   B.d_mu, 0.0, 1, x, vt, nullptr, s));
+      } else {
+        NYS_TRY(op_matvec_f64(op, mu, x, vt, nullptr, rwork, s));
+      }
+    } else {
+      NYS_TRY(op_matvec_residual(op, mu, x, vt, nullptr, rwork, s));
+    }
+    sub_kernel<<<gb, 256, 0, s>>>(b, vt, rt, n); count_launch();
+    sys_sumsq_kernel<<<1, 256, 0, s>>>(rt, n, nrm); count_launch();
+    double h = 0.0;
+    NYS_CUDA_TRY(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    *rel = bn2 > 0.0 ? sqrt(h / bn2) : sqrt(h);
+    return NYS_OK;
+  };
+
+  // state: thresh2 = tol^2 ||b||^2, the recurrence's own stopping test
+  init_state_kernel<double><<<1, 256, 0, s>>>(b, n, a.st, B.d_mu, lam_ell, tol, maxit);
+  count_launch();
+  double rel = 1.0;
+  if (use_x0) {
+    NYS_TRY(true_residual(&rel));
+  } else {
+    NYS_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    NYS_CUDA_TRY(cudaMemcpyAsync(rt, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rel = bn2 > 0.0 ? 1.0 : 0.0;
+  }
+  *updates = 0;
+  *iters = 0;
+  *status_out = NYS_ERR_MAXIT;
+  *rel_out = rel;
+  if (rel <= tol) {
+    *status_out = NYS_OK;
+    return NYS_OK;
+  }
+  // first segment: r = fp32(rt), x_lo = 0, z = P^{-1} r, p = z
+  f64_to_f32_kernel<<<gb, 256, 0, s>>>(rt, a.r, n); count_launch();
+  NYS_CUDA_TRY(cudaMemsetAsync(a.x, 0, vec, s));
+  L.update(a, 0, s);
+  L.z(a, 1, s);
+  p_kernel<float, float><<<L.g_d, 256, 0, s>>>(a, 1); count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+
+  auto iteration = [&](cudaStream_t st) -> int32_t {
+    NYS_TRY(matvec_T<float>(op, mu, a.p, a.v, &a.st[0].done, B.op_work, st));
+    pv_alpha_kernel<float, float><<<L.g_d, PC_THREADS, 0, st>>>(a); count_launch();
+    L.update(a, 1, st);
+    L.z(a, 0, st);
+    p_kernel<float, float><<<L.g_d, 256, 0, st>>>(a, 0); count_launch();
+    NYS_CUDA_TRY(cudaGetLastError());
+    return NYS_OK;
+  };
+  IterGraph graph;
+  if (maxit > 0 && pcg_graphs_enabled()) {
+    if (op->kind == NYS_OP_RBF && rbf_tc_tune_pending(n, op->d, 1, 3))
+      NYS_TRY(matvec_T<float>(op, mu, a.p, a.v, nullptr, B.op_work, s));
+    graph.build(iteration);
+  }
+  SysState h;
+  NYS_CUDA_TRY(cudaMemcpyAsync(&h, a.st, sizeof(SysState), cudaMemcpyDeviceToHost, s));
+  NYS_CUDA_TRY(cudaStreamSynchronize(s));
+  double rr_seg = h.rr;  // recurrence ||r||^2 at the start of the segment
+  double rel_prev = rel;
+  int stall = 0;
+  int64_t launched = 0;
+  int chunk = 4;
+  while (true) {
+    if (graph.ok()) {
+      for (int c = 0; c < chunk && launched < maxit; c += kGraphIters, launched += kGraphIters)
+        NYS_TRY(graph.replay(s));
+    } else {
+      for (int c = 0; c < chunk && launched < maxit; ++c, ++launched) NYS_TRY(iteration(s));
+    }
+    NYS_CUDA_TRY(cudaMemcpyAsync(&h, a.st, sizeof(SysState), cudaMemcpyDeviceToHost, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    *iters = h.it;
+    if (h.status == NYS_ERR_BREAKDOWN) {
+      // p^T A p <= 0 with FP32 products: at this shift their error can make
+      // the FP32 operator indefinite; the escalating loop takes over (its
+      // FP64-accurate inner solve reports a genuine breakdown)
+      fold_kernel<<<gb, 256, 0, s>>>(x, a.x, n); count_launch();
+      *stalled = true;
+      break;
+    }
+    const bool end_seg = h.done || h.rr <= delta * delta * rr_seg || launched >= maxit;
+    if (!end_seg) {
+      if (chunk < 16) chunk *= 2;
+      continue;
+    }
+    // fold the FP32 correction into x and replace the recurrence residual
+    fold_kernel<<<gb, 256, 0, s>>>(x, a.x, n); count_launch();
+    NYS_TRY(true_residual(&rel));
+    *updates += 1;
+    *rel_out = rel;
+    if (rel <= tol) {
+      *status_out = NYS_OK;
+      break;
+    }
+    if (!std::isfinite(rel)) {
+      *status_out = NYS_ERR_BREAKDOWN;
+      break;
+    }
+    if (h.it >= maxit || launched >= maxit) {
+      // budget spent above tol: the escalating loop continues (its
+      // FP64-accurate inner solves have a budget of their own)
+      *stalled = true;
+      break;
+    }
+    if (rel > 0.5 * rel_prev) {
+      // no progress since the last replacement: first take the residual in
+      // native FP64 (the double-FP32 floor may sit above tol), then hand the
+      // system to the escalating refinement loop
+      if (!*exq_io) {
+        *exq_io = true;
+        NYS_TRY(true_residual(&rel));
+        *rel_out = rel;
+        if (rel <= tol) {
+          *status_out = NYS_OK;
+          break;
+        }
+      }
+      if (++stall >= 2) {
+        *stalled = true;
+        break;
+      }
+    } else {
+      stall = 0;
+    }
+    rel_prev = rel;
+    // Keep the search direction only while the recurrence residual was a
+    // faithful estimate of the true one: when they differ by more than a
+    // factor of two (the FP32 products' error, not rounding, dominates), the
+    // old direction is scaled for the wrong residual and the next step size
+    // would be meaningless, so the recurrence restarts from p = z.
+    const double rr_true = rel * rel * (bn2 > 0.0 ? bn2 : 1.0);
+    const bool restart = !(rr_true <= 4.0 * h.rr);
+    f64_to_f32_kernel<<<gb, 256, 0, s>>>(rt, a.r, n); count_launch();
+    reopen_state_kernel<<<1, 1, 0, s>>>(a.st); count_launch();
+    L.update(a, 0, s);
+    L.z(a, 1, s);
+    if (restart) {
+      p_kernel<float, float><<<L.g_d, 256, 0, s>>>(a, 1); count_launch();
+    }
+    NYS_CUDA_TRY(cudaGetLastError());
+    NYS_CUDA_TRY(cudaMemcpyAsync(&h, a.st, sizeof(SysState), cudaMemcpyDeviceToHost, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    rr_seg = h.rr;
+    chunk = 4;
+  }
+  int err = 0;
+  NYS_CUDA_TRY(cudaMemcpyAsync(&err, B.op_work, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NYS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (err) return NYS_ERR_TIMEOUT;
+  return NYS_OK;
+}
+
 // Mixed precision: FP64 outer loop r = b - (A + mu I) x (FP64-accurate
 // matvec), inner Algorithm 3 on FP32 vectors for the correction.
 int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu, int64_t nsys,
@@ -1114,6 +1413,30 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   std::vector<double> bn2(nsys), rn2(nsys);
   sys_sumsq_kernel<<<(unsigned)nsys, 256, 0, s>>>(b, n, nrm); count_launch();
   NYS_CUDA_TRY(cudaMemcpyAsync(bn2.data(), nrm, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // One system: a single FP32 recurrence with reliable updates; the
+  // escalating refinement loop below takes over only if that stalls.
+  bool rel_exq = op->kind == NYS_OP_DENSE, rel_stalled = false;
+  int rel_it = 0, rel_upd = 0;
+  // (Gaussian-kernel systems keep the refinement loop: their FP32 products'
+  // error, not rounding, usually sets the gap between the recurrence and the
+  // true residual, and the recurrence would restart at every replacement.)
+  if (nsys == 1 && maxit > 0 && op->kind != NYS_OP_RBF && pcg_reliable_enabled()) {
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    int st0 = NYS_ERR_MAXIT;
+    double rel0 = 1.0;
+    NYS_TRY(pcg_reliable_one(op, U, f ? f->lam : nullptr, f ? f->ell : 0, f ? f->lam_ell : 0.0,
+                             Edef, mu[0], b, x, bn2[0], tol, maxit, use_x0, reliable_delta(),
+                             &rel_exq, &rel_it, &rel_upd, &rel0, &st0, &rel_stalled, hist, s));
+    if (!rel_stalled) {
+      res[0].status = st0;
+      res[0].iterations = rel_it;
+      res[0].refinements = rel_upd;
+      res[0].escalated = 0;
+      res[0].rel_residual = rel0;
+      return NYS_OK;
+    }
+    use_x0 = 1;  // the refinement loop continues from the stalled iterate
+  }
   std::vector<int> active(nsys, 1), total_it(nsys, 0), outer(nsys, 0), stt(nsys, NYS_ERR_MAXIT);
   std::vector<double> rel(nsys, 1.0), prev(nsys, 0.0);
   // Escalation of the inner solve: with FP64-accurate residuals, a system
@@ -1131,6 +1454,13 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   const double* U64 = nullptr;
   const float* E64 = nullptr;
   double *ra = nullptr, *dd = nullptr;
+  if (rel_stalled) {
+    // the reliable-update recurrence made no progress with FP64-accurate
+    // residuals: FP64-accurate inner solves from the start
+    total_it[0] = rel_it;
+    outer[0] = rel_upd;
+    acc[0] = 1;
+  }
   std::vector<double> before(nsys, 0.0);
   std::vector<char> bex(nsys, 0);
   const unsigned gb = (unsigned)cdiv(n, 256) > 1024 ? 1024 : (unsigned)cdiv(n, 256);
@@ -1142,6 +1472,7 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
   // native FP64 (slower on this part, exact to FP64 rounding); the others
   // keep the double-FP32 products.
   std::vector<char> exq(nsys, op->kind == NYS_OP_DENSE ? 1 : 0);
+  if (rel_stalled && rel_exq) exq[0] = 1;
   const bool may_escalate = op->kind != NYS_OP_DENSE;
   // The Gaussian residual runs as one pass over the kernel for a set of
   // systems (gathered into contiguous buffers unless it is all of them).
@@ -1222,9 +1553,12 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       } else {
         if (exq[q] && bex[q] && outer[q] > 0)
           stag[q] = (rel[q] > 0.5 * before[q]) ? stag[q] + 1 : 0;
-        if (!acc[q] && ((exq[q] && stag[q] >= 1) || total_it[q] >= maxit)) {
-          acc[q] = 1;  // FP64-accurate inner solves (and FP64 residuals) from now on
-          exq[q] = 1;
+        // a system whose true residual contracted by less than the escalation
+        // ratio over its last FP32 inner solve (asked for a 1e-4 reduction) is
+        // limited by the FP32 products: FP64-accurate inner solves from now on
+        const bool slow = outer[q] >= 2 && rel[q] > escalation_ratio() * before[q];
+        if (!acc[q] && ((exq[q] && stag[q] >= 1) || total_it[q] >= maxit || slow)) {
+          acc[q] = 1;
           stag[q] = 0;
         }
         if (stag[q] >= 2 || (acc[q] ? acc_it[q] >= maxit : total_it[q] >= maxit)) {
@@ -1336,10 +1670,10 @@ int32_t pcg_mixed(const nys_operator* op, const nys_factor* f, const double* mu,
       axpy_to_f64_kernel<float><<<gb, 256, 0, s>>>(x + q * n, df + t * n, n); count_launch();
       total_it[q] += it[t];
       outer[q] += 1;
-      if (st[t] == NYS_ERR_BREAKDOWN) {
-        active[q] = 0;
-        stt[q] = NYS_ERR_BREAKDOWN;
-      }
+      // an FP32 inner solve that broke down (p^T A p <= 0 with FP32 products,
+      // whose error can make the operator indefinite at a small shift): the
+      // system takes FP64-accurate inner solves from now on
+      if (st[t] == NYS_ERR_BREAKDOWN) acc[q] = 1;
     }
     NYS_CUDA_TRY(cudaGetLastError());
   }

@@ -764,8 +764,8 @@ int32_t rbf_exact_products(const float* tg, int64_t nt, int64_t ldt, const float
 }
 
 // y_q = (K + mu_q I) v_q for q < nvec (device FP64 arrays), FP64-accurate.
-// Up to 4 vectors take the symmetric products (each entry once); more take
-// the row-block products.  skip (device, may be NULL): nothing is computed
+// Up to 8 vectors take the symmetric products (each entry once, for 4 or 8
+// vectors at a time); more take the row-block products (32 vectors per entry).  skip (device, may be NULL): nothing is computed
 // while *skip is nonzero.
 int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_t nvec,
                               const double* v, double* y, cudaStream_t s, const int* skip) {
@@ -781,6 +781,13 @@ int32_t rbf_residual_products(const nys_operator* op, const double* d_mu, int64_
     if (d <= 16) return sym_go<16, 2, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
     if (d <= 32) return sym_go<32, 2, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
     return sym_go<64, 1, 4>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+  }
+  if (nvec <= 8) {
+    // each kernel entry serves 8 vectors (fewer rows per thread above d = 16
+    // keep the accumulators in registers)
+    if (d <= 16) return sym_go<16, 2, 8>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+    if (d <= 32) return sym_go<32, 1, 8>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
+    return sym_go<64, 1, 8>(pts, n, ld, d, op->sigma, d_mu, nvec, v, y, skip, s);
   }
   return products(false, pts, n, ld, pts, n, ld, d, op->sigma, 0, d_mu ? 2 : 0, d_mu, 0.0, nvec,
                   v, y, skip, s);

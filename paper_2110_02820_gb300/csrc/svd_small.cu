@@ -15,17 +15,19 @@
 //     sweep a task only rotates the w^2 pairs across its two blocks.  Column pairs whose cosine
 //     is below tol (just above the FP32 rounding level of the dot product)
 //     are skipped; a sweep with no rotation ends the iteration.
-//  2. FP64 path only: the FP32 vectors X seed the iterative refinement for
-//     symmetric eigenproblems of Ogita and Aishima (Japan J. Indust. Appl.
-//     Math. 35, 2018), applied to R R^T = Ut Sigma^2 Ut^T without forming it:
+//  2. The FP32 vectors X seed the iterative refinement for symmetric
+//     eigenproblems of Ogita and Aishima (Japan J. Indust. Appl. Math. 35,
+//     2018), applied to R R^T = Ut Sigma^2 Ut^T without forming it:
 //     with G = X^T X, S = X^T R R^T X = (R^T X)^T (R^T X),
 //     lambda_i = S_ii / G_ii and E_ij = (S_ij + lambda_j (I - G)_ij) /
 //     (lambda_j - lambda_i) for well separated pairs, (I - G)_ij / 2
 //     otherwise, X <- X (I + E).  A pair counts as separated when its gap
 //     exceeds the method's threshold delta and its first-order correction
 //     is below 1e-2 (the second condition is ours).  Each step squares the
-//     error and costs four ell^3 FP64 products; two or three steps take the
-//     FP32 start to FP64 accuracy.
+//     error and costs four ell^3 products, formed in double-FP32 arithmetic
+//     (gemm_dfl: ~2^-48 relative, several times faster than FP64 products on
+//     GB300; the two symmetric ones by their upper triangle); two or three
+//     steps take the FP32 start to that accuracy.
 //     Eigenvalues closer than the separation threshold stay mixed inside
 //     their (orthonormal) subspace, which leaves U Lambda U^T unchanged to
 //     that threshold.
@@ -115,8 +117,37 @@ struct BJArgs {
   int* status;
 };
 
+// Hestenes rotation of the column pair (x, y): one butterfly for the three
+// lane sums of x . x, y . y, x . y, and the rotation (cs, sn) that zeroes
+// x . y when |cos| exceeds tol.  Returns false when the pair is already
+// orthogonal to tol.
+__device__ __forceinline__ bool hestenes_angle(float al, float be, float ga, float tol, float* cs,
+                                               float* sn) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  // |gamma| > tol sqrt(alpha beta), without the square roots
+  if (!(ga * ga > tol * tol * (al * be))) return false;
+  // 2 x 2 rotation that zeroes the inner product (Hestenes):
+  // zeta = (beta - alpha) / (2 gamma), t = tan of the angle.
+  const float zeta = (be - al) / (2.0f * ga);
+  const float az = fabsf(zeta);
+  const float t = az > 1e18f ? 0.5f / zeta : copysignf(1.0f, zeta) / (az + sqrtf(1.0f + zeta * zeta));
+  *cs = rsqrtf(1.0f + t * t);
+  *sn = *cs * t;
+  return true;
+}
+
 // Block one-sided Jacobi; blockDim = 32 * WB (one warp per local column pair).
-template <int WB>
+// PR > 0: in the rounds after the first of a sweep, warp w keeps its fixed
+// column (w) in registers (PR float4 per lane) for all WB local rounds, so a
+// round moves only the partner column through shared memory (the shared
+// memory traffic of a round, not its arithmetic, set the pace).  PR = 0:
+// every column goes through shared memory.
+template <int WB, int PR>
 __global__ void __launch_bounds__(32 * WB) bjacobi_kernel(BJArgs a) {
   extern __shared__ float4 sm4[];  // 2 WB rows of ellp / 4 float4
   __shared__ int blk_rot;
@@ -137,53 +168,85 @@ __global__ void __launch_bounds__(32 * WB) bjacobi_kernel(BJArgs a) {
         }
         __syncthreads();
         bool rot = false;
-        // Round 0 of a sweep meets every pair of the two blocks (a cyclic
-        // sweep over their 2 WB columns); later rounds only the WB^2 pairs
-        // across the blocks (WB shifts), the pairs inside a block having had
-        // their turn in round 0.  Same sweep count, ~45 % fewer local rounds.
-        const int nlr = (r == 0) ? 2 * WB - 1 : WB;
-        for (int lr = 0; lr < nlr; ++lr) {
-          int p, q;
-          if (r == 0) {
-            circle_pair(2 * WB, lr, warp, &p, &q);
-          } else {
-            p = warp;
-            q = WB + (warp + lr) % WB;
-          }
-          float4* P = sm4 + p * rq;
-          float4* Q = sm4 + q * rq;
-          float al = 0.f, be = 0.f, ga = 0.f;
-          for (int c = lane; c < rq; c += 32) {
-            const float4 x = P[c], y = Q[c];
-            al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
-            be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
-            ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
-          }
-          // the three sums share one butterfly (three independent shuffles per level)
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            al += __shfl_xor_sync(0xffffffffu, al, o);
-            be += __shfl_xor_sync(0xffffffffu, be, o);
-            ga += __shfl_xor_sync(0xffffffffu, ga, o);
-          }
-          // |gamma| > tol sqrt(alpha beta), without the square roots
-          if (ga * ga > a.tol * a.tol * (al * be)) {
-            // 2 x 2 rotation that zeroes the inner product (Hestenes):
-            // zeta = (beta - alpha) / (2 gamma), t = tan of the angle.
-            const float zeta = (be - al) / (2.0f * ga);
-            const float az = fabsf(zeta);
-            const float t = az > 1e18f ? 0.5f / zeta
-                                       : copysignf(1.0f, zeta) / (az + sqrtf(1.0f + zeta * zeta));
-            const float cs = rsqrtf(1.0f + t * t);
-            const float sn = cs * t;
+        if (r == 0 || PR == 0) {
+          // Round 0 of a sweep meets every pair of the two blocks (a cyclic
+          // sweep over their 2 WB columns); later rounds only the WB^2 pairs
+          // across the blocks (WB shifts), the pairs inside a block having had
+          // their turn in round 0.  Same sweep count, ~45 % fewer local rounds.
+          const int nlr = (r == 0) ? 2 * WB - 1 : WB;
+          for (int lr = 0; lr < nlr; ++lr) {
+            int p, q;
+            if (r == 0) {
+              circle_pair(2 * WB, lr, warp, &p, &q);
+            } else {
+              p = warp;
+              q = WB + (warp + lr) % WB;
+            }
+            float4* P = sm4 + p * rq;
+            float4* Q = sm4 + q * rq;
+            float al = 0.f, be = 0.f, ga = 0.f;
             for (int c = lane; c < rq; c += 32) {
               const float4 x = P[c], y = Q[c];
-              P[c] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z,
-                                 cs * x.w - sn * y.w);
-              Q[c] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z,
-                                 sn * x.w + cs * y.w);
+              al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
+              be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+              ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
             }
-            rot = true;
+            float cs, sn;
+            if (hestenes_angle(al, be, ga, a.tol, &cs, &sn)) {
+              for (int c = lane; c < rq; c += 32) {
+                const float4 x = P[c], y = Q[c];
+                P[c] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z,
+                                   cs * x.w - sn * y.w);
+                Q[c] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z,
+                                   sn * x.w + cs * y.w);
+              }
+              rot = true;
+            }
+            __syncthreads();
+          }
+        } else {
+          // cross rounds: column p = warp stays in registers; the partner
+          // column q is read once per round, rotated with it and written back
+          float4* P = sm4 + warp * rq;
+          float4 pr[PR > 0 ? PR : 1];
+#pragma unroll
+          for (int k = 0; k < PR; ++k) {
+            const int c = lane + 32 * k;
+            pr[k] = c < rq ? P[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          for (int lr = 0; lr < WB; ++lr) {
+            float4* Q = sm4 + (WB + (warp + lr) % WB) * rq;
+            float4 qr[PR > 0 ? PR : 1];
+            float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+            for (int k = 0; k < PR; ++k) {
+              const int c = lane + 32 * k;
+              qr[k] = c < rq ? Q[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+              const float4 x = pr[k], y = qr[k];
+              al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
+              be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+              ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
+            }
+            float cs, sn;
+            if (hestenes_angle(al, be, ga, a.tol, &cs, &sn)) {
+#pragma unroll
+              for (int k = 0; k < PR; ++k) {
+                const int c = lane + 32 * k;
+                const float4 x = pr[k], y = qr[k];
+                pr[k] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z,
+                                    cs * x.w - sn * y.w);
+                if (c < rq)
+                  Q[c] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z,
+                                     sn * x.w + cs * y.w);
+              }
+              rot = true;
+            }
+            __syncthreads();
+          }
+#pragma unroll
+          for (int k = 0; k < PR; ++k) {
+            const int c = lane + 32 * k;
+            if (c < rq) P[c] = pr[k];
           }
           __syncthreads();
         }
@@ -399,9 +462,9 @@ __global__ void permute_cols_kernel(const double* __restrict__ X, const int* __r
   }
 }
 
-template <int WB>
+template <int WB, int PR>
 int32_t launch_bjacobi(BJArgs& a, size_t smem, cudaStream_t s) {
-  auto kern = bjacobi_kernel<WB>;
+  auto kern = bjacobi_kernel<WB, PR>;
   NYS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   NYS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WB, smem));
@@ -477,11 +540,20 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, bool
   a.rot = aux->rot;
   a.sweeps = &aux->sweeps;
   a.status = d_status;
-  switch (wb) {
-    case 16: NYS_TRY(launch_bjacobi<16>(a, smem, s)); break;
-    case 8: NYS_TRY(launch_bjacobi<8>(a, smem, s)); break;
-    case 4: NYS_TRY(launch_bjacobi<4>(a, smem, s)); break;
-    default: NYS_TRY(launch_bjacobi<2>(a, smem, s)); break;
+  // columns of up to 512 (4 float4 per lane) or 1024 (8) entries stay in
+  // registers during the cross rounds
+  const int64_t pr = cdiv(ellp / 4, 32);
+  if (wb == 16 && pr <= 4) {
+    NYS_TRY((launch_bjacobi<16, 4>(a, smem, s)));
+  } else if (wb == 16 && pr <= 8) {
+    NYS_TRY((launch_bjacobi<16, 8>(a, smem, s)));
+  } else {
+    switch (wb) {
+      case 16: NYS_TRY((launch_bjacobi<16, 0>(a, smem, s))); break;
+      case 8: NYS_TRY((launch_bjacobi<8, 0>(a, smem, s))); break;
+      case 4: NYS_TRY((launch_bjacobi<4, 0>(a, smem, s))); break;
+      default: NYS_TRY((launch_bjacobi<2, 0>(a, smem, s))); break;
+    }
   }
   row_norm_kernel<<<(unsigned)cdiv(ell, 8), 256, 0, s>>>(Wm, ellp, ell, &aux->maxbits, rn, sigma);
   count_launch();
@@ -507,15 +579,15 @@ int32_t jacobi_svd(const double* R, double* Ut, double* sigma, int64_t ell, bool
     const dim3 ug((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 8));
     double em_prev = 1.0;
     for (int k = 0; k < kMaxRefine; ++k) {
-      NYS_TRY(gemm_f64(true, ell, ell, ell, X, ell, X, ell, G, ell, s));  // G = X^T X
-      NYS_TRY(gemm_f64(true, ell, ell, ell, R, ell, X, ell, T, ell, s));  // T = R^T X
-      NYS_TRY(gemm_f64(true, ell, ell, ell, T, ell, T, ell, S, ell, s));  // S = T^T T
+      NYS_TRY(gemm_dfl(true, ell, ell, ell, X, ell, X, ell, G, ell, true, s));   // G = X^T X
+      NYS_TRY(gemm_dfl(true, ell, ell, ell, R, ell, X, ell, T, ell, false, s));  // T = R^T X
+      NYS_TRY(gemm_dfl(true, ell, ell, ell, T, ell, T, ell, S, ell, true, s));   // S = T^T T
       oa_partial_kernel<<<(unsigned)oa_blocks, 256, 0, s>>>(G, S, ell, lam, part); count_launch();
       oa_final_kernel<<<1, 256, 0, s>>>(part, oa_blocks, delta); count_launch();
       oa_update_kernel<<<ug, dim3(32, 8), 0, s>>>(G, S, lam, delta, ell, F, &aux->emax[k],
                                                   &aux->e2max[k]);
       count_launch();
-      NYS_TRY(gemm_f64(false, ell, ell, ell, X, ell, F, ell, Xn, ell, s));  // X <- X (I + E)
+      NYS_TRY(gemm_dfl(false, ell, ell, ell, X, ell, F, ell, Xn, ell, false, s));  // X <- X (I + E)
       double* tmp = X;
       X = Xn;
       Xn = tmp;

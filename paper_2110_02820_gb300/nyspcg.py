@@ -131,6 +131,16 @@ def pcg_graphs(on: int | None = None) -> bool:
     return bool(lib().nys_pcg_graphs(arg))
 
 
+def pcg_reliable(on: int | None = None) -> bool:
+    """Reliable-update mode of one-system mixed solves (True = on); sets it when
+    `on` is 0 or 1 and returns the previous mode."""
+    f = lib().nys_pcg_reliable
+    if f.argtypes is None:
+        f.argtypes = [C.c_int32]
+        f.restype = C.c_int32
+    return bool(f(-1 if on is None else int(on)))
+
+
 def pcg_graph_replays() -> int:
     """PCG iteration graphs replayed so far in this process."""
     return int(lib().nys_pcg_graph_replays())
@@ -368,6 +378,7 @@ class PcgResult:
     iterations: int
     refinements: int
     rel_residual: float
+    escalated: int = 0
 
 
 def pcg_solve(op: Operator, f: Factor | None, mu, b: torch.Tensor, x: torch.Tensor | None = None,
@@ -391,7 +402,7 @@ def pcg_solve(op: Operator, f: Factor | None, mu, b: torch.Tensor, x: torch.Tens
                          C.byref(opts), res, _stream())
     if st not in (NYS_OK, NYS_ERR_MAXIT, NYS_ERR_BREAKDOWN):
         raise NysError(st, "pcg_solve")
-    out = [PcgResult(r.status, r.iterations, r.refinements, r.rel_residual) for r in res]
+    out = [PcgResult(r.status, r.iterations, r.refinements, r.rel_residual, r.escalated) for r in res]
     xo = xx if b.dim() == 2 else xx[0]
     return xo, out, hist
 
@@ -415,7 +426,7 @@ def nys_block_pcg(op: Operator, f: Factor | None, mu: float, B: torch.Tensor,
             C.byref(opts), res, _stream())
     if st not in (NYS_OK, NYS_ERR_MAXIT, NYS_ERR_BREAKDOWN):
         raise NysError(st, "nys_block_pcg")
-    return XX, [PcgResult(r.status, r.iterations, r.refinements, r.rel_residual) for r in res]
+    return XX, [PcgResult(r.status, r.iterations, r.refinements, r.rel_residual, r.escalated) for r in res]
 
 
 class _PathResult(C.Structure):
@@ -609,3 +620,17 @@ def nys_krr_gradients(points: torch.Tensor, vpoints: torch.Tensor | None, sigma:
     _check(f(_ptr(points), n, points.stride(0), _ptr(vpoints), m, ldv, d, float(sigma),
              _ptr(alpha), _ptr(lam), _ptr(g), out, _stream()), "nys_krr_gradients")
     return out[0], out[1]
+
+
+UNIT_FP64_FMA, UNIT_FP32_FMA, UNIT_MUFU_EX2 = 0, 1, 2
+
+
+def nys_unit_peak(unit: int) -> float:
+    """Measured FLOP/s (FMA pipes) or operations/s (MUFU ex2) of the device."""
+    f = lib().nys_unit_peak
+    if f.argtypes is None:
+        f.argtypes = [C.c_int32, C.POINTER(C.c_double), C.c_void_p]
+        f.restype = C.c_int32
+    out = C.c_double()
+    _check(f(unit, C.byref(out), _stream()), "nys_unit_peak")
+    return out.value

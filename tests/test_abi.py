@@ -156,3 +156,45 @@ def test_newer_entry_points_reject_bad_arguments(L):
 
     mu1 = (C.c_double * 1)(1e-3)
     assert L.nys_sketch_solve(None, mu1, i64(1), b, x, i32(0), None) == ny.NYS_ERR_ARG
+
+
+def test_generator_krr_and_probe_entry_points_reject_bad_arguments(L):
+    # Philox, the random stream, the KRR objective / gradients and the unit
+    # probe check their arguments on the host before any device work
+    from paper_2110_02820_gb300 import nyspcg as ny
+    i64, dbl, vp, u64, i32 = C.c_int64, C.c_double, C.c_void_p, C.c_uint64, C.c_int32
+    L.nys_philox4x32_10.argtypes = [vp, vp, i64, vp, vp]
+    L.nys_philox4x32_10.restype = i32
+    assert L.nys_philox4x32_10(None, vp(0x1000), 4, vp(0x2000), None) == ny.NYS_ERR_ARG
+    assert L.nys_philox4x32_10(vp(0x1000), vp(0x1000), -1, vp(0x2000), None) == ny.NYS_ERR_ARG
+    L.nys_random_stream.argtypes = [u64, u64, i64, i64, vp, vp, vp]
+    L.nys_random_stream.restype = i32
+    assert L.nys_random_stream(1, 2, -1, 4, vp(0x1000), None, None) == ny.NYS_ERR_ARG
+    assert L.nys_random_stream(1, 2, 0, -4, vp(0x1000), None, None) == ny.NYS_ERR_ARG
+    assert L.nys_random_stream(1, 2, 0, 4, None, None, None) == ny.NYS_ERR_ARG
+
+    L.nys_krr_validation.argtypes = [vp, i64, i64, vp, i64, i64, i64, dbl, vp, vp,
+                                     C.POINTER(dbl), vp, vp, vp]
+    L.nys_krr_validation.restype = i32
+    loss = dbl()
+    P, V, a, y, g, k = (vp(0x1000 * (i + 1)) for i in range(6))
+    # d out of range, sigma <= 0, aliasing outputs
+    assert L.nys_krr_validation(P, 10, 70, V, 5, 70, 65, 1.0, a, y, C.byref(loss), g, k,
+                                None) == ny.NYS_ERR_ARG
+    assert L.nys_krr_validation(P, 10, 4, V, 5, 4, 4, 0.0, a, y, C.byref(loss), g, k,
+                                None) == ny.NYS_ERR_ARG
+    assert L.nys_krr_validation(P, 10, 4, V, 5, 4, 4, 1.0, a, y, C.byref(loss), g, g,
+                                None) == ny.NYS_ERR_ARG
+    L.nys_krr_gradients.argtypes = [vp, i64, i64, vp, i64, i64, i64, dbl, vp, vp, vp,
+                                    C.POINTER(dbl), vp]
+    L.nys_krr_gradients.restype = i32
+    out = (dbl * 2)()
+    assert L.nys_krr_gradients(P, 10, 4, None, 0, 0, 4, 1.0, None, a, None, out,
+                               None) == ny.NYS_ERR_ARG
+    assert L.nys_krr_gradients(P, 10, 4, V, 5, 4, 4, 1.0, a, a, None, out,
+                               None) == ny.NYS_ERR_ARG  # validation points need g
+    L.nys_unit_peak.argtypes = [i32, C.POINTER(dbl), vp]
+    L.nys_unit_peak.restype = i32
+    r = dbl()
+    assert L.nys_unit_peak(3, C.byref(r), None) == ny.NYS_ERR_ARG
+    assert L.nys_unit_peak(0, None, None) == ny.NYS_ERR_ARG
