@@ -297,6 +297,19 @@ uint64_t nys_kernel_launch_count(void);
  * Process-wide; set it between solves, not during one. */
 int32_t nys_pcg_graphs(int32_t on);
 
+/* Device-side PCG loop (no counterpart in the paper).  With `on` = 1 (the
+ * default, unless the environment sets NYS_PCG_LOOP=0 before the first
+ * solve) and graph mode on, a PCG solve whose products allocate nothing
+ * (FP32 products of every operator, FP64 products of the dense and ridge
+ * operators) and whose products are not being timed runs its whole
+ * iteration loop as ONE launch of a CUDA graph: a conditional WHILE node
+ * repeats one iteration and a one-block kernel that ends the loop once every
+ * system's done word is set or maxit iterations have run.  The host reads
+ * the systems' states once per solve (in mixed precision: once per inner
+ * solve).  Results are bit-identical to the replayed-chunk and plain modes.
+ * Returns the previous mode; any other `on` only queries it.  Process-wide. */
+int32_t nys_pcg_loop(int32_t on);
+
 /* Mixed-precision solves of ONE system with a dense or ridge operator (no
  * counterpart in the paper; Gaussian-kernel systems always take the
  * refinement loop).  With `on` = 1 (the default, unless the environment sets

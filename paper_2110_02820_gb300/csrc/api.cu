@@ -675,6 +675,8 @@ int32_t nys_pcg_graphs(int32_t on) { return nys::pcg_graphs(on); }
 
 int32_t nys_pcg_reliable(int32_t on) { return nys::pcg_reliable(on); }
 
+int32_t nys_pcg_loop(int32_t on) { return nys::pcg_loop(on); }
+
 uint64_t nys_pcg_graph_replays(void) { return (uint64_t)nys::pcg_graph_replays(); }
 
 int32_t nys_autotune(int32_t on) { return nys::tune_switch(on); }

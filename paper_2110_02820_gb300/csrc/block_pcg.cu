@@ -451,7 +451,7 @@ int32_t block_matvec<float>(const nys_operator* op, double mu, const double* d_m
                             cudaStream_t s) {
   const int64_t n = op->n;
   if (op->kind == NYS_OP_RBF)
-    return op_matvec_batched_f32(op, d_mu, k, P, V, skip, 0, err, s);
+    return op_matvec_batched_f32(op, d_mu, k, P, V, skip, 0, err, nullptr, s);
   for (int q = 0; q < k; ++q) NYS_TRY(op_matvec_f32(op, mu, P + q * n, V + q * n, skip, work, s));
   return NYS_OK;
 }

@@ -50,6 +50,8 @@ unsigned long long tune_timed();
 int32_t pcg_graphs(int32_t on);
 // Reliable-update mode of single-system mixed solves behind nys_pcg_reliable (pcg.cu).
 int32_t pcg_reliable(int32_t on);
+// Device-side PCG loop switch behind nys_pcg_loop (pcg.cu).
+int32_t pcg_loop(int32_t on);
 unsigned long long pcg_graph_replays();
 
 // ---------------------------------------------------------------- workspace
@@ -195,6 +197,8 @@ struct GraphTiming {
   int products = 0;
 };
 void timing_capture_begin();
+// True while nys_timing_start's event timing is on.
+bool timing_active();
 int32_t timing_graph_nodes(cudaGraph_t g, GraphTiming* gt);
 int32_t timing_graph_rebind(cudaGraphExec_t ge, const GraphTiming& gt);
 int32_t timing_stop(double* total_ms, int64_t* products);
@@ -204,9 +208,11 @@ int32_t op_matvec_f64(const nys_operator* op, double mu, const double* p, double
 // Batched FP32 matvec V[s] = (A + mu_s I) P[s] for nsys systems sharing the
 // operator (RBF only; NYS_ERR_ARG otherwise, and the caller loops).  d_mu:
 // device [nsys]; done0[s * done_stride] != 0 marks a converged system.
+// work: NULL, or rbf_tc_work_bytes(n, nsys, 3) bytes (then nothing is
+// allocated during the call).
 int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_t nsys,
                               const float* P, float* V, const int* done0, int64_t done_stride,
-                              int* err, cudaStream_t s);
+                              int* err, void* work, cudaStream_t s);
 // y_q = (K + mu_q I) v_q, q < nvec, FP64-accurate in double-FP32 arithmetic
 // (rbf_residual.cu).  d_mu: device [nvec].  NYS_ERR_ARG unless RBF, d <= 64.
 // skip (device, may be NULL): nothing is computed while *skip is nonzero.
@@ -243,6 +249,8 @@ bool rbf_tc_supported(int64_t d);
 // (the tuner is on and has no entry for it): a solve runs one product
 // before it captures its iteration graph, where nothing can be timed.
 bool rbf_tc_tune_pending(int64_t n, int64_t d, int64_t nvec, int passes);
+// Work buffer of rbf_tc_products (input re-layouts and the partial sums of
+// point slices), error word first.
 size_t rbf_tc_work_bytes(int64_t n, int64_t nvec, int passes);
 int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, double sigma,
                         int64_t nvec, const float* V, int64_t ldv, int shift, const double* d_mu,

@@ -44,48 +44,53 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 }
 
 // Factor the diagonal block D = M[k:k+nb, k:k+nb] in place: D = C_kk^T C_kk.
-// One warp, registers only: lane c holds column c (rows 0..31); step j
-// broadcasts the pivot and row j by shuffles, and lane c updates rows
-// j < r <= c of its column.  Loops are unrolled so the column stays in
-// registers.  The pivot's reciprocal square root comes from rsqrt_newton
-// (GB300 runs FP64 division and square root as long dependent chains): the
-// row is scaled by it and the pivot is d times it.
+// One warp; the block sits in shared memory and lane c owns column c.  Step
+// j: lane j takes the pivot's reciprocal square root (rsqrt_newton: GB300
+// runs FP64 division and square root as long dependent chains), the lanes
+// scale row j (C[j][c] = D[j][c] / C_jj), and lane c updates rows
+// j < r <= c of its column with the broadcast C[j][r].  The step loop is not
+// unrolled: a fully unrolled 32 x 32 body (the first version) is thousands
+// of instructions, which one warp cannot keep in the instruction cache.
 __global__ void __launch_bounds__(32) chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb,
                                                        int* info) {
   if (*info != 0) return;
+  __shared__ double D[CH_NB][CH_NB + 1];
+  __shared__ double s_rp;
+  __shared__ int s_bad;
   const int c = threadIdx.x;
-  double col[CH_NB];
 #pragma unroll
   for (int r = 0; r < CH_NB; ++r)
-    col[r] = (r < nb && c < nb) ? M[(k + r) * ell + k + c] : (r == c ? 1.0 : 0.0);
-  int bad = 0;
-#pragma unroll
-  for (int j = 0; j < CH_NB; ++j) {
-    if (j < nb && !bad) {
-      const double d = __shfl_sync(0xffffffffu, col[j], j);  // D[j][j] (lane j)
+    D[r][c] = (r < nb && c < nb) ? M[(k + r) * ell + k + c] : (r == c ? 1.0 : 0.0);
+  if (c == 0) s_bad = 0;
+  __syncwarp();
+  for (int j = 0; j < nb; ++j) {
+    if (c == j) {
+      const double d = D[j][j];
       if (!(d > 0.0) || !isfinite(d)) {
-        bad = (int)(k + j + 1);
+        s_bad = (int)(k + j + 1);
       } else {
         const double rp = rsqrt_newton(d);
-        if (c == j) col[j] = d * rp;                       // sqrt(d)
-        else if (c > j) col[j] = col[j] * rp;              // C[j][c]
-        // C[j][r] for r > j sits in lane r at index j: rows r <= c of this column
-#pragma unroll
-        for (int r = j + 1; r < CH_NB; ++r) {
-          const double cjr = __shfl_sync(0xffffffffu, col[j], r);
-          if (r <= c && c < nb) col[r] -= cjr * col[j];
-        }
+        s_rp = rp;
+        D[j][j] = d * rp;  // sqrt(d)
       }
     }
+    __syncwarp();
+    if (s_bad) break;
+    if (c > j && c < nb) D[j][c] *= s_rp;  // C[j][c]
+    __syncwarp();
+    if (c > j && c < nb) {
+      const double cjc = D[j][c];
+      for (int r = j + 1; r <= c; ++r) D[r][c] = fma(-D[j][r], cjc, D[r][c]);
+    }
+    __syncwarp();
   }
-  if (bad) {
-    if (c == 0) atomicCAS(info, 0, bad);
+  if (s_bad) {
+    if (c == 0) atomicCAS(info, 0, s_bad);
     return;
   }
   if (c < nb) {
-#pragma unroll
-    for (int r = 0; r < CH_NB; ++r)
-      if (r < nb) M[(k + r) * ell + k + c] = (c >= r) ? col[r] : 0.0;
+#pragma unroll 4
+    for (int r = 0; r < nb; ++r) M[(k + r) * ell + k + c] = (c >= r) ? D[r][c] : 0.0;
   }
 }
 

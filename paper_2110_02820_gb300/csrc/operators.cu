@@ -1004,6 +1004,11 @@ struct MatvecTimer {
 };
 }  // namespace
 
+bool timing_active() {
+  std::lock_guard<std::mutex> lk(g_tm_mutex);
+  return g_tm_on;
+}
+
 void timing_capture_begin() {
   std::lock_guard<std::mutex> lk(g_tm_mutex);
   g_tm_ph_used = 0;
@@ -1246,12 +1251,12 @@ rbf_batched_kernel(const float* __restrict__ pts, int64_t n, int64_t d, int64_t 
 
 int32_t op_matvec_batched_f32(const nys_operator* op, const double* d_mu, int64_t nsys,
                               const float* P, float* V, const int* done0, int64_t done_stride,
-                              int* err, cudaStream_t s) {
+                              int* err, void* work, cudaStream_t s) {
   if (op->kind != NYS_OP_RBF) return NYS_ERR_ARG;
   MatvecTimer timer(s);
   if (rbf_tc_supported(op->d))
     return rbf_tc_products((const float*)op->data, op->n, op->d, op->ld, op->sigma, nsys, P, op->n,
-                           2, d_mu, 0.0, V, op->n, 3, done0, done_stride, nullptr, err, s);
+                           2, d_mu, 0.0, V, op->n, 3, done0, done_stride, work, err, s);
   dim3 grid((unsigned)cdiv(op->n, RB_BI), (unsigned)cdiv(nsys, RB_BS));
   rbf_batched_kernel<<<grid, 256, 0, s>>>((const float*)op->data, op->n, op->d, op->ld, op->sigma,
                                           nsys, d_mu, P, V, done0, done_stride);

@@ -776,6 +776,26 @@ static bool pcg_graphs_enabled() {
   return v == 1;
 }
 
+// Device-side loop (a conditional WHILE node) instead of replayed chunks:
+// NYS_PCG_LOOP=0 in the environment turns it off at start-up; nys_pcg_loop()
+// switches it.
+static std::atomic<int> g_pcg_loop{-1};
+static bool pcg_loop_enabled() {
+  int v = g_pcg_loop.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("NYS_PCG_LOOP");
+    v = (e && e[0] == '0') ? 0 : 1;
+    g_pcg_loop.store(v, std::memory_order_relaxed);
+  }
+  return v == 1;
+}
+
+int32_t pcg_loop(int32_t on) {
+  const int32_t prev = pcg_loop_enabled() ? 1 : 0;
+  if (on == 0 || on == 1) g_pcg_loop.store(on, std::memory_order_relaxed);
+  return prev;
+}
+
 static std::atomic<unsigned long long> g_graph_replays{0};
 unsigned long long pcg_graph_replays() { return g_graph_replays.load(std::memory_order_relaxed); }
 
@@ -846,6 +866,93 @@ struct IterGraph {
   }
 };
 
+// The whole PCG loop as one CUDA graph: a conditional WHILE node whose body
+// is one iteration (the product and the PCG kernels) followed by a one-block
+// kernel that counts the iteration and keeps the loop going while a system
+// is still running and fewer than `limit` iterations have run.  A solve is
+// then a single launch with no host round trip.  Conditional bodies may hold
+// kernels, memsets and copies only, so this is used when the products of the
+// iteration allocate nothing and no timing events are recorded; otherwise
+// IterGraph replays fixed chunks between host checks.
+__global__ void loop_cond_kernel(const SysState* __restrict__ st, int64_t nsys,
+                                 unsigned* __restrict__ count, unsigned limit,
+                                 cudaGraphConditionalHandle h) {
+  __shared__ int running;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int64_t q = threadIdx.x; q < nsys; q += blockDim.x) mine |= (st[q].done == 0);
+  if (mine) running = 1;  // benign race: every writer stores 1
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned c = *count + 1;
+    *count = c;
+    cudaGraphSetConditional(h, (running && c < limit) ? 1u : 0u);
+  }
+}
+
+struct LoopGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  long long body_launches = 0;  // kernels per loop iteration
+  ~LoopGraph() {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+  }
+  bool ok() const { return ge != nullptr; }
+  template <typename F>
+  void build(F& iteration, const SysState* st, int64_t nsys, unsigned* count, unsigned limit) {
+    thread_local cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+      cudaGetLastError();
+      return;
+    }
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+      streams[dev] = nullptr;
+      cudaGetLastError();
+      return;
+    }
+    cudaStream_t cs = streams[dev];
+    cudaGraphConditionalHandle h;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess ||
+        cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const unsigned long long c0 = launch_count();
+    int32_t st_ok = NYS_ERR_CUDA;
+    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      st_ok = iteration(cs);
+      loop_cond_kernel<<<1, 256, 0, cs>>>(st, nsys, count, limit, h);
+      count_launch();
+      cudaGraph_t out = nullptr;
+      if (cudaStreamEndCapture(cs, &out) != cudaSuccess) st_ok = NYS_ERR_CUDA;
+    }
+    body_launches = (long long)(launch_count() - c0);
+    count_launches(-body_launches);  // recorded, not run
+    if (st_ok == NYS_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
+    if (st_ok != NYS_OK) ge = nullptr;
+    cudaGetLastError();  // a refused capture leaves no sticky error
+  }
+  int32_t launch(cudaStream_t s) {
+    NYS_CUDA_TRY(cudaGraphLaunch(ge, s));
+    g_graph_replays.fetch_add(1, std::memory_order_relaxed);
+    return NYS_OK;
+  }
+};
+
 // Runs Algorithm 3 on T vectors.  x (device, T, [nsys][n]) receives the
 // solution; b_dev (device FP64 [nsys][n]) is the right-hand side; with
 // use_x0 the incoming x is the initial guess.  Fills iterations/status.
@@ -893,7 +1000,13 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
     }
   }
   size_t wbytes = op_matvec_work_bytes(op, sizeof(T) == sizeof(double));
+  const bool rbf_tc_batch = std::is_same<T, float>::value && !accurate && nsys > 1 &&
+                            op->kind == NYS_OP_RBF && rbf_tc_supported(op->d);
+  // the batched Gaussian product works in this buffer (no allocation per product)
+  if (rbf_tc_batch) wbytes = std::max(wbytes, rbf_tc_work_bytes(n, nsys, 3));
   NYS_TRY(B.get(&B.op_work, wbytes));
+  unsigned* loop_count;
+  NYS_TRY(B.get((void**)&loop_count, sizeof(unsigned)));
   NYS_CUDA_TRY(cudaMemsetAsync(B.op_work, 0, 256, s));
   NYS_CUDA_TRY(cudaMemsetAsync(a.counters, 0, (size_t)nsys * 4 * sizeof(unsigned), s));
   NYS_CUDA_TRY(cudaMemcpyAsync(B.d_mu, mus_host, nsys * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -954,7 +1067,8 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
       // one pass over the kernel matrix for all systems
       return op_matvec_batched_f32(op, B.d_mu, nsys, (const float*)a.p, (float*)a.v,
                                    &a.st[0].done, (int64_t)(sizeof(SysState) / sizeof(int)),
-                                   reinterpret_cast<int*>(B.op_work), st);
+                                   reinterpret_cast<int*>(B.op_work),
+                                   rbf_tc_batch ? B.op_work : nullptr, st);
     }
     for (int64_t q = 0; q < nsys; ++q)
       NYS_TRY(matvec_T<T>(op, mus_host[q], a.p + q * n, a.v + q * n, &a.st[q].done, B.op_work,
@@ -974,6 +1088,11 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
   // and replayed between host checks (one launch instead of ~7 per
   // iteration).  Falls back to plain launches when capture is not possible.
   IterGraph graph;
+  LoopGraph loop;
+  // The device-side loop needs products that allocate nothing inside the
+  // iteration (FP64 Gaussian products and the FP64-accurate ones do) and no
+  // timing events.
+  const bool alloc_free = !accurate && (op->kind != NYS_OP_RBF || std::is_same<T, float>::value);
   if (maxit > 0 && pcg_graphs_enabled()) {
     // the tuner times launch shapes on a live stream only: let it see this
     // solve's product once before the capture (v is recomputed by the first
@@ -981,12 +1100,25 @@ static int32_t run_pcg(const nys_operator* op, const TU* U, const double* lam, i
     if (!accurate && std::is_same<T, float>::value && op->kind == NYS_OP_RBF &&
         rbf_tc_tune_pending(n, op->d, batched_rbf ? nsys : 1, 3))
       NYS_TRY(products(s));
-    graph.build(iteration);
+    if (alloc_free && pcg_loop_enabled() && !timing_active())
+      loop.build(iteration, a.st, nsys, loop_count, (unsigned)maxit);
+    if (!loop.ok()) graph.build(iteration);
   }
   std::vector<SysState> hst(nsys);
   int64_t launched = 0;
   int chunk = 4;
-  while (true) {
+  if (loop.ok()) {
+    // one launch runs the iterations until every system is done or maxit
+    NYS_CUDA_TRY(cudaMemsetAsync(loop_count, 0, sizeof(unsigned), s));
+    NYS_TRY(loop.launch(s));
+    unsigned ran = 0;
+    NYS_CUDA_TRY(cudaMemcpyAsync(&ran, loop_count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    NYS_CUDA_TRY(cudaMemcpyAsync(hst.data(), a.st, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s));
+    NYS_CUDA_TRY(cudaStreamSynchronize(s));
+    count_launches(loop.body_launches * (long long)ran);
+    launched = ran;
+  }
+  while (!loop.ok()) {
     if (graph.ok()) {
       for (int c = 0; c < chunk && launched < maxit; c += kGraphIters, launched += kGraphIters)
         NYS_TRY(graph.replay(s));
@@ -1279,7 +1411,7 @@ static int32_t pcg_reliable_one(const nys_operator* op, const float* U, const do
   NYS_CUDA_TRY(cudaStreamSynchronize(s));
   double rr_seg = h.rr;  // recurrence ||r||^2 at the start of the segment
   double rel_prev = rel;
-  int stall = 0;
+  int stall = 0, slow = 0;
   int64_t launched = 0;
   int chunk = 4;
   while (true) {
@@ -1321,6 +1453,14 @@ static int32_t pcg_reliable_one(const nys_operator* op, const float* U, const do
     if (h.it >= maxit || launched >= maxit) {
       // budget spent above tol: the escalating loop continues (its
       // FP64-accurate inner solves have a budget of their own)
+      *stalled = true;
+      break;
+    }
+    // a segment that cut the true residual by less than 10 (the recurrence
+    // promised 1/delta) twice in a row: the FP32 products' error, not the
+    // recurrence, sets the pace; the escalating loop takes over
+    slow = (rel > 0.1 * rel_prev) ? slow + 1 : 0;
+    if (slow >= 2 && rel <= 0.5 * rel_prev) {
       *stalled = true;
       break;
     }

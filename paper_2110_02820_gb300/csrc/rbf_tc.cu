@@ -65,6 +65,7 @@ constexpr int RT_THREADS = 64 + 32 * RT_EXP_WARPS;
 constexpr uint32_t RT_TMEM_COLS = 512;
 // TMEM column map: P tiles at 0 / 64, K tiles (hi, lo) at 128 / 256, Yacc at 384 (/ 448).
 constexpr uint32_t TM_P = 0, TM_K = 128, TM_Y = 384;
+constexpr int kMaxSlices = 4;  // point slices of a product (partial sums in the work buffer)
 constexpr int RT_CH = 2;  // tiles per GEMM2 accumulation chunk
 // exp group 0 takes the even tiles and promotes a chunk when it reaches the
 // next chunk's first tile, so a chunk must span an even number of tiles
@@ -924,20 +925,22 @@ __global__ void rt_prep_vecs_kernel(const float* __restrict__ V, int64_t nvec, i
   }
 }
 
+// part_ws: room for kMaxSlices x nvec x npad partial sums (inside the work
+// buffer, so that a product allocates nothing while a graph is captured)
 template <int S, int P2>
 int32_t rt_launch(const CUtensorMap& tx, const CUtensorMap& tv, const RtArgs& a0, int64_t npad,
-                  int64_t nblk_y, int nz, cudaStream_t s) {
+                  int64_t nblk_y, int nz, float* part_ws, cudaStream_t s) {
   using Cfg = RtCfg<S, P2>;
   auto kern = rbf_tc_kernel<S, P2>;
   NYS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
   RtArgs a = a0;
-  Scratch sp(s);
   if (nz > 1) {
+    if (nz > kMaxSlices) return NYS_ERR_ARG;
     const int chunk = (int)cdiv(a.ntiles, nz);
     nz = (int)cdiv(a.ntiles, chunk);
     a.tile_chunk = chunk;
     a.part_stride = npad;
-    NYS_TRY(sp.get(&a.ypart, (size_t)nz * a.nvec * npad));
+    a.ypart = part_ws;
   }
   kern<<<dim3((unsigned)(npad / RT_BM), (unsigned)nblk_y, (unsigned)nz), RT_THREADS, Cfg::SMEM,
          s>>>(tx, tv, a);
@@ -953,13 +956,13 @@ int32_t rt_launch(const CUtensorMap& tx, const CUtensorMap& tv, const RtArgs& a0
 
 // One vector at a time (nvec <= 2), the points split into nz slices.
 int32_t gv_run(const CUtensorMap& tx16, const RtArgs& a, const float* VS, const float* m2c_dev,
-               int64_t npad, int64_t ntiles, int64_t d, int64_t nvec, int nz, cudaStream_t s) {
+               int64_t npad, int64_t ntiles, int64_t d, int64_t nvec, int nz, float* part_ws,
+               cudaStream_t s) {
   const int64_t ctas = npad / RT_BM;
+  if (nz > kMaxSlices) return NYS_ERR_ARG;
   const int chunk = (int)cdiv(ntiles, nz);
   nz = (int)cdiv(ntiles, chunk);
-  Scratch sp(s);
-  float* part = nullptr;
-  if (nz > 1) NYS_TRY(sp.get(&part, (size_t)nz * npad));
+  float* part = nz > 1 ? part_ws : nullptr;  // kMaxSlices x npad, reused vector by vector
   for (int64_t q = 0; q < nvec; ++q) {
     RtArgs aq = a;
     aq.vec = q;
@@ -987,7 +990,7 @@ int32_t gv_run(const CUtensorMap& tx16, const RtArgs& a, const float* VS, const 
 // partial sums (slices x nvec x npad floats) at most 256 MB.
 std::vector<int> gv_slice_candidates(int64_t ntiles) {
   std::vector<int> c;
-  for (int z = 1; z <= 4; ++z)
+  for (int z = 1; z <= kMaxSlices; ++z)
     if (z == 1 || ntiles >= 2 * z) c.push_back(z);
   return c;
 }
@@ -996,7 +999,7 @@ std::vector<int> rt_slice_candidates(int64_t npad, int64_t nvec, int64_t ctas, i
   std::vector<int> c{1};
   if (ctas >= 8 * sms) return c;
   const int64_t ntiles = npad / RT_BN;
-  for (int z = 2; z <= 4; ++z)
+  for (int z = 2; z <= kMaxSlices; ++z)
     if (ntiles >= 4 * z && (double)z * nvec * npad * 4.0 <= 256.0 * (1 << 20)) c.push_back(z);
   return c;
 }
@@ -1052,13 +1055,19 @@ bool rbf_tc_tune_pending(int64_t n, int64_t d, int64_t nvec, int passes) {
   return c.size() > 1 && !tune_cached(rt_tune_key(S, passes, npad, d, nblk_y), nullptr);
 }
 
+// Layout of the work buffer: [256: error word and one-vector scalars]
+// [XS: npad x 64 FP32] [cn: npad] [VS: nv x spad x npad] [partial sums of up
+// to kMaxSlices point slices: kMaxSlices x (nvec or 1) x npad].
+static size_t rt_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
 size_t rbf_tc_work_bytes(int64_t n, int64_t nvec, int passes) {
   const int64_t npad = cdiv(n, RT_BM) * RT_BM;
   const int S = rt_block(nvec, passes);
   const int64_t spad = cdiv(nvec, S) * S;
   const int nv = S == 1 ? 1 : (passes == 3 ? 2 : 1);
-  return 256 + (size_t)npad * 64 * 4 + 256 + (size_t)npad * 4 + 256 +
-         (size_t)nv * spad * npad * 4 + 256;
+  return 256 + rt_align((size_t)npad * 64 * 4) + rt_align((size_t)npad * 4) +
+         rt_align((size_t)nv * spad * npad * 4) +
+         rt_align((size_t)kMaxSlices * (S == 1 ? 1 : nvec) * npad * 4);
 }
 
 int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, double sigma,
@@ -1079,10 +1088,11 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
     NYS_CUDA_TRY(cudaMemsetAsync(w, 0, 256, s));
   }
   if (!err) err = reinterpret_cast<int*>(w);
-  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
   float* XS = reinterpret_cast<float*>(w + 256);
-  float* cn = reinterpret_cast<float*>(w + 256 + align((size_t)npad * 64 * 4));
-  float* VS = reinterpret_cast<float*>((unsigned char*)cn + align((size_t)npad * 4));
+  float* cn = reinterpret_cast<float*>(w + 256 + rt_align((size_t)npad * 64 * 4));
+  float* VS = reinterpret_cast<float*>((unsigned char*)cn + rt_align((size_t)npad * 4));
+  float* part_ws = reinterpret_cast<float*>((unsigned char*)VS +
+                                            rt_align((size_t)(nv ? nv : 1) * spad * npad * 4));
   const double l2e = 1.4426950408889634;
   const double c = -l2e / (2.0 * sigma * sigma);
   if (S > 1) {  // one vector uses the FP16 layout below
@@ -1145,18 +1155,19 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
     int nz = 1;
     NYS_TRY(tune_pick(gv_tune_key(npad, d, nvec), cands, wave_fill_rule(ctas, cands, sms),
                       [&](int z) -> int32_t {
-                        return gv_run(tx16, a, VS, m2c_dev, npad, ntiles, d, nvec, z, s);
+                        return gv_run(tx16, a, VS, m2c_dev, npad, ntiles, d, nvec, z, part_ws,
+                                      s);
                       },
                       s, &nz));
-    return gv_run(tx16, a, VS, m2c_dev, npad, ntiles, d, nvec, nz, s);
+    return gv_run(tx16, a, VS, m2c_dev, npad, ntiles, d, nvec, nz, part_ws, s);
   }
   // many vectors: point slices over grid.z where the grid is only a few waves
   const int64_t nblk_y = spad / S;
   const int64_t ctas = (npad / RT_BM) * nblk_y, sms = num_sms();
   const std::vector<int> cands = rt_slice_candidates(npad, nvec, ctas, sms);
   auto run = [&](int z) -> int32_t {
-    return S == 64 ? rt_launch<64, 3>(tx, tv, a, npad, nblk_y, z, s)
-                   : rt_launch<128, 1>(tx, tv, a, npad, nblk_y, z, s);
+    return S == 64 ? rt_launch<64, 3>(tx, tv, a, npad, nblk_y, z, part_ws, s)
+                   : rt_launch<128, 1>(tx, tv, a, npad, nblk_y, z, part_ws, s);
   };
   int nz = 1;
   NYS_TRY(tune_pick(rt_tune_key(S, passes, npad, d, nblk_y), cands,

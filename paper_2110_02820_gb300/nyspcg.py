@@ -131,6 +131,16 @@ def pcg_graphs(on: int | None = None) -> bool:
     return bool(lib().nys_pcg_graphs(arg))
 
 
+def pcg_loop(on: int | None = None) -> bool:
+    """Device-side PCG loop (one graph launch per solve; True = on); sets it
+    when `on` is 0 or 1 and returns the previous mode."""
+    f = lib().nys_pcg_loop
+    if f.argtypes is None:
+        f.argtypes = [C.c_int32]
+        f.restype = C.c_int32
+    return bool(f(-1 if on is None else int(on)))
+
+
 def pcg_reliable(on: int | None = None) -> bool:
     """Reliable-update mode of one-system mixed solves (True = on); sets it when
     `on` is 0 or 1 and returns the previous mode."""

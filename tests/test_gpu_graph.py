@@ -1,8 +1,10 @@
-"""PCG under a CUDA graph: the iteration loop of Algorithm 3 captured once per
-solve and replayed gives bit-identical results to plain stream launches (the
-same kernels with the same arguments in the same order), launches the same
-kernels, overruns the iteration cap safely and keeps the per-product event
-timing."""
+"""PCG under a CUDA graph: the iteration loop of Algorithm 3 run on the device
+(one launch of a graph whose conditional WHILE node repeats one iteration),
+or captured as a chunk of four iterations and replayed between host checks,
+gives bit-identical results to plain stream launches (the same kernels with
+the same arguments in the same order); the replayed chunks launch the same
+kernels as plain launches, both graph forms stop at the iteration cap, and
+timed products keep their event timing."""
 
 import numpy as np
 import pytest
@@ -19,31 +21,37 @@ def ny():
     from paper_2110_02820_gb300 import build, nyspcg
     build.build()
     nyspcg.lib()
-    prev = nyspcg.pcg_graphs()
+    prev, prev_loop = nyspcg.pcg_graphs(), nyspcg.pcg_loop()
     yield nyspcg
     nyspcg.pcg_graphs(prev)
+    nyspcg.pcg_loop(prev_loop)
 
 
 def T(a):
     return torch.tensor(np.ascontiguousarray(a), device="cuda")
 
 
-def both_modes(ny, solve):
-    """Runs `solve` with graphs on, then off; returns both results and the
-    kernel launches of each."""
+def both_modes(ny, solve, loop_result=True):
+    """Runs `solve` with replayed graph chunks, then plain launches (and
+    checks the device-side loop against them); returns the chunked and plain
+    results and the kernel launches of each."""
     out = []
-    for on in (True, False):
-        ny.pcg_graphs(on)
+    for graphs, loop in ((True, False), (False, False), (True, True)):
+        ny.pcg_graphs(graphs)
+        ny.pcg_loop(loop)
         torch.cuda.synchronize()
         c0, g0 = ny.kernel_launch_count(), ny.pcg_graph_replays()
         r = solve()
         torch.cuda.synchronize()
         replays = ny.pcg_graph_replays() - g0
-        # graph mode really replayed graphs; plain mode replayed none
-        assert (replays > 0) if on else (replays == 0)
+        # graph modes really launched graphs; plain mode launched none
+        assert (replays > 0) if graphs else (replays == 0)
         out.append((r, ny.kernel_launch_count() - c0))
     ny.pcg_graphs(True)
-    return out
+    ny.pcg_loop(True)
+    if loop_result:
+        same(out[2][0], out[0][0])  # the device-side loop: same kernels, same results
+    return out[:2]
 
 
 def same(ra, rb):
@@ -141,3 +149,32 @@ def test_graph_replays_keep_product_timing(ny):
     assert ms_g > 0 and ms_p > 0
     # the same kernels: the mean product time agrees within launch jitter
     assert 0.5 < (ms_g / cnt_g) / (ms_p / cnt_p) < 2.0
+
+
+def test_device_loop_is_one_launch_per_solve(ny):
+    # with the device-side loop, an FP64 solve is one graph launch whatever its
+    # iteration count, and a batched mixed solve one launch per inner solve
+    n, ell = 900, 30
+    A, _ = wl.dense_spd(n, seed=25)
+    op = ny.dense_operator(T(A))
+    f = ny.nys_sketch(op, ell, omega=T(wl.omega(n, ell, 25)))
+    b = T(wl.rhs(n, seed=25))
+    ny.pcg_graphs(True)
+    ny.pcg_loop(True)
+    g0 = ny.pcg_graph_replays()
+    x, res, _ = ny.pcg_solve(op, f, 1e-5, b, tol=1e-10)
+    assert res[0].status == ny.NYS_OK and res[0].iterations > 16
+    assert ny.pcg_graph_replays() - g0 == 1
+    # 8 systems of a Gaussian kernel, mixed precision: one launch per refinement step
+    m, d, ell2 = 1200, 16, 80
+    P = wl.gmm_points(m, d, seed=26)
+    sigma = wl.median_distance(P, seed=26)
+    opk = ny.rbf_operator(T(P), sigma)
+    fk = ny.nys_sketch(opk, ell2, omega=T(wl.omega(m, ell2, 26)), precision=ny.NYS_PREC_MIXED)
+    mus = list(np.repeat(wl.regularization_path(2, 1e-3 * m, 1e-1 * m), 4))
+    B = T(np.tile(wl.rhs(m, seed=26, nrhs=4), (2, 1)))
+    ny.pcg_solve(opk, fk, mus, B, tol=1e-8, precision=ny.NYS_PREC_MIXED)  # tuner warm-up
+    g0 = ny.pcg_graph_replays()
+    X, resk, _ = ny.pcg_solve(opk, fk, mus, B, tol=1e-8, precision=ny.NYS_PREC_MIXED)
+    assert all(r.status == ny.NYS_OK for r in resk)
+    assert ny.pcg_graph_replays() - g0 == max(r.refinements for r in resk)

@@ -422,12 +422,13 @@ def test_reliable_updates_match_refinement_and_fp64(ny, kind, reliable_mode):
 
 
 def test_reliable_updates_fall_back_to_escalation(ny, reliable_mode):
-    # a dense system whose FP32 products carry an error far above mu (40
-    # eigenvalues in [1e-2, 1], the rest in [1e-10, 3e-9], mu = 1e-9) while
-    # the preconditioned system is well conditioned: the reliable recurrence
-    # cannot reach the tolerance, hands the system to the escalating loop,
-    # whose FP64 inner solves do
-    n, ell, mu = 600, 48, 1e-9
+    # a dense system whose FP32 products carry an error comparable to mu (40
+    # eigenvalues in [1e-2, 1], the rest in [1e-10, 3e-9], mu = 1e-7: FP32
+    # products err by ~6e-8 ||A||) while the preconditioned system is well
+    # conditioned and FP64 residuals resolve 1e-8 (kappa u_64 ~ 1e-9): the
+    # reliable recurrence cannot reach the tolerance, hands the system to the
+    # escalating loop, whose FP64 inner solves do
+    n, ell, mu = 600, 48, 1e-7
     lam = np.concatenate([np.logspace(0, -2, 40), np.logspace(np.log10(3e-9), -10, n - 40)])
     A, _ = wl.dense_spd(n, seed=17, eigenvalues=lam)
     b = wl.rhs(n, seed=17)
