@@ -717,7 +717,7 @@ def workload_record(args, name, steps, warmup, peaks=None):
         mv_total, mv_cnt = ny.timing_stop()
         mv_ms = mv_total / max(mv_cnt, 1)
         kern = ("rbf_gemv_kernel (tensor-core distances, one vector)" if name == "krr"
-                else "rbf_tc_kernel<64,3> (tensor cores, 64 systems per CTA)")
+                else "rbf_tc_kernel<S,3,fp16> (tensor cores)")
         if args.precision == "f64":
             kern = "rbf_products_kernel (FP64 entries and sums; not event-timed)"
         line.update({"dtype": "f64" if args.precision == "f64" else "f32",
@@ -751,23 +751,35 @@ def workload_record(args, name, steps, warmup, peaks=None):
                              "status_by_mu": [[float(m), r.status, r.iterations, r.rel_residual]
                                               for m, r in list(zip(mus, res))[::4]]}
             if peaks and args.precision != "f64":
-                # the full 128-vector product alone (3xTF32 passes on the TF32 pipe)
+                # the full 128-vector product alone: FP16 splits (kind::f16, three
+                # passes of each GEMM) in the tuned shape (vectors per CTA)
                 V = T(np.tile(wl.rhs(n, seed=1, nrhs=4), (32, 1)))
                 ny.nys_op_matvec(op, 1e-6 * n, V, mode=1)
                 pms, _ = _events_steps(lambda: ny.nys_op_matvec(op, 1e-6 * n, V, mode=1), 3)
+                npad = (n + 127) // 128 * 128
+                code = next((c for k, c in ny.autotune_choices().items()
+                             if k.startswith(f"rbf_tc16 passes=3 npad={npad} ")), None)
+                S = (128, 64, 32)[code // 8] if code is not None else 128
+                cols = -(-V.shape[0] // S)
                 alg = 2.0 * n * n * (V.shape[0] + d)
-                exe = 3.0 * 2.0 * n * n * (V.shape[0] + 2 * d)
+                ks16 = 16 * (-(-d // 16))
+                exe = 3.0 * 2.0 * npad * npad * (cols * S + cols * ks16)
+                line["dominant_kernel"]["kernel"] = f"rbf_tc_kernel<{S},3,fp16> (tensor cores, " \
+                                                    f"{S} systems per CTA)"
                 line["roofline"] = {"bound": "tensor", "unit": "TFLOP/s",
                                     "achieved": alg / (pms * 1e-3) / 1e12,
-                                    "peak": peaks["tf32_tflops"],
-                                    "frac": alg / (pms * 1e-3) / 1e12 / peaks["tf32_tflops"],
+                                    "peak": peaks["bf16_tflops"],
+                                    "frac": alg / (pms * 1e-3) / 1e12 / peaks["bf16_tflops"],
                                     "executed_tflops": exe / (pms * 1e-3) / 1e12,
-                                    "tensor_pipe_frac": exe / (pms * 1e-3) / 1e12 / peaks["tf32_tflops"],
+                                    "tensor_pipe_frac": exe / (pms * 1e-3) / 1e12 / peaks["bf16_tflops"],
                                     "ms_per_launch": pms,
+                                    "vectors_per_cta": S, "tuned_code": code,
                                     "work": "algorithmic 2 n^2 (nvec + d) FLOP for 128 vectors; "
-                                            "executed = 3 TF32 passes of the distance GEMM per "
-                                            "64-vector group and of the kernel-times-vectors GEMM",
-                                    "peak_source": "TF32 = measured BF16 x 1.1/2.25 (nominal ratio)"}
+                                            "executed = 3 FP16 passes of the distance GEMM (K "
+                                            "padded to 16) per CTA column and of the "
+                                            "kernel-times-vectors GEMM, padded n",
+                                    "peak_source": "FP16 dense = measured BF16 rate (same "
+                                                   "nominal rate)"}
         line["phases_ms"] = dict(phase)
     elif name == "block":
         # block Nystrom PCG: nrhs right-hand sides of one shifted Gaussian-kernel

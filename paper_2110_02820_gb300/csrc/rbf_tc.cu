@@ -34,13 +34,24 @@
 //                   Yacc chunks and writes the result (+ mu_s v_i).
 // Tensor-core FP32 accumulation does not round to nearest; a long chain of
 // accumulating MMAs drifts toward zero (~1e-8 relative per MMA, measured), so
-// GEMM2 accumulates RT_CH tiles at a time and group 0 adds each chunk into
-// FP32 sums with ordinary rounding.  Two tiles per chunk (48 chained MMAs)
-// leave 1.5e-6 norm-wise error on a product against 2.6e-6 with four
+// GEMM2 accumulates a chunk of tiles at a time (48 chained MMAs) and the exp
+// groups add each chunk into FP32 sums with ordinary rounding.  Chunks of 48
+// MMAs leave 1.5e-6 norm-wise error on a product against 2.6e-6 with 96
 // (measured at n = 5e4), and the regularisation path's refinement then
-// contracts faster (7.7 s per path instead of 9.6 s).  Every wait is bounded; on expiry the CTA
-// records NYS_ERR_TIMEOUT in *err, lets its copies in flight land, frees its
-// TMEM and returns.
+// contracts faster.  Every wait is bounded; on expiry the CTA records
+// NYS_ERR_TIMEOUT in *err, lets its copies in flight land, frees its TMEM and
+// returns.
+//
+// Many vectors run by default on FP16 splits (rbf_h16_kernel below: kind::f16
+// at twice the TF32 rate, K tiles half the size in TMEM, a four-deep TMEM
+// pipeline); the 3xTF32 kernel above it stays selectable (NYS_RBF_TF32=1).
+// FP16 splits: the points scaled by a power of two (max |x| in [2^9, 2^10)),
+// the kernel entries by 2^15 (k in (0, 2^15]) and each vector by its own
+// power of two (max |v| in [2^14, 2^15)), each value split as hi = fp16(x),
+// lo = fp16(x - hi), and the result scaled back by 2^-(15 + e_s).  An FP16
+// hi + lo pair carries 22 significant bits like a TF32 pair; below the FP16
+// normal range the split is absolute, at most 2^-39 of the largest entry of
+// the operand.
 
 #include <cuda_fp16.h>
 
@@ -63,31 +74,40 @@ constexpr int RT_DP = 32;    // padded point dimension (d <= 32)
 constexpr int RT_EXP_WARPS = 8;
 constexpr int RT_THREADS = 64 + 32 * RT_EXP_WARPS;
 constexpr uint32_t RT_TMEM_COLS = 512;
-// TMEM column map: P tiles at 0 / 64, K tiles (hi, lo) at 128 / 256, Yacc at 384 (/ 448).
-constexpr uint32_t TM_P = 0, TM_K = 128, TM_Y = 384;
 constexpr int kMaxSlices = 4;  // point slices of a product (partial sums in the work buffer)
-constexpr int RT_CH = 2;  // tiles per GEMM2 accumulation chunk
-// exp group 0 takes the even tiles and promotes a chunk when it reaches the
-// next chunk's first tile, so a chunk must span an even number of tiles
-static_assert(RT_CH % 2 == 0 && RT_CH >= 2, "RT_CH");
 
+// The 3xTF32 kernel (kind::tf32, K = 8 per MMA): X_I, X_J and the vectors
+// as TF32 hi and lo arrays.
 template <int S, int P2>
 struct RtCfg {
-  static constexpr bool GEMV = (S == 1);        // one vector: no GEMM2
-  static constexpr int NV = GEMV ? 0 : (P2 == 3 ? 2 : 1);
-  static constexpr int A_BYTES = RT_BM * 128;   // X_I hi (or lo): 128 rows x 32 FP32
-  static constexpr int XJ_BYTES = RT_BN * 128;  // X_J hi (or lo)
-  static constexpr int VSLAB = GEMV ? 0 : S * 128;
-  static constexpr int CN_OFF = 2 * XJ_BYTES + NV * 2 * VSLAB;
-  static constexpr int VJ_OFF = CN_OFF + RT_BN * 4;  // one vector: v_J
-  static constexpr int TX = GEMV ? VJ_OFF + RT_BN * 4 : CN_OFF + RT_BN * 4;
+  static constexpr int NV = P2 == 3 ? 2 : 1;    // V arrays: hi, lo (or hi only)
+  static constexpr int A_BYTES = RT_BM * 128;   // X_I: 128 rows x 128 bytes, per array
+  static constexpr int A_ARR = 2;               // hi, lo
+  static constexpr int XJ_BYTES = RT_BN * 128;  // X_J: 64 rows x 128 bytes, per array
+  static constexpr int XJ_ARR = 2;
+  static constexpr int VSLAB = S * 128;         // S vectors x 128 bytes of points
+  static constexpr int VSLABS = 2;              // slabs of 32 points per V array per tile
+  static constexpr int V_OFF = XJ_ARR * XJ_BYTES;
+  static constexpr int CN_OFF = V_OFF + NV * VSLABS * VSLAB;
+  static constexpr int TX = CN_OFF + RT_BN * 4;
   static constexpr int STAGE = (TX + 1023) / 1024 * 1024;
-  static constexpr int NS = GEMV ? 6 : 3;
-  static constexpr bool CHUNKED = !GEMV && S <= 64;
-  static constexpr int SUM_BYTES = GEMV ? RT_BM * 8 : (CHUNKED ? S * RT_BM * 4 : 0);
-  static constexpr int SMEM = 1024 + 2 * A_BYTES + NS * STAGE + SUM_BYTES + 256;
-  static constexpr uint32_t EMPTY_COUNT = GEMV ? 1 + 4 : 1;
-  static_assert(GEMV || (S % 16 == 0 && S <= 128), "S");
+  static constexpr int NS = 3;
+  // tiles per GEMM2 accumulation chunk (24 MMAs per tile at three passes);
+  // exp group 0 takes the even tiles and promotes a chunk when it reaches
+  // the next chunk's first tile, so a chunk spans an even number of tiles
+  static constexpr int CH = 2;
+  static constexpr bool CHUNKED = S <= 64;
+  static constexpr int SUM_BYTES = CHUNKED ? S * RT_BM * 4 : 0;
+  static constexpr int SMEM = 1024 + A_ARR * A_BYTES + NS * STAGE + SUM_BYTES + 256;
+  // TMEM columns: P tiles at 0 / 64; K tiles (hi, lo) at TM_K, KCOLS columns
+  // per part; Yacc (2 chunks) at TM_Y
+  static constexpr uint32_t KCOLS = RT_BN;
+  static constexpr uint32_t TM_K = 128;
+  static constexpr uint32_t TM_Y = TM_K + 4 * KCOLS;
+  static constexpr uint32_t YCOLS = CHUNKED ? 2 * S : S;
+  static_assert(S % 32 == 0 && S <= 128, "S");
+  static_assert(CH % 2 == 0 && CH >= 2, "CH");
+  static_assert(TM_Y + YCOLS <= RT_TMEM_COLS, "tensor memory");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -116,6 +136,7 @@ struct RtArgs {
   float* ypart;        // partial sums (NULL: write y directly): one vector [slices][npad],
                        // many [slices][nvec][part_stride], no shift term
   int64_t part_stride;
+  const float* vscale;  // [nvec] result scale per vector (FP16 products), or NULL
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -129,6 +150,53 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Instruction descriptor: kind::f16 with FP16 A and B (both K-major), FP32 D.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+  return (1u << 4)                      // D format: F32
+         | (0u << 7)                    // A format: F16
+         | (0u << 10)                   // B format: F16
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+// A operand from tensor memory (the kernel tile, FP16 packed two to a
+// column), B from shared memory.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Two FP32 values rounded to FP16 (nearest even) in one word: x0 in the low
+// half, x1 in the high half.
+__device__ __forceinline__ uint32_t pack_f16x2(float x0, float x1) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+  return r;
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
       : "memory");
 }
 
@@ -200,23 +268,22 @@ __device__ __forceinline__ void reg_fence32(uint32_t (&r)[32]) {
                  "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7])::"memory");
 }
 
-__device__ __forceinline__ void exp_bar_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * RT_EXP_WARPS) : "memory");
-}
 
-// Add Yacc chunk c (TMEM columns TM_Y + 64 (c & 1)) into the FP32 sums of
+// Add Yacc chunk c (TMEM columns TMY + S (c & 1)) into the FP32 sums of
 // row r (sY[s][r]) and release the buffer.  Called by each warp of group 0.
-template <int S>
+template <int S, uint32_t TMY>
 __device__ __forceinline__ bool promote(uint32_t tmem, uint32_t lane_base, int c, uint64_t* ycf,
                                         uint64_t* ycfree, float* sY, int r, int lane) {
   if (!mbar_wait_bounded(&ycf[c & 1], (uint32_t)((c >> 1) & 1))) return false;
   tc_fence_after();
 #pragma unroll 1
-  for (int c0 = 0; c0 < S; c0 += 16) {
-    uint32_t v[16];
-    tmem_ld16(tmem + lane_base + TM_Y + (uint32_t)((c & 1) * 64 + c0), v);
+  for (int c0 = 0; c0 < S; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld32_nw(tmem + lane_base + TMY + (uint32_t)((c & 1) * S + c0), v);
+    tmem_wait_ld();
+    reg_fence32(v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < 32; ++j) {
       float* p = &sY[(c0 + j) * RT_BM + r];
       *p = (c == 0) ? __uint_as_float(v[j]) : *p + __uint_as_float(v[j]);
     }
@@ -230,6 +297,7 @@ __device__ __forceinline__ bool promote(uint32_t tmem, uint32_t lane_base, int c
 // Many vectors: y[sv][row] = val (+ mu_sv v[sv][row]), or, with point
 // slices, the slice's partial sum (the shift is added once, by rt_sum_kernel).
 __device__ __forceinline__ void rt_store(const RtArgs& a, int64_t sv, int64_t row, float val) {
+  if (a.vscale) val *= a.vscale[sv];
   if (a.ypart) {
     a.ypart[((int64_t)blockIdx.z * a.nvec + sv) * a.part_stride + row] = val;
     return;
@@ -248,7 +316,7 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   unsigned char* sm =
       reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;
-  unsigned char* sSt = sm + 2 * Cfg::A_BYTES;
+  unsigned char* sSt = sm + Cfg::A_ARR * Cfg::A_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(sSt + NS * Cfg::STAGE);
   uint64_t* empty = full + NS;
   uint64_t* afull = empty + NS;
@@ -265,7 +333,7 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * RT_BM;
-  const int64_t s0 = Cfg::GEMV ? a.vec : (int64_t)blockIdx.y * S;
+  const int64_t s0 = (int64_t)blockIdx.y * S;
   // this CTA's slice of the point tiles, [t0, t0 + T) (grid.z; see ypart)
   const int t0 = a.tile_chunk > 0 ? (int)blockIdx.z * a.tile_chunk : 0;
   const int T = a.tile_chunk > 0 ? min(a.ntiles - t0, a.tile_chunk) : a.ntiles;
@@ -283,7 +351,7 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     if (!skip) {
       for (int i = 0; i < NS; ++i) {
         mbar_init(&full[i], 1);
-        mbar_init(&empty[i], Cfg::EMPTY_COUNT);
+        mbar_init(&empty[i], 1);
       }
       mbar_init(afull, 1);
       for (int i = 0; i < 2; ++i) {
@@ -297,7 +365,7 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       mbar_init(yfull, 1);
       fence_barrier_init();
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmX) : "memory");
-      if (!Cfg::GEMV) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmV) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmV) : "memory");
     }
   }
   __syncthreads();
@@ -315,11 +383,13 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   } else if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      mbar_arrive_expect_tx(afull, 2u * Cfg::A_BYTES);
-      tma_load_2d(sA, &tmX, 0, (int)m0, afull);
-      tma_load_2d(sA + Cfg::A_BYTES / 2, &tmX, 0, (int)m0 + 64, afull);
-      tma_load_2d(sA + Cfg::A_BYTES, &tmX, RT_DP, (int)m0, afull);
-      tma_load_2d(sA + Cfg::A_BYTES + Cfg::A_BYTES / 2, &tmX, RT_DP, (int)m0 + 64, afull);
+      mbar_arrive_expect_tx(afull, (uint32_t)(Cfg::A_ARR * Cfg::A_BYTES));
+#pragma unroll
+      for (int arr = 0; arr < Cfg::A_ARR; ++arr) {
+        tma_load_2d(sA + arr * Cfg::A_BYTES, &tmX, arr * RT_DP, (int)m0, afull);
+        tma_load_2d(sA + arr * Cfg::A_BYTES + Cfg::A_BYTES / 2, &tmX, arr * RT_DP, (int)m0 + 64,
+                    afull);
+      }
       int issued = 0;
       for (int t = 0; t < T; ++t) {
         const int s = t % NS;
@@ -331,16 +401,16 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         unsigned char* st = sSt + s * Cfg::STAGE;
         const int j0 = (t0 + t) * RT_BN;
         mbar_arrive_expect_tx(&full[s], (uint32_t)Cfg::TX);
-        tma_load_2d(st, &tmX, 0, j0, &full[s]);
-        tma_load_2d(st + Cfg::XJ_BYTES, &tmX, RT_DP, j0, &full[s]);
+#pragma unroll
+        for (int arr = 0; arr < Cfg::XJ_ARR; ++arr)
+          tma_load_2d(st + arr * Cfg::XJ_BYTES, &tmX, arr * RT_DP, j0, &full[s]);
 #pragma unroll
         for (int arr = 0; arr < Cfg::NV; ++arr)
 #pragma unroll
-          for (int slab = 0; slab < 2; ++slab)
-            tma_load_2d(st + 2 * Cfg::XJ_BYTES + (arr * 2 + slab) * Cfg::VSLAB, &tmV,
+          for (int slab = 0; slab < Cfg::VSLABS; ++slab)
+            tma_load_2d(st + Cfg::V_OFF + (arr * Cfg::VSLABS + slab) * Cfg::VSLAB, &tmV,
                         j0 + 32 * slab, (int)(arr * a.spad + s0), &full[s]);
         bulk_g2s(st + Cfg::CN_OFF, a.cn + j0, RT_BN * 4, &full[s]);
-        if (Cfg::GEMV) bulk_g2s(st + Cfg::VJ_OFF, a.vj + j0, RT_BN * 4, &full[s]);
         issued = t + 1;
       }
       if (*(volatile int*)&s_fail) {
@@ -359,13 +429,15 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t idesc1 = tf32_idesc(RT_BM, RT_BN);
-      constexpr uint32_t idesc2 = tf32_idesc(RT_BM, Cfg::GEMV ? 16 : S);
+      constexpr uint32_t idesc2 = tf32_idesc(RT_BM, S);
+      // one K-step (8 TF32) is 32 bytes of a 128-byte row: +2 in the
+      // descriptor's 16-byte units
+      constexpr int K1 = RT_DP / 8;  // K-steps of GEMM1 at d = 32
       bool ok = mbar_wait_bounded(afull, 0u);
       const uint64_t aHiD = sw128_kmajor_desc(smem_u32(sA));
       const uint64_t aLoD = sw128_kmajor_desc(smem_u32(sA + Cfg::A_BYTES));
       const int ks = a.ksteps;
-      const int tend = Cfg::GEMV ? T - 1 : T;
-      for (int t = 0; ok && t <= tend; ++t) {
+      for (int t = 0; ok && t <= T; ++t) {
         if (t < T) {
           const int s = t % NS, b = t & 1;
           if (!mbar_wait_bounded(&full[s], (uint32_t)((t / NS) & 1))) { ok = false; break; }
@@ -376,60 +448,57 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tc_fence_after();
           const uint64_t bHiD = sw128_kmajor_desc(smem_u32(sSt + s * Cfg::STAGE));
           const uint64_t bLoD = bHiD + (uint64_t)(Cfg::XJ_BYTES >> 4);
-          const uint32_t dP = tmem + TM_P + (uint32_t)(b * RT_BN);
+          const uint32_t dP = tmem + (uint32_t)(b * RT_BN);
 #pragma unroll
           for (int pass = 0; pass < 3; ++pass) {
             const uint64_t ad = pass == 2 ? aLoD : aHiD;
             const uint64_t bd = pass == 1 ? bLoD : bHiD;
 #pragma unroll
-            for (int k = 0; k < RT_DP / 8; ++k)
+            for (int k = 0; k < K1; ++k)
               if (k < ks)
                 mma_tf32(dP, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc1,
                          (pass > 0 || k > 0) ? 1u : 0u);
           }
           mma_commit(&pfull[b]);
-          if (Cfg::GEMV) mma_commit(&empty[s]);
         }
-        if (!Cfg::GEMV && t >= 1) {
+        if (t >= 1) {
           const int u = t - 1, bu = u & 1, su = u % NS;
           if (!mbar_wait_bounded(&kfull[bu], (uint32_t)((u >> 1) & 1))) { ok = false; break; }
-          const int c = u / RT_CH;
-          const bool first = Cfg::CHUNKED ? (u % RT_CH == 0) : (u == 0);
+          const int c = u / Cfg::CH;
+          const bool first = Cfg::CHUNKED ? (u % Cfg::CH == 0) : (u == 0);
           if (Cfg::CHUNKED && first && c >= 2 &&
               !mbar_wait_bounded(&ycfree[c & 1], (uint32_t)(((c - 2) >> 1) & 1))) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t kHi = tmem + TM_K + (uint32_t)(bu * 2 * RT_BN);
-          const uint32_t kLo = kHi + RT_BN;
-          const uint64_t vD = sw128_kmajor_desc(smem_u32(sSt + su * Cfg::STAGE + 2 * Cfg::XJ_BYTES));
-          const uint32_t dY = tmem + TM_Y + (Cfg::CHUNKED ? (uint32_t)((c & 1) * 64) : 0u);
+          const uint32_t kHi = tmem + Cfg::TM_K + (uint32_t)(bu * 2 * Cfg::KCOLS);
+          const uint32_t kLo = kHi + Cfg::KCOLS;
+          const uint64_t vD = sw128_kmajor_desc(smem_u32(sSt + su * Cfg::STAGE + Cfg::V_OFF));
+          const uint32_t dY = tmem + Cfg::TM_Y + (Cfg::CHUNKED ? (uint32_t)((c & 1) * S) : 0u);
 #pragma unroll
           for (int pass = 0; pass < P2; ++pass) {
             const uint32_t ka = (pass == 2) ? kLo : kHi;
             const int arr = (pass == 1) ? 1 : 0;
 #pragma unroll
             for (int k = 0; k < RT_BN / 8; ++k) {
-              const uint64_t vd =
-                  vD + (uint64_t)(((arr * 2 + (k >> 2)) * Cfg::VSLAB) >> 4) + (uint64_t)(2 * (k & 3));
+              const uint64_t vd = vD + (uint64_t)(((arr * 2 + (k >> 2)) * Cfg::VSLAB) >> 4) +
+                                  (uint64_t)(2 * (k & 3));
               mma_tf32_ts(dY, ka + (uint32_t)(8 * k), vd, idesc2,
                           (!first || pass > 0 || k > 0) ? 1u : 0u);
             }
           }
           mma_commit(&kfree[bu]);
           mma_commit(&empty[su]);
-          if (Cfg::CHUNKED && (u % RT_CH == RT_CH - 1 || u == T - 1)) mma_commit(&ycf[c & 1]);
+          if (Cfg::CHUNKED && (u % Cfg::CH == Cfg::CH - 1 || u == T - 1)) mma_commit(&ycf[c & 1]);
         }
       }
       if (ok) {
-        if (!Cfg::GEMV && !Cfg::CHUNKED) mma_commit(yfull);
-        if (!Cfg::GEMV) {
-          // the kfree arrivals of the last two tiles are not awaited by the
-          // exp groups: wait here so that none lands after the CTA exits
-          for (int u = (T > 2 ? T - 2 : 0); u < T; ++u)
-            if (!mbar_wait_bounded(&kfree[u & 1], (uint32_t)((u >> 1) & 1))) ok = false;
-        }
+        if (!Cfg::CHUNKED) mma_commit(yfull);
+        // the kfree arrivals of the last two tiles are not awaited by the
+        // exp groups: wait here so that none lands after the CTA exits
+        for (int u = (T > 2 ? T - 2 : 0); u < T; ++u)
+          if (!mbar_wait_bounded(&kfree[u & 1], (uint32_t)((u >> 1) & 1))) ok = false;
       }
       if (!ok) atomicOr(&s_fail, 1);
     }
@@ -443,56 +512,29 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     const float ai = a.cn[row];
     const float m2c = a.m2c;
     bool ok = true;
-    float acc = 0.f, comp = 0.f;  // one vector: Kahan-compensated row sum
     for (int t = g; t < T; t += 2) {
       const int b = g, s = t % NS;
       if (!mbar_wait_bounded(&pfull[b], (uint32_t)((t >> 1) & 1))) { ok = false; break; }
       tc_fence_after();
       uint32_t r0[32], r1[32];
-      tmem_ld32_nw(tmem + lane_base + TM_P + (uint32_t)(b * RT_BN), r0);
-      tmem_ld32_nw(tmem + lane_base + TM_P + (uint32_t)(b * RT_BN) + 32, r1);
+      tmem_ld32_nw(tmem + lane_base + (uint32_t)(b * RT_BN), r0);
+      tmem_ld32_nw(tmem + lane_base + (uint32_t)(b * RT_BN) + 32, r1);
       tmem_wait_ld();
       reg_fence32(r0);
       reg_fence32(r1);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&pfree[b]);
-      // the stage (cn_J, v_J) is resident: GEMM1(t) consumed it
+      // the stage (cn_J) is resident: GEMM1(t) consumed it
       if (!mbar_wait_bounded(&full[s], (uint32_t)((t / NS) & 1))) { ok = false; break; }
       const float4* cn4 = reinterpret_cast<const float4*>(sSt + s * Cfg::STAGE + Cfg::CN_OFF);
-      if (Cfg::GEMV) {
-        const float4* v4 = reinterpret_cast<const float4*>(sSt + s * Cfg::STAGE + Cfg::VJ_OFF);
-        float ts = 0.f;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t(&pr)[32] = h ? r1 : r0;
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) {
-            const float4 c4 = cn4[h * 8 + j4], w4 = v4[h * 8 + j4];
-            const float cj[4] = {c4.x, c4.y, c4.z, c4.w};
-            const float vj[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float kv = ex2_approx(fmaf(__uint_as_float(pr[j4 * 4 + e]), m2c, ai + cj[e]));
-              ts = fmaf(kv, vj[e], ts);
-            }
-          }
-        }
-        const float yk = ts - comp;
-        const float tk = acc + yk;
-        comp = (tk - acc) - yk;
-        acc = tk;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-        continue;
-      }
       if (t >= 2 && !mbar_wait_bounded(&kfree[b], (uint32_t)(((t - 2) >> 1) & 1))) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t kHi = tmem + lane_base + TM_K + (uint32_t)(b * 2 * RT_BN);
-      const uint32_t kLo = kHi + RT_BN;
+      const uint32_t kHi = tmem + lane_base + Cfg::TM_K + (uint32_t)(b * 2 * Cfg::KCOLS);
+      const uint32_t kLo = kHi + Cfg::KCOLS;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         uint32_t(&pr)[32] = h ? r1 : r0;
@@ -519,27 +561,17 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&kfull[b]);
-      if (Cfg::CHUNKED && g == 0 && t % RT_CH == 0 && t >= RT_CH) {
-        if (!promote<S>(tmem, lane_base, t / RT_CH - 1, ycf, ycfree, sY, r, lane)) {
+      if (Cfg::CHUNKED && g == 0 && t % Cfg::CH == 0 && t >= Cfg::CH) {
+        if (!promote<S, Cfg::TM_Y>(tmem, lane_base, t / Cfg::CH - 1, ycf, ycfree, sY, r, lane)) {
           ok = false;
           break;
         }
       }
     }
     if (!ok) atomicOr(&s_fail, 1);
-    if (Cfg::GEMV) {
-      // combine the two groups' row sums and write y_i (+ mu v_i)
-      double* sD = reinterpret_cast<double*>(sY);
-      if (g == 1) sD[r] = (double)acc - (double)comp;
-      exp_bar_sync();
-      if (g == 0 && ok && !*(volatile int*)&s_fail && row < a.n) {
-        float val = (float)(((double)acc - (double)comp) + sD[r]);
-        if (a.v) val = fmaf(a.mus ? (float)a.mus[s0] : a.mu0, a.v[s0 * a.ldv + row], val);
-        a.y[s0 * a.ldy + row] = val;
-      }
-    } else if (g == 0) {
+    if (g == 0) {
       if (Cfg::CHUNKED) {
-        if (ok) ok = promote<S>(tmem, lane_base, (T - 1) / RT_CH, ycf, ycfree, sY, r, lane);
+        if (ok) ok = promote<S, Cfg::TM_Y>(tmem, lane_base, (T - 1) / Cfg::CH, ycf, ycfree, sY, r, lane);
         if (!ok) atomicOr(&s_fail, 1);
         if (ok && row < a.n) {
           for (int sv = 0; sv < S && s0 + sv < a.nvec; ++sv)
@@ -553,7 +585,7 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 #pragma unroll 1
           for (int c0 = 0; c0 < S; c0 += 16) {
             uint32_t v[16];
-            tmem_ld16(tmem + lane_base + TM_Y + (uint32_t)c0, v);
+            tmem_ld16(tmem + lane_base + Cfg::TM_Y + (uint32_t)c0, v);
             if (row < a.n) {
 #pragma unroll
               for (int jj = 0; jj < 16; ++jj) {
@@ -599,23 +631,6 @@ constexpr int GV_STAGE = (GV_TX + 1023) / 1024 * 1024;
 constexpr int GV_A = RT_BM * 128;             // X_I [hi | lo]
 constexpr int GV_SMEM = 1024 + GV_A + GV_NS * GV_STAGE + 256 + GV_G * RT_BM * 8;
 
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// Instruction descriptor: kind::f16 with FP16 A and B (both K-major), FP32 D.
-__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
-  return (1u << 4)                      // D format: F32
-         | (0u << 7)                    // A format: F16
-         | (0u << 10)                   // B format: F16
-         | ((uint32_t)(N >> 3) << 17)   // N / 8
-         | ((uint32_t)(M >> 4) << 24);  // M / 16
-}
 static_assert(GV_SMEM <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ void gv_bar_sync() {
@@ -925,6 +940,476 @@ __global__ void rt_prep_vecs_kernel(const float* __restrict__ V, int64_t nvec, i
   }
 }
 
+// amax[s] = max_j |V[s][j]| (bit pattern of a non-negative float; the
+// array is cleared first).
+__global__ void rt_vec_absmax_kernel(const float* __restrict__ V, int64_t nvec, int64_t n,
+                                     int64_t ldv, unsigned int* amax) {
+  for (int64_t sv = blockIdx.y; sv < nvec; sv += gridDim.y) {
+    float m = 0.f;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+      m = fmaxf(m, fabsf(V[sv * ldv + j]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(&amax[sv], __float_as_uint(m));
+  }
+}
+
+// FP16 vector layout: VS16[arr][s][j] (spad x npad each), arr 0 = fp16(c_s v),
+// arr 1 = fp16(c_s v - fp16(c_s v)) (nv = 2), with c_s = 2^(15 - e_s) and
+// max |v_s| in [2^(e_s - 1), 2^e_s), so that max |c_s v_s| lies in
+// [2^14, 2^15); vscale[s] = 2^-15 / c_s undoes it and the 2^15 of the kernel
+// entries.  Zero padding.
+__global__ void rt_prep_vecs16_kernel(const float* __restrict__ V, int64_t nvec, int64_t n,
+                                      int64_t ldv, int64_t spad, int64_t npad, int nv,
+                                      const unsigned int* __restrict__ amax,
+                                      __half* __restrict__ VS, float* __restrict__ vscale) {
+  const int64_t total = spad * npad;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sv = e / npad, j = e - sv * npad;
+    float c = 1.f;
+    if (sv < nvec) {
+      const float mx = __uint_as_float(amax[sv]);
+      int ex = 0;
+      if (mx > 0.f) frexpf(mx, &ex);
+      ex = max(ex, -100);
+      c = ldexpf(1.f, 15 - ex);
+      if (j == 0) vscale[sv] = ldexpf(1.f, ex - 30);
+    }
+    const float v = (sv < nvec && j < n) ? V[sv * ldv + j] * c : 0.0f;
+    const __half hi = __float2half_rn(v);
+    VS[e] = hi;
+    if (nv > 1) VS[total + e] = __float2half_rn(v - __half2float(hi));
+  }
+}
+
+// ---------------------------------------------------------------- many vectors, FP16 splits
+//
+// The same product on FP16 splits (kind::f16) with a deeper pipeline: four
+// 64-column TMEM tile buffers, each holding a P tile (FP32) and then, in the
+// same columns, its kernel tile K (hi | lo, FP16 packed two to a column), so
+// that GEMM1 runs up to three tiles ahead of GEMM2 and an exp group finds its
+// next P tile ready.  X_J / cn_J and the vector slabs come through separate
+// rings (each refilled by its own producer warp): GEMM1 and the exp groups
+// need X_J / cn_J several tiles before GEMM2 needs V_J.
+//
+//   warp 0, lane 0:  X producer.  X_I once; X_J and cn_J per tile (ring HX_NS).
+//   warp 10, lane 0: V producer.  The tile's slabs of the vectors (ring HV_NS).
+//   warp 1, lane 0:  MMA issuer.  Per tile t, in order: GEMM2(t) into the
+//                    Yacc chunk (once the exp group stored K_t), then
+//                    GEMM1(t + 3) into the buffer GEMM2(t - 1) released.
+//   warps 2..9:      two exp groups (tiles of one parity each).  P_t from
+//                    TMEM, k 2^15 split into FP16 hi + lo, stored over P_t;
+//                    each group promotes half of the Yacc columns of a chunk.
+constexpr int HB = 4;        // TMEM tile buffers (64 columns each)
+constexpr int HX_NS = 5;     // X_J / cn_J ring
+constexpr int HV_NS = 3;     // vector-slab ring
+constexpr int H_THREADS = 64 + 32 * RT_EXP_WARPS + 32;  // + the V producer warp
+constexpr int H_XSLOT = 9 * 1024;                        // X_J (8 KB) + cn_J (256 B)
+
+template <int S, int P2>
+struct H16Cfg {
+  static constexpr int NV = P2 == 3 ? 2 : 1;
+  static constexpr int A_BYTES = RT_BM * 128;       // X_I [hi | lo]
+  static constexpr int VSLOT = NV * S * 128;        // S vectors x 64 points x FP16, per array
+  static constexpr int CH = 4;                      // tiles per GEMM2 chunk (48 MMAs)
+  static constexpr bool CHUNKED = P2 == 3;
+  static constexpr int HALF = S / 2;                // Yacc columns promoted by each group
+  static constexpr int SUM_BYTES = CHUNKED ? S * RT_BM * 4 : 0;
+  static constexpr int BAR_BYTES = 512;
+  static constexpr int SMEM = 1024 + A_BYTES + HX_NS * H_XSLOT + HV_NS * VSLOT + BAR_BYTES +
+                              SUM_BYTES;
+  static constexpr uint32_t TM_Y = 64 * HB;
+  static constexpr uint32_t YCOLS = CHUNKED ? 2 * S : S;
+  static_assert(S % 32 == 0 && S <= 128, "S");
+  static_assert(TM_Y + YCOLS <= RT_TMEM_COLS, "tensor memory");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+  static_assert(VSLOT % 1024 == 0 && H_XSLOT % 1024 == 0, "1024-byte aligned tiles");
+};
+
+// Add columns [c0, c0 + HALF) of Yacc chunk c into the FP32 sums sY[s][r]
+// (assign for chunk 0) and release the chunk (one arrival per warp).
+template <int S, int HALF, uint32_t TMY>
+__device__ __forceinline__ bool h_promote(uint32_t tmem, uint32_t lane_base, int c, int c0,
+                                          uint64_t* ycf, uint64_t* ycfree, float* sY, int r,
+                                          int lane) {
+  if (!mbar_wait_bounded(&ycf[c & 1], (uint32_t)((c >> 1) & 1))) return false;
+  tc_fence_after();
+#pragma unroll 1
+  for (int j0 = 0; j0 < HALF; j0 += 16) {
+    uint32_t v[16];
+    tmem_ld16(tmem + lane_base + TMY + (uint32_t)((c & 1) * S + c0 + j0), v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float* p = &sY[(c0 + j0 + j) * RT_BM + r];
+      *p = (c == 0) ? __uint_as_float(v[j]) : *p + __uint_as_float(v[j]);
+    }
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&ycfree[c & 1]);
+  return true;
+}
+
+template <int S, int P2>
+__global__ void __launch_bounds__(H_THREADS, 1)
+rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV,
+               RtArgs a) {
+  using Cfg = H16Cfg<S, P2>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm =
+      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = sm;
+  unsigned char* sX = sA + Cfg::A_BYTES;
+  unsigned char* sV = sX + HX_NS * H_XSLOT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sV + HV_NS * Cfg::VSLOT);
+  uint64_t* afull = bars;
+  uint64_t* xfull = afull + 1;      // [HX_NS] X_J, cn_J landed
+  uint64_t* xempty = xfull + HX_NS; // [HX_NS] exp group read cn_J (GEMM1 is done by then)
+  uint64_t* vfull = xempty + HX_NS; // [HV_NS]
+  uint64_t* vempty = vfull + HV_NS; // [HV_NS] GEMM2 done with the slab
+  uint64_t* pfull = vempty + HV_NS; // [HB] GEMM1 wrote P
+  uint64_t* kfull = pfull + HB;     // [HB] exp group wrote K over P
+  uint64_t* bfree = kfull + HB;     // [HB] GEMM2 done with K: buffer free
+  uint64_t* yfull = bfree + HB;
+  uint64_t* ycf = yfull + 1;        // [2] Yacc chunk complete
+  uint64_t* ycfree = ycf + 2;       // [2] chunk promoted by both groups
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ycfree + 2);
+  float* sY = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + Cfg::BAR_BYTES);
+  __shared__ int s_fail, s_skip;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * RT_BM;
+  const int64_t s0 = (int64_t)blockIdx.y * S;
+  const int t0 = a.tile_chunk > 0 ? (int)blockIdx.z * a.tile_chunk : 0;
+  const int T = a.tile_chunk > 0 ? min(a.ntiles - t0, a.tile_chunk) : a.ntiles;
+
+  if (threadIdx.x == 0) {
+    int skip = 0;
+    if (a.done0) {
+      skip = 1;
+      const int64_t s1 = (s0 + S < a.nvec) ? s0 + S : a.nvec;
+      for (int64_t s = s0; s < s1; ++s)
+        if (!a.done0[s * a.done_stride]) { skip = 0; break; }
+    }
+    s_skip = skip;
+    s_fail = 0;
+    if (!skip) {
+      mbar_init(afull, 1);
+      for (int i = 0; i < HX_NS; ++i) {
+        mbar_init(&xfull[i], 1);
+        mbar_init(&xempty[i], 4);
+      }
+      for (int i = 0; i < HV_NS; ++i) {
+        mbar_init(&vfull[i], 1);
+        mbar_init(&vempty[i], 1);
+      }
+      for (int i = 0; i < HB; ++i) {
+        mbar_init(&pfull[i], 1);
+        mbar_init(&kfull[i], 4);
+        mbar_init(&bfree[i], 1);
+      }
+      mbar_init(yfull, 1);
+      for (int i = 0; i < 2; ++i) {
+        mbar_init(&ycf[i], 1);
+        mbar_init(&ycfree[i], 8);
+      }
+      fence_barrier_init();
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmX) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmV) : "memory");
+    }
+  }
+  __syncthreads();
+  if (s_skip) return;
+  if (warp == 1) tmem_alloc(tmem_slot, RT_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const bool tmem_ok = tmem == 0u;
+  if (!tmem_ok) {
+    if (threadIdx.x == 0) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
+  } else if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- X producer
+      mbar_arrive_expect_tx(afull, (uint32_t)Cfg::A_BYTES);
+      tma_load_2d(sA, &tmX, 0, (int)m0, afull);
+      tma_load_2d(sA + Cfg::A_BYTES / 2, &tmX, 0, (int)m0 + 64, afull);
+      int issued = 0;
+      for (int t = 0; t < T; ++t) {
+        const int s = t % HX_NS;
+        if (t >= HX_NS && !mbar_wait_bounded(&xempty[s], (uint32_t)(((t / HX_NS) - 1) & 1))) {
+          atomicOr(&s_fail, 1);
+          break;
+        }
+        if (*(volatile int*)&s_fail) break;
+        unsigned char* st = sX + s * H_XSLOT;
+        const int j0 = (t0 + t) * RT_BN;
+        mbar_arrive_expect_tx(&xfull[s], (uint32_t)(RT_BN * 128 + RT_BN * 4));
+        tma_load_2d(st, &tmX, 0, j0, &xfull[s]);
+        bulk_g2s(st + RT_BN * 128, a.cn + j0, RT_BN * 4, &xfull[s]);
+        issued = t + 1;
+      }
+      // every X copy is awaited by GEMM1 and the exp groups; after a failure,
+      // let the copies still in flight land before the CTA exits
+      if (*(volatile int*)&s_fail) {
+        mbar_wait_bounded(afull, 0u);
+        for (int t = (issued > HX_NS ? issued - HX_NS : 0); t < issued; ++t)
+          mbar_wait_bounded(&xfull[t % HX_NS], (uint32_t)((t / HX_NS) & 1));
+      }
+    }
+  } else if (warp == RT_EXP_WARPS + 2) {
+    if (lane == 0) {
+      // ---------------- V producer
+      int issued = 0;
+      for (int t = 0; t < T; ++t) {
+        const int s = t % HV_NS;
+        if (t >= HV_NS && !mbar_wait_bounded(&vempty[s], (uint32_t)(((t / HV_NS) - 1) & 1))) {
+          atomicOr(&s_fail, 1);
+          break;
+        }
+        if (*(volatile int*)&s_fail) break;
+        unsigned char* st = sV + s * Cfg::VSLOT;
+        const int j0 = (t0 + t) * RT_BN;
+        mbar_arrive_expect_tx(&vfull[s], (uint32_t)Cfg::VSLOT);
+#pragma unroll
+        for (int arr = 0; arr < Cfg::NV; ++arr)
+          tma_load_2d(st + arr * S * 128, &tmV, j0, (int)(arr * a.spad + s0), &vfull[s]);
+        issued = t + 1;
+      }
+      if (*(volatile int*)&s_fail) {
+        for (int t = (issued > HV_NS ? issued - HV_NS : 0); t < issued; ++t)
+          mbar_wait_bounded(&vfull[t % HV_NS], (uint32_t)((t / HV_NS) & 1));
+      } else {
+        // the last slabs' releases are the tensor core's asynchronous commit
+        // arrivals: they must land before the shared memory is freed
+        for (int t = (T > HV_NS ? T - HV_NS : 0); t < T; ++t)
+          if (!mbar_wait_bounded(&vempty[t % HV_NS], (uint32_t)((t / HV_NS) & 1)))
+            atomicOr(&s_fail, 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc1 = f16_idesc(RT_BM, RT_BN);
+      constexpr uint32_t idesc2 = f16_idesc(RT_BM, S);
+      bool ok = mbar_wait_bounded(afull, 0u);
+      const uint64_t aHiD = sw128_kmajor_desc(smem_u32(sA));
+      const uint64_t aLoD = aHiD + (uint64_t)(64 >> 4);  // lo halves: 64 bytes into each row
+      const int ks = a.ksteps;                             // ceil(d / 16)
+      // GEMM1(u): P_u = X_I X_J^T (hi.hi + hi.lo + lo.hi, K = 16 per MMA)
+      auto gemm1 = [&](int u) -> bool {
+        const int s = u % HX_NS;
+        if (!mbar_wait_bounded(&xfull[s], (uint32_t)((u / HX_NS) & 1))) return false;
+        tc_fence_after();
+        const uint64_t bHiD = sw128_kmajor_desc(smem_u32(sX + s * H_XSLOT));
+        const uint64_t bLoD = bHiD + (uint64_t)(64 >> 4);
+        const uint32_t dP = tmem + (uint32_t)((u % HB) * 64);
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint64_t ad = pass == 2 ? aLoD : aHiD;
+          const uint64_t bd = pass == 1 ? bLoD : bHiD;
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            if (k < ks)
+              mma_f16(dP, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc1,
+                      (pass > 0 || k > 0) ? 1u : 0u);
+        }
+        mma_commit(&pfull[u % HB]);
+        return true;
+      };
+      for (int u = 0; ok && u < HB - 1 && u < T; ++u) ok = gemm1(u);
+      for (int t = 0; ok && t < T; ++t) {
+        const int b = t % HB, sv = t % HV_NS;
+        if (!mbar_wait_bounded(&kfull[b], (uint32_t)((t / HB) & 1))) { ok = false; break; }
+        const int c = t / Cfg::CH;
+        const bool first = Cfg::CHUNKED ? (t % Cfg::CH == 0) : (t == 0);
+        if (Cfg::CHUNKED && first && c >= 2 &&
+            !mbar_wait_bounded(&ycfree[c & 1], (uint32_t)(((c - 2) >> 1) & 1))) {
+          ok = false;
+          break;
+        }
+        if (!mbar_wait_bounded(&vfull[sv], (uint32_t)((t / HV_NS) & 1))) { ok = false; break; }
+        tc_fence_after();
+        // GEMM2(t): Yacc += K_t V_t (Khi.Vhi + Khi.Vlo + Klo.Vhi); K_t in
+        // TMEM (hi: 32 columns, lo: the next 32), 16 points per K-step
+        const uint32_t kHi = tmem + (uint32_t)(b * 64);
+        const uint64_t vD = sw128_kmajor_desc(smem_u32(sV + sv * Cfg::VSLOT));
+        const uint32_t dY = tmem + Cfg::TM_Y + (Cfg::CHUNKED ? (uint32_t)((c & 1) * S) : 0u);
+#pragma unroll
+        for (int pass = 0; pass < P2; ++pass) {
+          const uint32_t ka = kHi + (pass == 2 ? 32u : 0u);
+          const uint64_t vd0 = vD + (uint64_t)(((pass == 1 ? 1 : 0) * S * 128) >> 4);
+#pragma unroll
+          for (int k = 0; k < RT_BN / 16; ++k)
+            mma_f16_ts(dY, ka + (uint32_t)(8 * k), vd0 + (uint64_t)(2 * k), idesc2,
+                       (!first || pass > 0 || k > 0) ? 1u : 0u);
+        }
+        mma_commit(&bfree[b]);
+        mma_commit(&vempty[sv]);
+        if (Cfg::CHUNKED && (t % Cfg::CH == Cfg::CH - 1 || t == T - 1)) mma_commit(&ycf[c & 1]);
+        // GEMM1(t + 3) into the buffer of tile t - 1, once GEMM2(t - 1) is
+        // done with it (GEMM2(t) is queued meanwhile)
+        const int u = t + HB - 1;
+        if (u < T) {
+          if (t >= 1 && !mbar_wait_bounded(&bfree[(t - 1) % HB], (uint32_t)(((t - 1) / HB) & 1))) {
+            ok = false;
+            break;
+          }
+          if (!gemm1(u)) { ok = false; break; }
+        }
+      }
+      if (ok) {
+        if (!Cfg::CHUNKED) mma_commit(yfull);
+        // the bfree arrivals of the last tiles are not awaited above: wait
+        // here so that none lands after the CTA exits
+        for (int t = (T > HB ? T - HB : 0); t < T; ++t)
+          if (!mbar_wait_bounded(&bfree[t % HB], (uint32_t)((t / HB) & 1))) ok = false;
+      }
+      if (!ok) atomicOr(&s_fail, 1);
+    }
+  } else {
+    // ---------------- exp groups (warps 2..9); TMEM lane quarter q = warp % 4
+    const int g = (warp - 2) >> 2;
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    const int64_t row = m0 + r;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const float ai = a.cn[row];
+    const float m2c = *a.m2c_dev;
+    const int c0 = g * Cfg::HALF;  // this group's Yacc columns
+    bool ok = true;
+    int next_chunk = 0;            // next chunk this group promotes
+    for (int t = g; t < T; t += 2) {
+      const int b = t % HB, s = t % HX_NS;
+      if (!mbar_wait_bounded(&pfull[b], (uint32_t)((t / HB) & 1))) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t buf = tmem + lane_base + (uint32_t)(b * 64);
+      uint32_t r0[32], r1[32];
+      tmem_ld32_nw(buf, r0);
+      tmem_ld32_nw(buf + 32, r1);
+      tmem_wait_ld();
+      reg_fence32(r0);
+      reg_fence32(r1);
+      // cn_J is resident (GEMM1(t) waited for it); this wait makes the
+      // asynchronous copy visible to this thread
+      if (!mbar_wait_bounded(&xfull[s], (uint32_t)((t / HX_NS) & 1))) { ok = false; break; }
+      const float4* cn4 = reinterpret_cast<const float4*>(sX + s * H_XSLOT + RT_BN * 128);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t(&pr)[32] = h ? r1 : r0;
+        // k 2^15 split into FP16 hi + lo, two points per TMEM column (the
+        // lower point index in the lower half), over the P columns just read
+        uint32_t hw[16], lw[16];
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 c4 = cn4[h * 8 + j4];
+          const float cj[4] = {c4.x, c4.y, c4.z, c4.w};
+          float kh[4], kl[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float kv =
+                ex2_approx(fmaf(__uint_as_float(pr[j4 * 4 + e]), m2c, ai + cj[e])) * 32768.f;
+            if (P2 == 3) {
+              kh[e] = __uint_as_float(tf32_rna(kv));  // exact in FP16 (10-bit fraction)
+              kl[e] = kv - kh[e];
+            } else {
+              kh[e] = kv;
+            }
+          }
+          hw[2 * j4] = pack_f16x2(kh[0], kh[1]);
+          hw[2 * j4 + 1] = pack_f16x2(kh[2], kh[3]);
+          if (P2 == 3) {
+            lw[2 * j4] = pack_f16x2(kl[0], kl[1]);
+            lw[2 * j4 + 1] = pack_f16x2(kl[2], kl[3]);
+          }
+        }
+        tmem_st16(buf + (uint32_t)(16 * h), hw);
+        if (P2 == 3) tmem_st16(buf + 32u + (uint32_t)(16 * h), lw);
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&kfull[b]);
+        mbar_arrive(&xempty[s]);
+      }
+      // promote chunk c - 1 once this group reaches chunk c
+      if (Cfg::CHUNKED && (t - g) % Cfg::CH == 0 && t >= Cfg::CH) {
+        if (!h_promote<S, Cfg::HALF, Cfg::TM_Y>(tmem, lane_base, next_chunk, c0, ycf, ycfree, sY,
+                                                 r, lane)) {
+          ok = false;
+          break;
+        }
+        ++next_chunk;
+      }
+    }
+    if (Cfg::CHUNKED) {
+      const int last = (T - 1) / Cfg::CH;
+      while (ok && next_chunk <= last) {
+        ok = h_promote<S, Cfg::HALF, Cfg::TM_Y>(tmem, lane_base, next_chunk, c0, ycf, ycfree, sY,
+                                                 r, lane);
+        ++next_chunk;
+      }
+      if (!ok) atomicOr(&s_fail, 1);
+      if (ok && row < a.n) {
+        for (int j = 0; j < Cfg::HALF && s0 + c0 + j < a.nvec; ++j)
+          rt_store(a, s0 + c0 + j, row, sY[(c0 + j) * RT_BM + r]);
+      }
+    } else {
+      if (ok) ok = mbar_wait_bounded(yfull, 0u, 1ll << 26);
+      if (!ok) atomicOr(&s_fail, 1);
+      tc_fence_after();
+      if (ok) {
+#pragma unroll 1
+        for (int j0 = 0; j0 < Cfg::HALF; j0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + lane_base + Cfg::TM_Y + (uint32_t)(c0 + j0), v);
+          if (row < a.n) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int64_t sv = s0 + c0 + j0 + j;
+              if (sv < a.nvec) rt_store(a, sv, row, __uint_as_float(v[j]));
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, RT_TMEM_COLS);
+  if (threadIdx.x == 0 && s_fail) atomicCAS(a.err, 0, (int)NYS_ERR_TIMEOUT);
+}
+
+template <int S, int P2>
+int32_t h16_launch(const CUtensorMap& tx, const CUtensorMap& tv, const RtArgs& a0, int64_t npad,
+                   int64_t nblk_y, int nz, float* part_ws, cudaStream_t s) {
+  using Cfg = H16Cfg<S, P2>;
+  auto kern = rbf_h16_kernel<S, P2>;
+  NYS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+  RtArgs a = a0;
+  if (nz > 1) {
+    if (nz > kMaxSlices) return NYS_ERR_ARG;
+    const int chunk = (int)cdiv(a.ntiles, nz);
+    nz = (int)cdiv(a.ntiles, chunk);
+    a.tile_chunk = chunk;
+    a.part_stride = npad;
+    a.ypart = part_ws;
+  }
+  kern<<<dim3((unsigned)(npad / RT_BM), (unsigned)nblk_y, (unsigned)nz), H_THREADS, Cfg::SMEM,
+         s>>>(tx, tv, a);
+  count_launch();
+  if (a.ypart) {
+    const unsigned gy = (unsigned)(a.nvec < 65535 ? a.nvec : 65535);
+    rt_sum_kernel<<<dim3((unsigned)cdiv(a.n, 256), gy), 256, 0, s>>>(a.ypart, nz, a);
+    count_launch();
+  }
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
 // part_ws: room for kMaxSlices x nvec x npad partial sums (inside the work
 // buffer, so that a product allocates nothing while a graph is captured)
 template <int S, int P2>
@@ -1031,11 +1516,56 @@ std::string rt_tune_key(int S, int passes, int64_t npad, int64_t d, int64_t nblk
          " blocks=" + std::to_string(nblk_y) + " sms=" + std::to_string(num_sms());
 }
 
-// Vectors per CTA: 1 (FP32 products on the exp warps) for one or two
-// vectors, else 64 (3xTF32 GEMM2) or 128 (TF32 GEMM2).
+std::string rt16_tune_key(int passes, int64_t npad, int64_t d, int64_t nvec) {
+  return "rbf_tc16 passes=" + std::to_string(passes) + " npad=" + std::to_string(npad) +
+         " d=" + std::to_string(d) + " nvec=" + std::to_string(nvec) +
+         " sms=" + std::to_string(num_sms());
+}
+
+// Vectors per CTA of the 3xTF32 kernel: 1 (FP32 products on the exp warps)
+// for one or two vectors, else 64 (three passes) or 128 (one pass).
 int rt_block(int64_t nvec, int passes) {
   if (nvec <= 2) return 1;
   return passes == 3 ? 64 : 128;
+}
+
+// Many vectors on the FP16 kernel (the default; NYS_RBF_TF32=1 selects the
+// 3xTF32 kernel).
+bool rt_half() {
+  static const bool h = [] {
+    const char* e = getenv("NYS_RBF_TF32");
+    return !(e && e[0] == '1' && e[1] == 0);
+  }();
+  return h;
+}
+
+// FP16 kernel shapes (vectors per CTA), tuned with the point-slice count:
+// candidate = shape index * 8 + slices.  Three passes: 128, 64 or 32 vectors
+// per CTA; one pass (the sketch): 128.
+constexpr int kShapes3[3] = {128, 64, 32};
+int rt16_nshapes(int passes) { return passes == 3 ? 3 : 1; }
+int rt16_shape(int passes, int si) { return passes == 3 ? kShapes3[si] : 128; }
+
+std::vector<int> rt16_candidates(int passes, int64_t npad, int64_t nvec, int64_t sms) {
+  std::vector<int> c;
+  for (int si = 0; si < rt16_nshapes(passes); ++si) {
+    const int S = rt16_shape(passes, si);
+    const int64_t ctas = (npad / RT_BM) * cdiv(nvec, S);
+    for (int z : rt_slice_candidates(npad, nvec, ctas, sms)) c.push_back(si * 8 + z);
+  }
+  return c;
+}
+
+// The untimed rule: the narrowest shape that holds every vector in one CTA
+// column (else the widest), with the fullest last wave of its slice counts.
+int rt16_rule(int passes, int64_t npad, int64_t nvec, int64_t sms) {
+  int si = 0;
+  for (int k = rt16_nshapes(passes) - 1; k >= 0; --k)
+    if (rt16_shape(passes, k) >= nvec) { si = k; break; }
+  const int S = rt16_shape(passes, si);
+  const int64_t ctas = (npad / RT_BM) * cdiv(nvec, S);
+  const std::vector<int> z = rt_slice_candidates(npad, nvec, ctas, sms);
+  return si * 8 + wave_fill_rule(ctas, z, sms);
 }
 
 }  // namespace
@@ -1050,24 +1580,37 @@ bool rbf_tc_tune_pending(int64_t n, int64_t d, int64_t nvec, int passes) {
     const std::vector<int> c = gv_slice_candidates(npad / GV_BN);
     return c.size() > 1 && !tune_cached(gv_tune_key(npad, d, nvec), nullptr);
   }
+  if (rt_half()) {
+    const std::vector<int> c = rt16_candidates(passes, npad, nvec, num_sms());
+    return c.size() > 1 && !tune_cached(rt16_tune_key(passes, npad, d, nvec), nullptr);
+  }
   const int64_t nblk_y = cdiv(nvec, S);
   const std::vector<int> c = rt_slice_candidates(npad, nvec, (npad / RT_BM) * nblk_y, num_sms());
   return c.size() > 1 && !tune_cached(rt_tune_key(S, passes, npad, d, nblk_y), nullptr);
 }
 
 // Layout of the work buffer: [256: error word and one-vector scalars]
-// [XS: npad x 64 FP32] [cn: npad] [VS: nv x spad x npad] [partial sums of up
-// to kMaxSlices point slices: kMaxSlices x (nvec or 1) x npad].
+// [XS: npad x 64 FP32 (or FP16)] [cn: npad] [VS: the vectors' hi / lo
+// copies] [partial sums of up to kMaxSlices point slices: kMaxSlices x
+// (nvec or 1) x npad] [vscale: spad16] [amax: spad16].
 static size_t rt_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t rt_vs_bytes(int64_t npad, int64_t nvec, int passes) {
+  const int S = rt_block(nvec, passes);
+  if (S == 1) return (size_t)nvec * npad * 4;
+  const int nv = passes == 3 ? 2 : 1;
+  const int64_t spad = cdiv(nvec, S) * S, spad16 = cdiv(nvec, 128) * 128;
+  return std::max((size_t)nv * spad * npad * 4, (size_t)nv * spad16 * npad * 2);
+}
 
 size_t rbf_tc_work_bytes(int64_t n, int64_t nvec, int passes) {
   const int64_t npad = cdiv(n, RT_BM) * RT_BM;
   const int S = rt_block(nvec, passes);
-  const int64_t spad = cdiv(nvec, S) * S;
-  const int nv = S == 1 ? 1 : (passes == 3 ? 2 : 1);
+  const int64_t spad16 = cdiv(nvec, 128) * 128;
   return 256 + rt_align((size_t)npad * 64 * 4) + rt_align((size_t)npad * 4) +
-         rt_align((size_t)nv * spad * npad * 4) +
-         rt_align((size_t)kMaxSlices * (S == 1 ? 1 : nvec) * npad * 4);
+         rt_align(rt_vs_bytes(npad, nvec, passes)) +
+         rt_align((size_t)kMaxSlices * (S == 1 ? 1 : nvec) * npad * 4) +
+         2 * rt_align((size_t)spad16 * 4);
 }
 
 int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, double sigma,
@@ -1078,7 +1621,8 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
   if (n > (1ll << 30) || (shift == 2 && !d_mu)) return NYS_ERR_ARG;
   const int64_t npad = cdiv(n, RT_BM) * RT_BM;
   const int S = rt_block(nvec, passes);
-  const int64_t spad = cdiv(nvec, S) * S;
+  const bool half = S > 1 && rt_half();
+  const int64_t spad = half ? cdiv(nvec, 128) * 128 : cdiv(nvec, S) * S;
   const int nv = S == 1 ? 0 : (passes == 3 ? 2 : 1);
   if (spad * (nv ? nv : 1) > (1ll << 30)) return NYS_ERR_ARG;
   Scratch sc(s);
@@ -1091,27 +1635,52 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
   float* XS = reinterpret_cast<float*>(w + 256);
   float* cn = reinterpret_cast<float*>(w + 256 + rt_align((size_t)npad * 64 * 4));
   float* VS = reinterpret_cast<float*>((unsigned char*)cn + rt_align((size_t)npad * 4));
-  float* part_ws = reinterpret_cast<float*>((unsigned char*)VS +
-                                            rt_align((size_t)(nv ? nv : 1) * spad * npad * 4));
+  float* part_ws =
+      reinterpret_cast<float*>((unsigned char*)VS + rt_align(rt_vs_bytes(npad, nvec, passes)));
+  float* vscale = reinterpret_cast<float*>(
+      (unsigned char*)part_ws + rt_align((size_t)kMaxSlices * (S == 1 ? 1 : nvec) * npad * 4));
+  unsigned int* vamax = reinterpret_cast<unsigned int*>(
+      (unsigned char*)vscale + rt_align((size_t)cdiv(nvec, 128) * 128 * 4));
   const double l2e = 1.4426950408889634;
   const double c = -l2e / (2.0 * sigma * sigma);
-  if (S > 1) {  // one vector uses the FP16 layout below
+  unsigned int* absmax = reinterpret_cast<unsigned int*>(w + 64);
+  float* m2c_dev = reinterpret_cast<float*>(w + 72);
+  __half* XS16 = reinterpret_cast<__half*>(XS);
+  if (S > 1 && !half) {
     rt_prep_points_kernel<<<(unsigned)cdiv(npad, 8), 256, 0, s>>>(pts, n, d, ld, npad, c, XS, cn);
+    count_launch();
+  } else {
+    // FP16 split layout of the points (in the FP32 layout's space)
+    NYS_CUDA_TRY(cudaMemsetAsync(absmax, 0, sizeof(unsigned int), s));
+    const int64_t nd = n * d;
+    rt_absmax_kernel<<<(unsigned)(cdiv(nd, 256) < 1024 ? cdiv(nd, 256) : 1024), 256, 0, s>>>(
+        pts, n, d, ld, absmax);
+    count_launch();
+    rt_prep_points16_kernel<<<(unsigned)cdiv(npad, 8), 256, 0, s>>>(
+        pts, n, d, ld, npad, c, l2e / (sigma * sigma), absmax, XS16, cn, m2c_dev);
     count_launch();
   }
   const int64_t tot = spad * npad;
   const unsigned gv = (unsigned)(cdiv(tot, 256) < 4096 ? cdiv(tot, 256) : 4096);
-  rt_prep_vecs_kernel<<<gv, 256, 0, s>>>(V, nvec, n, ldv, spad, npad, nv, VS); count_launch();
-  CUtensorMap tx, tv;
-  if (S > 1 && !tmap_f32_2d(&tx, XS, npad, 64, 64, 64, 32)) return NYS_ERR_CUDA;
-  if (S > 1 && !tmap_f32_2d(&tv, VS, nv * spad, npad, npad, S, 32)) return NYS_ERR_CUDA;
+  if (half) {
+    NYS_CUDA_TRY(cudaMemsetAsync(vamax, 0, (size_t)nvec * sizeof(unsigned int), s));
+    const unsigned bx = (unsigned)std::min<int64_t>(cdiv(n, 4096), 16);
+    rt_vec_absmax_kernel<<<dim3(bx, (unsigned)std::min<int64_t>(nvec, 65535)), 256, 0, s>>>(
+        V, nvec, n, ldv, vamax);
+    count_launch();
+    rt_prep_vecs16_kernel<<<gv, 256, 0, s>>>(V, nvec, n, ldv, spad, npad, nv, vamax,
+                                             reinterpret_cast<__half*>(VS), vscale);
+  } else {
+    rt_prep_vecs_kernel<<<gv, 256, 0, s>>>(V, nvec, n, ldv, spad, npad, nv, VS);
+  }
+  count_launch();
   RtArgs a;
   a.cn = cn;
   a.m2c = (float)(l2e / (sigma * sigma));
-  a.m2c_dev = nullptr;
+  a.m2c_dev = m2c_dev;
   a.n = n;
   a.ntiles = (int)(npad / RT_BN);
-  a.ksteps = (int)cdiv(d, 8);
+  a.ksteps = (int)cdiv(d, half ? 16 : 8);
   a.nvec = nvec;
   a.spad = spad;
   a.vec = 0;
@@ -1128,20 +1697,10 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
   a.tile_chunk = 0;
   a.ypart = nullptr;
   a.part_stride = 0;
+  a.vscale = half ? vscale : nullptr;
+  const int64_t sms = num_sms();
   if (S == 1) {
-    // FP16 split layout of the points (in the FP32 layout's space), then one
-    // launch per vector (nvec <= 2), each reading its own padded copy
-    unsigned int* absmax = reinterpret_cast<unsigned int*>(w + 64);
-    float* m2c_dev = reinterpret_cast<float*>(w + 72);
-    NYS_CUDA_TRY(cudaMemsetAsync(absmax, 0, sizeof(unsigned int), s));
-    const int64_t nd = n * d;
-    rt_absmax_kernel<<<(unsigned)(cdiv(nd, 256) < 1024 ? cdiv(nd, 256) : 1024), 256, 0, s>>>(
-        pts, n, d, ld, absmax);
-    count_launch();
-    __half* XS16 = reinterpret_cast<__half*>(XS);
-    rt_prep_points16_kernel<<<(unsigned)cdiv(npad, 8), 256, 0, s>>>(
-        pts, n, d, ld, npad, c, l2e / (sigma * sigma), absmax, XS16, cn, m2c_dev);
-    count_launch();
+    // one launch per vector (nvec <= 2), each reading its own padded copy
     CUtensorMap tx16;
     if (!tmap_f16_2d(&tx16, XS16, npad, 64, 64, 64, 64)) return NYS_ERR_CUDA;
     NYS_CUDA_TRY(
@@ -1150,7 +1709,7 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
     // (grid.y, fixed-order partial sums) so that the last wave of CTAs is
     // fuller.  The tuner times 1..4 slices; its fallback rule takes the
     // best last-wave fill.
-    const int64_t ctas = npad / RT_BM, ntiles = npad / GV_BN, sms = num_sms();
+    const int64_t ctas = npad / RT_BM, ntiles = npad / GV_BN;
     const std::vector<int> cands = gv_slice_candidates(ntiles);
     int nz = 1;
     NYS_TRY(tune_pick(gv_tune_key(npad, d, nvec), cands, wave_fill_rule(ctas, cands, sms),
@@ -1161,9 +1720,32 @@ int32_t rbf_tc_products(const float* pts, int64_t n, int64_t d, int64_t ld, doub
                       s, &nz));
     return gv_run(tx16, a, VS, m2c_dev, npad, ntiles, d, nvec, nz, part_ws, s);
   }
+  if (half) {
+    CUtensorMap tx16;
+    if (!tmap_f16_2d(&tx16, XS16, npad, 64, 64, 64, 64)) return NYS_ERR_CUDA;
+    __half* VS16 = reinterpret_cast<__half*>(VS);
+    auto run = [&](int code) -> int32_t {
+      const int si = code / 8, z = code % 8;
+      const int Sh = rt16_shape(passes, si);
+      const int64_t nblk_y = cdiv(nvec, Sh);
+      CUtensorMap tv16;
+      if (!tmap_f16_2d(&tv16, VS16, nv * spad, npad, npad, Sh, 64)) return NYS_ERR_CUDA;
+      if (passes == 1) return h16_launch<128, 1>(tx16, tv16, a, npad, nblk_y, z, part_ws, s);
+      if (Sh == 128) return h16_launch<128, 3>(tx16, tv16, a, npad, nblk_y, z, part_ws, s);
+      if (Sh == 64) return h16_launch<64, 3>(tx16, tv16, a, npad, nblk_y, z, part_ws, s);
+      return h16_launch<32, 3>(tx16, tv16, a, npad, nblk_y, z, part_ws, s);
+    };
+    int code = 1;
+    NYS_TRY(tune_pick(rt16_tune_key(passes, npad, d, nvec), rt16_candidates(passes, npad, nvec, sms),
+                      rt16_rule(passes, npad, nvec, sms), run, s, &code));
+    return run(code);
+  }
+  CUtensorMap tx, tv;
+  if (!tmap_f32_2d(&tx, XS, npad, 64, 64, 64, 32)) return NYS_ERR_CUDA;
+  if (!tmap_f32_2d(&tv, VS, nv * spad, npad, npad, S, 32)) return NYS_ERR_CUDA;
   // many vectors: point slices over grid.z where the grid is only a few waves
   const int64_t nblk_y = spad / S;
-  const int64_t ctas = (npad / RT_BM) * nblk_y, sms = num_sms();
+  const int64_t ctas = (npad / RT_BM) * nblk_y;
   const std::vector<int> cands = rt_slice_candidates(npad, nvec, ctas, sms);
   auto run = [&](int z) -> int32_t {
     return S == 64 ? rt_launch<64, 3>(tx, tv, a, npad, nblk_y, z, part_ws, s)

@@ -31,7 +31,7 @@ def run(code, env_extra):
 
 def test_cache_file_is_read_pinned_saved_and_cleared(tmp_path):
     path = tmp_path / "tune.json"
-    path.write_text('{\n  "rbf_tc S=64 passes=3 npad=50048 d=16 blocks=2 sms=152": 3,\n'
+    path.write_text('{\n  "rbf_tc16 passes=3 npad=50048 d=16 nvec=128 sms=152": 9,\n'
                     '  "rbf_gemv npad=100096 d=32 nvec=1 sms=152": 1\n}\n')
     got = run("""
         import json
@@ -43,7 +43,7 @@ def test_cache_file_is_read_pinned_saved_and_cleared(tmp_path):
         print(json.dumps([first, second, ny.autotune_choices()]))
     """, {"NYS_TUNE_CACHE": str(path)})
     first, second, cleared = got
-    assert first == {"rbf_tc S=64 passes=3 npad=50048 d=16 blocks=2 sms=152": 3,
+    assert first == {"rbf_tc16 passes=3 npad=50048 d=16 nvec=128 sms=152": 9,
                      "rbf_gemv npad=100096 d=32 nvec=1 sms=152": 1}
     assert second == dict(first, **{"extra key": 4})
     assert cleared == {}

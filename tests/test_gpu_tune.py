@@ -37,10 +37,12 @@ def keys_with(ny, prefix, fragment):
     return [k for k in ny.autotune_choices() if k.startswith(prefix) and fragment in k]
 
 
-@pytest.mark.parametrize("n,d,nvec,prefix", [(5000, 16, 128, "rbf_tc S=64"),
-                                              (4100, 9, 70, "rbf_tc S=64"),
+@pytest.mark.parametrize("n,d,nvec,prefix", [(5000, 16, 128, "rbf_tc16 passes=3"),
+                                              (4100, 9, 70, "rbf_tc16 passes=3"),
                                               (20000, 32, 1, "rbf_gemv")])
-def test_every_slice_count_gives_the_product(ny, n, d, nvec, prefix):
+def test_every_launch_shape_gives_the_product(ny, n, d, nvec, prefix):
+    # one vector: the slice count (1..4); many vectors: vectors per CTA
+    # (128, 64, 32) x slices, coded as shape index * 8 + slices
     P = wl.gmm_points(n, d, seed=31)
     sigma = wl.median_distance(P, seed=31)
     V = wl.rhs(n, seed=31, nrhs=nvec)
@@ -52,17 +54,20 @@ def test_every_slice_count_gives_the_product(ny, n, d, nvec, prefix):
     npad = (n + 127) // 128 * 128
     keys = keys_with(ny, prefix, f"npad={npad} d={d}")
     assert len(keys) == 1, ny.autotune_choices()
-    assert 1 <= ny.autotune_choices()[keys[0]] <= 4
+    many = nvec > 2
+    codes = [si * 8 + z for si in range(3) for z in (1, 2, 3, 4)] if many else [1, 2, 3, 4]
+    assert ny.autotune_choices()[keys[0]] in codes
     assert relerr(y0, ref) <= 1e-5
     outs = []
-    for z in (1, 2, 3, 4):
-        ny.autotune_set(keys[0], z)
+    for code in codes:
+        ny.autotune_set(keys[0], code)
         y = ny.nys_op_matvec(op, mu, T(V), mode=1).cpu().numpy()
-        assert relerr(y, ref) <= 1e-5, z
+        assert relerr(y, ref) <= 1e-5, code
         outs.append(y)
-    # the shapes differ only in how the FP32 sum over the points (N(0,1)
-    # vectors: the terms cancel) is grouped, each within the 1e-5 of the
-    # oracle above; a dropped or doubled slice would be off by O(1 / slices)
+    # the shapes differ only in how the FP32 sums are grouped (over the
+    # points, N(0,1) vectors: the terms cancel), each within the 1e-5 of the
+    # oracle above; a dropped or doubled slice or vector block would be off
+    # by O(1 / slices)
     for y in outs[1:]:
         assert relerr(y, outs[0]) <= 1e-5
     ny.autotune_clear()
@@ -80,7 +85,7 @@ def test_batched_solve_tunes_once_and_reuses_the_choice(ny):
     X1, r1, _ = ny.pcg_solve(op, f, mus, B, tol=1e-8, precision=ny.NYS_PREC_MIXED)
     choices = dict(ny.autotune_choices())
     npad = (n + 127) // 128 * 128
-    assert len(keys_with(ny, "rbf_tc S=64", f"npad={npad} d={d} blocks=1")) == 1, choices
+    assert len(keys_with(ny, "rbf_tc16 passes=3", f"npad={npad} d={d} nvec=32")) == 1, choices
     X2, r2, _ = ny.pcg_solve(op, f, mus, B, tol=1e-8, precision=ny.NYS_PREC_MIXED)
     assert ny.autotune_choices() == choices
     assert torch.equal(X1, X2)
