@@ -43,54 +43,70 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return ldexp(y, -ex / 2);
 }
 
+// 1/d for finite d > 0 in FP64 without a division: d = m 2^e with m in
+// [0.5, 1) (exact exponent arithmetic), a single-precision estimate of 1/m
+// (about 2^-23 relative), two Newton-Raphson steps y <- y + y (1 - m y), each
+// squaring the relative error, and the scale 2^-e.
+__device__ __forceinline__ double recip_newton(double d) {
+  int ex;
+  const double m = frexp(d, &ex);
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)m));
+  double y = (double)yf;
+  double h = fma(-m, y, 1.0);
+  y = fma(y, h, y);
+  h = fma(-m, y, 1.0);
+  y = fma(y, h, y);
+  return ldexp(y, -ex);
+}
+
 // Factor the diagonal block D = M[k:k+nb, k:k+nb] in place: D = C_kk^T C_kk.
-// One warp; the block sits in shared memory and lane c owns column c.  Step
-// j: lane j takes the pivot's reciprocal square root (rsqrt_newton: GB300
-// runs FP64 division and square root as long dependent chains), the lanes
-// scale row j (C[j][c] = D[j][c] / C_jj), and lane c updates rows
-// j < r <= c of its column with the broadcast C[j][r].  The step loop is not
-// unrolled: a fully unrolled 32 x 32 body (the first version) is thousands
-// of instructions, which one warp cannot keep in the instruction cache.
-__global__ void __launch_bounds__(32) chol_diag_kernel(double* M, int64_t ell, int64_t k, int nb,
-                                                       int* info) {
+// 32 warps: warp r owns row r of the block in shared memory, lane c column c
+// (the upper triangle).  The elimination runs without square roots (D =
+// L diag(d) L^T form): at step j the lanes of warp j form the pivot's
+// reciprocal (recip_newton: GB300 runs FP64 division and square root as long
+// dependent chains, and each FP64 warp instruction occupies the SM
+// sub-partition's FP64 unit for many cycles) and the scaled row W_j = D_j / d_j;
+// after one barrier every warp r > j updates its row, D_rc -= D_jr W_jc, one
+// FMA per thread, so the FP64 work of a step spreads over the four sub-
+// partitions.  Only the pivot chain is sequential.  At the end C_jc = D_jc /
+// sqrt(d_j) (C_jj = sqrt(d_j)) for all entries at once.
+__global__ void __launch_bounds__(32 * CH_NB) chol_diag_kernel(double* M, int64_t ell, int64_t k,
+                                                               int nb, int* info) {
   if (*info != 0) return;
   __shared__ double D[CH_NB][CH_NB + 1];
-  __shared__ double s_rp;
+  __shared__ double W[CH_NB][CH_NB + 1];
   __shared__ int s_bad;
-  const int c = threadIdx.x;
-#pragma unroll
-  for (int r = 0; r < CH_NB; ++r)
-    D[r][c] = (r < nb && c < nb) ? M[(k + r) * ell + k + c] : (r == c ? 1.0 : 0.0);
-  if (c == 0) s_bad = 0;
-  __syncwarp();
+  const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+  D[r][c] = (r < nb && c < nb) ? M[(k + r) * ell + k + c] : (r == c ? 1.0 : 0.0);
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    if (c == j) {
-      const double d = D[j][j];
+    if (r == j) {
+      const double d = D[j][j];  // final: row j took its last update at step j - 1
       if (!(d > 0.0) || !isfinite(d)) {
-        s_bad = (int)(k + j + 1);
-      } else {
-        const double rp = rsqrt_newton(d);
-        s_rp = rp;
-        D[j][j] = d * rp;  // sqrt(d)
+        if (c == 0) s_bad = (int)(k + j + 1);
+      } else if (c > j) {
+        W[j][c] = D[j][c] * recip_newton(d);
       }
     }
-    __syncwarp();
+    __syncthreads();
     if (s_bad) break;
-    if (c > j && c < nb) D[j][c] *= s_rp;  // C[j][c]
-    __syncwarp();
-    if (c > j && c < nb) {
-      const double cjc = D[j][c];
-      for (int r = j + 1; r <= c; ++r) D[r][c] = fma(-D[j][r], cjc, D[r][c]);
-    }
-    __syncwarp();
+    if (r > j && c >= r) D[r][c] = fma(-D[j][r], W[j][c], D[r][c]);
   }
   if (s_bad) {
-    if (c == 0) atomicCAS(info, 0, s_bad);
+    if (threadIdx.x == 0) atomicCAS(info, 0, s_bad);
     return;
   }
-  if (c < nb) {
-#pragma unroll 4
-    for (int r = 0; r < nb; ++r) M[(k + r) * ell + k + c] = (c >= r) ? D[r][c] : 0.0;
+  // row r is final once warp r has passed step r - 1 (its own updates)
+  if (r < nb && c < nb) {
+    double v = 0.0;
+    if (c >= r) {
+      const double dr = D[r][r];
+      const double sr = rsqrt_newton(dr);
+      v = (c == r) ? dr * sr : D[r][c] * sr;
+    }
+    M[(k + r) * ell + k + c] = v;
   }
 }
 
@@ -162,7 +178,7 @@ int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s) {
   NYS_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   for (int64_t k = 0; k < ell; k += CH_NB) {
     int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
-    chol_diag_kernel<<<1, 32, 0, s>>>(M, ell, k, nb, d_info); count_launch();
+    chol_diag_kernel<<<1, 32 * CH_NB, 0, s>>>(M, ell, k, nb, d_info); count_launch();
     int64_t rest = ell - k - nb;
     if (rest > 0) {
       chol_panel_kernel<<<(unsigned)cdiv(rest, 8), 256, 0, s>>>(M, ell, k, nb, d_info); count_launch();
