@@ -995,16 +995,22 @@ __global__ void rt_prep_vecs16_kernel(const float* __restrict__ V, int64_t nvec,
 //
 //   warp 0, lane 0:  X producer.  X_I once; X_J and cn_J per tile (ring HX_NS).
 //   warp 10, lane 0: V producer.  The tile's slabs of the vectors (ring HV_NS).
-//   warp 1, lane 0:  MMA issuer.  Per tile t, in order: GEMM2(t) into the
-//                    Yacc chunk (once the exp group stored K_t), then
-//                    GEMM1(t + 3) into the buffer GEMM2(t - 1) released.
+//   warp 11, lane 0: GEMM1 issuer.  GEMM1(u) into buffer u % HB once
+//                    GEMM2(u - HB) is done with it.
+//   warp 1, lane 0:  GEMM2 issuer.  GEMM2(t) into the Yacc chunk once the exp
+//                    group stored K_t; it never waits for an MMA to finish.
 //   warps 2..9:      two exp groups (tiles of one parity each).  P_t from
 //                    TMEM, k 2^15 split into FP16 hi + lo, stored over P_t;
 //                    each group promotes half of the Yacc columns of a chunk.
+// The two issuers are separate threads because a commit's completion takes
+// longer to reach a waiting thread than a tile's MMAs take to run: one
+// thread that waited for GEMM2(t - 1) before issuing GEMM1 kept the tensor
+// pipe idle two thirds of the time (measured with clock64 stamps).  Each
+// thread's commits track its own MMAs only.
 constexpr int HB = 4;        // TMEM tile buffers (64 columns each)
 constexpr int HX_NS = 5;     // X_J / cn_J ring
 constexpr int HV_NS = 3;     // vector-slab ring
-constexpr int H_THREADS = 64 + 32 * RT_EXP_WARPS + 32;  // + the V producer warp
+constexpr int H_THREADS = 64 + 32 * RT_EXP_WARPS + 64;  // + V producer and GEMM1 issuer warps
 constexpr int H_XSLOT = 9 * 1024;                        // X_J (8 KB) + cn_J (256 B)
 
 template <int S, int P2>
@@ -1188,23 +1194,26 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             atomicOr(&s_fail, 1);
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == RT_EXP_WARPS + 3) {
     if (lane == 0) {
-      // ---------------- MMA issuer
+      // ---------------- GEMM1 issuer: P_u = X_I X_J^T (hi.hi + hi.lo + lo.hi,
+      // K = 16 per MMA) into buffer u % HB
       constexpr uint32_t idesc1 = f16_idesc(RT_BM, RT_BN);
-      constexpr uint32_t idesc2 = f16_idesc(RT_BM, S);
       bool ok = mbar_wait_bounded(afull, 0u);
       const uint64_t aHiD = sw128_kmajor_desc(smem_u32(sA));
       const uint64_t aLoD = aHiD + (uint64_t)(64 >> 4);  // lo halves: 64 bytes into each row
       const int ks = a.ksteps;                             // ceil(d / 16)
-      // GEMM1(u): P_u = X_I X_J^T (hi.hi + hi.lo + lo.hi, K = 16 per MMA)
-      auto gemm1 = [&](int u) -> bool {
-        const int s = u % HX_NS;
-        if (!mbar_wait_bounded(&xfull[s], (uint32_t)((u / HX_NS) & 1))) return false;
+      for (int u = 0; ok && u < T; ++u) {
+        const int s = u % HX_NS, b = u % HB;
+        if (u >= HB && !mbar_wait_bounded(&bfree[b], (uint32_t)(((u - HB) / HB) & 1))) {
+          ok = false;
+          break;
+        }
+        if (!mbar_wait_bounded(&xfull[s], (uint32_t)((u / HX_NS) & 1))) { ok = false; break; }
         tc_fence_after();
         const uint64_t bHiD = sw128_kmajor_desc(smem_u32(sX + s * H_XSLOT));
         const uint64_t bLoD = bHiD + (uint64_t)(64 >> 4);
-        const uint32_t dP = tmem + (uint32_t)((u % HB) * 64);
+        const uint32_t dP = tmem + (uint32_t)(b * 64);
 #pragma unroll
         for (int pass = 0; pass < 3; ++pass) {
           const uint64_t ad = pass == 2 ? aLoD : aHiD;
@@ -1215,10 +1224,15 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
               mma_f16(dP, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc1,
                       (pass > 0 || k > 0) ? 1u : 0u);
         }
-        mma_commit(&pfull[u % HB]);
-        return true;
-      };
-      for (int u = 0; ok && u < HB - 1 && u < T; ++u) ok = gemm1(u);
+        mma_commit(&pfull[b]);
+      }
+      if (!ok) atomicOr(&s_fail, 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- GEMM2 issuer
+      constexpr uint32_t idesc2 = f16_idesc(RT_BM, S);
+      bool ok = true;
       for (int t = 0; ok && t < T; ++t) {
         const int b = t % HB, sv = t % HV_NS;
         if (!mbar_wait_bounded(&kfull[b], (uint32_t)((t / HB) & 1))) { ok = false; break; }
@@ -1248,21 +1262,11 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         mma_commit(&bfree[b]);
         mma_commit(&vempty[sv]);
         if (Cfg::CHUNKED && (t % Cfg::CH == Cfg::CH - 1 || t == T - 1)) mma_commit(&ycf[c & 1]);
-        // GEMM1(t + 3) into the buffer of tile t - 1, once GEMM2(t - 1) is
-        // done with it (GEMM2(t) is queued meanwhile)
-        const int u = t + HB - 1;
-        if (u < T) {
-          if (t >= 1 && !mbar_wait_bounded(&bfree[(t - 1) % HB], (uint32_t)(((t - 1) / HB) & 1))) {
-            ok = false;
-            break;
-          }
-          if (!gemm1(u)) { ok = false; break; }
-        }
       }
       if (ok) {
         if (!Cfg::CHUNKED) mma_commit(yfull);
-        // the bfree arrivals of the last tiles are not awaited above: wait
-        // here so that none lands after the CTA exits
+        // the GEMM1 issuer awaits the bfree arrivals of tiles below T - HB:
+        // wait for the others here so that none lands after the CTA exits
         for (int t = (T > HB ? T - HB : 0); t < T; ++t)
           if (!mbar_wait_bounded(&bfree[t % HB], (uint32_t)((t / HB) & 1))) ok = false;
       }
