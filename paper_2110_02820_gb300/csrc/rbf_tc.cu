@@ -235,6 +235,43 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Packed FP32 pairs (sm_100 family): two lanes of FP32 arithmetic per
+// instruction, each rounded as the scalar operation.
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// The two FP16 halves of a word as FP32 values (exact).
+__device__ __forceinline__ void unpack_f16x2(uint32_t w, float& lo, float& hi) {
+  asm("{.reg .f16 a, b;\n\tmov.b32 {a, b}, %2;\n\tcvt.f32.f16 %0, a;\n\tcvt.f32.f16 %1, b;\n\t}"
+      : "=f"(lo), "=f"(hi)
+      : "r"(w));
+}
+
 // Round to the nearest TF32 value (ties away from zero), kept in an FP32
 // container: add half a unit of the 13 dropped bits, then clear them.
 // Integer ALU work (finite inputs below 2^127 only, which holds here).
@@ -1281,6 +1318,8 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const float ai = a.cn[row];
     const float m2c = *a.m2c_dev;
+    const uint64_t m2c2 = f2pack(m2c, m2c), ai2 = f2pack(ai, ai),
+                   scale2 = f2pack(32768.f, 32768.f);
     const int c0 = g * Cfg::HALF;  // this group's Yacc columns
     bool ok = true;
     int next_chunk = 0;            // next chunk this group promotes
@@ -1304,28 +1343,31 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         const uint32_t(&pr)[32] = h ? r1 : r0;
         // k 2^15 split into FP16 hi + lo, two points per TMEM column (the
         // lower point index in the lower half), over the P columns just read
+        // pairs of points in packed FP32 pairs (each half rounds as the
+        // scalar operation): exponent, 2^15 scale, hi = fp16(k), lo =
+        // fp16(k - hi) with k - hi exact in FP32
         uint32_t hw[16], lw[16];
 #pragma unroll
         for (int j4 = 0; j4 < 8; ++j4) {
           const float4 c4 = cn4[h * 8 + j4];
-          const float cj[4] = {c4.x, c4.y, c4.z, c4.w};
-          float kh[4], kl[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float kv =
-                ex2_approx(fmaf(__uint_as_float(pr[j4 * 4 + e]), m2c, ai + cj[e])) * 32768.f;
+          for (int e = 0; e < 4; e += 2) {
+            const uint64_t cj2 = e ? f2pack(c4.z, c4.w) : f2pack(c4.x, c4.y);
+            const uint64_t p2 = f2pack(__uint_as_float(pr[j4 * 4 + e]),
+                                       __uint_as_float(pr[j4 * 4 + e + 1]));
+            float x0, x1;
+            f2unpack(f2fma(p2, m2c2, f2add(ai2, cj2)), x0, x1);
+            const uint64_t k2 = f2mul(f2pack(ex2_approx(x0), ex2_approx(x1)), scale2);
+            float k0, k1;
+            f2unpack(k2, k0, k1);
+            const uint32_t hp = pack_f16x2(k0, k1);
+            hw[2 * j4 + (e >> 1)] = hp;
             if (P2 == 3) {
-              kh[e] = __uint_as_float(tf32_rna(kv));  // exact in FP16 (10-bit fraction)
-              kl[e] = kv - kh[e];
-            } else {
-              kh[e] = kv;
+              float h0, h1, l0, l1;
+              unpack_f16x2(hp, h0, h1);
+              f2unpack(f2sub(k2, f2pack(h0, h1)), l0, l1);
+              lw[2 * j4 + (e >> 1)] = pack_f16x2(l0, l1);
             }
-          }
-          hw[2 * j4] = pack_f16x2(kh[0], kh[1]);
-          hw[2 * j4 + 1] = pack_f16x2(kh[2], kh[3]);
-          if (P2 == 3) {
-            lw[2 * j4] = pack_f16x2(kl[0], kl[1]);
-            lw[2 * j4 + 1] = pack_f16x2(kl[2], kl[3]);
           }
         }
         tmem_st16(buf + (uint32_t)(16 * h), hw);
