@@ -211,9 +211,14 @@ static int32_t gemm_launch(bool trans_a, int64_t M, int64_t N, int64_t K, const 
   int64_t splits = 1;
   if (tiles < target && K > 4 * BK) {
     splits = cdiv(target, tiles);
-    int64_t max_splits = cdiv(K, 256);  // at least 256 K per split
+    // at least 256 K per split, 32 for FP64: an SM does ~2 FP64 FMA per
+    // clock, so a small FP64 product (an ell x ell Gram of a tall block)
+    // needs every SM, and the partial sums it adds are small
+    constexpr int64_t kMinK = sizeof(T) == 8 ? 32 : 256;
+    constexpr int64_t kMaxSplits = sizeof(T) == 8 ? 128 : 64;
+    int64_t max_splits = cdiv(K, kMinK);
     if (splits > max_splits) splits = max_splits;
-    if (splits > 64) splits = 64;
+    if (splits > kMaxSplits) splits = kMaxSplits;
     if (splits < 1) splits = 1;
   }
   int64_t kchunk = cdiv(cdiv(K, splits), BK) * BK;

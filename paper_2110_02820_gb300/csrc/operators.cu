@@ -747,16 +747,20 @@ int32_t op_sketch(const nys_operator* op, bool f64, const void* Q, void* V, int6
                   cudaStream_t s) {
   const int64_t n = op->n;
   if (op->kind == NYS_OP_DENSE) {
+    // Y = A Omega in double-FP32 arithmetic (~2^-48 relative to sum |a| |omega|,
+    // on the FP32 pipes): the sketch only shapes the preconditioner, and the
+    // n x ell x n product is the one FP64 GEMM of the dense path that would
+    // otherwise run at GB300's FP64 rate
     if (f64)
-      return gemm_f64(false, n, ell, n, (const double*)op->data, op->ld, (const double*)Q, ell,
-                      (double*)V, ell, s);
-    // mixed: FP64 matrix, FP32 block -> compute in FP64 and round
+      return gemm_dfl(false, n, ell, n, (const double*)op->data, op->ld, (const double*)Q, ell,
+                      (double*)V, ell, false, s);
+    // mixed: FP64 matrix, FP32 block -> compute in double-FP32 and round
     Scratch sc(s);
     double *Qd, *Vd;
     NYS_TRY(sc.get(&Qd, n * ell));
     NYS_TRY(sc.get(&Vd, n * ell));
     NYS_TRY(convert_f32_to_f64((const float*)Q, Qd, n * ell, s));
-    NYS_TRY(gemm_f64(false, n, ell, n, (const double*)op->data, op->ld, Qd, ell, Vd, ell, s));
+    NYS_TRY(gemm_dfl(false, n, ell, n, (const double*)op->data, op->ld, Qd, ell, Vd, ell, false, s));
     return convert_f64_to_f32(Vd, (float*)V, n * ell, s);
   }
   if (op->kind == NYS_OP_GRAM) {
