@@ -165,7 +165,7 @@ static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool r
   for (int pass = 0; pass < passes; ++pass) {
     NYS_TRY(Ops<T>::gram(cur, cur, n, ell, ell, G, s));
     NYS_TRY(symmetrize(G, ell, s));
-    NYS_TRY(chol_upper(G, ell, info, s));
+    NYS_TRY(Ops<T>::f64 ? chol_upper(G, ell, info, s) : chol_upper_dfl(G, ell, info, s));
     int h_info = 0;
     NYS_TRY(read_int(info, &h_info, s));
     if (h_info != 0) {
@@ -180,12 +180,12 @@ static int32_t cholqr(T* X, int64_t n, int64_t ell, T* tmp, double* Racc, bool r
       double shift = 11.0 * ((double)n * ell + (double)ell * (ell + 1)) * u * h_dmax;
       if (!(shift > 0.0)) return NYS_ERR_NOT_PSD;
       NYS_TRY(add_diag(G, ell, shift, s));
-      NYS_TRY(chol_upper(G, ell, info, s));
+      NYS_TRY(Ops<T>::f64 ? chol_upper(G, ell, info, s) : chol_upper_dfl(G, ell, info, s));
       NYS_TRY(read_int(info, &h_info, s));
       if (h_info != 0) return NYS_ERR_NOT_PSD;
       passes = passes0 + 1;
     }
-    NYS_TRY(tri_inv_upper(G, Gi, ell, s));
+    NYS_TRY(Ops<T>::f64 ? tri_inv_upper(G, Gi, ell, s) : tri_inv_upper_dfl(G, Gi, ell, s));
     NYS_TRY(Ops<T>::mul_small(cur, Gi, n, ell, ell, other, s));
     // Racc <- R_pass Racc
     if (!Racc) {
@@ -282,14 +282,15 @@ static int32_t shifted_core(const T* Q, const T* Y, int64_t n, int64_t ell, bool
     NYS_TRY(Ops<T>::shift(Y, Q, Ynu, n * ell, nu, s));  // Y_nu = Y + nu Q
     NYS_TRY(Ops<T>::gram(Q, Ynu, n, ell, ell, M, s));    // Q^T Y_nu
     NYS_TRY(symmetrize(M, ell, s));
-    NYS_TRY(chol_upper(M, ell, info, s));                // C^T C = Q^T Y_nu
+    // C^T C = Q^T Y_nu
+    NYS_TRY(Ops<T>::f64 ? chol_upper(M, ell, info, s) : chol_upper_dfl(M, ell, info, s));
     int h = 0;
     NYS_TRY(read_int(info, &h, s));
     if (h == 0) break;
     if (esc >= kMaxEscalations) return NYS_ERR_NOT_PSD;
     scale_scalar_kernel<<<1, 1, 0, s>>>(nu, 10.0); count_launch();
   }
-  NYS_TRY(tri_inv_upper(M, Ci, ell, s));
+  NYS_TRY(Ops<T>::f64 ? tri_inv_upper(M, Ci, ell, s) : tri_inv_upper_dfl(M, Ci, ell, s));
   NYS_TRY(Ops<T>::mul_small(Ynu, Ci, n, ell, ell, Bb, s));  // B = Y_nu C^{-1}
   // thin SVD of B: B = Qb R (CholeskyQR2), R = Ut Sigma V^T (one-sided Jacobi)
   NYS_TRY(cholqr<T>(Bb, n, ell, Ynu, R, true, 2, s));

@@ -90,6 +90,11 @@ struct Scratch {
 int32_t chol_upper(double* M, int64_t ell, int* d_info, cudaStream_t s);
 // X = C^{-1} for upper-triangular C (ell x ell); X upper triangular.
 int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s);
+// The same inverse in double-FP32 arithmetic (~2^-48 relative; for the
+// mixed-precision path, whose products with C^{-1} run in FP32).
+int32_t tri_inv_upper_dfl(const double* C, double* X, int64_t ell, cudaStream_t s);
+// Blocked Cholesky as chol_upper in double-FP32 arithmetic (mixed path).
+int32_t chol_upper_dfl(double* M, int64_t ell, int* d_info, cudaStream_t s);
 // M = (M + M^T) / 2.
 int32_t symmetrize(double* M, int64_t ell, cudaStream_t s);
 // M += shift * I (shift read from device scalar times factor).

@@ -267,6 +267,302 @@ tri_inv_cols2_kernel(const double* __restrict__ CT, const double* __restrict__ C
   }
 }
 
+// ---- the same inverse in double-FP32 arithmetic (Dekker 1971) on the FP32
+// pipes, for the mixed-precision path, whose products with C^{-1} run in FP32:
+// a value is an unevaluated pair hi + lo of FP32 numbers (~2^-48 relative).
+// The column chain is the same; a step's FP64 FMAs, each occupying the FP64
+// unit of an SM sub-partition for many cycles on GB300, become ~11 FP32
+// operations with short latencies.
+struct Dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ Dfl dfl_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+
+// r + a b (a b formed exactly in its high part by an FMA two-product, the
+// cross terms hi.lo added, lo.lo dropped; the sum by Knuth's TwoSum)
+__device__ __forceinline__ Dfl dfl_fma(Dfl a, Dfl b, Dfl r) {
+  const float ph = a.hi * b.hi;
+  float pl = fmaf(a.hi, b.hi, -ph);
+  pl = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, pl));
+  const float s = r.hi + ph;
+  const float bb = s - r.hi;
+  float e = (r.hi - (s - bb)) + (ph - bb);
+  e += r.lo + pl;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ Dfl dfl_mul(Dfl a, Dfl b) {
+  const float ph = a.hi * b.hi;
+  float pl = fmaf(a.hi, b.hi, -ph);
+  pl = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, pl));
+  const float h = ph + pl;
+  return {h, pl - (h - ph)};
+}
+
+// CTf[t][i] = split(C[i][t]) (the transpose as double-FP32 pairs) and
+// dinvf[i] = split(1 / C_ii)
+__global__ void tri_split_kernel(const double* __restrict__ C, float2* __restrict__ CTf,
+                                 float2* __restrict__ dinvf, int64_t ell) {
+  __shared__ double tile[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = by + r, j = bx + threadIdx.x;
+    if (i < ell && j < ell) tile[r][threadIdx.x] = C[i * ell + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t t = bx + r, i = by + threadIdx.x;  // CTf[t][i] = C[i][t]
+    if (t < ell && i < ell) {
+      const double v = tile[threadIdx.x][r];
+      const Dfl d = dfl_from(v);
+      CTf[t * ell + i] = make_float2(d.hi, d.lo);
+      if (t == i) {
+        const Dfl q = dfl_from(1.0 / v);
+        dinvf[i] = make_float2(q.hi, q.lo);
+      }
+    }
+  }
+}
+
+// Column j of X = C^{-1} by back substitution, as tri_inv_cols2_kernel, in
+// double-FP32; writes X[i][j] (FP64) for i <= j and zero below.
+constexpr int TD_WARPS = 4;
+constexpr int TD_PF = 16;
+__global__ void __launch_bounds__(32 * TD_WARPS)
+tri_inv_dfl_kernel(const float2* __restrict__ CTf, const float2* __restrict__ dinvf, double* X,
+                   int64_t ell) {
+  extern __shared__ float2 rsf[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * TD_WARPS + wib;
+  if (j >= ell) return;
+  float2* r = rsf + (int64_t)wib * ell;
+  for (int64_t i = lane; i < ell; i += 32) {
+    r[i] = make_float2(0.f, 0.f);
+    if (i > j) X[i * ell + j] = 0.0;
+  }
+  __syncwarp();
+  const float2 d0 = dinvf[j];
+  Dfl xt = {d0.x, d0.y};
+  if (lane == 0) X[j * ell + j] = (double)xt.hi + (double)xt.lo;
+  float2 pf[TD_PF];
+  {
+    const float2* row = CTf + j * ell;
+#pragma unroll
+    for (int q = 0; q < TD_PF; ++q) {
+      const int64_t i = lane + 32 * q;
+      pf[q] = (i < j) ? row[i] : make_float2(0.f, 0.f);
+    }
+  }
+  for (int64_t t = j; t >= 1; --t) {
+    // r_i += C[i][t] x_t for i < t (the sign is applied when x is formed)
+    const float2* row = CTf + t * ell;
+    const float2* nrow = CTf + (t - 1) * ell;
+    float2 nxt[TD_PF];
+#pragma unroll
+    for (int q = 0; q < TD_PF; ++q) {
+      const int64_t i = lane + 32 * q;
+      nxt[q] = (i < t - 1) ? nrow[i] : make_float2(0.f, 0.f);
+      if (i < t) {
+        const float2 ri = r[i];
+        const Dfl v = dfl_fma({pf[q].x, pf[q].y}, xt, {ri.x, ri.y});
+        r[i] = make_float2(v.hi, v.lo);
+      }
+    }
+    for (int64_t i = lane + 32 * TD_PF; i < t; i += 32) {
+      const float2 ri = r[i], ci = row[i];
+      const Dfl v = dfl_fma({ci.x, ci.y}, xt, {ri.x, ri.y});
+      r[i] = make_float2(v.hi, v.lo);
+    }
+    __syncwarp();
+    const int64_t i1 = t - 1;
+    const float2 rr = r[i1], dd = dinvf[i1];
+    xt = dfl_mul({-rr.x, -rr.y}, {dd.x, dd.y});
+    if (lane == 0) X[i1 * ell + j] = (double)xt.hi + (double)xt.lo;
+#pragma unroll
+    for (int q = 0; q < TD_PF; ++q) pf[q] = nxt[q];
+    __syncwarp();
+  }
+}
+
+int32_t tri_inv_upper_dfl(const double* C, double* X, int64_t ell, cudaStream_t s) {
+  Scratch sc(s);
+  float2 *CTf, *dinvf;
+  NYS_TRY(sc.get(&CTf, ell * ell));
+  NYS_TRY(sc.get(&dinvf, ell));
+  dim3 g((unsigned)cdiv(ell, 32), (unsigned)cdiv(ell, 32));
+  tri_split_kernel<<<g, dim3(32, 8), 0, s>>>(C, CTf, dinvf, ell); count_launch();
+  const size_t sh = (size_t)TD_WARPS * ell * sizeof(float2);
+  if (sh > 48 * 1024)
+    NYS_CUDA_TRY(cudaFuncSetAttribute(tri_inv_dfl_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  tri_inv_dfl_kernel<<<(unsigned)cdiv(ell, TD_WARPS), 32 * TD_WARPS, sh, s>>>(CTf, dinvf, X, ell);
+  count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
+// ---- blocked Cholesky in double-FP32 arithmetic, for the mixed-precision
+// path (its shifted Grams are conditioned for FP32 data, far inside the
+// ~2^-48 of double-FP32).  Same three launches per 32-column step as
+// chol_upper; M stays FP64 in memory, each kernel splits what it reads into
+// FP32 pairs and rounds what it writes back to FP64.
+
+__device__ __forceinline__ Dfl dfl_neg(Dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ double dfl_to(Dfl a) { return (double)a.hi + (double)a.lo; }
+
+// 1/d for d > 0: FP32 estimate, one Newton-Raphson step y + y (1 - d y)
+// with the residual 1 - d y formed in double-FP32 (~2^-46 relative)
+__device__ __forceinline__ Dfl dfl_recip(Dfl d) {
+  float y0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(d.hi));
+  const float ph = d.hi * y0;
+  const float pl = fmaf(d.hi, y0, -ph);
+  const float e = ((1.0f - ph) - pl) - d.lo * y0;
+  const float yl = y0 * e;
+  const float h = y0 + yl;
+  return {h, yl - (h - y0)};
+}
+
+// Diagonal block, as chol_diag_kernel (32 warps, one element per thread, no
+// square root on the pivot chain), in double-FP32.
+__global__ void __launch_bounds__(32 * CH_NB) chol_diag_dfl_kernel(double* M, int64_t ell,
+                                                                   int64_t k, int nb, int* info) {
+  if (*info != 0) return;
+  __shared__ float2 D[CH_NB][CH_NB + 1];
+  __shared__ float2 W[CH_NB][CH_NB + 1];
+  __shared__ int s_bad;
+  const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+  {
+    const double v = (r < nb && c < nb) ? M[(k + r) * ell + k + c] : (r == c ? 1.0 : 0.0);
+    const Dfl d = dfl_from(v);
+    D[r][c] = make_float2(d.hi, d.lo);
+  }
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (r == j) {
+      const float2 dj = D[j][j];
+      if (!(dj.x > 0.f) || !isfinite(dj.x)) {
+        if (c == 0) s_bad = (int)(k + j + 1);
+      } else if (c > j) {
+        const Dfl y = dfl_recip({dj.x, dj.y});
+        const float2 djc = D[j][c];
+        const Dfl w = dfl_mul({djc.x, djc.y}, y);
+        W[j][c] = make_float2(w.hi, w.lo);
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    if (r > j && c >= r) {
+      const float2 a = D[j][r], b = W[j][c], m = D[r][c];
+      const Dfl v = dfl_fma(dfl_neg({a.x, a.y}), {b.x, b.y}, {m.x, m.y});
+      D[r][c] = make_float2(v.hi, v.lo);
+    }
+  }
+  if (s_bad) {
+    if (threadIdx.x == 0) atomicCAS(info, 0, s_bad);
+    return;
+  }
+  if (r < nb && c < nb) {
+    double v = 0.0;
+    if (c >= r) {
+      const float2 drr = D[r][r];
+      const double dr = dfl_to({drr.x, drr.y});
+      const double sr = rsqrt_newton(dr);
+      const float2 drc = D[r][c];
+      v = (c == r) ? dr * sr : dfl_to({drc.x, drc.y}) * sr;
+    }
+    M[(k + r) * ell + k + c] = v;
+  }
+}
+
+// Row panel, as chol_panel_kernel, in double-FP32.
+__global__ void chol_panel_dfl_kernel(double* M, int64_t ell, int64_t k, int nb, const int* info) {
+  if (*info != 0) return;
+  __shared__ float2 Ck[CH_NB][CH_NB + 1];
+  __shared__ float2 dinv[CH_NB];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int r = e / nb, c = e % nb;
+    const Dfl d = dfl_from(M[(k + r) * ell + k + c]);
+    Ck[r][c] = make_float2(d.hi, d.lo);
+  }
+  if (threadIdx.x < nb) {
+    const Dfl q = dfl_from(1.0 / M[(k + threadIdx.x) * ell + k + threadIdx.x]);
+    dinv[threadIdx.x] = make_float2(q.hi, q.lo);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t c = k + nb + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= ell) return;
+  Dfl m = dfl_from((lane < nb) ? M[(k + lane) * ell + c] : 0.0);
+  for (int r = 0; r < nb; ++r) {
+    Dfl xr = {0.f, 0.f};
+    if (lane == r) xr = dfl_mul(m, {dinv[r].x, dinv[r].y});
+    xr.hi = __shfl_sync(0xffffffffu, xr.hi, r);
+    xr.lo = __shfl_sync(0xffffffffu, xr.lo, r);
+    if (lane == r) {
+      m = xr;
+    } else if (lane > r && lane < nb) {
+      const float2 ck = Ck[r][lane];
+      m = dfl_fma(dfl_neg({ck.x, ck.y}), xr, m);
+    }
+  }
+  if (lane < nb) M[(k + lane) * ell + c] = dfl_to(m);
+}
+
+// Trailing update of the upper triangle, as chol_trail_kernel, with the
+// 32-term sums in double-FP32.
+__global__ void chol_trail_dfl_kernel(double* M, int64_t ell, int64_t k, int nb, const int* info) {
+  if (*info != 0) return;
+  const int64_t base = k + nb;
+  const int64_t ti = base + (int64_t)blockIdx.y * 32, tj = base + (int64_t)blockIdx.x * 32;
+  if (tj + 31 < ti) return;  // tile strictly below the diagonal
+  __shared__ float2 Pi[CH_NB][33], Pj[CH_NB][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < nb; r += 8) {
+    const Dfl a = dfl_from((ti + tx < ell) ? M[(k + r) * ell + ti + tx] : 0.0);
+    const Dfl b = dfl_from((tj + tx < ell) ? M[(k + r) * ell + tj + tx] : 0.0);
+    Pi[r][tx] = make_float2(a.hi, a.lo);
+    Pj[r][tx] = make_float2(b.hi, b.lo);
+  }
+  __syncthreads();
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t i = ti + rr, j = tj + tx;
+    if (i < ell && j < ell && j >= i) {
+      Dfl acc = {0.f, 0.f};
+      for (int t = 0; t < nb; ++t) {
+        const float2 a = Pi[t][rr], b = Pj[t][tx];
+        acc = dfl_fma({a.x, a.y}, {b.x, b.y}, acc);
+      }
+      M[i * ell + j] -= dfl_to(acc);
+    }
+  }
+}
+
+int32_t chol_upper_dfl(double* M, int64_t ell, int* d_info, cudaStream_t s) {
+  NYS_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  for (int64_t k = 0; k < ell; k += CH_NB) {
+    int nb = (int)((ell - k < CH_NB) ? ell - k : CH_NB);
+    chol_diag_dfl_kernel<<<1, 32 * CH_NB, 0, s>>>(M, ell, k, nb, d_info); count_launch();
+    int64_t rest = ell - k - nb;
+    if (rest > 0) {
+      chol_panel_dfl_kernel<<<(unsigned)cdiv(rest, 8), 256, 0, s>>>(M, ell, k, nb, d_info);
+      count_launch();
+      unsigned t = (unsigned)cdiv(rest, 32);
+      chol_trail_dfl_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(M, ell, k, nb, d_info);
+      count_launch();
+    }
+  }
+  zero_lower_kernel<<<(unsigned)cdiv(ell * ell, 256), 256, 0, s>>>(M, ell); count_launch();
+  NYS_CUDA_TRY(cudaGetLastError());
+  return NYS_OK;
+}
+
 int32_t tri_inv_upper(const double* C, double* X, int64_t ell, cudaStream_t s) {
   Scratch sc(s);
   double *XT, *CT;

@@ -292,12 +292,29 @@ __device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t (&r)[32]) 
       : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // Ties the registers written by tcgen05.ld to a point after the wait, so
 // that no use of them can be scheduled before tcgen05.wait::ld.
+__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16]) {
+#pragma unroll
+  for (int i = 0; i < 16; i += 8)
+    asm volatile("" : "+r"(r[i]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), "+r"(r[i + 4]),
+                 "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7])::"memory");
+}
+
 __device__ __forceinline__ void reg_fence32(uint32_t (&r)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; i += 8)
@@ -649,7 +666,7 @@ rbf_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 // exp warps (FP32, Kahan-compensated across tiles).  Four exp groups take
 // tiles round-robin, each with its own 128-column TMEM buffer, so that every
 // SMSP holds four exp warps to cover the tensor-memory latency; within a tile
-// the next 32 columns are loaded while the current ones are used.
+// the next 16 columns are loaded while the current ones are used.
 //
 // GEMM1 runs on FP16 splits: each point, scaled by a power of two so that its
 // largest coordinate lies in [2^9, 2^10), is one 128-byte row [hi(32) | lo(32)]
@@ -812,31 +829,33 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
       const float4* cn4 = reinterpret_cast<const float4*>(sSt + s * GV_STAGE + GV_CN);
       const float4* v4 = reinterpret_cast<const float4*>(sSt + s * GV_STAGE + GV_VJ);
       const uint32_t P = tmem + lane_base + (uint32_t)(g * GV_BN);
-      uint32_t ra[32], rb[32];
-      tmem_ld32_nw(P, ra);
+      uint32_t ra[16], rb[16];
+      tmem_ld16_nw(P, ra);
       tmem_wait_ld();
-      reg_fence32(ra);
-      float ts = 0.f;
+      reg_fence16(ra);
+      // four partial sums (one per point of a float4): four short dependent
+      // FMA chains per tile instead of one of 128
+      float ts[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int c = 0; c < GV_BN / 32; ++c) {
-        uint32_t(&cur)[32] = (c & 1) ? rb : ra;
-        uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
-        if (c + 1 < GV_BN / 32) tmem_ld32_nw(P + (uint32_t)(32 * (c + 1)), nxt);
+      for (int c = 0; c < GV_BN / 16; ++c) {
+        uint32_t(&cur)[16] = (c & 1) ? rb : ra;
+        uint32_t(&nxt)[16] = (c & 1) ? ra : rb;
+        if (c + 1 < GV_BN / 16) tmem_ld16_nw(P + (uint32_t)(16 * (c + 1)), nxt);
 #pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) {
-          const float4 c4 = cn4[c * 8 + j4], w4 = v4[c * 8 + j4];
+        for (int j4 = 0; j4 < 4; ++j4) {
+          const float4 c4 = cn4[c * 4 + j4], w4 = v4[c * 4 + j4];
           const float cj[4] = {c4.x, c4.y, c4.z, c4.w};
           const float vj[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const float kv = ex2_approx(fmaf(__uint_as_float(cur[j4 * 4 + e]), m2c, ai + cj[e]));
-            ts = fmaf(kv, vj[e], ts);
+            ts[e] = fmaf(kv, vj[e], ts[e]);
           }
         }
-        if (c + 1 < GV_BN / 32) {
+        if (c + 1 < GV_BN / 16) {
           tmem_wait_ld();
-          reg_fence32(nxt);
-          if (c + 2 == GV_BN / 32) {
+          reg_fence16(nxt);
+          if (c + 2 == GV_BN / 16) {
             // the whole tile is in registers: release the TMEM buffer
             tc_fence_before();
             __syncwarp();
@@ -844,7 +863,7 @@ rbf_gemv_kernel(const __grid_constant__ CUtensorMap tmX, RtArgs a) {
           }
         }
       }
-      const float yk = ts - comp;
+      const float yk = ((ts[0] + ts[1]) + (ts[2] + ts[3])) - comp;
       const float tk = acc + yk;
       comp = (tk - acc) - yk;
       acc = tk;
