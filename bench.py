@@ -29,7 +29,13 @@ import sys
 import threading
 import time
 
-import numpy as np
+# the oracle's BLAS runs on exactly the cores this process may use (the
+# thread count the CPU baseline reports), unless the caller pinned it
+_CORES = len(os.sched_getaffinity(0))
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(_CORES))
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -239,7 +245,7 @@ def cpu_baseline(m, n, ell, sample_rows):
     from oracle import operators as oops
     from oracle import pcg as opcg
     from paper_2110_02820_gb300 import workloads as wl
-    cores = len(os.sched_getaffinity(0))
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", len(os.sched_getaffinity(0))))
     Xs = wl.ridge_X(sample_rows, n, SEED + 1)
     ys = wl.ridge_y(sample_rows, SEED + 1)
     X64 = Xs.astype(np.float64)
@@ -252,6 +258,7 @@ def cpu_baseline(m, n, ell, sample_rows):
     t = time.perf_counter() - t0
     t_full = t * m / sample_rows
     return {"value": 1.0 / t_full, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample_fraction": sample_rows / m, "sample_s": t, "full_solve_s_extrapolated": t_full,
             "sample": f"rows {sample_rows} of {m} (n={n}, ell={ell}), FP64 numpy Algorithm 1 + "
                       f"Algorithm 3 to rel. residual {TOL}: {t:.2f} s, {out['iterations']} "
                       f"iterations; scaled linearly in rows"}
@@ -282,6 +289,11 @@ def run_reference(args):
             "config": {"workload": f"ridge X {args.m}x{args.n} fp32, ell={args.ell}, mu={MU}, tol={TOL}",
                        "parallelism": "replicas"},
             "cpu_baseline": cb,
+            # a step is one solve of a row sample (ms_per_step, what the clock around
+            # the run sees); value is solves/s of the full workload, the sample time
+            # scaled by m / rows (the oracle's cost is linear in the rows)
+            "step": {"kind": "row sample", "rows": rows, "of_rows": args.m,
+                     "ms_per_full_solve_extrapolated": 1e3 / v},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
