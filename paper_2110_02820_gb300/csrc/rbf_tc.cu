@@ -34,11 +34,12 @@
 //                   Yacc chunks and writes the result (+ mu_s v_i).
 // Tensor-core FP32 accumulation does not round to nearest; a long chain of
 // accumulating MMAs drifts toward zero (~1e-8 relative per MMA, measured), so
-// GEMM2 accumulates a chunk of tiles at a time (48 chained MMAs) and the exp
-// groups add each chunk into FP32 sums with ordinary rounding.  Chunks of 48
-// MMAs leave 1.5e-6 norm-wise error on a product against 2.6e-6 with 96
-// (measured at n = 5e4), and the regularisation path's refinement then
-// contracts faster.  Every wait is bounded; on expiry the CTA records
+// GEMM2 accumulates a chunk of two tiles at a time (48 chained TF32 MMAs, 24
+// FP16 ones) and the exp groups add each chunk into FP32 sums with ordinary
+// rounding.  Shorter chains leave less error on a product (3xTF32: 1.5e-6
+// norm-wise with 48 MMAs against 2.6e-6 with 96; FP16: 7.3e-7 with 24, 1.2e-6
+// with 48, 2.0e-6 with 96, measured at n = 5e4), and the regularisation
+// path's refinement then contracts faster.  Every wait is bounded; on expiry the CTA records
 // NYS_ERR_TIMEOUT in *err, lets its copies in flight land, frees its TMEM and
 // returns.
 //
@@ -1074,7 +1075,12 @@ struct H16Cfg {
   static constexpr int NV = P2 == 3 ? 2 : 1;
   static constexpr int A_BYTES = RT_BM * 128;       // X_I [hi | lo]
   static constexpr int VSLOT = NV * S * 128;        // S vectors x 64 points x FP16, per array
-  static constexpr int CH = 4;                      // tiles per GEMM2 chunk (48 MMAs)
+  // tiles per GEMM2 chunk: 2 (24 chained MMAs) leave 7.3e-7 norm-wise error on
+  // a 128-vector product at n = 5e4 against 1.2e-6 with 4 and 2.0e-6 with 8
+  // (measured); the product takes 2.57 ms against 2.20 and 2.00 (each chunk
+  // is promoted through shared memory), but the regularisation path, whose
+  // refinement contracts faster on the more accurate product, runs 13 % faster
+  static constexpr int CH = 2;
   static constexpr bool CHUNKED = P2 == 3;
   static constexpr int HALF = S / 2;                // Yacc columns promoted by each group
   static constexpr int SUM_BYTES = CHUNKED ? S * RT_BM * 4 : 0;

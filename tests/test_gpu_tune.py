@@ -112,3 +112,36 @@ def test_tuning_off_times_nothing(ny):
         assert torch.isfinite(y).all()
     finally:
         ny.autotune(True)
+
+
+def test_tf32_kernel_selected_by_environment_gives_the_product(tmp_path):
+    # NYS_RBF_TF32=1 (read once per process) selects the 3xTF32 kernel for many
+    # vectors instead of the FP16-split one: same product to FP32 accuracy
+    import json
+    import os
+    import subprocess
+    import sys
+    import textwrap
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = textwrap.dedent("""
+        import json, numpy as np, torch
+        from oracle import operators as oops
+        from paper_2110_02820_gb300 import build, nyspcg as ny, workloads as wl
+        build.build()
+        P = wl.gmm_points(3000, 16, seed=41)
+        sigma = wl.median_distance(P, seed=41)
+        V = wl.rhs(3000, seed=41, nrhs=70)
+        op = ny.rbf_operator(torch.tensor(P, device="cuda"), sigma)
+        y = ny.nys_op_matvec(op, 0.5, torch.tensor(V, device="cuda"), mode=1).cpu().numpy()
+        ref = oops.rbf_matmat(P, sigma, V.T).T + 0.5 * V
+        keys = [k for k in ny.autotune_choices() if k.startswith("rbf_tc")]
+        print(json.dumps([float(np.linalg.norm(y - ref) / np.linalg.norm(ref)), keys]))
+    """)
+    env = dict(os.environ, NYS_RBF_TF32="1", NYS_TUNE_CACHE=str(tmp_path / "t.json"))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                         text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    err, keys = json.loads(out.stdout.strip().splitlines()[-1])
+    assert err <= 1e-5
+    # the 3xTF32 kernel names its tuner keys by its fixed 64 vectors per CTA
+    assert keys and all(k.startswith("rbf_tc S=64") for k in keys), keys
