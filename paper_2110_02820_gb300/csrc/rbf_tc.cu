@@ -191,6 +191,13 @@ __device__ __forceinline__ uint32_t pack_f16x2(float x0, float x1) {
   return r;
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
@@ -1077,16 +1084,13 @@ struct H16Cfg {
   static constexpr int VSLOT = NV * S * 128;        // S vectors x 64 points x FP16, per array
   // tiles per GEMM2 chunk: 2 (24 chained MMAs) leave 7.3e-7 norm-wise error on
   // a 128-vector product at n = 5e4 against 1.2e-6 with 4 and 2.0e-6 with 8
-  // (measured); the product takes 2.57 ms against 2.20 and 2.00 (each chunk
-  // is promoted through shared memory), but the regularisation path, whose
-  // refinement contracts faster on the more accurate product, runs 13 % faster
+  // (measured), and the regularisation path, whose refinement contracts
+  // faster on the more accurate product, runs faster with 2
   static constexpr int CH = 2;
   static constexpr bool CHUNKED = P2 == 3;
   static constexpr int HALF = S / 2;                // Yacc columns promoted by each group
-  static constexpr int SUM_BYTES = CHUNKED ? S * RT_BM * 4 : 0;
   static constexpr int BAR_BYTES = 512;
-  static constexpr int SMEM = 1024 + A_BYTES + HX_NS * H_XSLOT + HV_NS * VSLOT + BAR_BYTES +
-                              SUM_BYTES;
+  static constexpr int SMEM = 1024 + A_BYTES + HX_NS * H_XSLOT + HV_NS * VSLOT + BAR_BYTES;
   static constexpr uint32_t TM_Y = 64 * HB;
   static constexpr uint32_t YCOLS = CHUNKED ? 2 * S : S;
   static_assert(S % 32 == 0 && S <= 128, "S");
@@ -1095,23 +1099,20 @@ struct H16Cfg {
   static_assert(VSLOT % 1024 == 0 && H_XSLOT % 1024 == 0, "1024-byte aligned tiles");
 };
 
-// Add columns [c0, c0 + HALF) of Yacc chunk c into the FP32 sums sY[s][r]
-// (assign for chunk 0) and release the chunk (one arrival per warp).
+// Add columns [c0, c0 + HALF) of Yacc chunk c into this thread's FP32 sums
+// (its row's, in registers) and release the chunk (one arrival per warp).
 template <int S, int HALF, uint32_t TMY>
 __device__ __forceinline__ bool h_promote(uint32_t tmem, uint32_t lane_base, int c, int c0,
-                                          uint64_t* ycf, uint64_t* ycfree, float* sY, int r,
+                                          uint64_t* ycf, uint64_t* ycfree, float (&ysum)[HALF],
                                           int lane) {
   if (!mbar_wait_bounded(&ycf[c & 1], (uint32_t)((c >> 1) & 1))) return false;
   tc_fence_after();
-#pragma unroll 1
+#pragma unroll
   for (int j0 = 0; j0 < HALF; j0 += 16) {
     uint32_t v[16];
     tmem_ld16(tmem + lane_base + TMY + (uint32_t)((c & 1) * S + c0 + j0), v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      float* p = &sY[(c0 + j0 + j) * RT_BM + r];
-      *p = (c == 0) ? __uint_as_float(v[j]) : *p + __uint_as_float(v[j]);
-    }
+    for (int j = 0; j < 16; ++j) ysum[j0 + j] += __uint_as_float(v[j]);
   }
   tc_fence_before();
   __syncwarp();
@@ -1143,7 +1144,6 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   uint64_t* ycf = yfull + 1;        // [2] Yacc chunk complete
   uint64_t* ycfree = ycf + 2;       // [2] chunk promoted by both groups
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ycfree + 2);
-  float* sY = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + Cfg::BAR_BYTES);
   __shared__ int s_fail, s_skip;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1308,17 +1308,17 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         if (!mbar_wait_bounded(&vfull[sv], (uint32_t)((t / HV_NS) & 1))) { ok = false; break; }
         tc_fence_after();
         // GEMM2(t): Yacc += K_t V_t (Khi.Vhi + Khi.Vlo + Klo.Vhi); K_t in
-        // TMEM (hi: 32 columns, lo: the next 32), 16 points per K-step
+        // TMEM, per 16 points (one K-step) 8 columns of hi then 8 of lo
         const uint32_t kHi = tmem + (uint32_t)(b * 64);
         const uint64_t vD = sw128_kmajor_desc(smem_u32(sV + sv * Cfg::VSLOT));
         const uint32_t dY = tmem + Cfg::TM_Y + (Cfg::CHUNKED ? (uint32_t)((c & 1) * S) : 0u);
 #pragma unroll
         for (int pass = 0; pass < P2; ++pass) {
-          const uint32_t ka = kHi + (pass == 2 ? 32u : 0u);
+          const uint32_t ka = kHi + (pass == 2 ? 8u : 0u);
           const uint64_t vd0 = vD + (uint64_t)(((pass == 1 ? 1 : 0) * S * 128) >> 4);
 #pragma unroll
           for (int k = 0; k < RT_BN / 16; ++k)
-            mma_f16_ts(dY, ka + (uint32_t)(8 * k), vd0 + (uint64_t)(2 * k), idesc2,
+            mma_f16_ts(dY, ka + (uint32_t)(16 * k), vd0 + (uint64_t)(2 * k), idesc2,
                        (!first || pass > 0 || k > 0) ? 1u : 0u);
         }
         mma_commit(&bfree[b]);
@@ -1346,6 +1346,9 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     const uint64_t m2c2 = f2pack(m2c, m2c), ai2 = f2pack(ai, ai),
                    scale2 = f2pack(32768.f, 32768.f);
     const int c0 = g * Cfg::HALF;  // this group's Yacc columns
+    float ysum[Cfg::HALF];         // this row's sums of those columns
+#pragma unroll
+    for (int j = 0; j < Cfg::HALF; ++j) ysum[j] = 0.f;
     bool ok = true;
     int next_chunk = 0;            // next chunk this group promotes
     for (int t = g; t < T; t += 2) {
@@ -1353,28 +1356,30 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       if (!mbar_wait_bounded(&pfull[b], (uint32_t)((t / HB) & 1))) { ok = false; break; }
       tc_fence_after();
       const uint32_t buf = tmem + lane_base + (uint32_t)(b * 64);
-      uint32_t r0[32], r1[32];
-      tmem_ld32_nw(buf, r0);
-      tmem_ld32_nw(buf + 32, r1);
-      tmem_wait_ld();
-      reg_fence32(r0);
-      reg_fence32(r1);
       // cn_J is resident (GEMM1(t) waited for it); this wait makes the
       // asynchronous copy visible to this thread
       if (!mbar_wait_bounded(&xfull[s], (uint32_t)((t / HX_NS) & 1))) { ok = false; break; }
       const float4* cn4 = reinterpret_cast<const float4*>(sX + s * H_XSLOT + RT_BN * 128);
+      // P in four 16-column chunks (the next one loading while this one is
+      // used); chunk q's K (hi: 8 columns, lo: 8) goes over chunk q's own
+      // columns once they are read
+      uint32_t pa[16], pb[16];
+      tmem_ld16_nw(buf, pa);
+      tmem_wait_ld();
+      reg_fence16(pa);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t(&pr)[32] = h ? r1 : r0;
-        // k 2^15 split into FP16 hi + lo, two points per TMEM column (the
-        // lower point index in the lower half), over the P columns just read
+      for (int qc = 0; qc < RT_BN / 16; ++qc) {
+        uint32_t(&pr)[16] = (qc & 1) ? pb : pa;
+        uint32_t(&pn)[16] = (qc & 1) ? pa : pb;
+        if (qc + 1 < RT_BN / 16) tmem_ld16_nw(buf + (uint32_t)(16 * (qc + 1)), pn);
         // pairs of points in packed FP32 pairs (each half rounds as the
         // scalar operation): exponent, 2^15 scale, hi = fp16(k), lo =
-        // fp16(k - hi) with k - hi exact in FP32
-        uint32_t hw[16], lw[16];
+        // fp16(k - hi) with k - hi exact in FP32; two points per TMEM column,
+        // the lower point index in the lower half
+        uint32_t hw[8], lw[8];
 #pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) {
-          const float4 c4 = cn4[h * 8 + j4];
+        for (int j4 = 0; j4 < 4; ++j4) {
+          const float4 c4 = cn4[qc * 4 + j4];
 #pragma unroll
           for (int e = 0; e < 4; e += 2) {
             const uint64_t cj2 = e ? f2pack(c4.z, c4.w) : f2pack(c4.x, c4.y);
@@ -1395,8 +1400,12 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             }
           }
         }
-        tmem_st16(buf + (uint32_t)(16 * h), hw);
-        if (P2 == 3) tmem_st16(buf + 32u + (uint32_t)(16 * h), lw);
+        tmem_st8(buf + (uint32_t)(16 * qc), hw);
+        if (P2 == 3) tmem_st8(buf + (uint32_t)(16 * qc + 8), lw);
+        if (qc + 1 < RT_BN / 16) {
+          tmem_wait_ld();
+          reg_fence16(pn);
+        }
       }
       tmem_st_wait();
       tc_fence_before();
@@ -1407,8 +1416,8 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       }
       // promote chunk c - 1 once this group reaches chunk c
       if (Cfg::CHUNKED && (t - g) % Cfg::CH == 0 && t >= Cfg::CH) {
-        if (!h_promote<S, Cfg::HALF, Cfg::TM_Y>(tmem, lane_base, next_chunk, c0, ycf, ycfree, sY,
-                                                 r, lane)) {
+        if (!h_promote<S, Cfg::HALF, Cfg::TM_Y>(tmem, lane_base, next_chunk, c0, ycf, ycfree,
+                                                 ysum, lane)) {
           ok = false;
           break;
         }
@@ -1418,14 +1427,15 @@ rbf_h16_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     if (Cfg::CHUNKED) {
       const int last = (T - 1) / Cfg::CH;
       while (ok && next_chunk <= last) {
-        ok = h_promote<S, Cfg::HALF, Cfg::TM_Y>(tmem, lane_base, next_chunk, c0, ycf, ycfree, sY,
-                                                 r, lane);
+        ok = h_promote<S, Cfg::HALF, Cfg::TM_Y>(tmem, lane_base, next_chunk, c0, ycf, ycfree,
+                                                 ysum, lane);
         ++next_chunk;
       }
       if (!ok) atomicOr(&s_fail, 1);
       if (ok && row < a.n) {
-        for (int j = 0; j < Cfg::HALF && s0 + c0 + j < a.nvec; ++j)
-          rt_store(a, s0 + c0 + j, row, sY[(c0 + j) * RT_BM + r]);
+#pragma unroll
+        for (int j = 0; j < Cfg::HALF; ++j)
+          if (s0 + c0 + j < a.nvec) rt_store(a, s0 + c0 + j, row, ysum[j]);
       }
     } else {
       if (ok) ok = mbar_wait_bounded(yfull, 0u, 1ll << 26);
