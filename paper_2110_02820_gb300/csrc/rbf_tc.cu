@@ -1065,7 +1065,8 @@ __global__ void rt_prep_vecs16_kernel(const float* __restrict__ V, int64_t nvec,
 //                    group stored K_t; it never waits for an MMA to finish.
 //   warps 2..9:      two exp groups (tiles of one parity each).  P_t from
 //                    TMEM, k 2^15 split into FP16 hi + lo, stored over P_t;
-//                    each group promotes half of the Yacc columns of a chunk.
+//                    each group adds half of the Yacc columns of a chunk into
+//                    FP32 sums held in its threads' registers (one row each).
 // The two issuers are separate threads because a commit's completion takes
 // longer to reach a waiting thread than a tile's MMAs take to run: one
 // thread that waited for GEMM2(t - 1) before issuing GEMM1 kept the tensor
