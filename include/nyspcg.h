@@ -64,10 +64,12 @@ typedef enum nys_op_kind {
 typedef enum nys_dtype { NYS_F64 = 0, NYS_F32 = 1 } nys_dtype;
 
 /* NYS_PREC_F64: every step in FP64.
- * NYS_PREC_MIXED: sketch and tall-skinny products in FP32/TF32 with FP32
+ * NYS_PREC_MIXED: sketch and tall-skinny products in FP32/TF32 (Gaussian
+ *   kernel: FP16 hi/lo splits, 22 significant bits per operand) with FP32
  *   accumulation, U stored FP32, inner PCG on FP32 vectors with FP64
- *   scalars; the ell x ell factorisations, the shift and the outer residual
- *   r = b - (A + mu I) x stay FP64-accurate. */
+ *   scalars; the shift and the outer residual r = b - (A + mu I) x stay
+ *   FP64-accurate, and the ell x ell factorisations run in FP64 or in
+ *   double-FP32 arithmetic (~2^-48 relative, on the FP32 pipes). */
 typedef enum nys_precision { NYS_PREC_F64 = 0, NYS_PREC_MIXED = 1 } nys_precision;
 
 typedef struct nys_operator {
@@ -386,8 +388,9 @@ int32_t nys_timing_stop(double* total_ms, int64_t* products);
  * mixed path's refinement residual (double-FP32 arithmetic for the ridge
  * operator and the Gaussian kernel, ~2^-44 relative; FP64 for dense).
  * For the Gaussian kernel with d <= 32, mode 1 runs on the tensor cores
- * (3xTF32 products, FP32 accuracy), all nvec vectors in one pass over the
- * kernel matrix.  Exposed so that each operator kernel can be checked on
+ * (FP16 hi/lo splits of points, kernel entries and vectors, three passes,
+ * FP32 accuracy; 3xTF32 when the environment sets NYS_RBF_TF32=1 before the
+ * first product), all nvec vectors in one pass over the kernel matrix.  Exposed so that each operator kernel can be checked on
  * its own.  Synchronises `stream`. */
 int32_t nys_op_matvec(const nys_operator* op, double mu, int64_t nvec, const double* x, double* y,
                       int32_t mode, void* stream);
