@@ -729,7 +729,7 @@ def workload_record(args, name, steps, warmup, peaks=None):
         mv_total, mv_cnt = ny.timing_stop()
         mv_ms = mv_total / max(mv_cnt, 1)
         kern = ("rbf_gemv_kernel (tensor-core distances, one vector)" if name == "krr"
-                else "rbf_tc_kernel<S,3,fp16> (tensor cores)")
+                else "rbf_h16_kernel<S,3> (FP16 splits, tensor cores)")
         if args.precision == "f64":
             kern = "rbf_products_kernel (FP64 entries and sums; not event-timed)"
         line.update({"dtype": "f64" if args.precision == "f64" else "f32",
@@ -776,7 +776,7 @@ def workload_record(args, name, steps, warmup, peaks=None):
                 alg = 2.0 * n * n * (V.shape[0] + d)
                 ks16 = 16 * (-(-d // 16))
                 exe = 3.0 * 2.0 * npad * npad * (cols * S + cols * ks16)
-                line["dominant_kernel"]["kernel"] = f"rbf_tc_kernel<{S},3,fp16> (tensor cores, " \
+                line["dominant_kernel"]["kernel"] = f"rbf_h16_kernel<{S},3> (FP16 splits, tensor cores, " \
                                                     f"{S} systems per CTA)"
                 line["roofline"] = {"bound": "tensor", "unit": "TFLOP/s",
                                     "achieved": alg / (pms * 1e-3) / 1e12,
