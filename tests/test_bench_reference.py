@@ -26,6 +26,13 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["unit"] == "solves/s" and d["steps"] == 1 and d["warmup"] == 1
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and "rows" in cb["sample"]
+    # a step is the row sample; value is the full workload, scaled by the rows
+    assert d["step"]["kind"] == "row sample" and d["step"]["of_rows"] == 8000
+    assert abs(cb["sample_fraction"] - d["step"]["rows"] / 8000) < 1e-12
+    assert abs(cb["full_solve_s_extrapolated"] - cb["sample_s"] / cb["sample_fraction"]) <= \
+        1e-9 * cb["full_solve_s_extrapolated"]
+    assert abs(d["step"]["ms_per_full_solve_extrapolated"] - 1e3 / d["value"]) <= \
+        1e-9 * d["step"]["ms_per_full_solve_extrapolated"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
